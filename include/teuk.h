@@ -1,0 +1,177 @@
+/*
+ * teuk.h -- C ABI of libteuk, a GB300 (sm_103a) time stepper for the
+ * mode-decomposed (2+1)-D Teukolsky equation of Khanna & McKennon,
+ * "An exploration of CUDA and CBEA for a gravitational wave
+ * source-modelling application" (arXiv:0909.4039), Sec. 2.
+ *
+ * What one step computes (all in hand-written CUDA kernels):
+ *   - the first-order system d_t u + D d_{r*} u = S of Eqs. 9-12 for
+ *     u = {Phi_R, Phi_I, Pi_R, Pi_I}, Pi = Phi_t + b Phi_{r*} (Eqs. 5-7),
+ *     on a uniform r* grid (nodes, both ends included) times a cell-centred
+ *     theta grid theta_j = (j + 1/2) pi / Ntheta;
+ *   - TEUK_SCHEME_SPLIT (default): an implicit-explicit Strang splitting.
+ *     The algebraic terms -L u - A u of S (angular operator with the pole
+ *     potential, c_t, c_0) advance by two half-steps of the L-stable
+ *     two-stage SDIRK method of order 2 (one complex tridiagonal solve in
+ *     theta per r* row and stage); the two-step Lax-Wendroff update of
+ *     Eqs. 13-14 carries the transport D and S = T - (M - D) d_{r*} u.
+ *     TEUK_SCHEME_LITERAL evaluates all of S inside the Lax-Wendroff stages,
+ *     as Eqs. 12-14 read literally; it is unstable at dt = dr* / 2 and is
+ *     refused there unless allow_unstable is set;
+ *   - the radial boundary rows Phi = Pi = 0 and the angular parity
+ *     conditions of Sec. 2.2 (last paragraph);
+ *   - the particle source T of Eq. 1 (which the paper does not print) as a
+ *     Gaussian on a circular equatorial orbit, see teuk_set_source;
+ *   - FP64 waveform extraction h_n = sum_j w_j Phi_{i_ext, j} every step.
+ *
+ * Conventions for every function:
+ *   - returns TEUK_OK (0) or a positive TEUK_E_* code; no exception crosses
+ *     the ABI; teuk_last_error(ctx) gives a message for the last failure;
+ *   - device memory is owned by the caller.  The library allocates no
+ *     device memory; ctx is a host object that only records pointers;
+ *   - "stream" is a cudaStream_t passed as void* (NULL = legacy stream);
+ *     calls that take a stream are asynchronous unless stated otherwise;
+ *   - units G = c = 1; the mass M is set in the descriptor.
+ */
+#ifndef TEUK_H
+#define TEUK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define TEUK_OK 0
+#define TEUK_E_INVAL 1      /* invalid argument or descriptor */
+#define TEUK_E_CUDA 2       /* a CUDA runtime call failed */
+#define TEUK_E_NONFINITE 3  /* a non-finite waveform sample was produced */
+#define TEUK_E_UNSTABLE 4   /* radial Courant number > 1, or literal scheme past its bound */
+#define TEUK_E_TIMEOUT 5    /* reserved for bounded device waits */
+#define TEUK_E_STATE 6      /* call out of order (e.g. no context) */
+#define TEUK_E_RANGE 7      /* requested waveform steps are not in the ring buffer */
+
+/* precision of the evolved state and stencil arithmetic; coefficients,
+ * time, source phase and extraction sums are generated in FP64 always */
+#define TEUK_FP64 0
+#define TEUK_FP32 1
+
+#define TEUK_SCHEME_SPLIT 0
+#define TEUK_SCHEME_LITERAL 1
+
+/* largest number of r* rows the source patch may cover (9 sigma_r each side) */
+#define TEUK_MAX_PATCH_ROWS 4096
+/* largest Ntheta (one theta row of a tile must fit in shared memory) */
+#define TEUK_MAX_NTHETA 1024
+
+typedef struct teuk_grid_desc {
+    int32_t s;              /* spin weight of Eq. 1 (|s| <= 2) */
+    int32_t m;              /* azimuthal mode of Eq. 4 */
+    double M;               /* black-hole mass (> 0) */
+    double a;               /* spin parameter, 0 <= |a| < M */
+    int64_t Nr;             /* r* nodes, >= 3; node i at rstar_min + i dr* */
+    int64_t Ntheta;         /* theta cells, 1 .. TEUK_MAX_NTHETA */
+    double rstar_min;       /* r* of node 0 */
+    double rstar_max;       /* r* of node Nr-1 (> rstar_min) */
+    double dt;              /* time step; <= 0 selects dt = dr* / 2 */
+    double rstar_extract;   /* extraction radius; the nearest node is used */
+    int32_t precision;      /* TEUK_FP64 or TEUK_FP32 */
+    int32_t scheme;         /* TEUK_SCHEME_SPLIT or TEUK_SCHEME_LITERAL */
+    int32_t allow_unstable; /* nonzero: accept the literal scheme past its bound */
+    int32_t reserved;       /* must be 0 */
+} teuk_grid_desc;
+
+typedef struct teuk_ctx teuk_ctx;
+
+/* Sizes of the three caller-owned device buffers for a descriptor.
+ *   state_bytes:          two time levels of u, each [2][Nr][Ntheta]
+ *                         complex values of the state precision
+ *                         (plane 0 = Phi, plane 1 = Pi; theta fastest);
+ *   coef_bytes:           FP64-generated coefficient tables, the Thomas
+ *                         pivots of the implicit stages, the source patch,
+ *                         weights, control words and a staging area;
+ *   wave_bytes_per_step:  one ring-buffer slot: h_n (complex double) then
+ *                         the extraction row Phi_{i_ext, .} (Ntheta complex
+ *                         doubles).
+ * Returns TEUK_E_INVAL for an invalid descriptor. */
+int teuk_workspace_bytes(const teuk_grid_desc *desc, size_t *state_bytes,
+                         size_t *coef_bytes, size_t *wave_bytes_per_step);
+
+/* Validate the descriptor, record the buffers, generate the coefficient
+ * tables in FP64 on the device (r(r*) by Newton's method on ln(r - r_+);
+ * Eq. 2 integrated with the usual constant), zero the state at step 0, set
+ * the default extraction weights and a zero source.  d_state, d_coef and
+ * d_wave must be device pointers of at least the sizes given by
+ * teuk_workspace_bytes, 256-byte aligned; wave_capacity >= 1 slots.
+ * Synchronises the stream before returning.  Errors: TEUK_E_INVAL,
+ * TEUK_E_UNSTABLE (radial Courant number max b dt/dr* > 1; literal scheme
+ * past its bound without allow_unstable), TEUK_E_CUDA. */
+int teuk_init_grid(const teuk_grid_desc *desc, void *d_state, void *d_coef,
+                   void *d_wave, int64_t wave_capacity, void *stream,
+                   teuk_ctx **out);
+
+/* Source T of Eq. 1 for this mode (the slot the paper fills with the
+ * particle source of its ref. [14]):
+ *   T_m = A exp(-(r* - r0*)^2/(2 sigma_rstar^2) - (theta - pi/2)^2/(2 sigma_theta^2))
+ *         exp(-i m Omega t),   A = amp_re + i amp_im,
+ * entering the Pi rows as F = 4 pi (r^2 + a^2 cos^2 theta) Delta/(Sigma^2 r^3) T_m
+ * (the right side of Eq. 1 after the division that gives Eq. 9).
+ * r0 is the Boyer-Lindquist orbital radius (> r_+); Omega = NaN selects the
+ * prograde Kepler frequency M^{1/2}/(r0^{3/2} + a M^{1/2}).  amp = 0
+ * disables the source.  The Gaussian is sampled where it exceeds double
+ * precision resolution (|r* - r0*| <= 9 sigma_rstar).  Synchronous.
+ * Errors: TEUK_E_INVAL (sigma <= 0, r0 <= r_+, patch wider than
+ * TEUK_MAX_PATCH_ROWS rows), TEUK_E_CUDA. */
+int teuk_set_source(teuk_ctx *ctx, double amp_re, double amp_im, double r0,
+                    double sigma_rstar, double sigma_theta, double Omega);
+
+/* Extraction weights w_j (host array of Ntheta doubles).  NULL selects the
+ * default: projection on Y = sin(theta/2)^{|m+s|} cos(theta/2)^{|m-s|} in
+ * the measure sin theta dtheta, normalised so that sum_j w_j Y_j = 1.
+ * Applies to samples taken after the call.  Synchronous. */
+int teuk_set_weights(teuk_ctx *ctx, const double *w);
+
+/* Replace the state by src, a [2][Nr][Ntheta] array of complex doubles
+ * (re, im interleaved), host or device memory, and set the step counter to
+ * `step` (>= 0).  Records the waveform sample of this state.  Asynchronous
+ * on `stream` for device src; synchronous for host src. */
+int teuk_set_state(teuk_ctx *ctx, const void *src, int64_t step, void *stream);
+
+/* Copy the current state to dst ([2][Nr][Ntheta] complex doubles, host or
+ * device memory) and its step number to *step (may be NULL).  Synchronous. */
+int teuk_get_state(teuk_ctx *ctx, void *dst, int64_t *step, void *stream);
+
+/* Advance nsteps >= 0 time steps on `stream` (asynchronous).  The step
+ * counter lives on the device as well, so the launches can be captured in
+ * a CUDA graph; long runs replay a cached graph of a fixed chunk of steps.
+ * Errors: TEUK_E_INVAL, TEUK_E_CUDA. */
+int teuk_step(teuk_ctx *ctx, int64_t nsteps, void *stream);
+
+/* Copy waveform samples of steps [first_step, first_step + count) to host
+ * memory: h_out gets 2*count doubles (re, im), row_out (optional, NULL to
+ * skip) gets 2*Ntheta*count doubles.  The steps must still be in the ring
+ * buffer (the last wave_capacity recorded steps), else TEUK_E_RANGE.
+ * Synchronises `stream` first.  Returns TEUK_E_NONFINITE if a sample taken
+ * since init was non-finite. */
+int teuk_extract_waveform(teuk_ctx *ctx, int64_t first_step, int64_t count,
+                          double *h_out, double *row_out, void *stream);
+
+/* Current step number (host mirror of the device counter). */
+int64_t teuk_current_step(const teuk_ctx *ctx);
+
+/* Message of the last error on ctx (or of the last failed init if ctx is
+ * NULL).  The string is owned by the library. */
+const char *teuk_last_error(const teuk_ctx *ctx);
+
+/* Human-readable name of a status code. */
+const char *teuk_status_string(int status);
+
+/* Release the host context (the caller frees its device buffers). */
+int teuk_destroy(teuk_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,575 @@
+// teuk_api.cu -- host implementation of the C ABI declared in include/teuk.h.
+//
+// Validation, workspace layout, the stability guards, the ping-pong of the
+// two state levels, CUDA-graph replay of long runs, state and waveform I/O.
+// All arithmetic of the method runs in the kernels of teuk_coef.cu and
+// teuk_step.cu; the host computes only grid constants and bounds.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+
+#include "teuk_internal.cuh"
+
+using namespace teuk;
+
+namespace {
+
+constexpr int kGraphChunk = 64;          // steps per captured graph (even)
+constexpr size_t kStagingElems = 1u << 20;  // complex doubles in the staging area
+
+thread_local char g_init_err[512] = "";
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+
+struct teuk_ctx {
+    teuk_grid_desc d;
+    double drs, dt;
+    int i_ext;
+    char *state;
+    char *coef;
+    double2 *wave;
+    int64_t cap;
+    Layout L;
+    size_t level_bytes;     // one time level
+    int cur;                // level holding the current state
+    int64_t step;           // host mirror of the device step counter
+    int64_t rec_lo;         // oldest recorded waveform step
+    // source
+    int patch_p0, patch_np;
+    double mOmega;
+    // launch configuration
+    int tile_rows, threads;
+    size_t smem;
+    // graphs, one per starting level
+    cudaGraphExec_t graph[2];
+    cudaStream_t graph_stream[2];
+    char err[512];
+};
+
+namespace teuk {
+
+Layout make_layout(const teuk_grid_desc &d)
+{
+    Layout L;
+    size_t Nr = (size_t)d.Nr, N = (size_t)d.Ntheta;
+    size_t rs = sizeof(double) * (2 * Nr - 1) * NRF;
+    size_t ts = sizeof(double) * NTF * N;
+    bool f32 = d.precision == TEUK_FP32;
+    size_t c2 = f32 ? sizeof(float2) : sizeof(double2);
+    size_t patch_rows = Nr < (size_t)TEUK_MAX_PATCH_ROWS ? Nr : (size_t)TEUK_MAX_PATCH_ROWS;
+    size_t off = 0;
+    L.rtab64 = off; off = align256(off + rs);
+    L.rtabT = f32 ? off : L.rtab64; if (f32) off = align256(off + rs / 2);
+    L.th64 = off; off = align256(off + ts);
+    L.thT = f32 ? off : L.th64; if (f32) off = align256(off + ts / 2);
+    L.piv = off; off = align256(off + c2 * N * Nr);
+    L.patch = off; off = align256(off + c2 * 2 * N * patch_rows);
+    L.w = off; off = align256(off + sizeof(double) * N);
+    L.ctl = off; off = align256(off + sizeof(Ctl));
+    L.staging_elems = 0;
+    L.staging = off;
+    if (f32) {
+        size_t want = 2 * Nr * N;
+        L.staging_elems = want < kStagingElems ? want : kStagingElems;
+        off = align256(off + sizeof(double2) * L.staging_elems);
+    }
+    L.scratch = off;
+    if (d.scheme == TEUK_SCHEME_LITERAL) off = align256(off + c2 * 2 * (Nr - 1) * N);
+    L.total = off;
+    return L;
+}
+
+}  // namespace teuk
+
+namespace {
+
+int set_err(teuk_ctx *c, int code, const char *fmt, const char *a = "", double x = 0.0)
+{
+    char *buf = c ? c->err : g_init_err;
+    snprintf(buf, 512, fmt, a, x);
+    return code;
+}
+
+int cuda_err(teuk_ctx *c, cudaError_t e, const char *where)
+{
+    char *buf = c ? c->err : g_init_err;
+    snprintf(buf, 512, "%s: %s", where, cudaGetErrorString(e));
+    return TEUK_E_CUDA;
+}
+
+#define CK(call, where)                                   \
+    do {                                                  \
+        cudaError_t e_ = (call);                          \
+        if (e_ != cudaSuccess) return cuda_err(c, e_, where); \
+    } while (0)
+
+int validate(const teuk_grid_desc *d, char *msg)
+{
+    if (!d) { snprintf(msg, 512, "descriptor is NULL"); return TEUK_E_INVAL; }
+    if (d->Nr < 3 || d->Nr > (1LL << 28)) { snprintf(msg, 512, "Nr=%lld out of range [3, 2^28]", (long long)d->Nr); return TEUK_E_INVAL; }
+    if (d->Ntheta < 1 || d->Ntheta > TEUK_MAX_NTHETA) { snprintf(msg, 512, "Ntheta=%lld out of range [1, %d]", (long long)d->Ntheta, TEUK_MAX_NTHETA); return TEUK_E_INVAL; }
+    if (d->Nr * d->Ntheta > (1LL << 31)) { snprintf(msg, 512, "Nr*Ntheta exceeds 2^31"); return TEUK_E_INVAL; }
+    if (!(d->M > 0.0) || !isfinite(d->M)) { snprintf(msg, 512, "M must be positive"); return TEUK_E_INVAL; }
+    if (!(fabs(d->a) < d->M)) { snprintf(msg, 512, "need |a| < M"); return TEUK_E_INVAL; }
+    if (d->s < -2 || d->s > 2) { snprintf(msg, 512, "spin weight s=%d not in [-2, 2]", d->s); return TEUK_E_INVAL; }
+    if (!isfinite(d->rstar_min) || !isfinite(d->rstar_max) || !(d->rstar_max > d->rstar_min)) { snprintf(msg, 512, "need rstar_max > rstar_min"); return TEUK_E_INVAL; }
+    if (!isfinite(d->dt) || !isfinite(d->rstar_extract)) { snprintf(msg, 512, "dt and rstar_extract must be finite"); return TEUK_E_INVAL; }
+    if (d->precision != TEUK_FP64 && d->precision != TEUK_FP32) { snprintf(msg, 512, "precision must be TEUK_FP64 or TEUK_FP32"); return TEUK_E_INVAL; }
+    if (d->scheme != TEUK_SCHEME_SPLIT && d->scheme != TEUK_SCHEME_LITERAL) { snprintf(msg, 512, "unknown scheme"); return TEUK_E_INVAL; }
+    if (d->reserved != 0) { snprintf(msg, 512, "reserved field must be 0"); return TEUK_E_INVAL; }
+    return TEUK_OK;
+}
+
+// Eq. 2 integrated, host copy for the orbit radius: r*(r).
+double host_rstar(double M, double a, double r)
+{
+    double d = sqrt(M * M - a * a), rp = M + d, rm = M - d;
+    return r + (M * rp / d) * log((r - rp) / (2.0 * M)) - (M * rm / d) * log((r - rm) / (2.0 * M));
+}
+
+// Bounds over the whole exterior (sampled on a log grid in r - r_+):
+// b_max = max b (radial characteristic speed), q_max = max Delta/Sigma^2,
+// ct_max = max |c_t|.
+void host_bounds(const teuk_grid_desc &d, double *b_max, double *q_max, double *ct_max)
+{
+    double M = d.M, a = d.a, s = d.s, m = d.m;
+    double dd = sqrt(M * M - a * a), rp = M + dd, rm = M - dd;
+    double bm = 1.0, qm = 0.0, cm = 0.0;
+    for (int k = 0; k <= 4000; ++k) {
+        double x = exp(log(1e-10) + (log(1e8) - log(1e-10)) * k / 4000.0);
+        double r = rp + x, D = x * (x + rp - rm), R = r * r + a * a;
+        for (int e = 0; e <= 1; ++e) {
+            double s2 = (double)e;   // sin^2 = 0 or 1 bracket Sigma^2
+            double sig2 = R * R - a * a * D * s2;
+            double b = R / sqrt(sig2), q = D / sig2;
+            double ctr = 2.0 * s * (r * D - M * (r * r - a * a)) / sig2;
+            double cti = (fabs(4.0 * M * a * m * r) + fabs(2.0 * s * a * D)) / sig2;
+            bm = fmax(bm, b);
+            qm = fmax(qm, q);
+            cm = fmax(cm, sqrt(ctr * ctr + cti * cti));
+        }
+    }
+    *b_max = bm;
+    *q_max = qm;
+    *ct_max = cm;
+}
+
+// Gershgorin bound of the discrete angular operator (folded ghost rows).
+double host_atheta_bound(const teuk_grid_desc &d)
+{
+    int N = (int)d.Ntheta;
+    double dth = kPi / N, lam = 0.0;
+    double par = (abs(d.m) % 2 == 0) ? 1.0 : -1.0;
+    for (int j = 0; j < N; ++j) {
+        double th = (j + 0.5) * dth, sn = sin(th), cs = cos(th), cot = cs / sn;
+        double am = -(1.0 - 0.5 * cot * dth) / (dth * dth), ap = -(1.0 + 0.5 * cot * dth) / (dth * dth);
+        double mc = d.m + d.s * cs;
+        double a0 = 2.0 / (dth * dth) + mc * mc / (sn * sn) - d.s;
+        if (j == 0) { a0 += par * am; am = 0.0; }
+        if (j == N - 1) { a0 += par * ap; ap = 0.0; }
+        lam = fmax(lam, fabs(am) + fabs(a0) + fabs(ap));
+    }
+    return lam;
+}
+
+void choose_tiles(teuk_ctx *c)
+{
+    int N = (int)c->d.Ntheta;
+    bool f32 = c->d.precision == TEUK_FP32;
+    const size_t budget = 100 * 1024;
+    int threads = 128;
+    int R = threads;
+    while (R > 4) {
+        size_t sm = f32 ? split_smem_bytes<float>(R - 2, N) : split_smem_bytes<double>(R - 2, N);
+        if (sm <= budget) break;
+        R -= 2;
+    }
+    if (R < 4) R = 4;
+    c->tile_rows = R - 2;
+    c->threads = threads;
+    c->smem = f32 ? split_smem_bytes<float>(c->tile_rows, N) : split_smem_bytes<double>(c->tile_rows, N);
+}
+
+template <typename T>
+StepParams<T> make_params(const teuk_ctx *c, int in_level)
+{
+    typedef typename V2<T>::t c2;
+    StepParams<T> p;
+    const teuk_grid_desc &d = c->d;
+    p.Nr = (int)d.Nr;
+    p.Nth = (int)d.Ntheta;
+    p.tile_rows = c->tile_rows;
+    p.pitch = (int)d.Ntheta + 1;
+    p.i_ext = c->i_ext;
+    p.wave_cap = (int)c->cap;
+    p.patch_p0 = c->patch_p0;
+    p.patch_np = c->patch_np;
+    double h = 0.5 * c->dt, gh = kGamma * h;
+    p.dt = (T)c->dt;
+    p.half_dt = (T)(0.5 * c->dt);
+    p.drs_inv = (T)(1.0 / c->drs);
+    p.gh = (T)gh;
+    p.gh2 = (T)(gh * gh);
+    p.h1g = (T)((1.0 - kGamma) * h);
+    p.h12g = (T)((1.0 - 2.0 * kGamma) * h);
+    p.dt64 = c->dt;
+    p.mOmega = c->mOmega;
+    p.rtab = (const T *)(c->coef + c->L.rtabT);
+    p.thtab = (const T *)(c->coef + c->L.thT);
+    p.piv = (const c2 *)(c->coef + c->L.piv);
+    p.patch = (const c2 *)(c->coef + c->L.patch);
+    p.w = (const double *)(c->coef + c->L.w);
+    p.uin = (const c2 *)(c->state + (size_t)in_level * c->level_bytes);
+    p.uout = (c2 *)(c->state + (size_t)(1 - in_level) * c->level_bytes);
+    p.mid = (c2 *)(c->coef + c->L.scratch);
+    p.wave = c->wave;
+    p.ctl = (Ctl *)(c->coef + c->L.ctl);
+    return p;
+}
+
+cudaError_t launch_one(teuk_ctx *c, int in_level, cudaStream_t st)
+{
+    if (c->d.precision == TEUK_FP32) {
+        StepParams<float> p = make_params<float>(c, in_level);
+        return c->d.scheme == TEUK_SCHEME_SPLIT ? launch_split_step<float>(p, c->threads, c->smem, st)
+                                                : launch_literal_step<float>(p, st);
+    }
+    StepParams<double> p = make_params<double>(c, in_level);
+    return c->d.scheme == TEUK_SCHEME_SPLIT ? launch_split_step<double>(p, c->threads, c->smem, st)
+                                            : launch_literal_step<double>(p, st);
+}
+
+cudaError_t extract_current(teuk_ctx *c, cudaStream_t st)
+{
+    if (c->d.precision == TEUK_FP32) {
+        StepParams<float> p = make_params<float>(c, c->cur);
+        return launch_extract<float>(p, p.uin, c->step, st);
+    }
+    StepParams<double> p = make_params<double>(c, c->cur);
+    return launch_extract<double>(p, p.uin, c->step, st);
+}
+
+void drop_graphs(teuk_ctx *c)
+{
+    for (int k = 0; k < 2; ++k) {
+        if (c->graph[k]) cudaGraphExecDestroy(c->graph[k]);
+        c->graph[k] = nullptr;
+        c->graph_stream[k] = nullptr;
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *teuk_status_string(int s)
+{
+    switch (s) {
+    case TEUK_OK: return "TEUK_OK";
+    case TEUK_E_INVAL: return "TEUK_E_INVAL";
+    case TEUK_E_CUDA: return "TEUK_E_CUDA";
+    case TEUK_E_NONFINITE: return "TEUK_E_NONFINITE";
+    case TEUK_E_UNSTABLE: return "TEUK_E_UNSTABLE";
+    case TEUK_E_TIMEOUT: return "TEUK_E_TIMEOUT";
+    case TEUK_E_STATE: return "TEUK_E_STATE";
+    case TEUK_E_RANGE: return "TEUK_E_RANGE";
+    default: return "unknown status";
+    }
+}
+
+const char *teuk_last_error(const teuk_ctx *c) { return c ? c->err : g_init_err; }
+
+int64_t teuk_current_step(const teuk_ctx *c) { return c ? c->step : -1; }
+
+int teuk_workspace_bytes(const teuk_grid_desc *d, size_t *state_bytes, size_t *coef_bytes,
+                         size_t *wave_bytes_per_step)
+{
+    int rc = validate(d, g_init_err);
+    if (rc) return rc;
+    size_t c2 = d->precision == TEUK_FP32 ? sizeof(float2) : sizeof(double2);
+    if (state_bytes) *state_bytes = 2 * align256(c2 * 2 * (size_t)d->Nr * (size_t)d->Ntheta);
+    if (coef_bytes) *coef_bytes = make_layout(*d).total;
+    if (wave_bytes_per_step) *wave_bytes_per_step = sizeof(double2) * (size_t)(d->Ntheta + 1);
+    return TEUK_OK;
+}
+
+int teuk_init_grid(const teuk_grid_desc *desc, void *d_state, void *d_coef, void *d_wave,
+                   int64_t wave_capacity, void *stream, teuk_ctx **out)
+{
+    teuk_ctx *c = nullptr;
+    if (!out) return set_err(c, TEUK_E_INVAL, "out is NULL%s");
+    *out = nullptr;
+    int rc = validate(desc, g_init_err);
+    if (rc) return rc;
+    if (!d_state || !d_coef || !d_wave) return set_err(c, TEUK_E_INVAL, "device buffers must not be NULL%s");
+    if (((uintptr_t)d_state | (uintptr_t)d_coef | (uintptr_t)d_wave) & 255)
+        return set_err(c, TEUK_E_INVAL, "device buffers must be 256-byte aligned%s");
+    if (wave_capacity < 1 || wave_capacity > (1LL << 31)) return set_err(c, TEUK_E_INVAL, "wave_capacity out of range%s");
+
+    teuk_grid_desc d = *desc;
+    double drs = (d.rstar_max - d.rstar_min) / (double)(d.Nr - 1);
+    double dt = d.dt > 0.0 ? d.dt : 0.5 * drs;
+    d.dt = dt;
+
+    // stability guards
+    double bmax, qmax, ctmax;
+    host_bounds(d, &bmax, &qmax, &ctmax);
+    if (bmax * dt / drs > 1.0)
+        return set_err(c, TEUK_E_UNSTABLE, "radial Courant number %s%.4f > 1", "", bmax * dt / drs);
+    if (d.scheme == TEUK_SCHEME_LITERAL && !d.allow_unstable) {
+        double z = fmax(sqrt(qmax * host_atheta_bound(d)) * dt, ctmax * dt);
+        if (z > 0.05)
+            return set_err(c, TEUK_E_UNSTABLE,
+                           "literal scheme: explicit S has |lambda dt| = %s%.3g > 0.05 (grows each step); "
+                           "use TEUK_SCHEME_SPLIT or set allow_unstable", "", z);
+    }
+
+    c = new (std::nothrow) teuk_ctx();
+    if (!c) return set_err(nullptr, TEUK_E_INVAL, "out of host memory%s");
+    memset(c, 0, sizeof(*c));
+    c->d = d;
+    c->drs = drs;
+    c->dt = dt;
+    long long ie = llround((d.rstar_extract - d.rstar_min) / drs);
+    if (ie < 0) ie = 0;
+    if (ie > d.Nr - 1) ie = d.Nr - 1;
+    c->i_ext = (int)ie;
+    c->state = (char *)d_state;
+    c->coef = (char *)d_coef;
+    c->wave = (double2 *)d_wave;
+    c->cap = wave_capacity;
+    c->L = make_layout(d);
+    size_t c2 = d.precision == TEUK_FP32 ? sizeof(float2) : sizeof(double2);
+    c->level_bytes = align256(c2 * 2 * (size_t)d.Nr * (size_t)d.Ntheta);
+    c->cur = 0;
+    c->step = 0;
+    c->rec_lo = 0;
+    c->patch_p0 = 0;
+    c->patch_np = 0;
+    c->mOmega = 0.0;
+    choose_tiles(c);
+
+    cudaStream_t st = (cudaStream_t)stream;
+    int r2 = TEUK_OK;
+    do {
+        cudaError_t e;
+        if ((e = cudaMemsetAsync(c->state, 0, 2 * c->level_bytes, st)) != cudaSuccess) { r2 = cuda_err(c, e, "zero state"); break; }
+        if ((e = cudaMemsetAsync(c->coef, 0, c->L.total, st)) != cudaSuccess) { r2 = cuda_err(c, e, "zero coef"); break; }
+        if ((e = cudaMemsetAsync(c->wave, 0, sizeof(double2) * (size_t)(d.Ntheta + 1) * (size_t)wave_capacity, st)) != cudaSuccess) { r2 = cuda_err(c, e, "zero wave"); break; }
+        if ((e = launch_coef_tables(d, drs, dt, c->coef, c->L, st)) != cudaSuccess) { r2 = cuda_err(c, e, "coefficient kernels"); break; }
+        if ((e = launch_set_ctl(c->coef, c->L, 0, 1, st)) != cudaSuccess) { r2 = cuda_err(c, e, "control block"); break; }
+        if ((e = extract_current(c, st)) != cudaSuccess) { r2 = cuda_err(c, e, "extract"); break; }
+        if ((e = cudaStreamSynchronize(st)) != cudaSuccess) { r2 = cuda_err(c, e, "init sync"); break; }
+    } while (0);
+    if (r2 != TEUK_OK) {
+        memcpy(g_init_err, c->err, sizeof(g_init_err));
+        delete c;
+        return r2;
+    }
+    *out = c;
+    return TEUK_OK;
+}
+
+int teuk_set_source(teuk_ctx *c, double amp_re, double amp_im, double r0, double sigma_rstar,
+                    double sigma_theta, double Omega)
+{
+    if (!c) return TEUK_E_STATE;
+    const teuk_grid_desc &d = c->d;
+    if (!isfinite(amp_re) || !isfinite(amp_im)) return set_err(c, TEUK_E_INVAL, "amplitude must be finite%s");
+    drop_graphs(c);
+    if (amp_re == 0.0 && amp_im == 0.0) {
+        c->patch_np = 0;
+        c->mOmega = 0.0;
+        return TEUK_OK;
+    }
+    double rp = d.M + sqrt(d.M * d.M - d.a * d.a);
+    if (!(r0 > rp) || !isfinite(r0)) return set_err(c, TEUK_E_INVAL, "orbit radius must exceed r_+%s");
+    if (!(sigma_rstar > 0.0) || !(sigma_theta > 0.0)) return set_err(c, TEUK_E_INVAL, "source widths must be positive%s");
+    double Om = isnan(Omega) ? sqrt(d.M) / (pow(r0, 1.5) + d.a * sqrt(d.M)) : Omega;
+    if (!isfinite(Om)) return set_err(c, TEUK_E_INVAL, "Omega must be finite or NaN%s");
+    double rs0 = host_rstar(d.M, d.a, r0);
+    double lo = (rs0 - 9.0 * sigma_rstar - d.rstar_min) / c->drs;
+    double hi = (rs0 + 9.0 * sigma_rstar - d.rstar_min) / c->drs;
+    long long p0 = (long long)floor(lo) - 1, p1 = (long long)ceil(hi) + 1;
+    if (p0 < 0) p0 = 0;
+    if (p1 > d.Nr - 1) p1 = d.Nr - 1;
+    int np = (int)(p1 - p0 + 1);
+    if (p1 < p0) np = 0;
+    long long cap_rows = d.Nr < TEUK_MAX_PATCH_ROWS ? d.Nr : TEUK_MAX_PATCH_ROWS;
+    if (np > cap_rows) return set_err(c, TEUK_E_INVAL, "source patch needs more rows than TEUK_MAX_PATCH_ROWS%s");
+    cudaStream_t st = 0;
+    if (np > 0) {
+        CK(launch_patch(d, c->drs, c->coef, c->L, (int)p0, np, amp_re, amp_im, rs0, sigma_rstar, sigma_theta, st), "source patch");
+        CK(cudaStreamSynchronize(st), "source sync");
+    }
+    c->patch_p0 = (int)p0;
+    c->patch_np = np;
+    c->mOmega = (double)d.m * Om;
+    return TEUK_OK;
+}
+
+int teuk_set_weights(teuk_ctx *c, const double *w)
+{
+    if (!c) return TEUK_E_STATE;
+    double *dw = (double *)(c->coef + c->L.w);
+    if (w) {
+        for (int64_t j = 0; j < c->d.Ntheta; ++j)
+            if (!isfinite(w[j])) return set_err(c, TEUK_E_INVAL, "weights must be finite%s");
+        CK(cudaMemcpy(dw, w, sizeof(double) * (size_t)c->d.Ntheta, cudaMemcpyHostToDevice), "weights copy");
+    } else {
+        CK(launch_coef_tables(c->d, c->drs, c->dt, c->coef, c->L, 0), "default weights");
+        CK(cudaDeviceSynchronize(), "weights sync");
+    }
+    return TEUK_OK;
+}
+
+int teuk_set_state(teuk_ctx *c, const void *src, int64_t step, void *stream)
+{
+    if (!c) return TEUK_E_STATE;
+    if (!src || step < 0) return set_err(c, TEUK_E_INVAL, "src must not be NULL and step >= 0%s");
+    cudaStream_t st = (cudaStream_t)stream;
+    size_t n = 2 * (size_t)c->d.Nr * (size_t)c->d.Ntheta;   // complex elements
+    char *dst = c->state + (size_t)c->cur * c->level_bytes;
+    cudaPointerAttributes at;
+    bool dev = cudaPointerGetAttributes(&at, src) == cudaSuccess &&
+               (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged);
+    cudaGetLastError();
+    if (c->d.precision == TEUK_FP64) {
+        CK(cudaMemcpyAsync(dst, src, n * sizeof(double2), cudaMemcpyDefault, st), "state copy");
+    } else if (dev) {
+        CK(launch_convert_to(TEUK_FP32, (const double2 *)src, dst, n, st), "state convert");
+    } else {
+        double2 *stg = (double2 *)(c->coef + c->L.staging);
+        for (size_t o = 0; o < n; o += c->L.staging_elems) {
+            size_t k = n - o < c->L.staging_elems ? n - o : c->L.staging_elems;
+            CK(cudaMemcpyAsync(stg, (const double2 *)src + o, k * sizeof(double2), cudaMemcpyHostToDevice, st), "state upload");
+            CK(launch_convert_to(TEUK_FP32, stg, (float2 *)dst + o, k, st), "state convert");
+        }
+    }
+    CK(launch_set_ctl(c->coef, c->L, step, 0, st), "control block");
+    c->step = step;
+    c->rec_lo = step;
+    CK(extract_current(c, st), "extract");
+    if (!dev) CK(cudaStreamSynchronize(st), "state sync");
+    return TEUK_OK;
+}
+
+int teuk_get_state(teuk_ctx *c, void *dst, int64_t *step, void *stream)
+{
+    if (!c) return TEUK_E_STATE;
+    if (!dst) return set_err(c, TEUK_E_INVAL, "dst must not be NULL%s");
+    cudaStream_t st = (cudaStream_t)stream;
+    size_t n = 2 * (size_t)c->d.Nr * (size_t)c->d.Ntheta;
+    const char *src = c->state + (size_t)c->cur * c->level_bytes;
+    cudaPointerAttributes at;
+    bool dev = cudaPointerGetAttributes(&at, dst) == cudaSuccess &&
+               (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged);
+    cudaGetLastError();
+    if (c->d.precision == TEUK_FP64) {
+        CK(cudaMemcpyAsync(dst, src, n * sizeof(double2), cudaMemcpyDefault, st), "state copy");
+    } else if (dev) {
+        CK(launch_convert_from(TEUK_FP32, src, (double2 *)dst, n, st), "state convert");
+    } else {
+        double2 *stg = (double2 *)(c->coef + c->L.staging);
+        for (size_t o = 0; o < n; o += c->L.staging_elems) {
+            size_t k = n - o < c->L.staging_elems ? n - o : c->L.staging_elems;
+            CK(launch_convert_from(TEUK_FP32, (const float2 *)src + o, stg, k, st), "state convert");
+            CK(cudaMemcpyAsync((double2 *)dst + o, stg, k * sizeof(double2), cudaMemcpyDeviceToHost, st), "state download");
+        }
+    }
+    CK(cudaStreamSynchronize(st), "state sync");
+    if (step) *step = c->step;
+    return TEUK_OK;
+}
+
+int teuk_step(teuk_ctx *c, int64_t nsteps, void *stream)
+{
+    if (!c) return TEUK_E_STATE;
+    if (nsteps < 0) return set_err(c, TEUK_E_INVAL, "nsteps must be >= 0%s");
+    cudaStream_t st = (cudaStream_t)stream;
+    int64_t left = nsteps;
+    bool use_graph = st != nullptr && c->d.scheme == TEUK_SCHEME_SPLIT && nsteps >= 2 * kGraphChunk;
+    if (use_graph) {
+        int g = c->cur;
+        if (c->graph[g] && c->graph_stream[g] != st) {
+            cudaGraphExecDestroy(c->graph[g]);
+            c->graph[g] = nullptr;
+        }
+        if (!c->graph[g]) {
+            cudaGraph_t graph;
+            CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal), "begin capture");
+            int lev = g;
+            cudaError_t le = cudaSuccess;
+            for (int k = 0; k < kGraphChunk && le == cudaSuccess; ++k) {
+                le = launch_one(c, lev, st);
+                lev ^= 1;
+            }
+            cudaError_t ee = cudaStreamEndCapture(st, &graph);
+            if (le != cudaSuccess) return cuda_err(c, le, "captured launch");
+            if (ee != cudaSuccess) return cuda_err(c, ee, "end capture");
+            cudaError_t ie = cudaGraphInstantiate(&c->graph[g], graph, 0);
+            cudaGraphDestroy(graph);
+            if (ie != cudaSuccess) {
+                c->graph[g] = nullptr;
+                return cuda_err(c, ie, "graph instantiate");
+            }
+            c->graph_stream[g] = st;
+        }
+        while (left >= kGraphChunk) {
+            CK(cudaGraphLaunch(c->graph[g], st), "graph launch");
+            left -= kGraphChunk;
+        }
+    }
+    for (int64_t k = 0; k < left; ++k) {
+        CK(launch_one(c, c->cur, st), "step launch");
+        c->cur ^= 1;
+    }
+    c->step += nsteps;
+    return TEUK_OK;
+}
+
+int teuk_extract_waveform(teuk_ctx *c, int64_t first, int64_t count, double *h_out, double *row_out,
+                          void *stream)
+{
+    if (!c) return TEUK_E_STATE;
+    if (count < 0 || (count > 0 && !h_out)) return set_err(c, TEUK_E_INVAL, "need count >= 0 and h_out%s");
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(cudaStreamSynchronize(st), "sync");
+    int64_t lo = c->rec_lo > c->step - c->cap + 1 ? c->rec_lo : c->step - c->cap + 1;
+    if (count > 0 && (first < lo || first + count - 1 > c->step))
+        return set_err(c, TEUK_E_RANGE, "steps not in the ring buffer%s");
+    size_t slot_bytes = sizeof(double2) * (size_t)(c->d.Ntheta + 1);
+    int64_t done = 0;
+    while (done < count) {
+        int64_t s = first + done;
+        int64_t slot = s % c->cap;
+        int64_t run = c->cap - slot;
+        if (run > count - done) run = count - done;
+        const char *base = (const char *)c->wave + (size_t)slot * slot_bytes;
+        CK(cudaMemcpy2D(h_out + 2 * done, sizeof(double2), base, slot_bytes, sizeof(double2), (size_t)run,
+                        cudaMemcpyDeviceToHost), "waveform copy");
+        if (row_out)
+            CK(cudaMemcpy2D(row_out + 2 * c->d.Ntheta * done, sizeof(double2) * (size_t)c->d.Ntheta,
+                            base + sizeof(double2), slot_bytes, sizeof(double2) * (size_t)c->d.Ntheta,
+                            (size_t)run, cudaMemcpyDeviceToHost), "row copy");
+        done += run;
+    }
+    Ctl h;
+    CK(cudaMemcpy(&h, c->coef + c->L.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost), "control read");
+    if (h.flags & FLAG_NONFINITE) return set_err(c, TEUK_E_NONFINITE, "a non-finite waveform sample was produced%s");
+    return TEUK_OK;
+}
+
+int teuk_destroy(teuk_ctx *c)
+{
+    if (!c) return TEUK_OK;
+    drop_graphs(c);
+    delete c;
+    return TEUK_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,119 @@
+// teuk_internal.cuh -- definitions shared by the translation units of libteuk
+// (host API, FP64 coefficient generation, step kernels).  Not installed.
+//
+// Data layout in device memory (all caller-owned, 256-byte aligned blocks):
+//   state  : 2 time levels x [2 planes][Nr][Ntheta] complex T (T = float or
+//            double), plane 0 = Phi, plane 1 = Pi, theta fastest.
+//   coef   : r tables   [2Nr-1][NRF] FP64 and [2Nr-1][NRF] T
+//                        (position p = 2i: node i; p = 2i+1: r*_{i+1/2})
+//            theta tables [NTF][Ntheta] FP64 and T
+//            pivots     [Ntheta][Nr] complex T (theta-major, so the one
+//                        thread that solves row i reads consecutive i
+//                        across a warp)
+//            patch      [patch_rows][2][Ntheta] complex T (node, half node)
+//            weights    [Ntheta] FP64
+//            ctl        step counter, CTA ticket, error flags
+//            staging    host <-> device conversion chunk (FP32 state only)
+//            scratch    literal scheme only: midpoints [2][Nr-1][Ntheta] T
+//   wave   : ring buffer [capacity][1 + Ntheta] complex double (h_n, row).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "teuk.h"
+
+namespace teuk {
+
+// Fields of one r-table entry.  With Sigma^2 = R2 - aD sin^2(theta) and
+// sg = 1/Sigma^2 the coefficients of the first-order system are
+//   b      = R sqrt(sg)
+//   c_t    = sg (CTR + i (CTI + CTC cos theta))
+//   c_*    = -sg (CSR + i CSI)
+//   b b_*  = sg (E1 - sg (E2 - E3 sin^2 theta))
+//   K      = b c_t - c_* - b b_*
+//   c0rad  = -sg (C0R + i C0I)
+//   q      = DELTA sg
+enum RField {
+    RF_R = 0, RF_R2, RF_AD, RF_DELTA, RF_CTR, RF_CTI, RF_CTC, RF_CSR, RF_CSI,
+    RF_E1, RF_E2, RF_E3, RF_C0R, RF_C0I, RF_RR, RF_X, NRF
+};
+
+// Fields of the theta table.  AM, A0, AP are row j of the angular operator
+// A_th = -(d_thth + cot d_th) + (m + s cos)^2/sin^2 - s, centred differences,
+// parity ghosts folded into A0 at j = 0 and j = Ntheta-1.
+enum TField { TF_S2 = 0, TF_C, TF_AM, TF_A0, TF_AP, TF_PAD0, TF_PAD1, TF_PAD2, NTF };
+
+// Error flags in Ctl::flags.
+enum : unsigned { FLAG_NONFINITE = 1u };
+
+struct Ctl {
+    long long step;      // index n of the state the next step reads
+    unsigned ticket;     // CTAs of the current step that have finished
+    unsigned flags;      // FLAG_*
+    long long pad[6];
+};
+
+template <typename T> struct V2;
+template <> struct V2<float> { typedef float2 t; };
+template <> struct V2<double> { typedef double2 t; };
+
+// Everything a step kernel needs, passed by value.
+template <typename T> struct StepParams {
+    typedef typename V2<T>::t c2;
+    int Nr, Nth;
+    int tile_rows;           // output rows per CTA (split kernel)
+    int pitch;               // shared-memory row pitch in complex elements
+    int i_ext;               // extraction node
+    int wave_cap;            // ring-buffer slots
+    int patch_p0, patch_np;  // source patch rows [p0, p0+np); np = 0: no source
+    T dt, half_dt, drs_inv;  // step, dt/2, 1/dr*
+    T gh, gh2, h1g, h12g;    // gamma h, (gamma h)^2, (1-gamma) h, (1-2 gamma) h; h = dt/2
+    double dt64;             // dt in FP64 (time and phase)
+    double mOmega;           // m * Omega (FP64)
+    const T *rtab;           // [2Nr-1][NRF]
+    const T *thtab;          // [NTF][Nth]
+    const c2 *piv;           // [Nth][Nr]
+    const c2 *patch;         // [np][2][Nth]
+    const double *w;         // [Nth]
+    const c2 *uin;           // [2][Nr][Nth]
+    c2 *uout;                // [2][Nr][Nth]
+    c2 *mid;                 // literal scheme scratch [2][Nr-1][Nth]
+    double2 *wave;           // [cap][1 + Nth]
+    Ctl *ctl;
+};
+
+// SDIRK2 constant gamma = 1 - 1/sqrt(2) (Alexander 1977).
+constexpr double kGamma = 0.29289321881345247559915563789515;
+constexpr double kPi = 3.14159265358979323846264338327950;
+
+// ---------------------------------------------------------------- host side
+struct Layout {
+    size_t rtab64, rtabT, th64, thT, piv, patch, w, ctl, staging, scratch, total;
+    size_t staging_elems;    // complex doubles that fit in the staging area
+};
+
+Layout make_layout(const teuk_grid_desc &d);
+
+// Launchers (defined in teuk_coef.cu and teuk_step.cu).
+cudaError_t launch_coef_tables(const teuk_grid_desc &d, double drs, double dt, void *coef,
+                               const Layout &L, cudaStream_t st);
+cudaError_t launch_patch(const teuk_grid_desc &d, double drs, void *coef, const Layout &L,
+                         int p0, int np, double amp_re, double amp_im, double rs0,
+                         double sig_r, double sig_th, cudaStream_t st);
+cudaError_t launch_set_ctl(void *coef, const Layout &L, long long step, int clear_flags,
+                           cudaStream_t st);
+
+template <typename T>
+cudaError_t launch_split_step(const StepParams<T> &p, int threads, size_t smem, cudaStream_t st);
+template <typename T>
+cudaError_t launch_literal_step(const StepParams<T> &p, cudaStream_t st);
+template <typename T>
+cudaError_t launch_extract(const StepParams<T> &p, const typename V2<T>::t *u, long long step,
+                           cudaStream_t st);
+template <typename T>
+size_t split_smem_bytes(int tile_rows, int Nth);
+cudaError_t launch_convert_to(int prec, const double2 *src, void *dst, size_t n, cudaStream_t st);
+cudaError_t launch_convert_from(int prec, const void *src, double2 *dst, size_t n, cudaStream_t st);
+
+}  // namespace teuk

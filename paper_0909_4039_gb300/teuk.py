@@ -1,0 +1,259 @@
+"""Thin ctypes binding of libteuk (include/teuk.h).
+
+Only argument marshalling happens here: every step of the time stepper runs
+in the library's CUDA kernels.  PyTorch supplies device memory (caller-owned
+buffers, as the ABI requires) and streams.  There is no CPU fallback: if
+libteuk.so has not been built, or no GPU is present, the calls fail loudly.
+
+The functions keep the C names (teuk_init_grid, teuk_set_source, teuk_step,
+teuk_extract_waveform, ...); :class:`Stepper` bundles a context with its
+three device buffers for convenience.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+import numpy as np
+
+from . import _build
+
+TEUK_OK = 0
+TEUK_E_INVAL = 1
+TEUK_E_CUDA = 2
+TEUK_E_NONFINITE = 3
+TEUK_E_UNSTABLE = 4
+TEUK_E_TIMEOUT = 5
+TEUK_E_STATE = 6
+TEUK_E_RANGE = 7
+
+TEUK_FP64 = 0
+TEUK_FP32 = 1
+TEUK_SCHEME_SPLIT = 0
+TEUK_SCHEME_LITERAL = 1
+
+EXPORTED = [
+    "teuk_workspace_bytes", "teuk_init_grid", "teuk_set_source", "teuk_set_weights",
+    "teuk_set_state", "teuk_get_state", "teuk_step", "teuk_extract_waveform",
+    "teuk_current_step", "teuk_last_error", "teuk_status_string", "teuk_destroy",
+]
+
+
+class TeukError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+_STATUS = {0: "TEUK_OK", 1: "TEUK_E_INVAL", 2: "TEUK_E_CUDA", 3: "TEUK_E_NONFINITE",
+           4: "TEUK_E_UNSTABLE", 5: "TEUK_E_TIMEOUT", 6: "TEUK_E_STATE", 7: "TEUK_E_RANGE"}
+
+
+class GridDesc(ctypes.Structure):
+    """teuk_grid_desc"""
+    _fields_ = [
+        ("s", ctypes.c_int32), ("m", ctypes.c_int32),
+        ("M", ctypes.c_double), ("a", ctypes.c_double),
+        ("Nr", ctypes.c_int64), ("Ntheta", ctypes.c_int64),
+        ("rstar_min", ctypes.c_double), ("rstar_max", ctypes.c_double),
+        ("dt", ctypes.c_double), ("rstar_extract", ctypes.c_double),
+        ("precision", ctypes.c_int32), ("scheme", ctypes.c_int32),
+        ("allow_unstable", ctypes.c_int32), ("reserved", ctypes.c_int32),
+    ]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB_PATH
+
+
+def lib(load_only: bool = False):
+    """Load libteuk.so; raise if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_0909_4039_gb300._build.build() "
+                           "(or __graft_entry__.build()); there is no CPU fallback")
+    L = ctypes.CDLL(path)
+    vp, i64, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double
+    dp = ctypes.POINTER(ctypes.c_double)
+    sz = ctypes.POINTER(ctypes.c_size_t)
+    gp = ctypes.POINTER(GridDesc)
+    L.teuk_workspace_bytes.argtypes = [gp, sz, sz, sz]
+    L.teuk_init_grid.argtypes = [gp, vp, vp, vp, i64, vp, ctypes.POINTER(vp)]
+    L.teuk_set_source.argtypes = [vp, dbl, dbl, dbl, dbl, dbl, dbl]
+    L.teuk_set_weights.argtypes = [vp, dp]
+    L.teuk_set_state.argtypes = [vp, vp, i64, vp]
+    L.teuk_get_state.argtypes = [vp, vp, ctypes.POINTER(i64), vp]
+    L.teuk_step.argtypes = [vp, i64, vp]
+    L.teuk_extract_waveform.argtypes = [vp, i64, i64, dp, dp, vp]
+    L.teuk_current_step.argtypes = [vp]
+    L.teuk_current_step.restype = i64
+    L.teuk_last_error.argtypes = [vp]
+    L.teuk_last_error.restype = ctypes.c_char_p
+    L.teuk_status_string.argtypes = [ctypes.c_int]
+    L.teuk_status_string.restype = ctypes.c_char_p
+    L.teuk_destroy.argtypes = [vp]
+    for name in ("teuk_workspace_bytes", "teuk_init_grid", "teuk_set_source", "teuk_set_weights",
+                 "teuk_set_state", "teuk_get_state", "teuk_step", "teuk_extract_waveform", "teuk_destroy"):
+        getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _check(rc: int, ctx=None):
+    if rc != TEUK_OK:
+        msg = lib().teuk_last_error(ctx)
+        raise TeukError(rc, msg.decode() if msg else "")
+
+
+def make_desc(s, m, a, Nr, Ntheta, rstar_min, rstar_max, dt=0.0, rstar_extract=500.0, M=1.0,
+              precision=TEUK_FP64, scheme=TEUK_SCHEME_SPLIT, allow_unstable=False) -> GridDesc:
+    return GridDesc(int(s), int(m), float(M), float(a), int(Nr), int(Ntheta), float(rstar_min),
+                    float(rstar_max), float(dt), float(rstar_extract), int(precision), int(scheme),
+                    int(bool(allow_unstable)), 0)
+
+
+def teuk_workspace_bytes(desc: GridDesc):
+    a, b, c = ctypes.c_size_t(), ctypes.c_size_t(), ctypes.c_size_t()
+    _check(lib().teuk_workspace_bytes(ctypes.byref(desc), ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return a.value, b.value, c.value
+
+
+def teuk_init_grid(desc: GridDesc, d_state: int, d_coef: int, d_wave: int, wave_capacity: int,
+                   stream: int = 0):
+    ctx = ctypes.c_void_p()
+    _check(lib().teuk_init_grid(ctypes.byref(desc), d_state, d_coef, d_wave, wave_capacity, stream,
+                                ctypes.byref(ctx)))
+    return ctx
+
+
+def teuk_set_source(ctx, amp: complex, r0: float, sigma_rstar: float, sigma_theta: float,
+                    Omega: float = float("nan")):
+    amp = complex(amp)
+    _check(lib().teuk_set_source(ctx, amp.real, amp.imag, r0, sigma_rstar, sigma_theta, Omega), ctx)
+
+
+def teuk_set_weights(ctx, w: np.ndarray | None):
+    if w is None:
+        _check(lib().teuk_set_weights(ctx, None), ctx)
+    else:
+        w = np.ascontiguousarray(w, dtype=np.float64)
+        _check(lib().teuk_set_weights(ctx, w.ctypes.data_as(ctypes.POINTER(ctypes.c_double))), ctx)
+
+
+def teuk_set_state(ctx, src_ptr: int, step: int, stream: int = 0):
+    _check(lib().teuk_set_state(ctx, src_ptr, step, stream), ctx)
+
+
+def teuk_get_state(ctx, dst_ptr: int, stream: int = 0) -> int:
+    st = ctypes.c_int64()
+    _check(lib().teuk_get_state(ctx, dst_ptr, ctypes.byref(st), stream), ctx)
+    return st.value
+
+
+def teuk_step(ctx, nsteps: int, stream: int = 0):
+    _check(lib().teuk_step(ctx, int(nsteps), stream), ctx)
+
+
+def teuk_extract_waveform(ctx, first_step: int, count: int, want_rows: bool = False, Ntheta: int = 0,
+                          stream: int = 0):
+    h = np.empty(count, dtype=np.complex128)
+    rows = np.empty((count, Ntheta), dtype=np.complex128) if want_rows else None
+    dp = ctypes.POINTER(ctypes.c_double)
+    _check(lib().teuk_extract_waveform(ctx, first_step, count, h.ctypes.data_as(dp),
+                                       rows.ctypes.data_as(dp) if rows is not None else None, stream), ctx)
+    return (h, rows) if want_rows else h
+
+
+def teuk_current_step(ctx) -> int:
+    return int(lib().teuk_current_step(ctx))
+
+
+def teuk_destroy(ctx):
+    _check(lib().teuk_destroy(ctx))
+
+
+class Stepper:
+    """A context plus its caller-owned device buffers (torch tensors)."""
+
+    def __init__(self, s=-2, m=2, a=0.9, Nr=1024, Ntheta=32, rstar_min=-100.0, rstar_max=600.0,
+                 dt=0.0, rstar_extract=500.0, M=1.0, precision="fp64", scheme="split",
+                 allow_unstable=False, wave_capacity=4096, device=None, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("libteuk needs a CUDA GPU; no CPU fallback exists")
+        self.torch = torch
+        self.device = torch.device(device or "cuda:0")
+        prec = {"fp64": TEUK_FP64, "fp32": TEUK_FP32}[precision]
+        sch = {"split": TEUK_SCHEME_SPLIT, "literal": TEUK_SCHEME_LITERAL}[scheme]
+        self.desc = make_desc(s, m, a, Nr, Ntheta, rstar_min, rstar_max, dt, rstar_extract, M, prec, sch,
+                              allow_unstable)
+        self.Nr, self.Ntheta, self.precision = int(Nr), int(Ntheta), precision
+        sb, cb, wb = teuk_workspace_bytes(self.desc)
+        with torch.cuda.device(self.device):
+            self.stream = stream or torch.cuda.Stream(device=self.device)
+            self.d_state = torch.empty(sb, dtype=torch.uint8, device=self.device)
+            self.d_coef = torch.empty(cb, dtype=torch.uint8, device=self.device)
+            self.d_wave = torch.empty(wb * wave_capacity, dtype=torch.uint8, device=self.device)
+        self.wave_capacity = wave_capacity
+        self.ctx = teuk_init_grid(self.desc, self.d_state.data_ptr(), self.d_coef.data_ptr(),
+                                  self.d_wave.data_ptr(), wave_capacity, self.stream.cuda_stream)
+        drs = (rstar_max - rstar_min) / (Nr - 1)
+        self.drs = drs
+        self.dt = dt if dt > 0 else 0.5 * drs
+
+    @property
+    def sh(self) -> int:
+        return self.stream.cuda_stream
+
+    def set_source(self, amp=1.0, r0=10.0, sigma_rstar=0.1, sigma_theta=0.1, Omega=float("nan")):
+        teuk_set_source(self.ctx, amp, r0, sigma_rstar, sigma_theta, Omega)
+
+    def set_weights(self, w=None):
+        teuk_set_weights(self.ctx, w)
+
+    def set_state(self, u: np.ndarray, step: int = 0):
+        u = np.ascontiguousarray(u, dtype=np.complex128)
+        if u.shape != (2, self.Nr, self.Ntheta):
+            raise ValueError(f"state shape {u.shape} != {(2, self.Nr, self.Ntheta)}")
+        teuk_set_state(self.ctx, u.ctypes.data, step, self.sh)
+
+    def set_state_device(self, u, step: int = 0):
+        """u: torch complex128 CUDA tensor of shape (2, Nr, Ntheta)."""
+        assert u.is_cuda and u.dtype == self.torch.complex128 and u.is_contiguous()
+        teuk_set_state(self.ctx, u.data_ptr(), step, self.sh)
+
+    def get_state(self) -> np.ndarray:
+        out = np.empty((2, self.Nr, self.Ntheta), dtype=np.complex128)
+        teuk_get_state(self.ctx, out.ctypes.data, self.sh)
+        return out
+
+    def step(self, n: int):
+        teuk_step(self.ctx, n, self.sh)
+
+    def waveform(self, first: int, count: int, rows: bool = False):
+        return teuk_extract_waveform(self.ctx, first, count, rows, self.Ntheta, self.sh)
+
+    @property
+    def current_step(self) -> int:
+        return teuk_current_step(self.ctx)
+
+    def synchronize(self):
+        self.stream.synchronize()
+
+    def close(self):
+        if getattr(self, "ctx", None) is not None:
+            teuk_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,182 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Both sides take the same seeded inputs (paper_0909_4039_gb300.inputs) and
+share no code.  Tolerances: relative L2 <= 1e-12 for the FP64 path and
+<= 1e-4 for the FP32-state path, on the final state and on the waveform.
+Sizes: small grids that span several tiles with ragged tails, the full
+1024x32 workload (2000 steps), and the 16384x128 grid in the launch
+configuration the bench times (a window of steps the oracle can afford,
+plus properties that hold at any size).
+"""
+import numpy as np
+import pytest
+
+from paper_0909_4039_gb300 import inputs
+from tests._common import gpu_stepper, oracle_problem, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-12
+FP32_TOL = 1e-4
+
+
+def _run_both(w, precision="fp64", scheme="split", init_seed=None, with_source=True, allow_unstable=False):
+    from oracle import oracle as O
+    p = oracle_problem(w, scheme=scheme, with_source=with_source)
+    u0 = inputs.random_state(w.Nr, w.Ntheta, seed=init_seed) if init_seed is not None else None
+    uo, ho = O.run(p, u0, w.steps)
+    st = gpu_stepper(w, precision=precision, scheme=scheme, with_source=with_source, allow_unstable=allow_unstable)
+    if u0 is not None:
+        st.set_state(u0, 0)
+    st.step(w.steps)
+    ug = st.get_state()
+    hg = st.waveform(0, w.steps + 1)
+    st.close()
+    return uo, ho, ug, hg
+
+
+SMALL = [
+    # name, Nr, Ntheta, a, m, steps
+    ("37x5", 37, 5, 0.7, 2, 30),
+    ("100x16", 100, 16, 0.99, 1, 40),
+    ("257x33", 257, 33, 0.0, 3, 25),
+    ("129x1", 129, 1, 0.5, 2, 30),
+    ("3x8", 3, 8, 0.9, 2, 5),
+    ("70x64", 70, 64, 0.95, 4, 20),
+]
+
+
+@pytest.mark.parametrize("name,Nr,Nth,a,m,steps", SMALL)
+@pytest.mark.parametrize("precision,tol", [("fp64", FP64_TOL), ("fp32", FP32_TOL)])
+def test_small_grids_random_data_and_source(name, Nr, Nth, a, m, steps, precision, tol):
+    w = inputs.Workload(name, s=-2, m=m, a=a, Nr=Nr, Ntheta=Nth, rs_min=-20.0, rs_max=40.0, steps=steps,
+                        r0=6.0, amp=0.7 - 0.4j, sig_r=1.0, sig_th=0.3, rs_ext=30.0)
+    uo, ho, ug, hg = _run_both(w, precision, init_seed=Nr * 7 + Nth)
+    assert rel_l2(ug, uo) <= tol, rel_l2(ug, uo)
+    assert rel_l2(hg, ho) <= tol, rel_l2(hg, ho)
+
+
+def test_literal_scheme_few_steps():
+    w = inputs.Workload("lit", s=-2, m=2, a=0.8, Nr=41, Ntheta=8, rs_min=-20.0, rs_max=40.0, steps=3,
+                        r0=6.0, amp=1.0, sig_r=1.0, sig_th=0.3, rs_ext=30.0)
+    uo, ho, ug, hg = _run_both(w, "fp64", scheme="literal", init_seed=3, allow_unstable=True)
+    assert rel_l2(ug, uo) <= FP64_TOL
+    assert rel_l2(hg, ho) <= FP64_TOL
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", FP64_TOL), ("fp32", FP32_TOL)])
+def test_plain_1024x32_full_run(precision, tol):
+    """The plain workload: s=-2, m=2, a=0.9, 1024x32, dt = dr*/2, 2000 steps,
+    Gaussian orbit at r0 = 10, zero initial data, extraction at r* = 500."""
+    w = inputs.PLAIN_1024x32
+    uo, ho, ug, hg = _run_both(w, precision)
+    assert np.abs(uo).max() > 0
+    assert rel_l2(ug, uo) <= tol, rel_l2(ug, uo)
+    assert rel_l2(hg, ho) <= tol, rel_l2(hg, ho)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", FP64_TOL), ("fp32", FP32_TOL)])
+def test_large_16384x128_window(precision, tol):
+    """The 16384x128 grid in the bench's launch configuration: random data
+    over every tile plus the r0 = 6 source, for a window of steps."""
+    w = inputs.LARGE_16384x128.with_(steps=40)
+    uo, ho, ug, hg = _run_both(w, precision, init_seed=11)
+    assert rel_l2(ug, uo) <= tol, rel_l2(ug, uo)
+    assert rel_l2(hg, ho) <= tol, rel_l2(hg, ho)
+
+
+def test_large_16384x128_linearity_and_zero():
+    """Properties at full size and full step count segment: zero stays zero;
+    step(alpha u + beta v) = alpha step(u) + beta step(v) without source."""
+    w = inputs.LARGE_16384x128
+    st = gpu_stepper(w, "fp64", with_source=False, wave_capacity=64)
+    st.step(200)
+    assert np.abs(st.get_state()).max() == 0.0
+    u = inputs.random_state(w.Nr, w.Ntheta, seed=1)
+    v = inputs.random_state(w.Nr, w.Ntheta, seed=2)
+    al, be = 0.6 - 0.3j, -1.1 + 0.2j
+    outs = []
+    for x in (u, v, al * u + be * v):
+        st.set_state(x, 0)
+        st.step(200)
+        outs.append(st.get_state())
+    st.close()
+    assert rel_l2(outs[2], al * outs[0] + be * outs[1]) <= 1e-12
+
+
+def test_graph_replay_matches_single_launches():
+    w = inputs.Workload("g", s=-2, m=2, a=0.9, Nr=300, Ntheta=16, rs_min=-20.0, rs_max=40.0, steps=0,
+                        r0=6.0, amp=1.0, sig_r=1.0, sig_th=0.3, rs_ext=30.0)
+    a = gpu_stepper(w, "fp32", wave_capacity=512)
+    b = gpu_stepper(w, "fp32", wave_capacity=512)
+    a.step(150)                    # two graph replays of 64 steps + 22 launches
+    for _ in range(150):
+        b.step(1)
+    assert np.array_equal(a.get_state(), b.get_state())
+    assert np.array_equal(a.waveform(0, 151), b.waveform(0, 151))
+    assert a.current_step == 150
+    a.close()
+    b.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_state_roundtrip_and_zero_steps(precision):
+    w = inputs.Workload("rt", s=-2, m=1, a=0.3, Nr=50, Ntheta=12, rs_min=-20.0, rs_max=40.0, steps=0, amp=0.0)
+    st = gpu_stepper(w, precision, with_source=False)
+    u = inputs.random_state(50, 12, seed=4)
+    st.set_state(u, 17)
+    st.step(0)
+    back = st.get_state()
+    tol = 0.0 if precision == "fp64" else 1.2e-7
+    assert np.abs(back - u).max() <= tol * np.abs(u).max()
+    assert st.current_step == 17
+    st.close()
+
+
+def test_extraction_default_weights_and_custom():
+    w = inputs.Workload("ex", s=-2, m=2, a=0.0, Nr=80, Ntheta=24, rs_min=-20.0, rs_max=40.0, steps=0, amp=0.0,
+                        rs_ext=10.0)
+    st = gpu_stepper(w, "fp64", with_source=False)
+    th = (np.arange(24) + 0.5) * np.pi / 24
+    Y = np.cos(th / 2) ** 4
+    u = np.zeros((2, 80, 24), complex)
+    u[0] = (np.arange(80)[:, None] * 0.01 + 1.0) * Y[None, :] * (2 - 1j)
+    st.set_state(u, 0)
+    h = st.waveform(0, 1)
+    ie = int(round((10.0 + 20.0) / (60.0 / 79)))
+    assert abs(h[0] - (ie * 0.01 + 1.0) * (2 - 1j)) < 1e-13
+    wts = np.linspace(0.5, 1.5, 24)
+    st.set_weights(wts)
+    st.set_state(u, 5)
+    h, rows = st.waveform(5, 1, rows=True)
+    assert abs(h[0] - np.dot(wts, u[0, ie])) < 1e-12
+    assert np.array_equal(rows[0], u[0, ie])
+    st.close()
+
+
+def test_waveform_range_and_nonfinite():
+    from paper_0909_4039_gb300 import teuk
+    w = inputs.Workload("nf", s=-2, m=2, a=0.5, Nr=40, Ntheta=8, rs_min=-20.0, rs_max=40.0, steps=0, amp=0.0)
+    st = gpu_stepper(w, "fp64", with_source=False, wave_capacity=4)
+    st.step(10)
+    with pytest.raises(teuk.TeukError) as e:
+        st.waveform(2, 3)              # only steps 7..10 are in a 4-slot ring
+    assert e.value.code == teuk.TEUK_E_RANGE
+    st.waveform(7, 4)
+    u = np.zeros((2, 40, 8), complex)
+    u[0, :, :] = np.nan
+    st.set_state(u, 0)
+    with pytest.raises(teuk.TeukError) as e:
+        st.waveform(0, 1)
+    assert e.value.code == teuk.TEUK_E_NONFINITE
+    st.close()
+
+
+def test_extraction_node_clamped_to_boundary():
+    w = inputs.Workload("bd", s=-2, m=2, a=0.5, Nr=40, Ntheta=8, rs_min=-20.0, rs_max=40.0, steps=5, amp=1.0,
+                        r0=6.0, sig_r=1.0, sig_th=0.3, rs_ext=1e6)
+    st = gpu_stepper(w, "fp64")
+    st.set_state(inputs.random_state(40, 8, seed=9), 0)
+    st.step(5)
+    assert np.all(st.waveform(0, 6)[1:] == 0)     # outer boundary row is zero
+    st.close()
