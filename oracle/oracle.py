@@ -14,6 +14,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import platform
 import subprocess
 import threading
 from dataclasses import dataclass
@@ -32,18 +33,56 @@ _lock = threading.Lock()
 _lib = None
 
 
-def build(force: bool = False) -> str:
-    """Compile teuk_oracle.c into oracle/_build/liboracle.so with gcc."""
+def _build_lib(path: str, extra: list[str], force: bool) -> str:
     os.makedirs(BUILD_DIR, exist_ok=True)
-    if (not force and os.path.exists(LIB_PATH)
-            and os.path.getmtime(LIB_PATH) >= max(os.path.getmtime(SRC),
-                                                  os.path.getmtime(os.path.join(HERE, "teuk_oracle.h")))):
-        return LIB_PATH
-    tmp = LIB_PATH + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", "-o", tmp, SRC, "-lm"]
+    if (not force and os.path.exists(path)
+            and os.path.getmtime(path) >= max(os.path.getmtime(SRC),
+                                              os.path.getmtime(os.path.join(HERE, "teuk_oracle.h")))):
+        return path
+    tmp = path + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", *extra, "-fopenmp", "-fPIC", "-shared", "-o", tmp, SRC, "-lm"]
     subprocess.run(cmd, check=True)
-    os.replace(tmp, LIB_PATH)
-    return LIB_PATH
+    os.replace(tmp, path)
+    return path
+
+
+def build(force: bool = False) -> str:
+    """Compile teuk_oracle.c into oracle/_build/liboracle.so with gcc
+    (ISO C, no floating-point contraction)."""
+    return _build_lib(LIB_PATH, ["-ffp-contract=off"], force)
+
+
+FMA_LIB_PATH = os.path.join(BUILD_DIR, "liboracle_fma.so")
+
+
+def build_fma_variant(force: bool = False) -> str:
+    """The same source compiled with fused multiply-adds wherever the
+    compiler may contract a*b+c.  It computes the same method with a
+    different rounding order; its disagreement with build() measures how
+    strongly a run amplifies rounding (the floor any second FP64
+    implementation, such as the GPU path, can be held to)."""
+    extra = ["-ffp-contract=fast"]
+    if platform.machine() in ("x86_64", "AMD64"):
+        extra.append("-mfma")
+    return _build_lib(FMA_LIB_PATH, extra, force)
+
+
+def run_fma_variant(p: "OracleProblem", u0, nsteps: int, n0: int = 0):
+    """run() with the FMA-contracted build of the oracle."""
+    global _lib
+    saved = lib()
+    path = build_fma_variant()
+    with _lock:
+        _lib = None
+    try:
+        L = ctypes.CDLL(path)
+        _bind(L)
+        with _lock:
+            _lib = L
+        return run(p, u0, nsteps, n0)
+    finally:
+        with _lock:
+            _lib = saved
 
 
 class Grid(ctypes.Structure):
@@ -72,38 +111,40 @@ class Coef(ctypes.Structure):
         "K_re", "K_im", "Fpref")]
 
 
+def _bind(L):
+    dp = ctypes.POINTER(ctypes.c_double)
+    gp = ctypes.POINTER(Grid)
+    sp = ctypes.POINTER(Source)
+    L.or_rstar_of_x.restype = ctypes.c_double
+    L.or_rstar_of_x.argtypes = [ctypes.c_double] * 3
+    L.or_x_of_rstar.restype = ctypes.c_int
+    L.or_x_of_rstar.argtypes = [ctypes.c_double] * 3 + [dp]
+    L.or_point_coef.restype = None
+    L.or_point_coef.argtypes = [gp, ctypes.c_double, ctypes.c_double, ctypes.POINTER(Coef)]
+    L.or_kepler_omega.restype = ctypes.c_double
+    L.or_kepler_omega.argtypes = [ctypes.c_double] * 3
+    L.or_apply_atheta.restype = None
+    L.or_apply_atheta.argtypes = [gp, dp, dp]
+    L.or_default_weights.restype = None
+    L.or_default_weights.argtypes = [gp, dp]
+    L.or_extract_index.restype = ctypes.c_long
+    L.or_extract_index.argtypes = [gp]
+    L.or_step.restype = ctypes.c_int
+    L.or_step.argtypes = [gp, sp, ctypes.c_long, ctypes.c_int, dp, dp]
+    L.or_run.restype = ctypes.c_int
+    L.or_run.argtypes = [gp, sp, ctypes.c_long, ctypes.c_long, dp, dp, dp]
+    L.or_imp.restype = ctypes.c_int
+    L.or_imp.argtypes = [gp, ctypes.c_double, dp, dp]
+    L.or_lw.restype = ctypes.c_int
+    L.or_lw.argtypes = [gp, sp, ctypes.c_long, ctypes.c_int, dp, dp]
+    return L
+
+
 def lib():
     global _lib
     with _lock:
         if _lib is None:
-            path = build()
-            L = ctypes.CDLL(path)
-            dp = ctypes.POINTER(ctypes.c_double)
-            gp = ctypes.POINTER(Grid)
-            sp = ctypes.POINTER(Source)
-            L.or_rstar_of_x.restype = ctypes.c_double
-            L.or_rstar_of_x.argtypes = [ctypes.c_double] * 3
-            L.or_x_of_rstar.restype = ctypes.c_int
-            L.or_x_of_rstar.argtypes = [ctypes.c_double] * 3 + [dp]
-            L.or_point_coef.restype = None
-            L.or_point_coef.argtypes = [gp, ctypes.c_double, ctypes.c_double, ctypes.POINTER(Coef)]
-            L.or_kepler_omega.restype = ctypes.c_double
-            L.or_kepler_omega.argtypes = [ctypes.c_double] * 3
-            L.or_apply_atheta.restype = None
-            L.or_apply_atheta.argtypes = [gp, dp, dp]
-            L.or_default_weights.restype = None
-            L.or_default_weights.argtypes = [gp, dp]
-            L.or_extract_index.restype = ctypes.c_long
-            L.or_extract_index.argtypes = [gp]
-            L.or_step.restype = ctypes.c_int
-            L.or_step.argtypes = [gp, sp, ctypes.c_long, dp, dp]
-            L.or_run.restype = ctypes.c_int
-            L.or_run.argtypes = [gp, sp, ctypes.c_long, ctypes.c_long, dp, dp, dp]
-            L.or_loc_half.restype = ctypes.c_int
-            L.or_loc_half.argtypes = [gp, dp, dp]
-            L.or_lw.restype = ctypes.c_int
-            L.or_lw.argtypes = [gp, sp, ctypes.c_long, ctypes.c_int, dp, dp]
-            _lib = L
+            _lib = _bind(ctypes.CDLL(build()))
         return _lib
 
 
@@ -194,23 +235,26 @@ def _state(u: np.ndarray, p: OracleProblem) -> np.ndarray:
     return u
 
 
-def step(p: OracleProblem, u: np.ndarray, n: int = 0) -> np.ndarray:
+def step(p: OracleProblem, u: np.ndarray, n: int = 0, first: bool = True) -> np.ndarray:
+    """Literal scheme: u^n -> u^{n+1}.  Split scheme: internal state
+    s_n -> s_{n+1} (first=True: from a physical state, LW_n C_{dt/2} u)."""
     u = _state(u, p)
     out = np.empty_like(u)
     g, s = p.grid(), p.source()
-    rc = lib().or_step(ctypes.byref(g), ctypes.byref(s), n, _dp(u), _dp(out))
+    rc = lib().or_step(ctypes.byref(g), ctypes.byref(s), n, int(first), _dp(u), _dp(out))
     if rc != 0:
         raise RuntimeError(f"or_step rc={rc}")
     return out
 
 
-def loc_half(p: OracleProblem, u: np.ndarray) -> np.ndarray:
+def imp(p: OracleProblem, u: np.ndarray, h: float) -> np.ndarray:
+    """Implicit SDIRK2 step of length h of the algebraic terms, every r* row."""
     u = _state(u, p)
     out = np.empty_like(u)
     g = p.grid()
-    rc = lib().or_loc_half(ctypes.byref(g), _dp(u), _dp(out))
+    rc = lib().or_imp(ctypes.byref(g), float(h), _dp(u), _dp(out))
     if rc != 0:
-        raise RuntimeError(f"or_loc_half rc={rc}")
+        raise RuntimeError(f"or_imp rc={rc}")
     return out
 
 

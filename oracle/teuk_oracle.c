@@ -413,7 +413,7 @@ static void solve_tri_c(long N, double c, const double *lo, const cplx *dg, cons
     for (long j = N - 2; j >= 0; --j) x[j] -= cp[j] * x[j + 1];
 }
 
-/* One step of length h = dt/2 for the algebraic part of the first-order
+/* One step of length h for the algebraic part of the first-order
  * system, i.e. the terms -L u - A u of S (Eq. 12):
  *     Phi_t = Pi,   Pi_t = -(B + c0rad) Phi - c_t Pi,   B = q A_th
  * (B is the angular operator with the pole potential; c0rad and c_t are the
@@ -430,12 +430,12 @@ static void solve_tri_c(long N, double c, const double *lo, const cplx *dg, cons
  * tridiagonal solve:
  *     [(1 + gh c_t) + gh^2 (B + c0rad)] U_Phi = (1 + gh c_t) rPhi + gh rPi
  *     U_Pi = (rPi - gh (B + c0rad) U_Phi) / (1 + gh c_t),      gh = gamma h. */
-static int loc_impl(const or_grid *g, const cplx *u, cplx *unew)
+static int loc_impl(const or_grid *g, double h, const cplx *u, cplx *unew)
 {
     const long Nr = g->Nr, N = g->Nth;
     const double drs = drs_of(g);
     const double gam = 1.0 - 1.0 / sqrt(2.0);
-    const double h = 0.5 * g->dt, gh = gam * h, c = gh * gh;
+    const double gh = gam * h, c = gh * gh;
     const cplx *Phi = u, *Pi = u + Nr * N;
     cplx *Phin = unew, *Pin = unew + Nr * N;
     int nt;
@@ -502,10 +502,10 @@ static int loc_impl(const or_grid *g, const cplx *u, cplx *unew)
 
 /* ------------------------------------------------------------ public ---- */
 
-int or_loc_half(const or_grid *g, const double *u_in, double *u_out)
+int or_imp(const or_grid *g, double h, const double *u_in, double *u_out)
 {
-    if (!grid_ok(g)) return -10;
-    return loc_impl(g, (const cplx *)u_in, (cplx *)u_out);
+    if (!grid_ok(g) || !(h > 0.0)) return -10;
+    return loc_impl(g, h, (const cplx *)u_in, (cplx *)u_out);
 }
 
 int or_lw(const or_grid *g, const or_source *src, long n, int full,
@@ -519,31 +519,58 @@ int or_lw(const or_grid *g, const or_source *src, long n, int full,
     return rc;
 }
 
-/* One time step n -> n+1.
- *   literal: Eqs. 13-14 with every term of Eq. 12 in S.
- *   split:   implicit half-step (dt/2) of -L u - A u, Eqs. 13-14 with
- *            S = T - (M - D) d_{r*} u, implicit half-step again (Strang
- *            splitting). */
-static int step_impl(const or_grid *g, const or_source *src, long n,
-                     const cplx *u, cplx *unew, cplx *t1, cplx *t2, cplx *mid)
+/* Time stepping.
+ *   literal: u^{n+1} = LW_n(u^n), Eqs. 13-14 with every term of Eq. 12 in S.
+ *   split:   Strang splitting u^{n+1} = C_{dt/2} LW_n C_{dt/2} u^n, where
+ *            C_h is the implicit step of the algebraic terms -L u - A u
+ *            (loc_impl) and LW_n carries D and S = T - (M - D) d_{r*} u.
+ *            Between consecutive steps the two half steps that meet,
+ *            C_{dt/2} C_{dt/2}, are taken as one implicit step C_dt (both
+ *            are second-order approximations of the same flow, so the
+ *            composition stays second order).  The run therefore keeps the
+ *            internal state s_n = LW_{n-1} C(s_{n-1}) and outputs the
+ *            physical state u_n = C_{dt/2} s_n:
+ *                s_{n0+1} = LW_{n0} C_{dt/2} u_{n0}         (first step)
+ *                s_{n+1}  = LW_n C_dt s_n                    (later steps)
+ *                u_{n}    = C_{dt/2} s_n. */
+static int first_impl(const or_grid *g, const or_source *src, long n, const cplx *u, cplx *s_out,
+                      cplx *t1, cplx *mid)
 {
-    if (g->scheme == OR_SCHEME_LITERAL)
-        return lw_impl(g, src, n, 1, u, unew, mid);
-    int rc = loc_impl(g, u, t1);
+    int rc = loc_impl(g, 0.5 * g->dt, u, t1);
     if (rc) return rc;
-    rc = lw_impl(g, src, n, 0, t1, t2, mid);
-    if (rc) return rc;
-    return loc_impl(g, t2, unew);
+    return lw_impl(g, src, n, 0, t1, s_out, mid);
 }
 
-int or_step(const or_grid *g, const or_source *src, long n,
+static int next_impl(const or_grid *g, const or_source *src, long n, const cplx *s, cplx *s_out,
+                     cplx *t1, cplx *mid)
+{
+    int rc = loc_impl(g, g->dt, s, t1);
+    if (rc) return rc;
+    return lw_impl(g, src, n, 0, t1, s_out, mid);
+}
+
+static cplx *scratch(const or_grid *g)
+{
+    size_t plane = (size_t)g->Nr * (size_t)g->Nth;
+    return (cplx *)malloc(sizeof(cplx) * (plane * 2 + (size_t)(g->Nr - 1) * g->Nth * 2));
+}
+
+/* literal scheme: u^n -> u^{n+1};  split scheme: internal s_n -> s_{n+1}
+ * (first = 1: from a physical state u_n, s_{n+1} = LW_n C_{dt/2} u_n). */
+int or_step(const or_grid *g, const or_source *src, long n, int first,
             const double *u_in, double *u_out)
 {
     if (!grid_ok(g)) return -10;
     size_t plane = (size_t)g->Nr * (size_t)g->Nth;
-    cplx *buf = (cplx *)malloc(sizeof(cplx) * (plane * 4 + (size_t)(g->Nr - 1) * g->Nth * 2));
+    cplx *buf = scratch(g);
     if (!buf) return -11;
-    int rc = step_impl(g, src, n, (const cplx *)u_in, (cplx *)u_out, buf, buf + 2 * plane, buf + 4 * plane);
+    int rc;
+    if (g->scheme == OR_SCHEME_LITERAL)
+        rc = lw_impl(g, src, n, 1, (const cplx *)u_in, (cplx *)u_out, buf + 2 * plane);
+    else if (first)
+        rc = first_impl(g, src, n, (const cplx *)u_in, (cplx *)u_out, buf, buf + 2 * plane);
+    else
+        rc = next_impl(g, src, n, (const cplx *)u_in, (cplx *)u_out, buf, buf + 2 * plane);
     free(buf);
     return rc;
 }
@@ -584,8 +611,9 @@ static void extract(const or_grid *g, const cplx *u, const double *w, double *h)
     h[1] = cimag(acc);
 }
 
-/* Advance u (in place) from step n0 by nsteps; h_out[2k], h_out[2k+1] get
- * the waveform sample of state n0+k, k = 0..nsteps. */
+/* Advance the physical state u (in place) from step n0 by nsteps;
+ * h_out[2k], h_out[2k+1] get the waveform sample of state n0+k,
+ * k = 0..nsteps.  The split scheme starts a new Strang sequence at n0. */
 int or_run(const or_grid *g, const or_source *src, long n0, long nsteps,
            double *u, const double *weights, double *h_out)
 {
@@ -596,14 +624,23 @@ int or_run(const or_grid *g, const or_source *src, long n0, long nsteps,
     if (!w || !buf) { free(w); free(buf); return -11; }
     if (weights) memcpy(w, weights, sizeof(double) * (size_t)g->Nth);
     else or_default_weights(g, w);
-    cplx *cur = (cplx *)u, *nxt = buf, *t1 = buf + 2 * plane, *t2 = buf + 4 * plane, *mid = buf + 6 * plane;
-    if (h_out) extract(g, cur, w, h_out);
+    cplx *ph = (cplx *)u, *s = buf, *s2 = buf + 2 * plane, *t1 = buf + 4 * plane, *mid = buf + 6 * plane;
+    if (h_out) extract(g, ph, w, h_out);
     int rc = 0;
     for (long k = 0; k < nsteps; ++k) {
-        rc = step_impl(g, src, n0 + k, cur, nxt, t1, t2, mid);
-        if (rc) break;
-        memcpy(cur, nxt, sizeof(cplx) * 2 * plane);
-        if (h_out) extract(g, cur, w, h_out + 2 * (k + 1));
+        if (g->scheme == OR_SCHEME_LITERAL) {
+            rc = lw_impl(g, src, n0 + k, 1, ph, s, mid);
+            if (rc) break;
+            memcpy(ph, s, sizeof(cplx) * 2 * plane);
+        } else {
+            if (k == 0) rc = first_impl(g, src, n0, ph, s, t1, mid);
+            else rc = next_impl(g, src, n0 + k, s, s2, t1, mid);
+            if (rc) break;
+            if (k > 0) memcpy(s, s2, sizeof(cplx) * 2 * plane);
+            rc = loc_impl(g, 0.5 * g->dt, s, ph);      /* physical u_{n0+k+1} */
+            if (rc) break;
+        }
+        if (h_out) extract(g, ph, w, h_out + 2 * (k + 1));
     }
     free(w);
     free(buf);

@@ -21,9 +21,10 @@
  *   - two schemes.  "literal": Eqs. 13-14 with every term of Eq. 12 in S
  *     (unstable at dt = dr* / 2; kept for few-step checks).  "split": an
  *     implicit-explicit Strang splitting -- the algebraic terms -L u - A u
- *     of S are integrated by half steps of the L-stable two-stage SDIRK
- *     method of order 2, and the Lax-Wendroff step of Eqs. 13-14 carries
- *     the transport D and S = T - (M - D) d_{r*} u;
+ *     of S are integrated by the L-stable two-stage SDIRK method of order
+ *     2 (half steps at the ends of a run, one full step between two
+ *     Lax-Wendroff steps), and the Lax-Wendroff step of Eqs. 13-14
+ *     carries the transport D and S = T - (M - D) d_{r*} u;
  *   - the source T is a Gaussian on a circular equatorial orbit.
  *
  * State layout: u = [2][Nr][Ntheta] complex double, re/im interleaved,
@@ -86,11 +87,11 @@ void or_apply_atheta(const or_grid *g, const double *row_in, double *row_out);
 void or_default_weights(const or_grid *g, double *w);
 long or_extract_index(const or_grid *g);
 
-int or_step(const or_grid *g, const or_source *src, long n,
+int or_step(const or_grid *g, const or_source *src, long n, int first,
             const double *u_in, double *u_out);
 int or_run(const or_grid *g, const or_source *src, long n0, long nsteps,
            double *u, const double *weights, double *h_out);
-int or_loc_half(const or_grid *g, const double *u_in, double *u_out);
+int or_imp(const or_grid *g, double h, const double *u_in, double *u_out);
 int or_lw(const or_grid *g, const or_source *src, long n, int full,
           const double *u_in, double *u_out);
 

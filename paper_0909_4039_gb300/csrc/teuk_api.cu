@@ -36,6 +36,7 @@ struct teuk_ctx {
     Layout L;
     size_t level_bytes;     // one time level
     int cur;                // level holding the current state
+    int shifted;            // split scheme: the level holds s_n (u_n = C_{dt/2} s_n)
     int64_t step;           // host mirror of the device step counter
     int64_t rec_lo;         // oldest recorded waveform step
     // source
@@ -67,6 +68,7 @@ Layout make_layout(const teuk_grid_desc &d)
     L.th64 = off; off = align256(off + ts);
     L.thT = f32 ? off : L.th64; if (f32) off = align256(off + ts / 2);
     L.piv = off; off = align256(off + c2 * N * Nr);
+    L.pivh = off; off = align256(off + c2 * N * Nr);
     L.patch = off; off = align256(off + c2 * 2 * N * patch_rows);
     L.w = off; off = align256(off + sizeof(double) * N);
     L.ctl = off; off = align256(off + sizeof(Ctl));
@@ -180,9 +182,9 @@ void choose_tiles(teuk_ctx *c)
 {
     int N = (int)c->d.Ntheta;
     bool f32 = c->d.precision == TEUK_FP32;
-    const size_t budget = 100 * 1024;
-    int threads = 128;
-    int R = threads;
+    const size_t budget = 110 * 1024;          // two CTAs per SM
+    int threads = 256;
+    int R = 256;
     while (R > 4) {
         size_t sm = f32 ? split_smem_bytes<float>(R - 2, N) : split_smem_bytes<double>(R - 2, N);
         if (sm <= budget) break;
@@ -204,23 +206,29 @@ StepParams<T> make_params(const teuk_ctx *c, int in_level)
     p.Nth = (int)d.Ntheta;
     p.tile_rows = c->tile_rows;
     p.pitch = (int)d.Ntheta + 1;
+    p.group = implicit_group((int)d.Ntheta);
+    p.first = c->shifted ? 0 : 1;
+    p.imp_only = 0;
     p.i_ext = c->i_ext;
     p.wave_cap = (int)c->cap;
     p.patch_p0 = c->patch_p0;
     p.patch_np = c->patch_np;
-    double h = 0.5 * c->dt, gh = kGamma * h;
     p.dt = (T)c->dt;
     p.half_dt = (T)(0.5 * c->dt);
     p.drs_inv = (T)(1.0 / c->drs);
-    p.gh = (T)gh;
-    p.gh2 = (T)(gh * gh);
-    p.h1g = (T)((1.0 - kGamma) * h);
-    p.h12g = (T)((1.0 - 2.0 * kGamma) * h);
+    for (int k = 0; k < 2; ++k) {
+        double h = k ? 0.5 * c->dt : c->dt, gh = kGamma * h;
+        ImpConst<T> &K = k ? p.half : p.full;
+        K.gh = (T)gh;
+        K.gh2 = (T)(gh * gh);
+        K.h1g = (T)((1.0 - kGamma) * h);
+        K.h12g = (T)((1.0 - 2.0 * kGamma) * h);
+        K.piv = (const c2 *)(c->coef + (k ? c->L.pivh : c->L.piv));
+    }
     p.dt64 = c->dt;
     p.mOmega = c->mOmega;
     p.rtab = (const T *)(c->coef + c->L.rtabT);
     p.thtab = (const T *)(c->coef + c->L.thT);
-    p.piv = (const c2 *)(c->coef + c->L.piv);
     p.patch = (const c2 *)(c->coef + c->L.patch);
     p.w = (const double *)(c->coef + c->L.w);
     p.uin = (const c2 *)(c->state + (size_t)in_level * c->level_bytes);
@@ -241,6 +249,20 @@ cudaError_t launch_one(teuk_ctx *c, int in_level, cudaStream_t st)
     StepParams<double> p = make_params<double>(c, in_level);
     return c->d.scheme == TEUK_SCHEME_SPLIT ? launch_split_step<double>(p, c->threads, c->smem, st)
                                             : launch_literal_step<double>(p, st);
+}
+
+// Physical state u_n = C_{dt/2} s_n of a shifted split-scheme state, written
+// to the other level (which the next step overwrites anyway).
+cudaError_t physical_to_other(teuk_ctx *c, cudaStream_t st)
+{
+    if (c->d.precision == TEUK_FP32) {
+        StepParams<float> p = make_params<float>(c, c->cur);
+        p.imp_only = 1;
+        return launch_split_step<float>(p, c->threads, c->smem, st);
+    }
+    StepParams<double> p = make_params<double>(c, c->cur);
+    p.imp_only = 1;
+    return launch_split_step<double>(p, c->threads, c->smem, st);
 }
 
 cudaError_t extract_current(teuk_ctx *c, cudaStream_t st)
@@ -453,6 +475,7 @@ int teuk_set_state(teuk_ctx *c, const void *src, int64_t step, void *stream)
     CK(launch_set_ctl(c->coef, c->L, step, 0, st), "control block");
     c->step = step;
     c->rec_lo = step;
+    c->shifted = 0;
     CK(extract_current(c, st), "extract");
     if (!dev) CK(cudaStreamSynchronize(st), "state sync");
     return TEUK_OK;
@@ -465,6 +488,10 @@ int teuk_get_state(teuk_ctx *c, void *dst, int64_t *step, void *stream)
     cudaStream_t st = (cudaStream_t)stream;
     size_t n = 2 * (size_t)c->d.Nr * (size_t)c->d.Ntheta;
     const char *src = c->state + (size_t)c->cur * c->level_bytes;
+    if (c->d.scheme == TEUK_SCHEME_SPLIT && c->shifted) {
+        CK(physical_to_other(c, st), "physical state");
+        src = c->state + (size_t)(1 - c->cur) * c->level_bytes;
+    }
     cudaPointerAttributes at;
     bool dev = cudaPointerGetAttributes(&at, dst) == cudaSuccess &&
                (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged);
@@ -492,7 +519,14 @@ int teuk_step(teuk_ctx *c, int64_t nsteps, void *stream)
     if (nsteps < 0) return set_err(c, TEUK_E_INVAL, "nsteps must be >= 0%s");
     cudaStream_t st = (cudaStream_t)stream;
     int64_t left = nsteps;
-    bool use_graph = st != nullptr && c->d.scheme == TEUK_SCHEME_SPLIT && nsteps >= 2 * kGraphChunk;
+    if (left > 0 && c->d.scheme == TEUK_SCHEME_SPLIT && !c->shifted) {
+        // first step from a physical state: s_{n+1} = LW C_{dt/2} u_n
+        CK(launch_one(c, c->cur, st), "first step launch");
+        c->cur ^= 1;
+        c->shifted = 1;
+        left -= 1;
+    }
+    bool use_graph = st != nullptr && c->d.scheme == TEUK_SCHEME_SPLIT && left >= 2 * kGraphChunk;
     if (use_graph) {
         int g = c->cur;
         if (c->graph[g] && c->graph_stream[g] != st) {

@@ -101,7 +101,7 @@ struct CoefArgs {
     int s, m;
     int Nr, Nth;
     double rs_min, drs, dth;
-    double gh, gh2;            // gamma h and its square, h = dt/2
+    double gh, gh2;            // gamma h and its square for the pivot table being built
     int prec;                  // TEUK_FP64 / TEUK_FP32
     double *rtab64;
     void *rtabT;
@@ -170,7 +170,8 @@ __global__ void k_theta(CoefArgs A)
     if (j < N) A.w[j] = Yw / red[0];
 }
 
-// Complex Thomas pivots of the implicit stage matrix of every node row i:
+// Complex Thomas pivots of the implicit stage matrix (step h, gh = gamma h)
+// of every node row i:
 //   diag_j = 1 + gh c_t + gh^2 (c0rad + q A0_j),  sub_j = gh^2 q AM_j,
 //   sup_j = gh^2 q AP_j;  d_0 = diag_0, d_j = diag_j - sub_j sup_{j-1}/d_{j-1};
 // stored as e_j = 1/d_j at [j][i].
@@ -270,20 +271,25 @@ cudaError_t launch_coef_tables(const teuk_grid_desc &d, double drs, double dt, v
     A.rs_min = d.rstar_min;
     A.drs = drs;
     A.dth = kPi / (double)d.Ntheta;
-    A.gh = kGamma * 0.5 * dt;
-    A.gh2 = A.gh * A.gh;
     A.prec = d.precision;
     char *base = (char *)coef;
     A.rtab64 = (double *)(base + L.rtab64);
     A.rtabT = base + L.rtabT;
     A.th64 = (double *)(base + L.th64);
     A.thT = base + L.thT;
-    A.piv = base + L.piv;
     A.w = (double *)(base + L.w);
     int np = 2 * A.Nr - 1;
     k_rtab<<<(np + 127) / 128, 128, 0, st>>>(A);
     int tb = ((A.Nth + 31) / 32) * 32;
     k_theta<<<1, tb, 0, st>>>(A);
+    // pivots for implicit steps of length dt and dt/2
+    A.gh = kGamma * dt;
+    A.gh2 = A.gh * A.gh;
+    A.piv = base + L.piv;
+    k_pivots<<<(A.Nr + 127) / 128, 128, 0, st>>>(A);
+    A.gh = kGamma * 0.5 * dt;
+    A.gh2 = A.gh * A.gh;
+    A.piv = base + L.pivh;
     k_pivots<<<(A.Nr + 127) / 128, 128, 0, st>>>(A);
     return cudaGetLastError();
 }

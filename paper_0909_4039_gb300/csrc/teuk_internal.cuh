@@ -7,9 +7,10 @@
 //   coef   : r tables   [2Nr-1][NRF] FP64 and [2Nr-1][NRF] T
 //                        (position p = 2i: node i; p = 2i+1: r*_{i+1/2})
 //            theta tables [NTF][Ntheta] FP64 and T
-//            pivots     [Ntheta][Nr] complex T (theta-major, so the one
-//                        thread that solves row i reads consecutive i
-//                        across a warp)
+//            pivots     two tables [Ntheta][Nr] complex T, for implicit
+//                        steps of length dt and dt/2 (theta-major, so the
+//                        threads that solve consecutive rows read
+//                        consecutive addresses)
 //            patch      [patch_rows][2][Ntheta] complex T (node, half node)
 //            weights    [Ntheta] FP64
 //            ctl        step counter, CTA ticket, error flags
@@ -58,22 +59,31 @@ template <typename T> struct V2;
 template <> struct V2<float> { typedef float2 t; };
 template <> struct V2<double> { typedef double2 t; };
 
+// Constants of one implicit SDIRK2 step of length h.
+template <typename T> struct ImpConst {
+    typedef typename V2<T>::t c2;
+    T gh, gh2, h1g, h12g;    // gamma h, (gamma h)^2, (1-gamma) h, (1-2 gamma) h
+    const c2 *piv;           // Thomas pivots of the stage matrix, [Nth][Nr]
+};
+
 // Everything a step kernel needs, passed by value.
 template <typename T> struct StepParams {
     typedef typename V2<T>::t c2;
     int Nr, Nth;
     int tile_rows;           // output rows per CTA (split kernel)
     int pitch;               // shared-memory row pitch in complex elements
+    int group;               // threads per theta row in the implicit phase
+    int first;               // 1: implicit step dt/2 (input is a physical state)
+    int imp_only;            // 1: only C_{dt/2} on the tile rows (state output)
     int i_ext;               // extraction node
     int wave_cap;            // ring-buffer slots
     int patch_p0, patch_np;  // source patch rows [p0, p0+np); np = 0: no source
     T dt, half_dt, drs_inv;  // step, dt/2, 1/dr*
-    T gh, gh2, h1g, h12g;    // gamma h, (gamma h)^2, (1-gamma) h, (1-2 gamma) h; h = dt/2
+    ImpConst<T> full, half;  // implicit steps of length dt and dt/2
     double dt64;             // dt in FP64 (time and phase)
     double mOmega;           // m * Omega (FP64)
     const T *rtab;           // [2Nr-1][NRF]
     const T *thtab;          // [NTF][Nth]
-    const c2 *piv;           // [Nth][Nr]
     const c2 *patch;         // [np][2][Nth]
     const double *w;         // [Nth]
     const c2 *uin;           // [2][Nr][Nth]
@@ -89,7 +99,7 @@ constexpr double kPi = 3.14159265358979323846264338327950;
 
 // ---------------------------------------------------------------- host side
 struct Layout {
-    size_t rtab64, rtabT, th64, thT, piv, patch, w, ctl, staging, scratch, total;
+    size_t rtab64, rtabT, th64, thT, piv, pivh, patch, w, ctl, staging, scratch, total;
     size_t staging_elems;    // complex doubles that fit in the staging area
 };
 
@@ -113,6 +123,9 @@ cudaError_t launch_extract(const StepParams<T> &p, const typename V2<T>::t *u, l
                            cudaStream_t st);
 template <typename T>
 size_t split_smem_bytes(int tile_rows, int Nth);
+int implicit_group(int Nth);            // threads per theta row
+constexpr int kSeg = 8;                 // theta elements per thread (Ntheta <= 256)
+constexpr int kSegWide = 32;            // theta elements per thread (Ntheta <= 1024)
 cudaError_t launch_convert_to(int prec, const double2 *src, void *dst, size_t n, cudaStream_t st);
 cudaError_t launch_convert_from(int prec, const void *src, double2 *dst, size_t n, cudaStream_t st);
 

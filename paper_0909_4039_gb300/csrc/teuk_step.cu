@@ -88,114 +88,211 @@ __device__ __forceinline__ Loc<T> local_coef(T sg, const T *f, T C, T gh)
     return L;
 }
 
-// One implicit half step of length h = dt/2 on one r* row held in shared
-// memory (phi, pi, sig: element j at [j]); f: the row's r table; th: theta
-// tables; piv: pivots of this row (element j at piv[j * Nr]).
-// SDIRK2: stage (I - gamma h J) U = (rPhi, rPi) is solved as
+template <typename C> __device__ __forceinline__ C shfl_up_c(C v, int d, int w)
+{
+    v.x = __shfl_up_sync(0xffffffffu, v.x, d, w);
+    v.y = __shfl_up_sync(0xffffffffu, v.y, d, w);
+    return v;
+}
+template <typename C> __device__ __forceinline__ C shfl_down_c(C v, int d, int w)
+{
+    v.x = __shfl_down_sync(0xffffffffu, v.x, d, w);
+    v.y = __shfl_down_sync(0xffffffffu, v.y, d, w);
+    return v;
+}
+
+// One implicit SDIRK2 step of length h (constants K) on one r* row held in
+// shared memory (phi, pi, sig: element j at [j]; f: the row's r table; th:
+// theta tables), by a group of G consecutive lanes.  Lane g holds the
+// contiguous theta segment [g S, g S + S) in registers.
+//
+// Stage (I - gamma h J) U = (rPhi, rPi), J u = (Pi, -(B + c0rad) Phi - c_t Pi),
+// B = q A_th, is solved as
 //   [(1 + gh c_t) + gh^2 (B + c0rad)] U_Phi = (1 + gh c_t) rPhi + gh rPi,
-//   U_Pi = (rPi - gh (B + c0rad) U_Phi)/(1 + gh c_t),   B = q A_th,
-// stage 1 with r = u, stage 2 with r = u + (1 - gamma) h J U1.  The stage-2
-// right side uses u_Phi = U1_Phi - gh U1_Pi (stage-1 relation), so the
-// original row need not be kept.
-template <typename T>
-__device__ void implicit_half_row(const StepParams<T> &p, typename V2<T>::t *phi,
-                                  typename V2<T>::t *pi, const T *sig, const T *f,
-                                  const T *th, const typename V2<T>::t *piv)
+//   U_Pi = (rPi - gh (B + c0rad) U_Phi) / (1 + gh c_t);
+// stage 1 with r = u, stage 2 with r = u + (1 - gamma) h J U1, u^new = U2.
+// The tridiagonal solve uses the FP64-generated LU pivots e_j = 1/d_j:
+//   forward   z_j = r_j - m_j z_{j-1},  m_j = sub_j e_{j-1}
+//   backward  x_j = e_j z_j - f_j x_{j+1},  f_j = e_j sup_j.
+// Both are first-order affine recurrences; each lane composes the affine
+// map of its segment, the maps are scanned across the G lanes with
+// shuffles (log2 G levels), and each lane then runs its segment from the
+// incoming value.  Rows with active == false (boundary or outside the grid)
+// take part in the shuffles with neutral data and write zeros.
+template <typename T, int S>
+__device__ void implicit_row_group(const ImpConst<T> &K, typename V2<T>::t *phi, typename V2<T>::t *pi,
+                                   const T *sig, const T *f, const T *th, int N, int Nr, int gi,
+                                   bool active, bool in_tile, int g, int G)
 {
     typedef typename V2<T>::t c2;
-    const int N = p.Nth;
-    const size_t ps = (size_t)p.Nr;
-    const T gh = p.gh, gh2 = p.gh2, h1g = p.h1g, h12g = p.h12g;
-    const T *S2 = th + TF_S2 * N;
-    (void)S2;
+    const c2 zero = cmk<c2>(T(0), T(0));
+    const c2 one = cmk<c2>(T(1), T(0));
+    const int j0 = g * S;
+    int len = N - j0;
+    len = len < 0 ? 0 : (len > S ? S : len);
+    if (!active) len = 0;
+    const T gh = K.gh, gh2 = K.gh2;
     const T *Cc = th + TF_C * N;
     const T *Am = th + TF_AM * N;
     const T *A0 = th + TF_A0 * N;
     const T *Ap = th + TF_AP * N;
-    const c2 zero = cmk<c2>(T(0), T(0));
 
-    // ---- stage 1, forward elimination: z_j = r_j - (sub_j e_{j-1}) z_{j-1}
-    {
-        c2 zprev = zero, eprev = zero;
-        for (int j = 0; j < N; ++j) {
-            Loc<T> L = local_coef<T>(sig[j], f, Cc[j], gh);
-            c2 r = caxpy(gh, pi[j], cmul(L.a1, phi[j]));
-            if (j > 0) {
-                T sub = gh2 * L.q * Am[j];
-                r = csub(r, cmul(cscale<c2>(sub, eprev), zprev));
-            }
-            phi[j] = r;
-            zprev = r;
-            eprev = piv[(size_t)j * ps];
+    c2 e[S], y[S], w[S];
+    T sg[S];
+#pragma unroll
+    for (int k = 0; k < S; ++k) {
+        if (k < len) {
+            int j = j0 + k;
+            sg[k] = sig[j];
+            w[k] = phi[j];
+            y[k] = pi[j];
+            e[k] = K.piv[(size_t)j * Nr + gi];
+        } else {
+            sg[k] = T(0);
+            w[k] = zero;
+            y[k] = zero;
+            e[k] = one;
         }
     }
-    // ---- stage 1, back substitution; element jj = j + 1 is finished one
-    // iteration late, once its three neighbours are known
-    {
-        c2 x2 = zero, x1 = zero, x0;   // x_{j+2}, x_{j+1}, x_j
-        for (int j = N - 1; j >= -1; --j) {
-            if (j >= 0) {
-                Loc<T> L = local_coef<T>(sig[j], f, Cc[j], gh);
-                c2 t = phi[j];
-                if (j < N - 1) t = csub(t, cscale<c2>(gh2 * L.q * Ap[j], x1));
-                x0 = cmul(t, piv[(size_t)j * ps]);
-            } else {
-                x0 = zero;
+    const c2 e_prev = shfl_up_c(e[S - 1], 1, G);   // e_{j0-1} (lane g-1 holds a full segment)
+
+    // tridiagonal solve of w in place (stage right side -> U_Phi)
+    auto solve = [&]() {
+        // forward: compose z_out = A z_in + B over the segment
+        c2 A = one, B = zero;
+#pragma unroll
+        for (int k = 0; k < S; ++k) {
+            if (k < len) {
+                int j = j0 + k;
+                c2 m = cscale<c2>(gh2 * f[RF_DELTA] * sg[k] * Am[j], k ? e[k - 1] : e_prev);
+                B = csub(w[k], cmul(m, B));
+                A = cmul(cmk<c2>(-m.x, -m.y), A);
             }
-            int jj = j + 1;
-            if (jj <= N - 1) {
-                Loc<T> L = local_coef<T>(sig[jj], f, Cc[jj], gh);
-                // BF = (B + c0rad) U1_Phi at jj
-                c2 bf = cscale<c2>(L.q, cadd(cadd(cscale<c2>(Am[jj], x0), cscale<c2>(A0[jj], x1)),
-                                             cscale<c2>(Ap[jj], x2)));
-                bf = cadd(bf, cmul(L.c0, x1));
-                c2 P1 = cmul(csub(pi[jj], cscale<c2>(gh, bf)), cinv(L.a1));
-                c2 rphi = caxpy(h12g, P1, x1);
-                c2 rpi = csub(pi[jj], cscale<c2>(h1g, cadd(bf, cmul(L.ct, P1))));
-                phi[jj] = caxpy(gh, rpi, cmul(L.a1, rphi));   // stage-2 right side
-                pi[jj] = rpi;
+        }
+        for (int d = 1; d < G; d <<= 1) {
+            c2 Ao = shfl_up_c(A, d, G), Bo = shfl_up_c(B, d, G);
+            if (g >= d) {
+                B = cadd(cmul(A, Bo), B);
+                A = cmul(A, Ao);
             }
-            x2 = x1;
-            x1 = x0;
+        }
+        c2 z = shfl_up_c(B, 1, G);
+        if (g == 0) z = zero;
+#pragma unroll
+        for (int k = 0; k < S; ++k) {
+            if (k < len) {
+                int j = j0 + k;
+                c2 m = cscale<c2>(gh2 * f[RF_DELTA] * sg[k] * Am[j], k ? e[k - 1] : e_prev);
+                z = csub(w[k], cmul(m, z));
+                w[k] = z;
+            }
+        }
+        // backward: compose x_start = A x_in + B over the segment, from its end
+        A = one;
+        B = zero;
+#pragma unroll
+        for (int k = S - 1; k >= 0; --k) {
+            if (k < len) {
+                int j = j0 + k;
+                c2 fk = cscale<c2>(gh2 * f[RF_DELTA] * sg[k] * Ap[j], e[k]);
+                c2 bk = cmul(e[k], w[k]);
+                B = csub(bk, cmul(fk, B));
+                A = cmul(cmk<c2>(-fk.x, -fk.y), A);
+            }
+        }
+        for (int d = 1; d < G; d <<= 1) {
+            c2 Ao = shfl_down_c(A, d, G), Bo = shfl_down_c(B, d, G);
+            if (g + d < G) {
+                B = cadd(cmul(A, Bo), B);
+                A = cmul(A, Ao);
+            }
+        }
+        c2 x = shfl_down_c(B, 1, G);
+        if (g == G - 1) x = zero;
+#pragma unroll
+        for (int k = S - 1; k >= 0; --k) {
+            if (k < len) {
+                int j = j0 + k;
+                c2 fk = cscale<c2>(gh2 * f[RF_DELTA] * sg[k] * Ap[j], e[k]);
+                x = csub(cmul(e[k], w[k]), cmul(fk, x));
+                w[k] = x;
+            }
+        }
+    };
+    // (B + c0rad) U_Phi at segment element k, neighbours from the adjacent lanes
+    auto apply_B = [&](int k, c2 xl, c2 xr, const Loc<T> &L) {
+        int j = j0 + k;
+        c2 xm = k ? w[k - 1] : xl;
+        c2 xp = (k + 1 < S) ? w[k + 1] : xr;
+        if (k + 1 >= len) xp = xr;
+        c2 v = cadd(cadd(cscale<c2>(Am[j], xm), cscale<c2>(A0[j], w[k])), cscale<c2>(Ap[j], xp));
+        return cadd(cscale<c2>(L.q, v), cmul(L.c0, w[k]));
+    };
+
+    // ---- stage 1: r = (1 + gh c_t) Phi + gh Pi
+#pragma unroll
+    for (int k = 0; k < S; ++k) {
+        if (k < len) {
+            Loc<T> L = local_coef<T>(sg[k], f, Cc[j0 + k], gh);
+            w[k] = caxpy(gh, y[k], cmul(L.a1, w[k]));
         }
     }
-    // ---- stage 2, forward elimination
+    solve();
     {
-        c2 zprev = zero, eprev = zero;
-        for (int j = 0; j < N; ++j) {
-            c2 r = phi[j];
-            if (j > 0) {
-                T q = f[RF_DELTA] * sig[j];
-                r = csub(r, cmul(cscale<c2>(gh2 * q * Am[j], eprev), zprev));
+        c2 xl = shfl_up_c(w[S - 1], 1, G), xr = shfl_down_c(w[0], 1, G);
+        if (g == 0) xl = zero;
+        if (g == G - 1) xr = zero;
+        c2 bf[S];
+#pragma unroll
+        for (int k = 0; k < S; ++k) {
+            if (k < len) {
+                Loc<T> L = local_coef<T>(sg[k], f, Cc[j0 + k], gh);
+                bf[k] = apply_B(k, xl, xr, L);
             }
-            phi[j] = r;
-            zprev = r;
-            eprev = piv[(size_t)j * ps];
+        }
+#pragma unroll
+        for (int k = 0; k < S; ++k) {
+            if (k < len) {
+                Loc<T> L = local_coef<T>(sg[k], f, Cc[j0 + k], gh);
+                c2 P1 = cmul(csub(y[k], cscale<c2>(gh, bf[k])), cinv(L.a1));
+                c2 rphi = caxpy(K.h12g, P1, w[k]);                     // u_Phi + (1-gamma) h U1_Pi
+                c2 rpi = csub(y[k], cscale<c2>(K.h1g, cadd(bf[k], cmul(L.ct, P1))));
+                w[k] = caxpy(gh, rpi, cmul(L.a1, rphi));
+                y[k] = rpi;
+            }
         }
     }
-    // ---- stage 2, back substitution and the Pi row
+    // ---- stage 2
+    solve();
     {
-        c2 x2 = zero, x1 = zero, x0;
-        for (int j = N - 1; j >= -1; --j) {
-            if (j >= 0) {
-                T q = f[RF_DELTA] * sig[j];
-                c2 t = phi[j];
-                if (j < N - 1) t = csub(t, cscale<c2>(gh2 * q * Ap[j], x1));
-                x0 = cmul(t, piv[(size_t)j * ps]);
-            } else {
-                x0 = zero;
+        c2 xl = shfl_up_c(w[S - 1], 1, G), xr = shfl_down_c(w[0], 1, G);
+        if (g == 0) xl = zero;
+        if (g == G - 1) xr = zero;
+        c2 bf[S];
+#pragma unroll
+        for (int k = 0; k < S; ++k) {
+            if (k < len) {
+                Loc<T> L = local_coef<T>(sg[k], f, Cc[j0 + k], gh);
+                bf[k] = apply_B(k, xl, xr, L);
             }
-            int jj = j + 1;
-            if (jj <= N - 1) {
-                Loc<T> L = local_coef<T>(sig[jj], f, Cc[jj], gh);
-                c2 bf = cscale<c2>(L.q, cadd(cadd(cscale<c2>(Am[jj], x0), cscale<c2>(A0[jj], x1)),
-                                             cscale<c2>(Ap[jj], x2)));
-                bf = cadd(bf, cmul(L.c0, x1));
-                pi[jj] = cmul(csub(pi[jj], cscale<c2>(gh, bf)), cinv(L.a1));
-                phi[jj] = x1;
+        }
+#pragma unroll
+        for (int k = 0; k < S; ++k) {
+            if (k < len) {
+                Loc<T> L = local_coef<T>(sg[k], f, Cc[j0 + k], gh);
+                y[k] = cmul(csub(y[k], cscale<c2>(gh, bf[k])), cinv(L.a1));
             }
-            x2 = x1;
-            x1 = x0;
+        }
+    }
+    if (in_tile) {
+        int lenw = N - j0;
+        lenw = lenw < 0 ? 0 : (lenw > S ? S : lenw);
+#pragma unroll
+        for (int k = 0; k < S; ++k) {
+            if (k < lenw) {
+                phi[j0 + k] = active ? w[k] : zero;
+                pi[j0 + k] = active ? y[k] : zero;
+            }
         }
     }
 }
@@ -222,22 +319,27 @@ __device__ __forceinline__ typename V2<T>::t patch_val(const StepParams<T> &p, i
     return cmul(v, phase);
 }
 
-// Split-scheme Lax-Wendroff update of one theta column of the tile.
+// Split-scheme Lax-Wendroff update (Eqs. 13-14 with S = F + K Phi_{r*}) of
+// tile rows [ra, rb) in theta column j, in place.  (pf, pg) is the old value
+// of row ra-1 and (nf, ng) the old value of row rb: both may belong to other
+// threads' segments, so the caller reads them before a barrier.
 template <typename T>
-__device__ void lw_column(const StepParams<T> &p, typename V2<T>::t *sPhi, typename V2<T>::t *sPi,
-                          const T *sSig, const T *sRn, const T *sRh, const T *sTh, int j, int i0,
-                          typename V2<T>::t ph1, typename V2<T>::t ph2, bool src)
+__device__ void lw_segment(const StepParams<T> &p, typename V2<T>::t *sPhi, typename V2<T>::t *sPi,
+                           const T *sSig, const T *sRn, const T *sRh, const T *sTh, int j, int ra, int rb,
+                           typename V2<T>::t pf, typename V2<T>::t pg, typename V2<T>::t nf,
+                           typename V2<T>::t ng, int i0, typename V2<T>::t ph1, typename V2<T>::t ph2,
+                           bool src)
 {
     typedef typename V2<T>::t c2;
-    const int N = p.Nth, P = p.pitch, TR = p.tile_rows, Nr = p.Nr;
+    const int N = p.Nth, P = p.pitch, Nr = p.Nr;
     const T S2 = sTh[TF_S2 * N + j], C = sTh[TF_C * N + j];
     const T hdt = p.half_dt, dt = p.dt, ri = p.drs_inv;
     const c2 zero = cmk<c2>(T(0), T(0));
 
-    // midpoint u*_{k+1/2} between tile rows k and k+1 (Eq. 13, S = F + K Phi_{r*})
+    // u*_{k+1/2} between tile rows k and k+1 (Eq. 13)
     auto midpoint = [&](int k, c2 fa, c2 ga, c2 fb, c2 gb, c2 &mf, c2 &mg) {
-        int gh_ = i0 - 1 + k;   // global i of the lower node
-        if (gh_ < 0 || gh_ > Nr - 2) {
+        int gl = i0 - 1 + k;   // global index of the lower node
+        if (gl < 0 || gl > Nr - 2) {
             mf = zero;
             mg = zero;
             return;
@@ -251,25 +353,31 @@ __device__ void lw_column(const StepParams<T> &p, typename V2<T>::t *sPhi, typen
         c2 gbar = cscale<c2>(T(0.5), cadd(ga, gb));
         c2 df = cscale<c2>(ri, csub(fb, fa));
         c2 dg = cscale<c2>(ri, csub(gb, ga));
-        c2 S = cmul(K, df);
-        if (src) S = cadd(S, patch_val(p, gh_, 1, j, ph1));
+        c2 Sv = cmul(K, df);
+        if (src) Sv = cadd(Sv, patch_val(p, gl, 1, j, ph1));
         mf = csub(fbar, cscale<c2>(hdt * b, df));
-        mg = cadd(gbar, cscale<c2>(hdt, cadd(cscale<c2>(b, dg), S)));
+        mg = cadd(gbar, cscale<c2>(hdt, cadd(cscale<c2>(b, dg), Sv)));
     };
 
-    c2 fa = sPhi[j], ga = sPi[j];
-    c2 fb = sPhi[P + j], gb = sPi[P + j];
+    c2 fb = sPhi[ra * P + j], gb = sPi[ra * P + j];
     c2 mfp, mgp;
-    midpoint(0, fa, ga, fb, gb, mfp, mgp);
-    for (int lr = 1; lr <= TR; ++lr) {
+    midpoint(ra - 1, pf, pg, fb, gb, mfp, mgp);
+    for (int lr = ra; lr < rb; ++lr) {
         int gi = i0 + lr - 1;
         if (gi >= Nr) break;
-        c2 fc = sPhi[(lr + 1) * P + j], gc = sPi[(lr + 1) * P + j];
+        c2 fc, gc;
+        if (lr + 1 < rb) {
+            fc = sPhi[(lr + 1) * P + j];
+            gc = sPi[(lr + 1) * P + j];
+        } else {
+            fc = nf;
+            gc = ng;
+        }
         c2 mf, mg;
         midpoint(lr, fb, gb, fc, gc, mf, mg);
-        c2 nf = zero, ng = zero;
+        c2 nfv = zero, ngv = zero;
         if (gi >= 1 && gi <= Nr - 2) {
-            // Eq. 14 at node gi, S = F(t + dt/2) + K (u*_{i+1/2} - u*_{i-1/2})/dr*
+            // Eq. 14 at node gi
             const T *f = sRn + lr * NRF;
             T sg = sSig[lr * P + j];
             T b;
@@ -277,13 +385,13 @@ __device__ void lw_column(const StepParams<T> &p, typename V2<T>::t *sPhi, typen
             bK<T>(f, sg, S2, C, b, K);
             c2 df = cscale<c2>(ri, csub(mf, mfp));
             c2 dg = cscale<c2>(ri, csub(mg, mgp));
-            c2 S = cmul(K, df);
-            if (src) S = cadd(S, patch_val(p, gi, 0, j, ph2));
-            nf = csub(fb, cscale<c2>(dt * b, df));
-            ng = cadd(gb, cscale<c2>(dt, cadd(cscale<c2>(b, dg), S)));
+            c2 Sv = cmul(K, df);
+            if (src) Sv = cadd(Sv, patch_val(p, gi, 0, j, ph2));
+            nfv = csub(fb, cscale<c2>(dt * b, df));
+            ngv = cadd(gb, cscale<c2>(dt, cadd(cscale<c2>(b, dg), Sv)));
         }
-        sPhi[lr * P + j] = nf;
-        sPi[lr * P + j] = ng;
+        sPhi[lr * P + j] = nfv;
+        sPi[lr * P + j] = ngv;
         fb = fc;
         gb = gc;
         mfp = mf;
@@ -332,7 +440,13 @@ __device__ void extract_warp(const StepParams<T> &p, const typename V2<T>::t *ro
     for (int j = lane; j < N; j += 32) dst[1 + j] = make_double2((double)row[j].x, (double)row[j].y);
 }
 
-template <typename T>
+// Fused step of the split scheme (merged Strang composition): the tile's
+// input is s_n (or the physical state u_n when p.first), the output is
+//   s_{n+1} = LW_n C_h s_n,   h = dt (h = dt/2 when p.first),
+// and the physical sample u_{n+1} = C_{dt/2} s_{n+1} is taken on the
+// extraction row.  With p.imp_only the kernel only applies C_{dt/2} to the
+// tile rows (used to output the physical state).
+template <typename T, int S>
 __global__ void __launch_bounds__(256) k_split_step(const StepParams<T> p)
 {
     typedef typename V2<T>::t c2;
@@ -342,6 +456,7 @@ __global__ void __launch_bounds__(256) k_split_step(const StepParams<T> p)
     const int Nr = p.Nr, N = p.Nth, TR = p.tile_rows, R = TR + 2, P = p.pitch;
     const int tid = threadIdx.x, NT = blockDim.x;
     const int i0 = blockIdx.x * TR;
+    const int G = p.group;
 
     c2 *sPhi = (c2 *)smem_raw;
     c2 *sPi = sPhi + R * P;
@@ -350,7 +465,8 @@ __global__ void __launch_bounds__(256) k_split_step(const StepParams<T> p)
     T *sRh = sRn + R * NRF;
     T *sTh = sRh + (R - 1) * NRF;
 
-    const bool src = p.patch_np > 0 && i0 + TR >= p.patch_p0 && i0 - 1 <= p.patch_p0 + p.patch_np;
+    const bool src = !p.imp_only && p.patch_np > 0 && i0 + TR >= p.patch_p0 &&
+                     i0 - 1 <= p.patch_p0 + p.patch_np;
     if (tid == 0) {
         long long n = *((volatile long long *)&p.ctl->step);
         s_n = n;
@@ -360,18 +476,18 @@ __global__ void __launch_bounds__(256) k_split_step(const StepParams<T> p)
             sph[1] = phase_at(p.mOmega, t + 0.5 * p.dt64);
         }
     }
-    // ---- A: tile load (rows i0-1 .. i0+TR), tables
+    // ---- A: tile rows i0-1 .. i0+TR, r and theta tables, 1/Sigma^2 at the nodes
     const c2 zero = cmk<c2>(T(0), T(0));
     for (int idx = tid; idx < R * N; idx += NT) {
         int lr = idx / N, j = idx - lr * N;
         int gi = i0 - 1 + lr;
-        c2 f = zero, g = zero;
+        c2 fv = zero, gv = zero;
         if (gi >= 0 && gi < Nr) {
-            f = p.uin[(size_t)gi * N + j];
-            g = p.uin[((size_t)Nr + gi) * N + j];
+            fv = p.uin[(size_t)gi * N + j];
+            gv = p.uin[((size_t)Nr + gi) * N + j];
         }
-        sPhi[lr * P + j] = f;
-        sPi[lr * P + j] = g;
+        sPhi[lr * P + j] = fv;
+        sPi[lr * P + j] = gv;
     }
     for (int idx = tid; idx < R * NRF; idx += NT) {
         int lr = idx / NRF, q = idx - lr * NRF;
@@ -393,40 +509,55 @@ __global__ void __launch_bounds__(256) k_split_step(const StepParams<T> p)
         sSig[lr * P + j] = v;
     }
     __syncthreads();
-    // ---- B: implicit half step on all tile rows (boundary rows become zero)
-    if (tid < R) {
-        int gi = i0 - 1 + tid;
-        if (gi >= 1 && gi <= Nr - 2) {
-            implicit_half_row<T>(p, sPhi + tid * P, sPi + tid * P, sSig + tid * P, sRn + tid * NRF, sTh,
-                                 p.piv + gi);
-        } else {
-            for (int j = 0; j < N; ++j) {
-                sPhi[tid * P + j] = zero;
-                sPi[tid * P + j] = zero;
-            }
+    // ---- B: implicit step on the tile rows (all R rows; only rows 1..TR with imp_only)
+    {
+        const ImpConst<T> &K = (p.first || p.imp_only) ? p.half : p.full;
+        const int rows_per_pass = NT / G;
+        const int lo = p.imp_only ? 1 : 0, hi = p.imp_only ? TR + 1 : R;
+        const int g = tid % G;
+        for (int base = lo; base < hi; base += rows_per_pass) {
+            int lr = base + tid / G;
+            bool in_tile = lr < hi;
+            int gi = i0 - 1 + lr;
+            bool active = in_tile && gi >= 1 && gi <= Nr - 2;
+            int lrc = in_tile ? lr : lo;
+            implicit_row_group<T, S>(K, sPhi + lrc * P, sPi + lrc * P, sSig + lrc * P, sRn + lrc * NRF, sTh, N,
+                                     Nr, active ? gi : 1, active, in_tile, g, G);
         }
     }
     __syncthreads();
-    // ---- C: Lax-Wendroff, one thread per theta column
-    {
+    if (!p.imp_only) {
+        // ---- C: Lax-Wendroff on the output rows; NSEG row segments per column
         c2 ph1 = zero, ph2 = zero;
         if (src) {
             ph1 = from_d2<T>(sph[0]);
             ph2 = from_d2<T>(sph[1]);
         }
-        for (int j = tid; j < N; j += NT) lw_column<T>(p, sPhi, sPi, sSig, sRn, sRh, sTh, j, i0, ph1, ph2, src);
+        if (N <= NT) {
+            const int nseg = NT / N;
+            const int sl = (TR + nseg - 1) / nseg;
+            const int j = tid % N, sgm = tid / N;
+            int ra = 1 + sgm * sl, rb = 1 + (sgm + 1) * sl;
+            if (rb > TR + 1) rb = TR + 1;
+            bool work = sgm < nseg && ra < rb;
+            c2 pf = zero, pg = zero, nf = zero, ng = zero;
+            if (work) {
+                pf = sPhi[(ra - 1) * P + j];
+                pg = sPi[(ra - 1) * P + j];
+                nf = sPhi[rb * P + j];
+                ng = sPi[rb * P + j];
+            }
+            __syncthreads();
+            if (work) lw_segment<T>(p, sPhi, sPi, sSig, sRn, sRh, sTh, j, ra, rb, pf, pg, nf, ng, i0, ph1, ph2, src);
+        } else {
+            for (int j = tid; j < N; j += NT) {
+                c2 pf = sPhi[j], pg = sPi[j], nf = sPhi[(TR + 1) * P + j], ng = sPi[(TR + 1) * P + j];
+                lw_segment<T>(p, sPhi, sPi, sSig, sRn, sRh, sTh, j, 1, TR + 1, pf, pg, nf, ng, i0, ph1, ph2, src);
+            }
+        }
+        __syncthreads();
     }
-    __syncthreads();
-    // ---- D: implicit half step on the output rows
-    if (tid < TR) {
-        int lr = tid + 1;
-        int gi = i0 + tid;
-        if (gi >= 1 && gi <= Nr - 2)
-            implicit_half_row<T>(p, sPhi + lr * P, sPi + lr * P, sSig + lr * P, sRn + lr * NRF, sTh,
-                                 p.piv + gi);
-    }
-    __syncthreads();
-    // ---- E: store, extraction, step counter
+    // ---- D: store the output rows
     for (int idx = tid; idx < TR * N; idx += NT) {
         int k = idx / N, j = idx - k * N;
         int gi = i0 + k;
@@ -434,8 +565,21 @@ __global__ void __launch_bounds__(256) k_split_step(const StepParams<T> p)
         p.uout[(size_t)gi * N + j] = sPhi[(k + 1) * P + j];
         p.uout[((size_t)Nr + gi) * N + j] = sPi[(k + 1) * P + j];
     }
-    if (p.i_ext >= i0 && p.i_ext < i0 + TR && tid < 32)
-        extract_warp<T>(p, sPhi + (p.i_ext - i0 + 1) * P, s_n + 1);
+    if (p.imp_only) return;
+    // ---- E: physical sample u_{n+1} = C_{dt/2} s_{n+1} on the extraction row
+    const bool ext = p.i_ext >= i0 && p.i_ext < i0 + TR && p.i_ext < Nr;
+    if (ext) {
+        __syncthreads();
+        int lr = p.i_ext - i0 + 1;
+        if (tid < 32) {
+            bool mine = tid < G;
+            bool active = mine && p.i_ext >= 1 && p.i_ext <= Nr - 2;
+            implicit_row_group<T, S>(p.half, sPhi + lr * P, sPi + lr * P, sSig + lr * P, sRn + lr * NRF, sTh, N, Nr,
+                                     active ? p.i_ext : 1, active, mine, tid % G, G);
+            __syncwarp();
+            extract_warp<T>(p, sPhi + lr * P, s_n + 1);
+        }
+    }
     __syncthreads();
     if (tid == 0) {
         __threadfence();
@@ -464,7 +608,7 @@ __device__ __forceinline__ typename V2<T>::t literal_SPi(const StepParams<T> &p,
     T sg = rcp_(fma(-f[RF_AD], S2, f[RF_R2]));
     c2 K;
     bK<T>(f, sg, S2, C, b, K);
-    Loc<T> L = local_coef<T>(sg, f, C, p.gh);
+    Loc<T> L = local_coef<T>(sg, f, C, T(0));
     c2 aphi = cadd(cadd(cscale<c2>(th[TF_AM * N + j], phm), cscale<c2>(th[TF_A0 * N + j], ph0)),
                    cscale<c2>(th[TF_AP * N + j], php));
     c2 S = cmul(K, dphi);
@@ -569,19 +713,30 @@ size_t split_smem_bytes(int tile_rows, int Nth)
            (size_t)NTF * Nth * sizeof(T);
 }
 
+int implicit_group(int Nth)
+{
+    int seg = Nth <= 256 ? kSeg : kSegWide;
+    int need = (Nth + seg - 1) / seg;
+    int G = 1;
+    while (G < need) G <<= 1;
+    return G;
+}
+
 template <typename T>
 cudaError_t launch_split_step(const StepParams<T> &p, int threads, size_t smem, cudaStream_t st)
 {
     // opt in to the dynamic shared memory this launch needs (once per size)
-    static size_t configured[2] = {0, 0};
+    static size_t configured[2][2] = {{0, 0}, {0, 0}};
+    const bool wide = p.Nth > 256;
     int key = sizeof(T) == 4 ? 0 : 1;
-    if (smem > configured[key]) {
-        cudaError_t e = cudaFuncSetAttribute(k_split_step<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    auto fn = wide ? k_split_step<T, kSegWide> : k_split_step<T, kSeg>;
+    if (smem > configured[key][wide]) {
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        configured[key] = smem;
+        configured[key][wide] = smem;
     }
     int grid = (p.Nr + p.tile_rows - 1) / p.tile_rows;
-    k_split_step<T><<<grid, threads, smem, st>>>(p);
+    fn<<<grid, threads, smem, st>>>(p);
     return cudaGetLastError();
 }
 

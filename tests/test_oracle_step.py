@@ -118,11 +118,11 @@ def lw_numpy(p, u, n, full):
     return _from4(new)
 
 
-def implicit_half_numpy(p, u):
-    """SDIRK2 (gamma = 1 - 1/sqrt 2) on u_t = -(L + A) u, per r* row, by dense solves."""
+def implicit_numpy(p, u, h):
+    """SDIRK2 (gamma = 1 - 1/sqrt 2) step of length h on u_t = -(L + A) u,
+    per r* row, by dense solves of the stage equations."""
     Nr, N = p.Nr, p.Ntheta
     drs = (p.rs_max - p.rs_min) / (Nr - 1)
-    h = 0.5 * p.dt
     v = _to4(u)
     out = np.zeros_like(v)
     I = np.eye(4 * N)
@@ -158,18 +158,30 @@ def test_literal_step_bruteforce(a, m, N):
 def test_split_parts_bruteforce(a, m, N):
     p = _prob(N=N, a=a, m=m, amp=0.5 + 0.5j, scheme=O.SCHEME_SPLIT)
     u = inputs.random_state(p.Nr, N, seed=5)
-    # implicit half step
-    ref_h = implicit_half_numpy(p, u)
-    got_h = O.loc_half(p, u)
-    assert np.abs(got_h - ref_h).max() <= 1e-12 * np.abs(ref_h).max()
+    # implicit steps of length dt/2 and dt
+    for h in (0.5 * p.dt, p.dt):
+        ref_h = implicit_numpy(p, u, h)
+        got_h = O.imp(p, u, h)
+        assert np.abs(got_h - ref_h).max() <= 1e-12 * np.abs(ref_h).max()
     # derivative-only LW
     ref_lw = lw_numpy(p, u, 7, full=False)
     got_lw = O.lw(p, u, 7, full=False)
     assert np.abs(got_lw - ref_lw).max() <= 1e-12 * np.abs(ref_lw).max()
-    # the full split step is their Strang composition
-    ref = implicit_half_numpy(p, lw_numpy(p, implicit_half_numpy(p, u), 7, full=False))
-    got = O.step(p, u, 7)
-    assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
+    # split steps: first s = LW C_{dt/2} u, then s' = LW C_dt s
+    s1 = lw_numpy(p, implicit_numpy(p, u, 0.5 * p.dt), 7, full=False)
+    got1 = O.step(p, u, 7, first=True)
+    assert np.abs(got1 - s1).max() <= 1e-12 * np.abs(s1).max()
+    s2 = lw_numpy(p, implicit_numpy(p, s1, p.dt), 8, full=False)
+    got2 = O.step(p, s1, 8, first=False)
+    assert np.abs(got2 - s2).max() <= 1e-12 * np.abs(s2).max()
+    # a two-step run outputs u_2 = C_{dt/2} s_2 and samples u_1 = C_{dt/2} s_1
+    w = O.default_weights(p)
+    ie = O.extract_index(p)
+    u2, h = O.run(p, u, 2, n0=7)
+    ref_u2 = implicit_numpy(p, s2, 0.5 * p.dt)
+    assert np.abs(u2 - ref_u2).max() <= 1e-12 * np.abs(ref_u2).max()
+    ref_u1 = implicit_numpy(p, s1, 0.5 * p.dt)
+    assert abs(h[1] - np.dot(w, ref_u1[0, ie])) <= 1e-12 * max(abs(h[1]), 1e-300) + 1e-300
 
 
 def test_sdirk_half_step_is_second_order():
@@ -181,7 +193,7 @@ def test_sdirk_half_step_is_second_order():
         u = inputs.gaussian_pulse(4, 6, p.rs_min, p.rs_max, 3.0, 100.0,
                                   np.cos(((np.arange(6) + 0.5) * np.pi / 6) / 2) ** 4)
         u[1] = 0.3 * u[0]
-        got = O.loc_half(p, u)
+        got = O.imp(p, u, 0.5 * p.dt)
         # exact flow for row 1 from the same dense J
         Nr, N = p.Nr, p.Ntheta
         drs = (p.rs_max - p.rs_min) / (Nr - 1)
