@@ -158,6 +158,25 @@ int teuk_step(teuk_ctx *ctx, int64_t nsteps, void *stream);
 int teuk_extract_waveform(teuk_ctx *ctx, int64_t first_step, int64_t count,
                           double *h_out, double *row_out, void *stream);
 
+/* Launch configuration of the split-scheme step kernel: r* rows per CTA
+ * tile, threads per CTA, dynamic shared memory per CTA, and G, the threads
+ * that share one theta row in the implicit solve.  Any pointer may be NULL. */
+int teuk_tiling(const teuk_ctx *ctx, int *tile_rows, int *threads, size_t *smem_bytes, int *group);
+
+/* Measured tile autotuner.  Ranks the tile heights that fit on the device
+ * by a wave-quantisation cost model, times the best six for trial_steps
+ * steps each on this grid (CUDA events on `stream`), and keeps the fastest.
+ * The trials overwrite the state: afterwards the field is zero at step 0
+ * and the waveform ring buffer is empty (the source and weights are kept).
+ * Call it right after teuk_init_grid / teuk_set_source.  Synchronous.
+ * *tile_rows_out (may be NULL) receives the chosen tile height. */
+int teuk_autotune(teuk_ctx *ctx, int trial_steps, void *stream, int *tile_rows_out);
+
+/* Set the tile height (r* output rows per CTA) of the split-scheme kernel
+ * by hand; TEUK_E_INVAL if such a tile does not fit in shared memory.  The
+ * result of a step does not depend on the tile height. */
+int teuk_set_tiling(teuk_ctx *ctx, int tile_rows);
+
 /* Current step number (host mirror of the device counter). */
 int64_t teuk_current_step(const teuk_ctx *ctx);
 

@@ -178,22 +178,65 @@ double host_atheta_bound(const teuk_grid_desc &d)
     return lam;
 }
 
-void choose_tiles(teuk_ctx *c)
+// Tile height of the split kernel.  A tile of R = TR + 2 rows costs about
+// 0.6 Rpad + 0.4 R + 4 row-times, where Rpad rounds R up to whole passes of
+// the implicit phase (256 threads / G rows per pass) and the 4 stands for
+// load latency and barriers; k CTAs share an SM, so one wave costs k times
+// that and the grid needs ceil(tiles / (k SMs)) waves.  Minimise the product
+// over R, with a 20 % penalty for k = 1 (no second CTA to overlap memory
+// with compute).
+struct TileCand {
+    double cost;
+    int R;
+    size_t smem;
+};
+
+// All tile heights that fit, with their model cost, best first.
+int tile_candidates(teuk_ctx *c, TileCand *out, int maxn)
 {
     int N = (int)c->d.Ntheta;
     bool f32 = c->d.precision == TEUK_FP32;
-    const size_t budget = 110 * 1024;          // two CTAs per SM
-    int threads = 256;
-    int R = 256;
-    while (R > 4) {
+    const int threads = 256;
+    int dev = 0, nsm = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaGetLastError();
+    const long long Nr = c->d.Nr;
+    int n = 0;
+    for (int R = 4; R <= 256 && n < maxn; ++R) {
         size_t sm = f32 ? split_smem_bytes<float>(R - 2, N) : split_smem_bytes<double>(R - 2, N);
-        if (sm <= budget) break;
-        R -= 2;
+        if (sm > 227 * 1024) break;
+        int k = f32 ? split_blocks_per_sm<float>(N, threads, sm) : split_blocks_per_sm<double>(N, threads, sm);
+        if (k < 1) break;
+        long long tiles = (Nr + (R - 2) - 1) / (R - 2);
+        long long waves = (tiles + (long long)k * nsm - 1) / ((long long)k * nsm);
+        int rpp = threads / implicit_group(N);
+        int rpad = ((R + rpp - 1) / rpp) * rpp;
+        double rows = 0.6 * rpad + 0.4 * R + 4.0;
+        out[n].cost = (double)waves * k * rows * (k == 1 ? 1.2 : 1.0);
+        out[n].R = R;
+        out[n].smem = sm;
+        ++n;
+        if (tiles <= 1) break;
     }
-    if (R < 4) R = 4;
-    c->tile_rows = R - 2;
-    c->threads = threads;
-    c->smem = f32 ? split_smem_bytes<float>(c->tile_rows, N) : split_smem_bytes<double>(c->tile_rows, N);
+    // insertion sort by cost
+    for (int a = 1; a < n; ++a)
+        for (int b = a; b > 0 && out[b].cost < out[b - 1].cost; --b) {
+            TileCand t = out[b];
+            out[b] = out[b - 1];
+            out[b - 1] = t;
+        }
+    return n;
+}
+
+int choose_tiles(teuk_ctx *c)
+{
+    TileCand cand[256];
+    int n = tile_candidates(c, cand, 256);
+    if (n == 0) return set_err(c, TEUK_E_CUDA, "no tile of the split kernel fits on this device%s");
+    c->tile_rows = cand[0].R - 2;
+    c->threads = 256;
+    c->smem = cand[0].smem;
+    return TEUK_OK;
 }
 
 template <typename T>
@@ -205,7 +248,8 @@ StepParams<T> make_params(const teuk_ctx *c, int in_level)
     p.Nr = (int)d.Nr;
     p.Nth = (int)d.Ntheta;
     p.tile_rows = c->tile_rows;
-    p.pitch = (int)d.Ntheta + 1;
+    p.pitch = (int)d.Ntheta;
+    p.bulk = ((size_t)d.Ntheta * sizeof(c2)) % 16 == 0 ? 1 : 0;
     p.group = implicit_group((int)d.Ntheta);
     p.first = c->shifted ? 0 : 1;
     p.imp_only = 0;
@@ -373,7 +417,18 @@ int teuk_init_grid(const teuk_grid_desc *desc, void *d_state, void *d_coef, void
     c->patch_p0 = 0;
     c->patch_np = 0;
     c->mOmega = 0.0;
-    choose_tiles(c);
+    if (d.scheme == TEUK_SCHEME_SPLIT) {
+        int rt = choose_tiles(c);
+        if (rt != TEUK_OK) {
+            memcpy(g_init_err, c->err, sizeof(g_init_err));
+            delete c;
+            return rt;
+        }
+    } else {
+        c->tile_rows = 1;
+        c->threads = 256;
+        c->smem = 0;
+    }
 
     cudaStream_t st = (cudaStream_t)stream;
     int r2 = TEUK_OK;
@@ -594,6 +649,7 @@ int teuk_extract_waveform(teuk_ctx *c, int64_t first, int64_t count, double *h_o
     }
     Ctl h;
     CK(cudaMemcpy(&h, c->coef + c->L.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost), "control read");
+    if (h.flags & FLAG_TIMEOUT) return set_err(c, TEUK_E_TIMEOUT, "a bulk copy of a state tile did not complete%s");
     if (h.flags & FLAG_NONFINITE) return set_err(c, TEUK_E_NONFINITE, "a non-finite waveform sample was produced%s");
     return TEUK_OK;
 }
@@ -603,6 +659,92 @@ int teuk_destroy(teuk_ctx *c)
     if (!c) return TEUK_OK;
     drop_graphs(c);
     delete c;
+    return TEUK_OK;
+}
+
+int teuk_tiling(const teuk_ctx *c, int *tile_rows, int *threads, size_t *smem_bytes, int *group)
+{
+    if (!c) return TEUK_E_STATE;
+    if (tile_rows) *tile_rows = c->tile_rows;
+    if (threads) *threads = c->threads;
+    if (smem_bytes) *smem_bytes = c->smem;
+    if (group) *group = implicit_group((int)c->d.Ntheta);
+    return TEUK_OK;
+}
+
+int teuk_autotune(teuk_ctx *c, int trial_steps, void *stream, int *tile_rows_out)
+{
+    if (!c) return TEUK_E_STATE;
+    if (trial_steps < 1 || trial_steps > 100000) return set_err(c, TEUK_E_INVAL, "trial_steps out of range%s");
+    if (c->d.scheme != TEUK_SCHEME_SPLIT) {
+        if (tile_rows_out) *tile_rows_out = c->tile_rows;
+        return TEUK_OK;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    TileCand cand[256];
+    int n = tile_candidates(c, cand, 256);
+    if (n == 0) return set_err(c, TEUK_E_CUDA, "no tile of the split kernel fits on this device%s");
+    const int ntry = n < 6 ? n : 6;
+    drop_graphs(c);
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0), "event");
+    CK(cudaEventCreate(&e1), "event");
+    float best = 3.4e38f;
+    int bestk = 0;
+    for (int k = 0; k < ntry; ++k) {
+        c->tile_rows = cand[k].R - 2;
+        c->smem = cand[k].smem;
+        c->shifted = 1;
+        int lev = c->cur;
+        cudaError_t e = cudaSuccess;
+        for (int w = 0; w < 3 && e == cudaSuccess; ++w, lev ^= 1) e = launch_one(c, lev, st);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+        for (int w = 0; w < trial_steps && e == cudaSuccess; ++w, lev ^= 1) e = launch_one(c, lev, st);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return cuda_err(c, e, "autotune trial");
+        }
+        if (ms < best) {
+            best = ms;
+            bestk = k;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->tile_rows = cand[bestk].R - 2;
+    c->smem = cand[bestk].smem;
+    // back to a clean state: zero field at step 0, empty ring buffer
+    CK(cudaMemsetAsync(c->state, 0, 2 * c->level_bytes, st), "zero state");
+    CK(cudaMemsetAsync(c->wave, 0, sizeof(double2) * (size_t)(c->d.Ntheta + 1) * (size_t)c->cap, st), "zero wave");
+    CK(launch_set_ctl(c->coef, c->L, 0, 1, st), "control block");
+    c->cur = 0;
+    c->shifted = 0;
+    c->step = 0;
+    c->rec_lo = 0;
+    CK(extract_current(c, st), "extract");
+    CK(cudaStreamSynchronize(st), "autotune sync");
+    if (tile_rows_out) *tile_rows_out = c->tile_rows;
+    return TEUK_OK;
+}
+
+int teuk_set_tiling(teuk_ctx *c, int tile_rows)
+{
+    if (!c) return TEUK_E_STATE;
+    if (c->d.scheme != TEUK_SCHEME_SPLIT) return TEUK_OK;
+    if (tile_rows < 1 || tile_rows > 254) return set_err(c, TEUK_E_INVAL, "tile_rows out of range [1, 254]%s");
+    int N = (int)c->d.Ntheta;
+    bool f32 = c->d.precision == TEUK_FP32;
+    size_t sm = f32 ? split_smem_bytes<float>(tile_rows, N) : split_smem_bytes<double>(tile_rows, N);
+    int k = f32 ? split_blocks_per_sm<float>(N, c->threads, sm) : split_blocks_per_sm<double>(N, c->threads, sm);
+    if (sm > 227 * 1024 || k < 1) return set_err(c, TEUK_E_INVAL, "tile does not fit in shared memory%s");
+    drop_graphs(c);
+    c->tile_rows = tile_rows;
+    c->smem = sm;
     return TEUK_OK;
 }
 

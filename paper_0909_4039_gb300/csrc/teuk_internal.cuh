@@ -46,7 +46,7 @@ enum RField {
 enum TField { TF_S2 = 0, TF_C, TF_AM, TF_A0, TF_AP, TF_PAD0, TF_PAD1, TF_PAD2, NTF };
 
 // Error flags in Ctl::flags.
-enum : unsigned { FLAG_NONFINITE = 1u };
+enum : unsigned { FLAG_NONFINITE = 1u, FLAG_TIMEOUT = 2u };
 
 struct Ctl {
     long long step;      // index n of the state the next step reads
@@ -75,6 +75,7 @@ template <typename T> struct StepParams {
     int group;               // threads per theta row in the implicit phase
     int first;               // 1: implicit step dt/2 (input is a physical state)
     int imp_only;            // 1: only C_{dt/2} on the tile rows (state output)
+    int bulk;                // 1: tile rows move by TMA bulk copies (rows are 16-byte multiples)
     int i_ext;               // extraction node
     int wave_cap;            // ring-buffer slots
     int patch_p0, patch_np;  // source patch rows [p0, p0+np); np = 0: no source
@@ -123,7 +124,11 @@ cudaError_t launch_extract(const StepParams<T> &p, const typename V2<T>::t *u, l
                            cudaStream_t st);
 template <typename T>
 size_t split_smem_bytes(int tile_rows, int Nth);
+template <typename T>
+int split_blocks_per_sm(int Nth, int threads, size_t smem);   // 0 if the launch cannot fit
 int implicit_group(int Nth);            // threads per theta row
+int implicit_seg(int Nth);              // theta elements per thread
+constexpr int kSegNarrow = 4;           // theta elements per thread (Ntheta <= 128)
 constexpr int kSeg = 8;                 // theta elements per thread (Ntheta <= 256)
 constexpr int kSegWide = 32;            // theta elements per thread (Ntheta <= 1024)
 cudaError_t launch_convert_to(int prec, const double2 *src, void *dst, size_t n, cudaStream_t st);

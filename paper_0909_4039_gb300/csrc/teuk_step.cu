@@ -114,175 +114,176 @@ template <typename C> __device__ __forceinline__ C shfl_down_c(C v, int d, int w
 // The tridiagonal solve uses the FP64-generated LU pivots e_j = 1/d_j:
 //   forward   z_j = r_j - m_j z_{j-1},  m_j = sub_j e_{j-1}
 //   backward  x_j = e_j z_j - f_j x_{j+1},  f_j = e_j sup_j.
-// Both are first-order affine recurrences; each lane composes the affine
-// map of its segment, the maps are scanned across the G lanes with
-// shuffles (log2 G levels), and each lane then runs its segment from the
-// incoming value.  Rows with active == false (boundary or outside the grid)
-// take part in the shuffles with neutral data and write zeros.
+// Both are first-order affine recurrences.  Each lane composes the affine
+// map of its segment; the maps are scanned across the G lanes with
+// shuffles (Kogge-Stone, log2 G levels) and each lane then runs its segment
+// from the incoming value.  The multiplicative part of every map depends
+// only on the matrix, so it is scanned once per call and both stages scan
+// only the additive part.  Rows with active == false (boundary or outside
+// the grid) take part in the shuffles with neutral data and write zeros.
 template <typename T, int S>
 __device__ void implicit_row_group(const ImpConst<T> &K, typename V2<T>::t *phi, typename V2<T>::t *pi,
                                    const T *sig, const T *f, const T *th, int N, int Nr, int gi,
                                    bool active, bool in_tile, int g, int G)
 {
     typedef typename V2<T>::t c2;
+    constexpr int LOGMAX = 5;
     const c2 zero = cmk<c2>(T(0), T(0));
     const c2 one = cmk<c2>(T(1), T(0));
+    // Elements past the end of the row (and every element of an inactive
+    // row) are neutral: zero data, e = 1, m = f = 0.  Padded elements only
+    // follow the real ones of a segment and only feed lanes that hold no
+    // real element, so the recurrences need no bounds tests.
     const int j0 = g * S;
     int len = N - j0;
     len = len < 0 ? 0 : (len > S ? S : len);
     if (!active) len = 0;
+    const int jlast = N - 1;
     const T gh = K.gh, gh2 = K.gh2;
+    const T D = f[RF_DELTA], ctr = f[RF_CTR], cti = f[RF_CTI], ctc = f[RF_CTC], c0r = f[RF_C0R],
+            c0i = f[RF_C0I];
     const T *Cc = th + TF_C * N;
     const T *Am = th + TF_AM * N;
     const T *A0 = th + TF_A0 * N;
     const T *Ap = th + TF_AP * N;
 
-    c2 e[S], y[S], w[S];
-    T sg[S];
+    // per-element coefficients, computed once
+    c2 e[S], m[S], fk[S], ct[S], c0[S], ia1[S], y[S], w[S];
+    T q[S];
 #pragma unroll
     for (int k = 0; k < S; ++k) {
         if (k < len) {
             int j = j0 + k;
-            sg[k] = sig[j];
+            T sg = sig[j];
+            q[k] = D * sg;
+            ct[k] = cmk<c2>(sg * ctr, sg * fma(ctc, Cc[j], cti));
+            c0[k] = cmk<c2>(-sg * c0r, -sg * c0i);
+            ia1[k] = cinv(cmk<c2>(fma(gh, ct[k].x, T(1)), gh * ct[k].y));
+            e[k] = K.piv[(size_t)j * Nr + gi];
             w[k] = phi[j];
             y[k] = pi[j];
-            e[k] = K.piv[(size_t)j * Nr + gi];
         } else {
-            sg[k] = T(0);
+            q[k] = T(0);
+            ct[k] = zero;
+            c0[k] = zero;
+            ia1[k] = one;
+            e[k] = one;
             w[k] = zero;
             y[k] = zero;
-            e[k] = one;
         }
     }
     const c2 e_prev = shfl_up_c(e[S - 1], 1, G);   // e_{j0-1} (lane g-1 holds a full segment)
+    T am[S], a0[S], ap[S];
+#pragma unroll
+    for (int k = 0; k < S; ++k) {
+        int j = min(j0 + k, jlast);
+        am[k] = Am[j];
+        a0[k] = A0[j];
+        ap[k] = Ap[j];
+        m[k] = cscale<c2>(gh2 * q[k] * am[k], k ? e[k - 1] : e_prev);
+        fk[k] = cscale<c2>(gh2 * q[k] * ap[k], e[k]);
+    }
+    // multiplicative parts of the segment maps and their scans (matrix only)
+    c2 Afl[LOGMAX], Abl[LOGMAX];
+    {
+        c2 Af = one, Ab = one;
+#pragma unroll
+        for (int k = 0; k < S; ++k) Af = cmul(cmk<c2>(-m[k].x, -m[k].y), Af);
+#pragma unroll
+        for (int k = S - 1; k >= 0; --k) Ab = cmul(cmk<c2>(-fk[k].x, -fk[k].y), Ab);
+#pragma unroll
+        for (int l = 0; l < LOGMAX; ++l) {
+            int d = 1 << l;
+            Afl[l] = Af;
+            Abl[l] = Ab;
+            if (d < G) {
+                c2 Ao = shfl_up_c(Af, d, G), Bo = shfl_down_c(Ab, d, G);
+                if (g >= d) Af = cmul(Af, Ao);
+                if (g + d < G) Ab = cmul(Ab, Bo);
+            }
+        }
+    }
 
     // tridiagonal solve of w in place (stage right side -> U_Phi)
     auto solve = [&]() {
-        // forward: compose z_out = A z_in + B over the segment
-        c2 A = one, B = zero;
+        c2 B = zero;
 #pragma unroll
-        for (int k = 0; k < S; ++k) {
-            if (k < len) {
-                int j = j0 + k;
-                c2 m = cscale<c2>(gh2 * f[RF_DELTA] * sg[k] * Am[j], k ? e[k - 1] : e_prev);
-                B = csub(w[k], cmul(m, B));
-                A = cmul(cmk<c2>(-m.x, -m.y), A);
-            }
-        }
-        for (int d = 1; d < G; d <<= 1) {
-            c2 Ao = shfl_up_c(A, d, G), Bo = shfl_up_c(B, d, G);
-            if (g >= d) {
-                B = cadd(cmul(A, Bo), B);
-                A = cmul(A, Ao);
+        for (int k = 0; k < S; ++k) B = csub(w[k], cmul(m[k], B));
+#pragma unroll
+        for (int l = 0; l < LOGMAX; ++l) {
+            int d = 1 << l;
+            if (d < G) {
+                c2 Bo = shfl_up_c(B, d, G);
+                if (g >= d) B = cadd(cmul(Afl[l], Bo), B);
             }
         }
         c2 z = shfl_up_c(B, 1, G);
         if (g == 0) z = zero;
 #pragma unroll
         for (int k = 0; k < S; ++k) {
-            if (k < len) {
-                int j = j0 + k;
-                c2 m = cscale<c2>(gh2 * f[RF_DELTA] * sg[k] * Am[j], k ? e[k - 1] : e_prev);
-                z = csub(w[k], cmul(m, z));
-                w[k] = z;
-            }
+            z = csub(w[k], cmul(m[k], z));
+            w[k] = cmul(e[k], z);          // b_k = e_k z_k
         }
-        // backward: compose x_start = A x_in + B over the segment, from its end
-        A = one;
         B = zero;
 #pragma unroll
-        for (int k = S - 1; k >= 0; --k) {
-            if (k < len) {
-                int j = j0 + k;
-                c2 fk = cscale<c2>(gh2 * f[RF_DELTA] * sg[k] * Ap[j], e[k]);
-                c2 bk = cmul(e[k], w[k]);
-                B = csub(bk, cmul(fk, B));
-                A = cmul(cmk<c2>(-fk.x, -fk.y), A);
-            }
-        }
-        for (int d = 1; d < G; d <<= 1) {
-            c2 Ao = shfl_down_c(A, d, G), Bo = shfl_down_c(B, d, G);
-            if (g + d < G) {
-                B = cadd(cmul(A, Bo), B);
-                A = cmul(A, Ao);
+        for (int k = S - 1; k >= 0; --k) B = csub(w[k], cmul(fk[k], B));
+#pragma unroll
+        for (int l = 0; l < LOGMAX; ++l) {
+            int d = 1 << l;
+            if (d < G) {
+                c2 Bo = shfl_down_c(B, d, G);
+                if (g + d < G) B = cadd(cmul(Abl[l], Bo), B);
             }
         }
         c2 x = shfl_down_c(B, 1, G);
         if (g == G - 1) x = zero;
 #pragma unroll
         for (int k = S - 1; k >= 0; --k) {
-            if (k < len) {
-                int j = j0 + k;
-                c2 fk = cscale<c2>(gh2 * f[RF_DELTA] * sg[k] * Ap[j], e[k]);
-                x = csub(cmul(e[k], w[k]), cmul(fk, x));
-                w[k] = x;
-            }
+            x = csub(w[k], cmul(fk[k], x));
+            w[k] = x;
         }
     };
-    // (B + c0rad) U_Phi at segment element k, neighbours from the adjacent lanes
-    auto apply_B = [&](int k, c2 xl, c2 xr, const Loc<T> &L) {
-        int j = j0 + k;
-        c2 xm = k ? w[k - 1] : xl;
-        c2 xp = (k + 1 < S) ? w[k + 1] : xr;
-        if (k + 1 >= len) xp = xr;
-        c2 v = cadd(cadd(cscale<c2>(Am[j], xm), cscale<c2>(A0[j], w[k])), cscale<c2>(Ap[j], xp));
-        return cadd(cscale<c2>(L.q, v), cmul(L.c0, w[k]));
+    // (B + c0rad) U_Phi for the whole segment
+    auto apply_B = [&](c2 *bf) {
+        c2 xl = shfl_up_c(w[S - 1], 1, G), xr = shfl_down_c(w[0], 1, G);
+        if (g == 0) xl = zero;
+        if (g == G - 1) xr = zero;
+#pragma unroll
+        for (int k = 0; k < S; ++k) {
+            c2 xm = k ? w[k - 1] : xl;
+            c2 xp = (k + 1 < S) ? w[(k + 1) < S ? k + 1 : S - 1] : xr;
+            c2 v = cadd(cadd(cscale<c2>(am[k], xm), cscale<c2>(a0[k], w[k])), cscale<c2>(ap[k], xp));
+            bf[k] = cadd(cscale<c2>(q[k], v), cmul(c0[k], w[k]));
+        }
     };
 
     // ---- stage 1: r = (1 + gh c_t) Phi + gh Pi
 #pragma unroll
     for (int k = 0; k < S; ++k) {
-        if (k < len) {
-            Loc<T> L = local_coef<T>(sg[k], f, Cc[j0 + k], gh);
-            w[k] = caxpy(gh, y[k], cmul(L.a1, w[k]));
-        }
+        c2 a1 = cmk<c2>(fma(gh, ct[k].x, T(1)), gh * ct[k].y);
+        w[k] = caxpy(gh, y[k], cmul(a1, w[k]));
     }
     solve();
     {
-        c2 xl = shfl_up_c(w[S - 1], 1, G), xr = shfl_down_c(w[0], 1, G);
-        if (g == 0) xl = zero;
-        if (g == G - 1) xr = zero;
         c2 bf[S];
+        apply_B(bf);
 #pragma unroll
         for (int k = 0; k < S; ++k) {
-            if (k < len) {
-                Loc<T> L = local_coef<T>(sg[k], f, Cc[j0 + k], gh);
-                bf[k] = apply_B(k, xl, xr, L);
-            }
-        }
-#pragma unroll
-        for (int k = 0; k < S; ++k) {
-            if (k < len) {
-                Loc<T> L = local_coef<T>(sg[k], f, Cc[j0 + k], gh);
-                c2 P1 = cmul(csub(y[k], cscale<c2>(gh, bf[k])), cinv(L.a1));
-                c2 rphi = caxpy(K.h12g, P1, w[k]);                     // u_Phi + (1-gamma) h U1_Pi
-                c2 rpi = csub(y[k], cscale<c2>(K.h1g, cadd(bf[k], cmul(L.ct, P1))));
-                w[k] = caxpy(gh, rpi, cmul(L.a1, rphi));
-                y[k] = rpi;
-            }
+            c2 a1 = cmk<c2>(fma(gh, ct[k].x, T(1)), gh * ct[k].y);
+            c2 P1 = cmul(csub(y[k], cscale<c2>(gh, bf[k])), ia1[k]);
+            c2 rphi = caxpy(K.h12g, P1, w[k]);                     // u_Phi + (1-gamma) h U1_Pi
+            c2 rpi = csub(y[k], cscale<c2>(K.h1g, cadd(bf[k], cmul(ct[k], P1))));
+            w[k] = caxpy(gh, rpi, cmul(a1, rphi));
+            y[k] = rpi;
         }
     }
     // ---- stage 2
     solve();
     {
-        c2 xl = shfl_up_c(w[S - 1], 1, G), xr = shfl_down_c(w[0], 1, G);
-        if (g == 0) xl = zero;
-        if (g == G - 1) xr = zero;
         c2 bf[S];
+        apply_B(bf);
 #pragma unroll
-        for (int k = 0; k < S; ++k) {
-            if (k < len) {
-                Loc<T> L = local_coef<T>(sg[k], f, Cc[j0 + k], gh);
-                bf[k] = apply_B(k, xl, xr, L);
-            }
-        }
-#pragma unroll
-        for (int k = 0; k < S; ++k) {
-            if (k < len) {
-                Loc<T> L = local_coef<T>(sg[k], f, Cc[j0 + k], gh);
-                y[k] = cmul(csub(y[k], cscale<c2>(gh, bf[k])), cinv(L.a1));
-            }
-        }
+        for (int k = 0; k < S; ++k) y[k] = cmul(csub(y[k], cscale<c2>(gh, bf[k])), ia1[k]);
     }
     if (in_tile) {
         int lenw = N - j0;
@@ -415,6 +416,41 @@ template <typename T> __device__ __forceinline__ typename V2<T>::t from_d2(doubl
     return cmk<c2>((T)v.x, (T)v.y);
 }
 
+// ---- TMA bulk copies (1-D, global <-> shared) and the mbarrier that
+// completes them.  Every wait is bounded.
+__device__ __forceinline__ unsigned smem_u32(const void *ptr) { return (unsigned)__cvta_generic_to_shared(ptr); }
+__device__ __forceinline__ void mbar_init(unsigned long long *m, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(m)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *m, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(m)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, unsigned long long *m)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(m)) : "memory");
+}
+__device__ __forceinline__ bool mbar_wait(unsigned long long *m, unsigned parity, int limit)
+{
+    unsigned ok = 0;
+    for (int it = 0; it < limit && !ok; ++it)
+        asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+                     : "=r"(ok) : "r"(smem_u32(m)), "r"(parity) : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void bulk_s2g(void *dst, const void *src, unsigned bytes)
+{
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_u32(src)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+constexpr int kWaitLimit = 1 << 22;   // try_wait rounds before a copy is declared lost
+
 // FP64 extraction of one row held anywhere (shared or global); one warp.
 template <typename T>
 __device__ void extract_warp(const StepParams<T> &p, const typename V2<T>::t *row, long long step)
@@ -447,12 +483,13 @@ __device__ void extract_warp(const StepParams<T> &p, const typename V2<T>::t *ro
 // extraction row.  With p.imp_only the kernel only applies C_{dt/2} to the
 // tile rows (used to output the physical state).
 template <typename T, int S>
-__global__ void __launch_bounds__(256) k_split_step(const StepParams<T> p)
+__global__ void __launch_bounds__(256, (sizeof(T) == 4 && S <= 4) ? 2 : 1) k_split_step(const StepParams<T> p)
 {
     typedef typename V2<T>::t c2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double2 sph[2];
     __shared__ long long s_n;
+    __shared__ __align__(8) unsigned long long s_mbar;
     const int Nr = p.Nr, N = p.Nth, TR = p.tile_rows, R = TR + 2, P = p.pitch;
     const int tid = threadIdx.x, NT = blockDim.x;
     const int i0 = blockIdx.x * TR;
@@ -478,16 +515,45 @@ __global__ void __launch_bounds__(256) k_split_step(const StepParams<T> p)
     }
     // ---- A: tile rows i0-1 .. i0+TR, r and theta tables, 1/Sigma^2 at the nodes
     const c2 zero = cmk<c2>(T(0), T(0));
-    for (int idx = tid; idx < R * N; idx += NT) {
-        int lr = idx / N, j = idx - lr * N;
-        int gi = i0 - 1 + lr;
-        c2 fv = zero, gv = zero;
-        if (gi >= 0 && gi < Nr) {
-            fv = p.uin[(size_t)gi * N + j];
-            gv = p.uin[((size_t)Nr + gi) * N + j];
+    // (row, column) walk of the tile without integer division in the loop
+    const int t_lr = tid / N, t_j = tid - t_lr * N;
+    const int d_lr = NT / N, d_j = NT - d_lr * N;
+    // rows of the tile that exist on the grid: [ga, gb] globally, from tile row la
+    const int ga = i0 - 1 < 0 ? 0 : i0 - 1;
+    const int gb = i0 + TR > Nr - 1 ? Nr - 1 : i0 + TR;
+    const int la = ga - (i0 - 1), nrows = gb - ga + 1;
+    if (p.bulk) {
+        if (tid == 0) {
+            mbar_init(&s_mbar, 1);
+            unsigned bytes = (unsigned)nrows * (unsigned)N * (unsigned)sizeof(c2);
+            mbar_expect_tx(&s_mbar, 2 * bytes);
+            bulk_g2s(sPhi + la * P, p.uin + (size_t)ga * N, bytes, &s_mbar);
+            bulk_g2s(sPi + la * P, p.uin + ((size_t)Nr + ga) * N, bytes, &s_mbar);
         }
-        sPhi[lr * P + j] = fv;
-        sPi[lr * P + j] = gv;
+        // rows off the grid (first and last tile only) are zero
+        for (int lr = t_lr, j = t_j; lr < R;) {
+            if (lr < la || lr >= la + nrows) {
+                sPhi[lr * P + j] = zero;
+                sPi[lr * P + j] = zero;
+            }
+            lr += d_lr;
+            j += d_j;
+            if (j >= N) { j -= N; ++lr; }
+        }
+    } else {
+        for (int lr = t_lr, j = t_j; lr < R;) {
+            int gi = i0 - 1 + lr;
+            c2 fv = zero, gv = zero;
+            if (gi >= 0 && gi < Nr) {
+                fv = p.uin[(size_t)gi * N + j];
+                gv = p.uin[((size_t)Nr + gi) * N + j];
+            }
+            sPhi[lr * P + j] = fv;
+            sPi[lr * P + j] = gv;
+            lr += d_lr;
+            j += d_j;
+            if (j >= N) { j -= N; ++lr; }
+        }
     }
     for (int idx = tid; idx < R * NRF; idx += NT) {
         int lr = idx / NRF, q = idx - lr * NRF;
@@ -501,14 +567,26 @@ __global__ void __launch_bounds__(256) k_split_step(const StepParams<T> p)
     }
     for (int idx = tid; idx < NTF * N; idx += NT) sTh[idx] = p.thtab[idx];
     __syncthreads();
-    for (int idx = tid; idx < R * N; idx += NT) {
-        int lr = idx / N, j = idx - lr * N;
+    // 1/Sigma^2 at the node rows, while the state tile is in flight
+    for (int lr = t_lr, j = t_j; lr < R;) {
         int gi = i0 - 1 + lr;
         T v = T(0);
         if (gi >= 0 && gi < Nr) v = rcp_(fma(-sRn[lr * NRF + RF_AD], sTh[TF_S2 * N + j], sRn[lr * NRF + RF_R2]));
         sSig[lr * P + j] = v;
+        lr += d_lr;
+        j += d_j;
+        if (j >= N) { j -= N; ++lr; }
     }
-    __syncthreads();
+    {
+        // all threads agree on the outcome of the bounded wait before acting on it
+        int ok = p.bulk ? (int)mbar_wait(&s_mbar, 0, kWaitLimit) : 1;
+        if (!__syncthreads_and(ok)) {
+            // the copy did not complete: report, wait once more, leave the tile alone
+            if (tid == 0) atomicOr(&p.ctl->flags, FLAG_TIMEOUT);
+            mbar_wait(&s_mbar, 0, kWaitLimit);
+            return;
+        }
+    }
     // ---- B: implicit step on the tile rows (all R rows; only rows 1..TR with imp_only)
     {
         const ImpConst<T> &K = (p.first || p.imp_only) ? p.half : p.full;
@@ -558,14 +636,33 @@ __global__ void __launch_bounds__(256) k_split_step(const StepParams<T> p)
         __syncthreads();
     }
     // ---- D: store the output rows
-    for (int idx = tid; idx < TR * N; idx += NT) {
-        int k = idx / N, j = idx - k * N;
-        int gi = i0 + k;
-        if (gi >= Nr) continue;
-        p.uout[(size_t)gi * N + j] = sPhi[(k + 1) * P + j];
-        p.uout[((size_t)Nr + gi) * N + j] = sPi[(k + 1) * P + j];
+    const int nout = (Nr - i0) < TR ? (Nr - i0) : TR;
+    if (p.bulk) {
+        fence_proxy_async();      // shared-memory writes become visible to the bulk copy
+        __syncthreads();
+        if (tid == 0) {
+            unsigned bytes = (unsigned)nout * (unsigned)N * (unsigned)sizeof(c2);
+            bulk_s2g(p.uout + (size_t)i0 * N, sPhi + P, bytes);
+            bulk_s2g(p.uout + ((size_t)Nr + i0) * N, sPi + P, bytes);
+            bulk_commit();
+            bulk_wait_read();     // the tile may be reused (extraction) and the CTA may exit
+        }
+    } else {
+        for (int k = t_lr, j = t_j; k < TR;) {
+            int gi = i0 + k;
+            if (gi < Nr) {
+                p.uout[(size_t)gi * N + j] = sPhi[(k + 1) * P + j];
+                p.uout[((size_t)Nr + gi) * N + j] = sPi[(k + 1) * P + j];
+            }
+            k += d_lr;
+            j += d_j;
+            if (j >= N) { j -= N; ++k; }
+        }
     }
-    if (p.imp_only) return;
+    if (p.imp_only) {
+        if (p.bulk && tid == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+        return;
+    }
     // ---- E: physical sample u_{n+1} = C_{dt/2} s_{n+1} on the extraction row
     const bool ext = p.i_ext >= i0 && p.i_ext < i0 + TR && p.i_ext < Nr;
     if (ext) {
@@ -582,6 +679,7 @@ __global__ void __launch_bounds__(256) k_split_step(const StepParams<T> p)
     }
     __syncthreads();
     if (tid == 0) {
+        if (p.bulk) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");   // stores complete
         __threadfence();
         unsigned t = atomicAdd(&p.ctl->ticket, 1u);
         if (t == gridDim.x - 1) {
@@ -708,14 +806,16 @@ __global__ void k_from_f32(const float2 *src, double2 *dst, size_t n)
 template <typename T>
 size_t split_smem_bytes(int tile_rows, int Nth)
 {
-    size_t R = (size_t)tile_rows + 2, P = (size_t)Nth + 1;
+    size_t R = (size_t)tile_rows + 2, P = (size_t)Nth;
     return R * P * (2 * sizeof(typename V2<T>::t) + sizeof(T)) + (R + (R - 1)) * NRF * sizeof(T) +
            (size_t)NTF * Nth * sizeof(T);
 }
 
+int implicit_seg(int Nth) { return Nth <= 128 ? kSegNarrow : (Nth <= 256 ? kSeg : kSegWide); }
+
 int implicit_group(int Nth)
 {
-    int seg = Nth <= 256 ? kSeg : kSegWide;
+    int seg = implicit_seg(Nth);
     int need = (Nth + seg - 1) / seg;
     int G = 1;
     while (G < need) G <<= 1;
@@ -723,17 +823,35 @@ int implicit_group(int Nth)
 }
 
 template <typename T>
+int split_blocks_per_sm(int Nth, int threads, size_t smem)
+{
+    const int seg = implicit_seg(Nth);
+    auto fn = seg == kSegNarrow ? k_split_step<T, kSegNarrow> : (seg == kSeg ? k_split_step<T, kSeg> : k_split_step<T, kSegWide>);
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, threads, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return nb;
+}
+
+template <typename T>
 cudaError_t launch_split_step(const StepParams<T> &p, int threads, size_t smem, cudaStream_t st)
 {
     // opt in to the dynamic shared memory this launch needs (once per size)
-    static size_t configured[2][2] = {{0, 0}, {0, 0}};
-    const bool wide = p.Nth > 256;
+    static size_t configured[2][3] = {{0, 0, 0}, {0, 0, 0}};
+    const int seg = implicit_seg(p.Nth);
+    const int v = seg == kSegNarrow ? 0 : (seg == kSeg ? 1 : 2);
     int key = sizeof(T) == 4 ? 0 : 1;
-    auto fn = wide ? k_split_step<T, kSegWide> : k_split_step<T, kSeg>;
-    if (smem > configured[key][wide]) {
+    auto fn = v == 0 ? k_split_step<T, kSegNarrow> : (v == 1 ? k_split_step<T, kSeg> : k_split_step<T, kSegWide>);
+    if (smem > configured[key][v]) {
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        configured[key][wide] = smem;
+        configured[key][v] = smem;
     }
     int grid = (p.Nr + p.tile_rows - 1) / p.tile_rows;
     fn<<<grid, threads, smem, st>>>(p);
@@ -771,6 +889,8 @@ cudaError_t launch_convert_from(int prec, const void *src, double2 *dst, size_t 
     return cudaGetLastError();
 }
 
+template int split_blocks_per_sm<float>(int, int, size_t);
+template int split_blocks_per_sm<double>(int, int, size_t);
 template size_t split_smem_bytes<float>(int, int);
 template size_t split_smem_bytes<double>(int, int);
 template cudaError_t launch_split_step<float>(const StepParams<float> &, int, size_t, cudaStream_t);

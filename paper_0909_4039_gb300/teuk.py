@@ -37,6 +37,7 @@ EXPORTED = [
     "teuk_workspace_bytes", "teuk_init_grid", "teuk_set_source", "teuk_set_weights",
     "teuk_set_state", "teuk_get_state", "teuk_step", "teuk_extract_waveform",
     "teuk_current_step", "teuk_last_error", "teuk_status_string", "teuk_destroy",
+    "teuk_tiling", "teuk_autotune", "teuk_set_tiling",
 ]
 
 
@@ -99,8 +100,13 @@ def lib(load_only: bool = False):
     L.teuk_status_string.argtypes = [ctypes.c_int]
     L.teuk_status_string.restype = ctypes.c_char_p
     L.teuk_destroy.argtypes = [vp]
+    L.teuk_tiling.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                              ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_int)]
+    L.teuk_autotune.argtypes = [vp, ctypes.c_int, vp, ctypes.POINTER(ctypes.c_int)]
+    L.teuk_set_tiling.argtypes = [vp, ctypes.c_int]
     for name in ("teuk_workspace_bytes", "teuk_init_grid", "teuk_set_source", "teuk_set_weights",
-                 "teuk_set_state", "teuk_get_state", "teuk_step", "teuk_extract_waveform", "teuk_destroy"):
+                 "teuk_set_state", "teuk_get_state", "teuk_step", "teuk_extract_waveform", "teuk_destroy",
+                 "teuk_tiling", "teuk_autotune", "teuk_set_tiling"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -175,6 +181,23 @@ def teuk_current_step(ctx) -> int:
     return int(lib().teuk_current_step(ctx))
 
 
+def teuk_tiling(ctx) -> dict:
+    tr, th, g = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    sm = ctypes.c_size_t()
+    _check(lib().teuk_tiling(ctx, ctypes.byref(tr), ctypes.byref(th), ctypes.byref(sm), ctypes.byref(g)), ctx)
+    return {"tile_rows": tr.value, "threads": th.value, "smem_bytes": sm.value, "group": g.value}
+
+
+def teuk_autotune(ctx, trial_steps: int = 20, stream: int = 0) -> int:
+    tr = ctypes.c_int()
+    _check(lib().teuk_autotune(ctx, int(trial_steps), stream, ctypes.byref(tr)), ctx)
+    return tr.value
+
+
+def teuk_set_tiling(ctx, tile_rows: int):
+    _check(lib().teuk_set_tiling(ctx, int(tile_rows)), ctx)
+
+
 def teuk_destroy(ctx):
     _check(lib().teuk_destroy(ctx))
 
@@ -211,6 +234,15 @@ class Stepper:
     @property
     def sh(self) -> int:
         return self.stream.cuda_stream
+
+    def autotune(self, trial_steps: int = 20) -> int:
+        return teuk_autotune(self.ctx, trial_steps, self.sh)
+
+    def tiling(self) -> dict:
+        return teuk_tiling(self.ctx)
+
+    def set_tiling(self, tile_rows: int):
+        teuk_set_tiling(self.ctx, tile_rows)
 
     def set_source(self, amp=1.0, r0=10.0, sigma_rstar=0.1, sigma_theta=0.1, Omega=float("nan")):
         teuk_set_source(self.ctx, amp, r0, sigma_rstar, sigma_theta, Omega)

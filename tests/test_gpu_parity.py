@@ -198,3 +198,31 @@ def test_extraction_node_clamped_to_boundary():
     st.step(5)
     assert np.all(st.waveform(0, 6)[1:] == 0)     # outer boundary row is zero
     st.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_result_independent_of_tiling_and_autotune(precision):
+    """Tiles overlap by recomputed halo rows; every tile height gives the
+    bitwise same step.  The autotuner leaves a zero state at step 0."""
+    w = inputs.Workload("tiles", s=-2, m=2, a=0.95, Nr=1000, Ntheta=64, rs_min=-50.0, rs_max=150.0, steps=30,
+                        r0=7.0, amp=1.0 - 0.5j, sig_r=0.6, sig_th=0.2, rs_ext=100.0)
+    u0 = inputs.random_state(w.Nr, w.Ntheta, seed=21)
+    outs = []
+    for tr in (7, 22, 45):
+        st = gpu_stepper(w, precision, wave_capacity=64)
+        st.set_tiling(tr)
+        assert st.tiling()["tile_rows"] == tr
+        st.set_state(u0, 0)
+        st.step(w.steps)
+        outs.append((st.get_state(), st.waveform(0, w.steps + 1)))
+        st.close()
+    for u, h in outs[1:]:
+        assert np.array_equal(u, outs[0][0]) and np.array_equal(h, outs[0][1])
+    st = gpu_stepper(w, precision, wave_capacity=64)
+    tr = st.autotune(5)
+    assert tr == st.tiling()["tile_rows"] and tr >= 1
+    assert st.current_step == 0 and np.abs(st.get_state()).max() == 0.0
+    st.set_state(u0, 0)
+    st.step(w.steps)
+    assert np.array_equal(st.get_state(), outs[0][0])
+    st.close()
