@@ -177,6 +177,33 @@ int teuk_autotune(teuk_ctx *ctx, int trial_steps, void *stream, int *tile_rows_o
  * result of a step does not depend on the tile height. */
 int teuk_set_tiling(teuk_ctx *ctx, int tile_rows);
 
+/* One literal-scheme step (all of S inside the two Lax-Wendroff stages)
+ * that allocates nothing and needs no caller-allocated scratch.  The paper
+ * has no counterpart: this entry point exists for callers that cannot
+ * allocate device memory at the point where they step -- for example code
+ * running while a framework's caching allocator has claimed the device
+ * memory, or a latency-critical loop in which cudaMalloc/cudaFree, which
+ * synchronise the device, are not allowed.  It computes what teuk_step
+ * computes for a TEUK_SCHEME_LITERAL context, but keeps the midpoint
+ * scratch in a fixed array inside the library's device image (8 MiB,
+ * resident on every GPU that loads the library until the process exits)
+ * instead of the caller's coefficient workspace.
+ *   ctx    a context created with TEUK_SCHEME_LITERAL (its tables and source
+ *          are read, its state, step counter and waveform are not touched);
+ *   d_in   device buffer, [2][Nr][Ntheta] complex values of the context's
+ *          state precision (plane 0 Phi, plane 1 Pi); read only;
+ *   d_out  device buffer of the same shape, distinct from d_in; written;
+ *   n      step index of d_in (the source phase uses t = n dt).
+ * Grids whose midpoints need more than 8 MiB (2 (Nr-1) Ntheta complex
+ * values) are rejected with TEUK_E_INVAL before anything is launched.  The
+ * first call on a device looks the array's device address up
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the one array: calls whose
+ * work overlaps on the GPU race on it.  Nothing in it needs to start at
+ * zero (every midpoint is written before it is read).  Asynchronous on
+ * `stream`. */
+int teuk_literal_step_static(const teuk_ctx *ctx, const void *d_in, void *d_out, int64_t n, void *stream);
+
 /* Current step number (host mirror of the device counter). */
 int64_t teuk_current_step(const teuk_ctx *ctx);
 

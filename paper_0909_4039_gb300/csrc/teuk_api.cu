@@ -748,4 +748,34 @@ int teuk_set_tiling(teuk_ctx *c, int tile_rows)
     return TEUK_OK;
 }
 
+int teuk_literal_step_static(const teuk_ctx *c, const void *d_in, void *d_out, int64_t n, void *stream)
+{
+    teuk_ctx *cm = const_cast<teuk_ctx *>(c);
+    if (!c) return TEUK_E_STATE;
+    if (c->d.scheme != TEUK_SCHEME_LITERAL)
+        return set_err(cm, TEUK_E_INVAL, "teuk_literal_step_static needs a context of the literal scheme%s");
+    if (!d_in || !d_out || d_in == d_out || n < 0)
+        return set_err(cm, TEUK_E_INVAL, "need distinct non-NULL device buffers and n >= 0%s");
+    size_t c2 = c->d.precision == TEUK_FP32 ? sizeof(float2) : sizeof(double2);
+    size_t need = c2 * 2 * (size_t)(c->d.Nr - 1) * (size_t)c->d.Ntheta;
+    if (need > literal_static_scratch_bytes())
+        return set_err(cm, TEUK_E_INVAL, "grid needs %s%.0f bytes of midpoint scratch, above the static limit of 8 MiB", "",
+                       (double)need);
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e;
+    if (c->d.precision == TEUK_FP32) {
+        StepParams<float> p = make_params<float>(c, 0);
+        p.uin = (const float2 *)d_in;
+        p.uout = (float2 *)d_out;
+        e = launch_literal_step_static<float>(p, (long long)n, st);
+    } else {
+        StepParams<double> p = make_params<double>(c, 0);
+        p.uin = (const double2 *)d_in;
+        p.uout = (double2 *)d_out;
+        e = launch_literal_step_static<double>(p, (long long)n, st);
+    }
+    if (e != cudaSuccess) return cuda_err(cm, e, "literal step (static scratch)");
+    return TEUK_OK;
+}
+
 }  // extern "C"

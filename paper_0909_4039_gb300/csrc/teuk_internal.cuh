@@ -120,6 +120,9 @@ cudaError_t launch_split_step(const StepParams<T> &p, int threads, size_t smem, 
 template <typename T>
 cudaError_t launch_literal_step(const StepParams<T> &p, cudaStream_t st);
 template <typename T>
+cudaError_t launch_literal_step_static(const StepParams<T> &p, long long n, cudaStream_t st);
+size_t literal_static_scratch_bytes();
+template <typename T>
 cudaError_t launch_extract(const StepParams<T> &p, const typename V2<T>::t *u, long long step,
                            cudaStream_t st);
 template <typename T>

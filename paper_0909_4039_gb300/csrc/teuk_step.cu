@@ -24,6 +24,8 @@
 // boundary conditions stated after Eq. 14.
 #include <math.h>
 
+#include <mutex>
+
 #include "teuk_internal.cuh"
 
 namespace teuk {
@@ -790,6 +792,78 @@ __global__ void k_extract(const StepParams<T> p, const typename V2<T>::t *u, lon
     if (advance && threadIdx.x == 0) p.ctl->step = n;
 }
 
+// ------------------------------------------- literal step, static scratch
+// Midpoint scratch of the literal scheme for callers that cannot allocate
+// device memory (see teuk_literal_step_static): a fixed array in the
+// library's own device image, present on every GPU that loads the library
+// until the process exits.  Device code may name it directly; host code
+// must obtain its device address with cudaGetSymbolAddress.
+constexpr size_t kStaticScratchBytes = (size_t)8 << 20;
+static __device__ __align__(256) unsigned char g_literal_scratch[kStaticScratchBytes];
+
+// Same arithmetic as k_literal_mid / k_literal_node, with the step index
+// passed in (no control block) and the midpoints in caller-given scratch.
+template <typename T>
+__global__ void k_literal_mid_static(const StepParams<T> p, typename V2<T>::t *mid, long long n)
+{
+    typedef typename V2<T>::t c2;
+    const int N = p.Nth, Nr = p.Nr;
+    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (Nr - 1) * N) return;
+    int i = idx / N, j = idx - i * N;
+    const c2 *Phi = p.uin, *Pi = p.uin + (size_t)Nr * N;
+    auto avg = [&](int jj) {
+        return cscale<c2>(T(0.5), cadd(Phi[(size_t)i * N + jj], Phi[(size_t)(i + 1) * N + jj]));
+    };
+    c2 f0 = avg(j);
+    c2 fm = (j > 0) ? avg(j - 1) : zero_c2<c2>();
+    c2 fp = (j < N - 1) ? avg(j + 1) : zero_c2<c2>();
+    c2 gbar = cscale<c2>(T(0.5), cadd(Pi[(size_t)i * N + j], Pi[(size_t)(i + 1) * N + j]));
+    c2 df = cscale<c2>(p.drs_inv, csub(Phi[(size_t)(i + 1) * N + j], Phi[(size_t)i * N + j]));
+    c2 dg = cscale<c2>(p.drs_inv, csub(Pi[(size_t)(i + 1) * N + j], Pi[(size_t)i * N + j]));
+    const T *f = p.rtab + (size_t)(2 * i + 1) * NRF;
+    T b;
+    c2 S = literal_SPi<T>(p, f, p.thtab, j, fm, f0, fp, gbar, df, b);
+    if (p.patch_np > 0) S = cadd(S, patch_val(p, i, 1, j, from_d2<T>(phase_at(p.mOmega, (double)n * p.dt64))));
+    c2 *mPhi = mid, *mPi = mid + (size_t)(Nr - 1) * N;
+    mPhi[idx] = cadd(f0, cscale<c2>(p.half_dt, csub(gbar, cscale<c2>(b, df))));
+    mPi[idx] = cadd(gbar, cscale<c2>(p.half_dt, cadd(cscale<c2>(b, dg), S)));
+}
+
+template <typename T>
+__global__ void k_literal_node_static(const StepParams<T> p, const typename V2<T>::t *mid, long long n)
+{
+    typedef typename V2<T>::t c2;
+    const int N = p.Nth, Nr = p.Nr;
+    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= Nr * N) return;
+    int i = idx / N, j = idx - i * N;
+    c2 *oPhi = p.uout, *oPi = p.uout + (size_t)Nr * N;
+    if (i == 0 || i == Nr - 1) {
+        oPhi[idx] = zero_c2<c2>();
+        oPi[idx] = zero_c2<c2>();
+        return;
+    }
+    const c2 *Phi = p.uin, *Pi = p.uin + (size_t)Nr * N;
+    const c2 *mPhi = mid, *mPi = mid + (size_t)(Nr - 1) * N;
+    auto avg = [&](int jj) {
+        return cscale<c2>(T(0.5), cadd(mPhi[(size_t)i * N + jj], mPhi[(size_t)(i - 1) * N + jj]));
+    };
+    c2 f0 = avg(j);
+    c2 fm = (j > 0) ? avg(j - 1) : zero_c2<c2>();
+    c2 fp = (j < N - 1) ? avg(j + 1) : zero_c2<c2>();
+    c2 gt = cscale<c2>(T(0.5), cadd(mPi[(size_t)i * N + j], mPi[(size_t)(i - 1) * N + j]));
+    c2 df = cscale<c2>(p.drs_inv, csub(mPhi[(size_t)i * N + j], mPhi[(size_t)(i - 1) * N + j]));
+    c2 dg = cscale<c2>(p.drs_inv, csub(mPi[(size_t)i * N + j], mPi[(size_t)(i - 1) * N + j]));
+    const T *f = p.rtab + (size_t)(2 * i) * NRF;
+    T b;
+    c2 S = literal_SPi<T>(p, f, p.thtab, j, fm, f0, fp, gt, df, b);
+    if (p.patch_np > 0)
+        S = cadd(S, patch_val(p, i, 0, j, from_d2<T>(phase_at(p.mOmega, (double)n * p.dt64 + 0.5 * p.dt64))));
+    oPhi[idx] = cadd(Phi[idx], cscale<c2>(p.dt, csub(gt, cscale<c2>(b, df))));
+    oPi[idx] = cadd(Pi[idx], cscale<c2>(p.dt, cadd(cscale<c2>(b, dg), S)));
+}
+
 __global__ void k_to_f32(const double2 *src, float2 *dst, size_t n)
 {
     size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -868,6 +942,42 @@ cudaError_t launch_literal_step(const StepParams<T> &p, cudaStream_t st)
     return cudaGetLastError();
 }
 
+size_t literal_static_scratch_bytes() { return kStaticScratchBytes; }
+
+// Device address of g_literal_scratch, looked up once per device with that
+// device current (a host-side symbol is not a device address).
+static cudaError_t static_scratch_address(void **out)
+{
+    static std::mutex mu;
+    static void *addr[64] = {nullptr};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!addr[dev]) {
+        void *ptr = nullptr;
+        e = cudaGetSymbolAddress(&ptr, g_literal_scratch);
+        if (e != cudaSuccess) return e;
+        addr[dev] = ptr;
+    }
+    *out = addr[dev];
+    return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t launch_literal_step_static(const StepParams<T> &p, long long n, cudaStream_t st)
+{
+    typedef typename V2<T>::t c2;
+    void *scratch = nullptr;
+    cudaError_t e = static_scratch_address(&scratch);
+    if (e != cudaSuccess) return e;
+    int nm = (p.Nr - 1) * p.Nth, nn = p.Nr * p.Nth;
+    k_literal_mid_static<T><<<(nm + 255) / 256, 256, 0, st>>>(p, (c2 *)scratch, n);
+    k_literal_node_static<T><<<(nn + 255) / 256, 256, 0, st>>>(p, (const c2 *)scratch, n);
+    return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_extract(const StepParams<T> &p, const typename V2<T>::t *u, long long step, cudaStream_t st)
 {
@@ -895,6 +1005,8 @@ template size_t split_smem_bytes<float>(int, int);
 template size_t split_smem_bytes<double>(int, int);
 template cudaError_t launch_split_step<float>(const StepParams<float> &, int, size_t, cudaStream_t);
 template cudaError_t launch_split_step<double>(const StepParams<double> &, int, size_t, cudaStream_t);
+template cudaError_t launch_literal_step_static<float>(const StepParams<float> &, long long, cudaStream_t);
+template cudaError_t launch_literal_step_static<double>(const StepParams<double> &, long long, cudaStream_t);
 template cudaError_t launch_literal_step<float>(const StepParams<float> &, cudaStream_t);
 template cudaError_t launch_literal_step<double>(const StepParams<double> &, cudaStream_t);
 template cudaError_t launch_extract<float>(const StepParams<float> &, const float2 *, long long, cudaStream_t);

@@ -37,7 +37,7 @@ EXPORTED = [
     "teuk_workspace_bytes", "teuk_init_grid", "teuk_set_source", "teuk_set_weights",
     "teuk_set_state", "teuk_get_state", "teuk_step", "teuk_extract_waveform",
     "teuk_current_step", "teuk_last_error", "teuk_status_string", "teuk_destroy",
-    "teuk_tiling", "teuk_autotune", "teuk_set_tiling",
+    "teuk_tiling", "teuk_autotune", "teuk_set_tiling", "teuk_literal_step_static",
 ]
 
 
@@ -104,9 +104,10 @@ def lib(load_only: bool = False):
                               ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_int)]
     L.teuk_autotune.argtypes = [vp, ctypes.c_int, vp, ctypes.POINTER(ctypes.c_int)]
     L.teuk_set_tiling.argtypes = [vp, ctypes.c_int]
+    L.teuk_literal_step_static.argtypes = [vp, vp, vp, i64, vp]
     for name in ("teuk_workspace_bytes", "teuk_init_grid", "teuk_set_source", "teuk_set_weights",
                  "teuk_set_state", "teuk_get_state", "teuk_step", "teuk_extract_waveform", "teuk_destroy",
-                 "teuk_tiling", "teuk_autotune", "teuk_set_tiling"):
+                 "teuk_tiling", "teuk_autotune", "teuk_set_tiling", "teuk_literal_step_static"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -196,6 +197,13 @@ def teuk_autotune(ctx, trial_steps: int = 20, stream: int = 0) -> int:
 
 def teuk_set_tiling(ctx, tile_rows: int):
     _check(lib().teuk_set_tiling(ctx, int(tile_rows)), ctx)
+
+
+def teuk_literal_step_static(ctx, d_in: int, d_out: int, n: int, stream: int = 0):
+    """One literal-scheme step from d_in to d_out (device pointers in the
+    context's state precision) with the library's static midpoint scratch;
+    for callers that cannot allocate device memory.  See include/teuk.h."""
+    _check(lib().teuk_literal_step_static(ctx, d_in, d_out, int(n), stream), ctx)
 
 
 def teuk_destroy(ctx):
