@@ -251,6 +251,10 @@ StepParams<T> make_params(const teuk_ctx *c, int in_level)
     p.pitch = (int)d.Ntheta;
     p.bulk = ((size_t)d.Ntheta * sizeof(c2)) % 16 == 0 ? 1 : 0;
     p.group = implicit_group((int)d.Ntheta);
+    {
+        const int seg = implicit_seg((int)d.Ntheta);
+        p.vec = (d.Ntheta % seg == 0 && d.Ntheta % 4 == 0) ? 1 : 0;
+    }
     p.first = c->shifted ? 0 : 1;
     p.imp_only = 0;
     p.i_ext = c->i_ext;

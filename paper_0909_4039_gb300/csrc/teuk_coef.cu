@@ -174,7 +174,7 @@ __global__ void k_theta(CoefArgs A)
 // of every node row i:
 //   diag_j = 1 + gh c_t + gh^2 (c0rad + q A0_j),  sub_j = gh^2 q AM_j,
 //   sup_j = gh^2 q AP_j;  d_0 = diag_0, d_j = diag_j - sub_j sup_{j-1}/d_{j-1};
-// stored as e_j = 1/d_j at [j][i].
+// stored as e_j = 1/d_j at [i][j].
 __global__ void k_pivots(CoefArgs A)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -204,7 +204,7 @@ __global__ void k_pivots(CoefArgs A)
         prev_sup = A.gh2 * q * ap;
         double den = dre * dre + dim * dim;
         double ere = dre / den, eim = -dim / den;
-        size_t o = (size_t)j * A.Nr + i;
+        size_t o = (size_t)i * N + j;
         if (A.prec == TEUK_FP32) ((float2 *)A.piv)[o] = make_float2((float)ere, (float)eim);
         else ((double2 *)A.piv)[o] = make_double2(ere, eim);
     }

@@ -7,10 +7,10 @@
 //   coef   : r tables   [2Nr-1][NRF] FP64 and [2Nr-1][NRF] T
 //                        (position p = 2i: node i; p = 2i+1: r*_{i+1/2})
 //            theta tables [NTF][Ntheta] FP64 and T
-//            pivots     two tables [Ntheta][Nr] complex T, for implicit
-//                        steps of length dt and dt/2 (theta-major, so the
-//                        threads that solve consecutive rows read
-//                        consecutive addresses)
+//            pivots     two tables [Nr][Ntheta] complex T, for implicit
+//                        steps of length dt and dt/2 (row-major, so the
+//                        lanes that solve one theta row read it with
+//                        contiguous vector loads)
 //            patch      [patch_rows][2][Ntheta] complex T (node, half node)
 //            weights    [Ntheta] FP64
 //            ctl        step counter, CTA ticket, error flags
@@ -63,7 +63,7 @@ template <> struct V2<double> { typedef double2 t; };
 template <typename T> struct ImpConst {
     typedef typename V2<T>::t c2;
     T gh, gh2, h1g, h12g;    // gamma h, (gamma h)^2, (1-gamma) h, (1-2 gamma) h
-    const c2 *piv;           // Thomas pivots of the stage matrix, [Nth][Nr]
+    const c2 *piv;           // Thomas pivots of the stage matrix, [Nr][Nth]
 };
 
 // Everything a step kernel needs, passed by value.
@@ -76,6 +76,7 @@ template <typename T> struct StepParams {
     int first;               // 1: implicit step dt/2 (input is a physical state)
     int imp_only;            // 1: only C_{dt/2} on the tile rows (state output)
     int bulk;                // 1: tile rows move by TMA bulk copies (rows are 16-byte multiples)
+    int vec;                 // 1: theta segments are whole and 16-byte aligned (vector loads)
     int i_ext;               // extraction node
     int wave_cap;            // ring-buffer slots
     int patch_p0, patch_np;  // source patch rows [p0, p0+np); np = 0: no source
@@ -97,6 +98,26 @@ template <typename T> struct StepParams {
 // SDIRK2 constant gamma = 1 - 1/sqrt(2) (Alexander 1977).
 constexpr double kGamma = 0.29289321881345247559915563789515;
 constexpr double kPi = 3.14159265358979323846264338327950;
+
+// Shared-memory carve-up of the split kernel for R = tile_rows + 2 rows of
+// N theta points; every section starts on a 16-byte boundary.
+struct SplitSmem {
+    unsigned phi, pi, sig, rn, rh, th, total;
+};
+__host__ __device__ inline unsigned smem_align16(unsigned x) { return (x + 15u) & ~15u; }
+__host__ __device__ inline SplitSmem split_smem_plan(int R, int N, int tsize)
+{
+    SplitSmem s;
+    const unsigned plane = (unsigned)R * (unsigned)N * 2u * (unsigned)tsize;
+    s.phi = 0;
+    s.pi = smem_align16(plane);
+    s.sig = smem_align16(s.pi + plane);
+    s.rn = smem_align16(s.sig + (unsigned)R * (unsigned)N * (unsigned)tsize);
+    s.rh = smem_align16(s.rn + (unsigned)R * NRF * (unsigned)tsize);
+    s.th = smem_align16(s.rh + (unsigned)(R - 1) * NRF * (unsigned)tsize);
+    s.total = smem_align16(s.th + (unsigned)NTF * (unsigned)N * (unsigned)tsize);
+    return s;
+}
 
 // ---------------------------------------------------------------- host side
 struct Layout {

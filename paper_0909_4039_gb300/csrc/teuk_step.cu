@@ -31,12 +31,25 @@
 namespace teuk {
 namespace {
 
-template <typename T> __device__ __forceinline__ T rcp_(T x);
-template <> __device__ __forceinline__ float rcp_<float>(float x) { return __frcp_rn(x); }
-template <> __device__ __forceinline__ double rcp_<double>(double x) { return __drcp_rn(x); }
-template <typename T> __device__ __forceinline__ T sqrt_(T x);
-template <> __device__ __forceinline__ float sqrt_<float>(float x) { return __fsqrt_rn(x); }
-template <> __device__ __forceinline__ double sqrt_<double>(double x) { return __dsqrt_rn(x); }
+// 1/x and 1/sqrt(x) for coefficients: the hardware approximations in FP32
+// (relative error a few units in the last place, far below the FP32 state's
+// own rounding over a step), correctly rounded operations in FP64.
+template <typename T> __device__ __forceinline__ T rcp_fast(T x);
+template <> __device__ __forceinline__ float rcp_fast<float>(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+template <> __device__ __forceinline__ double rcp_fast<double>(double x) { return __drcp_rn(x); }
+template <typename T> __device__ __forceinline__ T rsq_(T x);
+template <> __device__ __forceinline__ float rsq_<float>(float x)
+{
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+template <> __device__ __forceinline__ double rsq_<double>(double x) { return __drcp_rn(__dsqrt_rn(x)); }
 
 template <typename C> __device__ __forceinline__ C cmk(decltype(C().x) a, decltype(C().x) b)
 {
@@ -65,8 +78,45 @@ template <typename C, typename T> __device__ __forceinline__ C caxpy(T s, C a, C
 }
 template <typename C> __device__ __forceinline__ C cinv(C a)
 {
-    auto d = rcp_(a.x * a.x + a.y * a.y);
+    auto d = rcp_fast(a.x * a.x + a.y * a.y);
     return cmk<C>(a.x * d, -a.y * d);
+}
+
+// ---- 16-byte vector moves between registers and memory.  The address
+// must be 16-byte aligned; S * sizeof(V) must be a multiple of 16.
+template <typename V> struct Q16;
+template <> struct Q16<float> { typedef float4 t; };
+template <> struct Q16<float2> { typedef float4 t; };
+template <> struct Q16<double> { typedef double2 t; };
+template <> struct Q16<double2> { typedef double2 t; };
+__device__ __forceinline__ void unpack16(const float4 &v, float *r) { r[0] = v.x; r[1] = v.y; r[2] = v.z; r[3] = v.w; }
+__device__ __forceinline__ void unpack16(const float4 &v, float2 *r)
+{
+    r[0] = make_float2(v.x, v.y);
+    r[1] = make_float2(v.z, v.w);
+}
+__device__ __forceinline__ void unpack16(const double2 &v, double *r) { r[0] = v.x; r[1] = v.y; }
+__device__ __forceinline__ void unpack16(const double2 &v, double2 *r) { r[0] = v; }
+__device__ __forceinline__ float4 pack16(const float2 *r) { return make_float4(r[0].x, r[0].y, r[1].x, r[1].y); }
+__device__ __forceinline__ double2 pack16(const double2 *r) { return r[0]; }
+
+template <int S, typename V> __device__ __forceinline__ void vload(V *r, const V *src)
+{
+    typedef typename Q16<V>::t Q;
+    constexpr int per = (int)(16 / sizeof(V));
+    static_assert(S % per == 0, "vector load of a partial 16-byte chunk");
+    const Q *q = reinterpret_cast<const Q *>(src);
+#pragma unroll
+    for (int i = 0; i < S / per; ++i) unpack16(q[i], r + i * per);
+}
+template <int S, typename V> __device__ __forceinline__ void vstore(V *dst, const V *r)
+{
+    typedef typename Q16<V>::t Q;
+    constexpr int per = (int)(16 / sizeof(V));
+    static_assert(S % per == 0, "vector store of a partial 16-byte chunk");
+    Q *q = reinterpret_cast<Q *>(dst);
+#pragma unroll
+    for (int i = 0; i < S / per; ++i) q[i] = pack16(r + i * per);
 }
 
 // Local coefficients of the implicit part at node row (table f) and theta j.
@@ -103,10 +153,18 @@ template <typename C> __device__ __forceinline__ C shfl_down_c(C v, int d, int w
     return v;
 }
 
+// Magnitude below which a scan multiplier is dropped: far below the unit
+// roundoff of the state precision (2^-24 in FP32, 2^-53 in FP64).
+template <typename T> struct ScanTol;
+template <> struct ScanTol<float> { static constexpr float v = 1e-10f; };
+template <> struct ScanTol<double> { static constexpr double v = 1e-19; };
+
 // One implicit SDIRK2 step of length h (constants K) on one r* row held in
-// shared memory (phi, pi, sig: element j at [j]; f: the row's r table; th:
-// theta tables), by a group of G consecutive lanes.  Lane g holds the
-// contiguous theta segment [g S, g S + S) in registers.
+// shared memory (phi, pi, sig = 1/Sigma: element j at [j]; f: the row's r table,
+// 16-byte aligned; th: theta tables), by a group of G consecutive lanes.
+// Lane g holds the contiguous theta segment [g S, g S + S) in registers;
+// with vec every segment is whole and 16-byte aligned and moves by vector
+// loads and stores.
 //
 // Stage (I - gamma h J) U = (rPhi, rPi), J u = (Pi, -(B + c0rad) Phi - c_t Pi),
 // B = q A_th, is solved as
@@ -125,84 +183,111 @@ template <typename C> __device__ __forceinline__ C shfl_down_c(C v, int d, int w
 // the grid) take part in the shuffles with neutral data and write zeros.
 template <typename T, int S>
 __device__ void implicit_row_group(const ImpConst<T> &K, typename V2<T>::t *phi, typename V2<T>::t *pi,
-                                   const T *sig, const T *f, const T *th, int N, int Nr, int gi,
-                                   bool active, bool in_tile, int g, int G)
+                                   const T *sig, const T *f, const T *th, int N, int gi, bool active,
+                                   bool in_tile, int g, int G, bool vec)
 {
     typedef typename V2<T>::t c2;
     constexpr int LOGMAX = 5;
     const c2 zero = cmk<c2>(T(0), T(0));
     const c2 one = cmk<c2>(T(1), T(0));
     // Elements past the end of the row (and every element of an inactive
-    // row) are neutral: zero data, e = 1, m = f = 0.  Padded elements only
-    // follow the real ones of a segment and only feed lanes that hold no
-    // real element, so the recurrences need no bounds tests.
+    // row) are neutral: sigma = 0 (so q = c_t = c0rad = 0), zero data, e = 1,
+    // zero angular row.  Padded elements only follow the real ones of a
+    // segment and only feed lanes that hold no real element, so the
+    // recurrences need no bounds tests, and a neutral row solves to zero.
     const int j0 = g * S;
     int len = N - j0;
     len = len < 0 ? 0 : (len > S ? S : len);
+    const int lenw = len;          // real elements of the segment (written back)
     if (!active) len = 0;
-    const int jlast = N - 1;
     const T gh = K.gh, gh2 = K.gh2;
-    const T D = f[RF_DELTA], ctr = f[RF_CTR], cti = f[RF_CTI], ctc = f[RF_CTC], c0r = f[RF_C0R],
-            c0i = f[RF_C0I];
+    T fr[NRF];
+    vload<NRF>(fr, f);
+    const T D = fr[RF_DELTA], ctr = fr[RF_CTR], cti = fr[RF_CTI], ctc = fr[RF_CTC], c0r = fr[RF_C0R],
+            c0i = fr[RF_C0I];
     const T *Cc = th + TF_C * N;
     const T *Am = th + TF_AM * N;
     const T *A0 = th + TF_A0 * N;
     const T *Ap = th + TF_AP * N;
 
-    // per-element coefficients, computed once
-    c2 e[S], m[S], fk[S], ct[S], c0[S], ia1[S], y[S], w[S];
-    T q[S];
+    T sgv[S], ccv[S], am[S], a0[S], ap[S];
+    c2 e[S], w[S], y[S];
+    if (vec && len == S) {
+        vload<S>(sgv, sig + j0);
+        vload<S>(ccv, Cc + j0);
+        vload<S>(am, Am + j0);
+        vload<S>(a0, A0 + j0);
+        vload<S>(ap, Ap + j0);
+        vload<S>(e, K.piv + (size_t)gi * N + j0);
+        vload<S>(w, phi + j0);
+        vload<S>(y, pi + j0);
+    } else {
 #pragma unroll
-    for (int k = 0; k < S; ++k) {
-        if (k < len) {
-            int j = j0 + k;
-            T sg = sig[j];
-            q[k] = D * sg;
-            ct[k] = cmk<c2>(sg * ctr, sg * fma(ctc, Cc[j], cti));
-            c0[k] = cmk<c2>(-sg * c0r, -sg * c0i);
-            ia1[k] = cinv(cmk<c2>(fma(gh, ct[k].x, T(1)), gh * ct[k].y));
-            e[k] = K.piv[(size_t)j * Nr + gi];
-            w[k] = phi[j];
-            y[k] = pi[j];
-        } else {
-            q[k] = T(0);
-            ct[k] = zero;
-            c0[k] = zero;
-            ia1[k] = one;
-            e[k] = one;
-            w[k] = zero;
-            y[k] = zero;
+        for (int k = 0; k < S; ++k) {
+            const bool real = k < len;
+            const int j = real ? j0 + k : 0;
+            sgv[k] = real ? sig[j] : T(0);
+            ccv[k] = real ? Cc[j] : T(0);
+            am[k] = real ? Am[j] : T(0);
+            a0[k] = real ? A0[j] : T(0);
+            ap[k] = real ? Ap[j] : T(0);
+            e[k] = real ? K.piv[(size_t)gi * N + j] : one;
+            w[k] = real ? phi[j] : zero;
+            y[k] = real ? pi[j] : zero;
         }
     }
-    const c2 e_prev = shfl_up_c(e[S - 1], 1, G);   // e_{j0-1} (lane g-1 holds a full segment)
-    T am[S], a0[S], ap[S];
+    // per-element coefficients, computed once.  Row j of B + c0rad is
+    // (qam_j, dg_j, qap_j) = (q AM_j, q A0_j + c0rad_j, q AP_j).
+    c2 m[S], fk[S], ct[S], dg[S], ia1[S];
+    T qam[S], qap[S];
 #pragma unroll
     for (int k = 0; k < S; ++k) {
-        int j = min(j0 + k, jlast);
-        am[k] = Am[j];
-        a0[k] = A0[j];
-        ap[k] = Ap[j];
-        m[k] = cscale<c2>(gh2 * q[k] * am[k], k ? e[k - 1] : e_prev);
-        fk[k] = cscale<c2>(gh2 * q[k] * ap[k], e[k]);
+        const T sg = sgv[k] * sgv[k];
+        const T q = D * sg;
+        ct[k] = cmk<c2>(sg * ctr, sg * fma(ctc, ccv[k], cti));
+        dg[k] = cmk<c2>(fma(q, a0[k], -sg * c0r), -sg * c0i);
+        qam[k] = q * am[k];
+        qap[k] = q * ap[k];
+        ia1[k] = cinv(cmk<c2>(fma(gh, ct[k].x, T(1)), gh * ct[k].y));
     }
-    // multiplicative parts of the segment maps and their scans (matrix only)
-    c2 Afl[LOGMAX], Abl[LOGMAX];
+    const c2 e_prev = shfl_up_c(e[S - 1], 1, G);   // e_{j0-1} (lane g-1 holds a full segment)
+#pragma unroll
+    for (int k = 0; k < S; ++k) {
+        m[k] = cscale<c2>(gh2 * qam[k], k ? e[k - 1] : e_prev);
+        fk[k] = cscale<c2>(gh2 * qap[k], e[k]);
+    }
+    // Multiplicative parts of the segment maps (matrix only): Af0, Ab0 for
+    // the lane's own segment.  Level l of a scan adds, to each lane's value,
+    // a neighbour's value times that level's multiplier (the product of the
+    // segment multipliers it spans).  Once every multiplier of a level is
+    // below ScanTol in magnitude the level adds nothing the state precision
+    // can hold, and neither do the levels above it (their multipliers are
+    // products of these), so the scans stop there: nf levels forward, nb
+    // backward (warp-uniform).  The data scans recompute the multipliers of
+    // the levels they use instead of keeping one per level in registers.
+    c2 Af0 = one, Ab0 = one;
+    int nf = 0, nb = 0;
     {
-        c2 Af = one, Ab = one;
 #pragma unroll
-        for (int k = 0; k < S; ++k) Af = cmul(cmk<c2>(-m[k].x, -m[k].y), Af);
+        for (int k = 0; k < S; ++k) Af0 = cmul(cmk<c2>(-m[k].x, -m[k].y), Af0);
 #pragma unroll
-        for (int k = S - 1; k >= 0; --k) Ab = cmul(cmk<c2>(-fk[k].x, -fk[k].y), Ab);
+        for (int k = S - 1; k >= 0; --k) Ab0 = cmul(cmk<c2>(-fk[k].x, -fk[k].y), Ab0);
+        const T tol2 = ScanTol<T>::v * ScanTol<T>::v;
+        c2 Af = Af0, Ab = Ab0;
+        bool gf = true, gb = true;
 #pragma unroll
         for (int l = 0; l < LOGMAX; ++l) {
-            int d = 1 << l;
-            Afl[l] = Af;
-            Abl[l] = Ab;
-            if (d < G) {
-                c2 Ao = shfl_up_c(Af, d, G), Bo = shfl_down_c(Ab, d, G);
-                if (g >= d) Af = cmul(Af, Ao);
-                if (g + d < G) Ab = cmul(Ab, Bo);
-            }
+            const int d = 1 << l;
+            if (d >= G) break;
+            gf = gf && __any_sync(0xffffffffu, g >= d && fma(Af.x, Af.x, Af.y * Af.y) > tol2);
+            gb = gb && __any_sync(0xffffffffu, g + d < G && fma(Ab.x, Ab.x, Ab.y * Ab.y) > tol2);
+            if (!gf && !gb) break;
+            if (gf) nf = l + 1;
+            if (gb) nb = l + 1;
+            if (2 * d >= G) break;
+            const c2 Ao = shfl_up_c(Af, d, G), Bo = shfl_down_c(Ab, d, G);
+            if (gf && g >= d) Af = cmul(Af, Ao);
+            if (gb && g + d < G) Ab = cmul(Ab, Bo);
         }
     }
 
@@ -212,11 +297,20 @@ __device__ void implicit_row_group(const ImpConst<T> &K, typename V2<T>::t *phi,
 #pragma unroll
         for (int k = 0; k < S; ++k) B = csub(w[k], cmul(m[k], B));
 #pragma unroll
-        for (int l = 0; l < LOGMAX; ++l) {
-            int d = 1 << l;
-            if (d < G) {
-                c2 Bo = shfl_up_c(B, d, G);
-                if (g >= d) B = cadd(cmul(Afl[l], Bo), B);
+        {
+            c2 A = Af0;
+#pragma unroll
+            for (int l = 0; l < LOGMAX; ++l) {
+                if (l < nf) {
+                    const int d = 1 << l;
+                    const bool more = l + 1 < nf;
+                    c2 Bo = shfl_up_c(B, d, G), Ao = one;
+                    if (more) Ao = shfl_up_c(A, d, G);
+                    if (g >= d) {
+                        B = cadd(cmul(A, Bo), B);
+                        if (more) A = cmul(A, Ao);
+                    }
+                }
             }
         }
         c2 z = shfl_up_c(B, 1, G);
@@ -230,11 +324,20 @@ __device__ void implicit_row_group(const ImpConst<T> &K, typename V2<T>::t *phi,
 #pragma unroll
         for (int k = S - 1; k >= 0; --k) B = csub(w[k], cmul(fk[k], B));
 #pragma unroll
-        for (int l = 0; l < LOGMAX; ++l) {
-            int d = 1 << l;
-            if (d < G) {
-                c2 Bo = shfl_down_c(B, d, G);
-                if (g + d < G) B = cadd(cmul(Abl[l], Bo), B);
+        {
+            c2 A = Ab0;
+#pragma unroll
+            for (int l = 0; l < LOGMAX; ++l) {
+                if (l < nb) {
+                    const int d = 1 << l;
+                    const bool more = l + 1 < nb;
+                    c2 Bo = shfl_down_c(B, d, G), Ao = one;
+                    if (more) Ao = shfl_down_c(A, d, G);
+                    if (g + d < G) {
+                        B = cadd(cmul(A, Bo), B);
+                        if (more) A = cmul(A, Ao);
+                    }
+                }
             }
         }
         c2 x = shfl_down_c(B, 1, G);
@@ -254,8 +357,7 @@ __device__ void implicit_row_group(const ImpConst<T> &K, typename V2<T>::t *phi,
         for (int k = 0; k < S; ++k) {
             c2 xm = k ? w[k - 1] : xl;
             c2 xp = (k + 1 < S) ? w[(k + 1) < S ? k + 1 : S - 1] : xr;
-            c2 v = cadd(cadd(cscale<c2>(am[k], xm), cscale<c2>(a0[k], w[k])), cscale<c2>(ap[k], xp));
-            bf[k] = cadd(cscale<c2>(q[k], v), cmul(c0[k], w[k]));
+            bf[k] = cadd(cmul(dg[k], w[k]), caxpy(qap[k], xp, cscale<c2>(qam[k], xm)));
         }
     };
 
@@ -287,24 +389,29 @@ __device__ void implicit_row_group(const ImpConst<T> &K, typename V2<T>::t *phi,
 #pragma unroll
         for (int k = 0; k < S; ++k) y[k] = cmul(csub(y[k], cscale<c2>(gh, bf[k])), ia1[k]);
     }
-    if (in_tile) {
-        int lenw = N - j0;
-        lenw = lenw < 0 ? 0 : (lenw > S ? S : lenw);
+    if (in_tile && lenw > 0) {
+        if (vec) {
+            vstore<S>(phi + j0, w);
+            vstore<S>(pi + j0, y);
+        } else {
 #pragma unroll
-        for (int k = 0; k < S; ++k) {
-            if (k < lenw) {
-                phi[j0 + k] = active ? w[k] : zero;
-                pi[j0 + k] = active ? y[k] : zero;
+            for (int k = 0; k < S; ++k) {
+                if (k < lenw) {
+                    phi[j0 + k] = w[k];
+                    pi[j0 + k] = y[k];
+                }
             }
         }
     }
 }
 
-// b and K at one point from the r table f and theta tables (S2 = sin^2, C = cos).
+// b and K at one point from the r table f, rs = 1/Sigma and the theta
+// tables (S2 = sin^2, C = cos).
 template <typename T>
-__device__ __forceinline__ void bK(const T *f, T sg, T S2, T C, T &b, typename V2<T>::t &K)
+__device__ __forceinline__ void bK(const T *f, T rs, T S2, T C, T &b, typename V2<T>::t &K)
 {
-    b = f[RF_R] * sqrt_(sg);
+    const T sg = rs * rs;
+    b = f[RF_R] * rs;
     T kre = fma(b, f[RF_CTR], f[RF_CSR] - f[RF_E1]) + sg * fma(-f[RF_E3], S2, f[RF_E2]);
     T kim = fma(b, fma(f[RF_CTC], C, f[RF_CTI]), f[RF_CSI]);
     K.x = sg * kre;
@@ -321,6 +428,11 @@ __device__ __forceinline__ typename V2<T>::t patch_val(const StepParams<T> &p, i
     c2 v = p.patch[((size_t)pr * 2 + pos) * p.Nth + j];
     return cmul(v, phase);
 }
+
+// The Lax-Wendroff phase reads the first 12 fields of an r-table entry.
+static_assert(RF_R < 12 && RF_R2 < 12 && RF_AD < 12 && RF_CTR < 12 && RF_CTI < 12 && RF_CTC < 12 &&
+                  RF_CSR < 12 && RF_CSI < 12 && RF_E1 < 12 && RF_E2 < 12 && RF_E3 < 12,
+              "r-table fields used by the Lax-Wendroff phase must lie in its first 12 entries");
 
 // Split-scheme Lax-Wendroff update (Eqs. 13-14 with S = F + K Phi_{r*}) of
 // tile rows [ra, rb) in theta column j, in place.  (pf, pg) is the old value
@@ -347,11 +459,12 @@ __device__ void lw_segment(const StepParams<T> &p, typename V2<T>::t *sPhi, type
             mg = zero;
             return;
         }
-        const T *f = sRh + k * NRF;
-        T sg = rcp_(fma(-f[RF_AD], S2, f[RF_R2]));
+        T f[12];   // fields R .. E3 of the half-node entry
+        vload<12>(f, sRh + k * NRF);
+        T rs = rsq_(fma(-f[RF_AD], S2, f[RF_R2]));
         T b;
         c2 K;
-        bK<T>(f, sg, S2, C, b, K);
+        bK<T>(f, rs, S2, C, b, K);
         c2 fbar = cscale<c2>(T(0.5), cadd(fa, fb));
         c2 gbar = cscale<c2>(T(0.5), cadd(ga, gb));
         c2 df = cscale<c2>(ri, csub(fb, fa));
@@ -381,11 +494,12 @@ __device__ void lw_segment(const StepParams<T> &p, typename V2<T>::t *sPhi, type
         c2 nfv = zero, ngv = zero;
         if (gi >= 1 && gi <= Nr - 2) {
             // Eq. 14 at node gi
-            const T *f = sRn + lr * NRF;
-            T sg = sSig[lr * P + j];
+            T f[12];   // fields R .. E3 of the node entry
+            vload<12>(f, sRn + lr * NRF);
+            T rs = sSig[lr * P + j];
             T b;
             c2 K;
-            bK<T>(f, sg, S2, C, b, K);
+            bK<T>(f, rs, S2, C, b, K);
             c2 df = cscale<c2>(ri, csub(mf, mfp));
             c2 dg = cscale<c2>(ri, csub(mg, mgp));
             c2 Sv = cmul(K, df);
@@ -488,27 +602,40 @@ template <typename T, int S>
 __global__ void __launch_bounds__(256, (sizeof(T) == 4 && S <= 4) ? 2 : 1) k_split_step(const StepParams<T> p)
 {
     typedef typename V2<T>::t c2;
+    constexpr int kMaxChunks = 8;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double2 sph[2];
     __shared__ long long s_n;
-    __shared__ __align__(8) unsigned long long s_mbar;
+    __shared__ __align__(8) unsigned long long s_mbar[kMaxChunks];
     const int Nr = p.Nr, N = p.Nth, TR = p.tile_rows, R = TR + 2, P = p.pitch;
     const int tid = threadIdx.x, NT = blockDim.x;
     const int i0 = blockIdx.x * TR;
     const int G = p.group;
 
-    c2 *sPhi = (c2 *)smem_raw;
-    c2 *sPi = sPhi + R * P;
-    T *sSig = (T *)(sPi + R * P);
-    T *sRn = sSig + R * P;
-    T *sRh = sRn + R * NRF;
-    T *sTh = sRh + (R - 1) * NRF;
+    const SplitSmem plan = split_smem_plan(R, N, (int)sizeof(T));
+    c2 *sPhi = (c2 *)(smem_raw + plan.phi);
+    c2 *sPi = (c2 *)(smem_raw + plan.pi);
+    T *sSig = (T *)(smem_raw + plan.sig);
+    T *sRn = (T *)(smem_raw + plan.rn);
+    T *sRh = (T *)(smem_raw + plan.rh);
+    T *sTh = (T *)(smem_raw + plan.th);
 
     const bool src = !p.imp_only && p.patch_np > 0 && i0 + TR >= p.patch_p0 &&
                      i0 - 1 <= p.patch_p0 + p.patch_np;
     if (tid == 0) {
         long long n = *((volatile long long *)&p.ctl->step);
         s_n = n;
+        if (!p.imp_only) {
+            // The last CTA to read the step index advances it.  Later kernels
+            // on the stream see the new value; no CTA of this launch reads it
+            // again, so no CTA has to wait for its own stores first.
+            __threadfence();
+            unsigned t = atomicAdd(&p.ctl->ticket, 1u);
+            if (t == gridDim.x - 1) {
+                p.ctl->ticket = 0u;
+                p.ctl->step = n + 1;
+            }
+        }
         if (src) {
             double t = (double)n * p.dt64;
             sph[0] = phase_at(p.mOmega, t);
@@ -524,13 +651,28 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && S <= 4) ? 2 : 1) k_spl
     const int ga = i0 - 1 < 0 ? 0 : i0 - 1;
     const int gb = i0 + TR > Nr - 1 ? Nr - 1 : i0 + TR;
     const int la = ga - (i0 - 1), nrows = gb - ga + 1;
+    // The state tile arrives in chunks of whole implicit passes, one mbarrier
+    // each, so that the first pass can start while later rows are in flight.
+    const int rpp = NT / G;   // theta rows per implicit pass
+    int cr = rpp;             // rows per chunk
+    while ((R + cr - 1) / cr > kMaxChunks) cr += rpp;
+    const int nch = (R + cr - 1) / cr;
     if (p.bulk) {
         if (tid == 0) {
-            mbar_init(&s_mbar, 1);
-            unsigned bytes = (unsigned)nrows * (unsigned)N * (unsigned)sizeof(c2);
-            mbar_expect_tx(&s_mbar, 2 * bytes);
-            bulk_g2s(sPhi + la * P, p.uin + (size_t)ga * N, bytes, &s_mbar);
-            bulk_g2s(sPi + la * P, p.uin + ((size_t)Nr + ga) * N, bytes, &s_mbar);
+            for (int c = 0; c < nch; ++c) mbar_init(&s_mbar[c], 1);
+            for (int c = 0; c < nch; ++c) {
+                int r0 = c * cr, r1 = r0 + cr;
+                if (r1 > R) r1 = R;
+                if (r0 < la) r0 = la;
+                if (r1 > la + nrows) r1 = la + nrows;
+                unsigned bytes = r1 > r0 ? (unsigned)(r1 - r0) * (unsigned)N * (unsigned)sizeof(c2) : 0u;
+                mbar_expect_tx(&s_mbar[c], 2 * bytes);   // with no bytes this is a plain arrival
+                if (bytes) {
+                    const size_t g0 = (size_t)(ga + r0 - la);
+                    bulk_g2s(sPhi + r0 * P, p.uin + g0 * N, bytes, &s_mbar[c]);
+                    bulk_g2s(sPi + r0 * P, p.uin + ((size_t)Nr + g0) * N, bytes, &s_mbar[c]);
+                }
+            }
         }
         // rows off the grid (first and last tile only) are zero
         for (int lr = t_lr, j = t_j; lr < R;) {
@@ -569,43 +711,52 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && S <= 4) ? 2 : 1) k_spl
     }
     for (int idx = tid; idx < NTF * N; idx += NT) sTh[idx] = p.thtab[idx];
     __syncthreads();
-    // 1/Sigma^2 at the node rows, while the state tile is in flight
+    // 1/Sigma at the node rows, while the state tile is in flight
     for (int lr = t_lr, j = t_j; lr < R;) {
         int gi = i0 - 1 + lr;
         T v = T(0);
-        if (gi >= 0 && gi < Nr) v = rcp_(fma(-sRn[lr * NRF + RF_AD], sTh[TF_S2 * N + j], sRn[lr * NRF + RF_R2]));
+        if (gi >= 0 && gi < Nr) v = rsq_(fma(-sRn[lr * NRF + RF_AD], sTh[TF_S2 * N + j], sRn[lr * NRF + RF_R2]));
         sSig[lr * P + j] = v;
         lr += d_lr;
         j += d_j;
         if (j >= N) { j -= N; ++lr; }
     }
-    {
-        // all threads agree on the outcome of the bounded wait before acting on it
-        int ok = p.bulk ? (int)mbar_wait(&s_mbar, 0, kWaitLimit) : 1;
-        if (!__syncthreads_and(ok)) {
-            // the copy did not complete: report, wait once more, leave the tile alone
-            if (tid == 0) atomicOr(&p.ctl->flags, FLAG_TIMEOUT);
-            mbar_wait(&s_mbar, 0, kWaitLimit);
-            return;
-        }
-    }
+    __syncthreads();
     // ---- B: implicit step on the tile rows (all R rows; only rows 1..TR with imp_only)
+    int ok = 1;   // every bounded wait of this thread succeeded
     {
         const ImpConst<T> &K = (p.first || p.imp_only) ? p.half : p.full;
-        const int rows_per_pass = NT / G;
         const int lo = p.imp_only ? 1 : 0, hi = p.imp_only ? TR + 1 : R;
         const int g = tid % G;
-        for (int base = lo; base < hi; base += rows_per_pass) {
+        const bool vec = p.vec != 0;
+        for (int base = lo; base < hi; base += rpp) {
+            if (p.bulk && ok) {
+                // the chunks that hold this pass's rows
+                int last = base + rpp - 1;
+                if (last > hi - 1) last = hi - 1;
+                for (int c = base / cr; c <= last / cr; ++c) ok &= (int)mbar_wait(&s_mbar[c], 0, kWaitLimit);
+            }
             int lr = base + tid / G;
             bool in_tile = lr < hi;
             int gi = i0 - 1 + lr;
             bool active = in_tile && gi >= 1 && gi <= Nr - 2;
             int lrc = in_tile ? lr : lo;
             implicit_row_group<T, S>(K, sPhi + lrc * P, sPi + lrc * P, sSig + lrc * P, sRn + lrc * NRF, sTh, N,
-                                     Nr, active ? gi : 1, active, in_tile, g, G);
+                                     active ? gi : 1, active, in_tile, g, G, vec);
         }
+        // the remaining phases read every row of the tile
+        if (p.bulk && ok)
+            for (int c = 0; c < nch; ++c) ok &= (int)mbar_wait(&s_mbar[c], 0, kWaitLimit);
     }
-    __syncthreads();
+    // all threads agree on the outcome of the bounded waits before acting on it
+    if (!__syncthreads_and(ok)) {
+        // a copy did not complete: report, wait once more, leave the tile alone
+        if (tid == 0) {
+            atomicOr(&p.ctl->flags, FLAG_TIMEOUT);
+            for (int c = 0; c < nch; ++c) mbar_wait(&s_mbar[c], 0, kWaitLimit);
+        }
+        return;
+    }
     if (!p.imp_only) {
         // ---- C: Lax-Wendroff on the output rows; NSEG row segments per column
         c2 ph1 = zero, ph2 = zero;
@@ -661,10 +812,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && S <= 4) ? 2 : 1) k_spl
             if (j >= N) { j -= N; ++k; }
         }
     }
-    if (p.imp_only) {
-        if (p.bulk && tid == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
-        return;
-    }
+    if (p.imp_only) return;
     // ---- E: physical sample u_{n+1} = C_{dt/2} s_{n+1} on the extraction row
     const bool ext = p.i_ext >= i0 && p.i_ext < i0 + TR && p.i_ext < Nr;
     if (ext) {
@@ -673,21 +821,10 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && S <= 4) ? 2 : 1) k_spl
         if (tid < 32) {
             bool mine = tid < G;
             bool active = mine && p.i_ext >= 1 && p.i_ext <= Nr - 2;
-            implicit_row_group<T, S>(p.half, sPhi + lr * P, sPi + lr * P, sSig + lr * P, sRn + lr * NRF, sTh, N, Nr,
-                                     active ? p.i_ext : 1, active, mine, tid % G, G);
+            implicit_row_group<T, S>(p.half, sPhi + lr * P, sPi + lr * P, sSig + lr * P, sRn + lr * NRF, sTh, N,
+                                     active ? p.i_ext : 1, active, mine, tid % G, G, p.vec != 0);
             __syncwarp();
             extract_warp<T>(p, sPhi + lr * P, s_n + 1);
-        }
-    }
-    __syncthreads();
-    if (tid == 0) {
-        if (p.bulk) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");   // stores complete
-        __threadfence();
-        unsigned t = atomicAdd(&p.ctl->ticket, 1u);
-        if (t == gridDim.x - 1) {
-            p.ctl->step = s_n + 1;
-            p.ctl->ticket = 0u;
-            __threadfence();
         }
     }
 }
@@ -705,10 +842,10 @@ __device__ __forceinline__ typename V2<T>::t literal_SPi(const StepParams<T> &p,
     typedef typename V2<T>::t c2;
     const int N = p.Nth;
     T S2 = th[TF_S2 * N + j], C = th[TF_C * N + j];
-    T sg = rcp_(fma(-f[RF_AD], S2, f[RF_R2]));
+    T rs = rsq_(fma(-f[RF_AD], S2, f[RF_R2]));
     c2 K;
-    bK<T>(f, sg, S2, C, b, K);
-    Loc<T> L = local_coef<T>(sg, f, C, T(0));
+    bK<T>(f, rs, S2, C, b, K);
+    Loc<T> L = local_coef<T>(rs * rs, f, C, T(0));
     c2 aphi = cadd(cadd(cscale<c2>(th[TF_AM * N + j], phm), cscale<c2>(th[TF_A0 * N + j], ph0)),
                    cscale<c2>(th[TF_AP * N + j], php));
     c2 S = cmul(K, dphi);
@@ -880,9 +1017,7 @@ __global__ void k_from_f32(const float2 *src, double2 *dst, size_t n)
 template <typename T>
 size_t split_smem_bytes(int tile_rows, int Nth)
 {
-    size_t R = (size_t)tile_rows + 2, P = (size_t)Nth;
-    return R * P * (2 * sizeof(typename V2<T>::t) + sizeof(T)) + (R + (R - 1)) * NRF * sizeof(T) +
-           (size_t)NTF * Nth * sizeof(T);
+    return split_smem_plan(tile_rows + 2, Nth, (int)sizeof(T)).total;
 }
 
 int implicit_seg(int Nth) { return Nth <= 128 ? kSegNarrow : (Nth <= 256 ? kSeg : kSegWide); }
