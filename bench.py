@@ -101,12 +101,12 @@ class ClockSampler:
                 "power_w_max": max(power) if power else None}
 
 
-def _profiled_traffic():
+def _profiled_traffic(kernel: str):
     """DRAM bytes per launch of the step kernel from the committed ncu summary,
     only while the kernel source is the one that was profiled."""
     import hashlib
     import re
-    md = os.path.join(ROOT, "profiles", "k_split_step_16384x128_fp32.md")
+    md = os.path.join(ROOT, "profiles", f"{kernel}_16384x128_fp32.md")
     src = os.path.join(ROOT, "paper_0909_4039_gb300", "csrc", "teuk_step.cu")
     try:
         text = open(md).read()
@@ -237,10 +237,21 @@ def run_native(args):
                       dt=w.cfl * drs, rstar_extract=w.rs_ext, precision=prec, device=dev,
                       wave_capacity=args.steps + args.warmup + 8)
     st.set_source(w.amp, w.r0, w.sig_r, w.sig_th)
-    tile_rows = st.autotune(20)
-    tiling = st.tiling()
-    stream = st.stream
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    if args.kernel == "auto":
+        # the timed steps start from a cold L2, so the configuration is chosen that way too
+        st.autotune(20, flush=flush)
+        tiling_source = ("teuk_autotune_cold (the 4 model-best configurations of each kernel, "
+                         "20 L2-flushed steps each)")
+    elif args.kernel == "tiled":
+        st.set_tiling(args.tile_rows)
+        tiling_source = "fixed by --kernel tiled"
+    else:
+        st.set_persistent(args.tile_rows, args.consumers)
+        tiling_source = "fixed by --kernel persistent"
+    tiling = st.tiling()
+    kernel = "k_split_persist" if tiling.get("persistent") else "k_split_step"
+    stream = st.stream
     pts = w.Nr * w.Ntheta
 
     def barrier():
@@ -328,11 +339,11 @@ def run_native(args):
                                f"Gaussian orbit source r0=6; {prec} state, FP64 coefficients/time/extraction",
                    "l2": "flushed between timed steps (256 MB write, outside the events)",
                    "parallelism": f"replicas x{ws}", "tiling": tiling,
-                   "tiling_source": "teuk_autotune (6 model-ranked tile heights timed for 20 steps)"},
+                   "tiling_source": tiling_source},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak,
-                     "traffic": _profiled_traffic() if prec == "fp32" else None,
-                     "kernel": "k_split_step", "bytes_per_point": bytes_per_pt,
+                     "traffic": _profiled_traffic(kernel) if prec == "fp32" else None,
+                     "kernel": kernel, "bytes_per_point": bytes_per_pt,
                      "peak_source": f"{peak_src} hbm_gbs (copy, burst)",
                      "median_kernel_us": med_kernel_s * 1e6,
                      "alu": {"flops_per_point": FLOPS_PER_POINT,
@@ -365,6 +376,10 @@ def main():
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--kernel", choices=["auto", "tiled", "persistent"], default="auto",
+                    help="auto: measured choice (cold-L2 autotune); otherwise the given kernel")
+    ap.add_argument("--tile-rows", type=int, default=28, help="tile height for --kernel tiled/persistent")
+    ap.add_argument("--consumers", type=int, default=480, help="consumer threads for --kernel persistent")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

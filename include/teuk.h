@@ -163,19 +163,43 @@ int teuk_extract_waveform(teuk_ctx *ctx, int64_t first_step, int64_t count,
  * that share one theta row in the implicit solve.  Any pointer may be NULL. */
 int teuk_tiling(const teuk_ctx *ctx, int *tile_rows, int *threads, size_t *smem_bytes, int *group);
 
-/* Measured tile autotuner.  Ranks the tile heights that fit on the device
- * by a wave-quantisation cost model, times the best six for trial_steps
- * steps each on this grid (CUDA events on `stream`), and keeps the fastest.
- * The trials overwrite the state: afterwards the field is zero at step 0
- * and the waveform ring buffer is empty (the source and weights are kept).
- * Call it right after teuk_init_grid / teuk_set_source.  Synchronous.
- * *tile_rows_out (may be NULL) receives the chosen tile height. */
+/* Which split-scheme kernel steps the grid.  *persistent = 1: the
+ * persistent kernel (one CTA per SM walks the tiles; a producer warp moves
+ * them by TMA into two shared-memory buffers while *consumer_threads threads
+ * compute, so tile loads and stores overlap the arithmetic); 0: the tiled
+ * kernel (one CTA per tile).  *grid is the number of CTAs per step.  Any
+ * pointer may be NULL.  For the literal scheme *persistent = 0. */
+int teuk_kernel_config(const teuk_ctx *ctx, int *persistent, int *consumer_threads, int *grid);
+
+/* Measured tile autotuner.  Ranks the launch configurations that fit on the
+ * device (tile heights of the tiled kernel and tile height x consumer count
+ * of the persistent kernel) by a wave-quantisation cost model, times the
+ * best four of each kernel for trial_steps steps each on this grid (CUDA
+ * events on `stream`), and keeps the fastest.  The trials overwrite the
+ * state: afterwards the field is zero at step 0 and the waveform ring buffer
+ * is empty (the source and weights are kept).  Call it right after
+ * teuk_init_grid / teuk_set_source.  Synchronous.  *tile_rows_out (may be
+ * NULL) receives the chosen tile height. */
 int teuk_autotune(teuk_ctx *ctx, int trial_steps, void *stream, int *tile_rows_out);
 
-/* Set the tile height (r* output rows per CTA) of the split-scheme kernel
- * by hand; TEUK_E_INVAL if such a tile does not fit in shared memory.  The
- * result of a step does not depend on the tile height. */
+/* teuk_autotune for steps that start from a cold L2 (state larger than L2,
+ * or a caller that evicts it between steps): before every timed trial step
+ * the caller-owned device buffer d_flush (flush_bytes, larger than the L2)
+ * is overwritten, outside the timed interval.  Same outcome otherwise. */
+int teuk_autotune_cold(teuk_ctx *ctx, int trial_steps, void *d_flush, size_t flush_bytes, void *stream,
+                       int *tile_rows_out);
+
+/* Select the tiled split-scheme kernel with the given tile height (r*
+ * output rows per CTA) by hand; TEUK_E_INVAL if such a tile does not fit in
+ * shared memory.  The result of a step depends on neither the kernel nor
+ * the tile height. */
 int teuk_set_tiling(teuk_ctx *ctx, int tile_rows);
+
+/* Select the persistent split-scheme kernel with the given tile height and
+ * consumer_threads in {384, 480}.  It exists for the FP32 state with
+ * Ntheta <= 128 whose theta rows are 16-byte multiples; TEUK_E_INVAL
+ * otherwise, or if the two tile buffers do not fit in shared memory. */
+int teuk_set_persistent(teuk_ctx *ctx, int tile_rows, int consumer_threads);
 
 /* One literal-scheme step (all of S inside the two Lax-Wendroff stages)
  * that allocates nothing and needs no caller-allocated scratch.  The paper

@@ -9,6 +9,7 @@
 #include <string.h>
 
 #include <new>
+#include <vector>
 
 #include "teuk_internal.cuh"
 
@@ -42,9 +43,14 @@ struct teuk_ctx {
     // source
     int patch_p0, patch_np;
     double mOmega;
-    // launch configuration
+    // launch configuration: tiled kernel (tile_rows, threads, smem) or the
+    // persistent kernel (persist = 1: nc consumer threads, grid CTAs,
+    // persist_smem); the tiled kernel at the same tile height also serves
+    // the state output (C_{dt/2} only)
     int tile_rows, threads;
     size_t smem;
+    int persist, nc, grid;
+    size_t persist_smem;
     // graphs, one per starting level
     cudaGraphExec_t graph[2];
     cudaStream_t graph_stream[2];
@@ -178,45 +184,99 @@ double host_atheta_bound(const teuk_grid_desc &d)
     return lam;
 }
 
-// Tile height of the split kernel.  A tile of R = TR + 2 rows costs about
-// 0.6 Rpad + 0.4 R + 4 row-times, where Rpad rounds R up to whole passes of
-// the implicit phase (256 threads / G rows per pass) and the 4 stands for
-// load latency and barriers; k CTAs share an SM, so one wave costs k times
-// that and the grid needs ceil(tiles / (k SMs)) waves.  Minimise the product
-// over R, with a 20 % penalty for k = 1 (no second CTA to overlap memory
-// with compute).
+// Launch configurations of the split step and their model cost.
+//
+// Tiled kernel (256 threads, one tile per CTA): a tile of R = TR + 2 rows
+// costs about 0.6 Rpad + 0.4 R + 4 row-times, where Rpad rounds R up to
+// whole passes of the implicit phase (256 threads / G rows per pass) and the
+// 4 stands for load latency and barriers; k CTAs share an SM, so one wave
+// costs k times that and the grid needs ceil(tiles / (k SMs)) waves, with a
+// 20 % penalty for k = 1 (no second CTA to overlap memory with compute).
+//
+// Persistent kernel (nc consumer threads + a producer warp, one CTA per SM,
+// tiles double-buffered): a CTA computes ceil(tiles / grid) tiles of
+// (0.6 Rpad + 0.4 R) (256 / nc) row-times each (Rpad in passes of nc / G
+// rows), plus the first tile's load.
 struct TileCand {
     double cost;
     int R;
+    int persist, nc, grid;
     size_t smem;
 };
 
-// All tile heights that fit, with their model cost, best first.
-int tile_candidates(teuk_ctx *c, TileCand *out, int maxn)
+static int sm_count()
 {
-    int N = (int)c->d.Ntheta;
-    bool f32 = c->d.precision == TEUK_FP32;
-    const int threads = 256;
     int dev = 0, nsm = 152;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     cudaGetLastError();
+    return nsm;
+}
+
+// A tiled-kernel candidate of height TR (false if it does not fit).
+static bool tiled_cand(const teuk_ctx *c, int TR, int nsm, TileCand *out)
+{
+    const int N = (int)c->d.Ntheta;
+    const bool f32 = c->d.precision == TEUK_FP32;
+    const int threads = 256, R = TR + 2;
+    size_t sm = f32 ? split_smem_bytes<float>(TR, N) : split_smem_bytes<double>(TR, N);
+    if (sm > 227 * 1024) return false;
+    int k = f32 ? split_blocks_per_sm<float>(N, threads, sm) : split_blocks_per_sm<double>(N, threads, sm);
+    if (k < 1) return false;
+    const long long Nr = c->d.Nr;
+    long long tiles = (Nr + TR - 1) / TR;
+    long long waves = (tiles + (long long)k * nsm - 1) / ((long long)k * nsm);
+    int rpp = threads / implicit_group(N);
+    int rpad = ((R + rpp - 1) / rpp) * rpp;
+    double rows = 0.6 * rpad + 0.4 * R + 4.0;
+    out->cost = (double)waves * k * rows * (k == 1 ? 1.2 : 1.0);
+    out->R = R;
+    out->persist = 0;
+    out->nc = 0;
+    out->grid = (int)tiles;
+    out->smem = sm;
+    return true;
+}
+
+// A persistent-kernel candidate of height TR with nc consumer threads.
+static bool persist_cand(const teuk_ctx *c, int TR, int nc, int nsm, TileCand *out)
+{
+    const int N = (int)c->d.Ntheta;
+    const bool f32 = c->d.precision == TEUK_FP32;
+    const bool ok = f32 ? persist_available<float>(N, nc) : persist_available<double>(N, nc);
+    if (!ok) return false;
+    if (((size_t)N * (f32 ? sizeof(float2) : sizeof(double2))) % 16 != 0) return false;   // rows move by TMA
+    const int R = TR + 2;
+    size_t sm = f32 ? persist_smem_bytes<float>(TR, N) : persist_smem_bytes<double>(TR, N);
+    if (sm > 227 * 1024) return false;
+    int k = f32 ? persist_blocks_per_sm<float>(N, nc, sm) : persist_blocks_per_sm<double>(N, nc, sm);
+    if (k < 1) return false;
+    const long long Nr = c->d.Nr;
+    long long tiles = (Nr + TR - 1) / TR;
+    long long grid = tiles < (long long)k * nsm ? tiles : (long long)k * nsm;
+    long long per = (tiles + grid - 1) / grid;
+    int rpp = nc / implicit_group(N);
+    int rpad = ((R + rpp - 1) / rpp) * rpp;
+    double rows = (0.6 * rpad + 0.4 * R) * 256.0 / nc;
+    out->cost = (double)per * k * rows + 4.0;
+    out->R = R;
+    out->persist = 1;
+    out->nc = nc;
+    out->grid = (int)grid;
+    out->smem = sm;
+    return true;
+}
+
+// All launch configurations that fit, best model cost first.
+int tile_candidates(teuk_ctx *c, TileCand *out, int maxn)
+{
+    const int nsm = sm_count();
     const long long Nr = c->d.Nr;
     int n = 0;
-    for (int R = 4; R <= 256 && n < maxn; ++R) {
-        size_t sm = f32 ? split_smem_bytes<float>(R - 2, N) : split_smem_bytes<double>(R - 2, N);
-        if (sm > 227 * 1024) break;
-        int k = f32 ? split_blocks_per_sm<float>(N, threads, sm) : split_blocks_per_sm<double>(N, threads, sm);
-        if (k < 1) break;
-        long long tiles = (Nr + (R - 2) - 1) / (R - 2);
-        long long waves = (tiles + (long long)k * nsm - 1) / ((long long)k * nsm);
-        int rpp = threads / implicit_group(N);
-        int rpad = ((R + rpp - 1) / rpp) * rpp;
-        double rows = 0.6 * rpad + 0.4 * R + 4.0;
-        out[n].cost = (double)waves * k * rows * (k == 1 ? 1.2 : 1.0);
-        out[n].R = R;
-        out[n].smem = sm;
-        ++n;
-        if (tiles <= 1) break;
+    for (int TR = 2; TR <= 254 && n < maxn; ++TR) {
+        if (tiled_cand(c, TR, nsm, &out[n])) ++n;
+        for (int nc : {384, 480})
+            if (n < maxn && persist_cand(c, TR, nc, nsm, &out[n])) ++n;
+        if (TR >= Nr) break;
     }
     // insertion sort by cost
     for (int a = 1; a < n; ++a)
@@ -228,15 +288,30 @@ int tile_candidates(teuk_ctx *c, TileCand *out, int maxn)
     return n;
 }
 
+// Make candidate k the launch configuration.  The tiled kernel at the same
+// height must fit too: it applies C_{dt/2} for the state output.
+static bool apply_cand(teuk_ctx *c, const TileCand &k)
+{
+    const int TR = k.R - 2;
+    TileCand t;
+    if (!tiled_cand(c, TR, sm_count(), &t)) return false;
+    c->tile_rows = TR;
+    c->threads = 256;
+    c->smem = t.smem;
+    c->persist = k.persist;
+    c->nc = k.persist ? k.nc : 0;
+    c->grid = k.persist ? k.grid : 0;
+    c->persist_smem = k.persist ? k.smem : 0;
+    return true;
+}
+
 int choose_tiles(teuk_ctx *c)
 {
-    TileCand cand[256];
-    int n = tile_candidates(c, cand, 256);
-    if (n == 0) return set_err(c, TEUK_E_CUDA, "no tile of the split kernel fits on this device%s");
-    c->tile_rows = cand[0].R - 2;
-    c->threads = 256;
-    c->smem = cand[0].smem;
-    return TEUK_OK;
+    std::vector<TileCand> cand(1024);
+    int n = tile_candidates(c, cand.data(), (int)cand.size());
+    for (int k = 0; k < n; ++k)
+        if (apply_cand(c, cand[k])) return TEUK_OK;
+    return set_err(c, TEUK_E_CUDA, "no tile of the split kernel fits on this device%s");
 }
 
 template <typename T>
@@ -287,16 +362,21 @@ StepParams<T> make_params(const teuk_ctx *c, int in_level)
     return p;
 }
 
+template <typename T>
+cudaError_t launch_split(const teuk_ctx *c, const StepParams<T> &p, cudaStream_t st)
+{
+    if (c->persist) return launch_split_persist<T>(p, c->nc, c->grid, c->persist_smem, st);
+    return launch_split_step<T>(p, c->threads, c->smem, st);
+}
+
 cudaError_t launch_one(teuk_ctx *c, int in_level, cudaStream_t st)
 {
     if (c->d.precision == TEUK_FP32) {
         StepParams<float> p = make_params<float>(c, in_level);
-        return c->d.scheme == TEUK_SCHEME_SPLIT ? launch_split_step<float>(p, c->threads, c->smem, st)
-                                                : launch_literal_step<float>(p, st);
+        return c->d.scheme == TEUK_SCHEME_SPLIT ? launch_split<float>(c, p, st) : launch_literal_step<float>(p, st);
     }
     StepParams<double> p = make_params<double>(c, in_level);
-    return c->d.scheme == TEUK_SCHEME_SPLIT ? launch_split_step<double>(p, c->threads, c->smem, st)
-                                            : launch_literal_step<double>(p, st);
+    return c->d.scheme == TEUK_SCHEME_SPLIT ? launch_split<double>(c, p, st) : launch_literal_step<double>(p, st);
 }
 
 // Physical state u_n = C_{dt/2} s_n of a shifted split-scheme state, written
@@ -670,58 +750,86 @@ int teuk_tiling(const teuk_ctx *c, int *tile_rows, int *threads, size_t *smem_by
 {
     if (!c) return TEUK_E_STATE;
     if (tile_rows) *tile_rows = c->tile_rows;
-    if (threads) *threads = c->threads;
-    if (smem_bytes) *smem_bytes = c->smem;
+    if (threads) *threads = c->persist ? c->nc + 32 : c->threads;
+    if (smem_bytes) *smem_bytes = c->persist ? c->persist_smem : c->smem;
     if (group) *group = implicit_group((int)c->d.Ntheta);
     return TEUK_OK;
 }
 
-int teuk_autotune(teuk_ctx *c, int trial_steps, void *stream, int *tile_rows_out)
+int teuk_kernel_config(const teuk_ctx *c, int *persistent, int *consumer_threads, int *grid)
 {
     if (!c) return TEUK_E_STATE;
+    if (persistent) *persistent = c->persist;
+    if (consumer_threads) *consumer_threads = c->persist ? c->nc : c->threads;
+    if (grid) *grid = c->persist ? c->grid : (int)((c->d.Nr + c->tile_rows - 1) / c->tile_rows);
+    return TEUK_OK;
+}
+
+// Times the best few launch configurations of each kernel and keeps the
+// fastest.  With a flush buffer every timed step starts from a cold L2 (the
+// buffer is overwritten between steps, outside the timed interval).
+static int autotune_impl(teuk_ctx *c, int trial_steps, void *flush, size_t flush_bytes, cudaStream_t st,
+                         int *tile_rows_out)
+{
     if (trial_steps < 1 || trial_steps > 100000) return set_err(c, TEUK_E_INVAL, "trial_steps out of range%s");
     if (c->d.scheme != TEUK_SCHEME_SPLIT) {
         if (tile_rows_out) *tile_rows_out = c->tile_rows;
         return TEUK_OK;
     }
-    cudaStream_t st = (cudaStream_t)stream;
-    TileCand cand[256];
-    int n = tile_candidates(c, cand, 256);
-    if (n == 0) return set_err(c, TEUK_E_CUDA, "no tile of the split kernel fits on this device%s");
-    const int ntry = n < 6 ? n : 6;
+    std::vector<TileCand> all(1024);
+    int n = tile_candidates(c, all.data(), (int)all.size());
+    // the best few of each kernel by the model
+    std::vector<TileCand> cand;
+    for (int kind = 0; kind < 2; ++kind) {
+        int taken = 0;
+        for (int k = 0; k < n && taken < 4; ++k)
+            if (all[k].persist == kind) {
+                cand.push_back(all[k]);
+                ++taken;
+            }
+    }
+    if (cand.empty()) return set_err(c, TEUK_E_CUDA, "no tile of the split kernel fits on this device%s");
     drop_graphs(c);
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0), "event");
     CK(cudaEventCreate(&e1), "event");
     float best = 3.4e38f;
-    int bestk = 0;
-    for (int k = 0; k < ntry; ++k) {
-        c->tile_rows = cand[k].R - 2;
-        c->smem = cand[k].smem;
+    int bestk = -1;
+    cudaError_t e = cudaSuccess;
+    for (size_t k = 0; k < cand.size() && e == cudaSuccess; ++k) {
+        if (!apply_cand(c, cand[k])) continue;
         c->shifted = 1;
         int lev = c->cur;
-        cudaError_t e = cudaSuccess;
         for (int w = 0; w < 3 && e == cudaSuccess; ++w, lev ^= 1) e = launch_one(c, lev, st);
-        if (e == cudaSuccess) e = cudaEventRecord(e0, st);
-        for (int w = 0; w < trial_steps && e == cudaSuccess; ++w, lev ^= 1) e = launch_one(c, lev, st);
-        if (e == cudaSuccess) e = cudaEventRecord(e1, st);
-        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-        float ms = 0.0f;
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-        if (e != cudaSuccess) {
-            cudaEventDestroy(e0);
-            cudaEventDestroy(e1);
-            return cuda_err(c, e, "autotune trial");
+        float total = 0.0f;
+        if (flush) {
+            for (int w = 0; w < trial_steps && e == cudaSuccess; ++w, lev ^= 1) {
+                float ms = 0.0f;
+                e = cudaMemsetAsync(flush, w & 0xff, flush_bytes, st);
+                if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+                if (e == cudaSuccess) e = launch_one(c, lev, st);
+                if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+                total += ms;
+            }
+        } else {
+            if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+            for (int w = 0; w < trial_steps && e == cudaSuccess; ++w, lev ^= 1) e = launch_one(c, lev, st);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&total, e0, e1);
         }
-        if (ms < best) {
-            best = ms;
-            bestk = k;
+        if (e == cudaSuccess && total < best) {
+            best = total;
+            bestk = (int)k;
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    c->tile_rows = cand[bestk].R - 2;
-    c->smem = cand[bestk].smem;
+    if (e != cudaSuccess) return cuda_err(c, e, "autotune trial");
+    if (bestk < 0) return set_err(c, TEUK_E_CUDA, "no tile of the split kernel fits on this device%s");
+    apply_cand(c, cand[bestk]);
     // back to a clean state: zero field at step 0, empty ring buffer
     CK(cudaMemsetAsync(c->state, 0, 2 * c->level_bytes, st), "zero state");
     CK(cudaMemsetAsync(c->wave, 0, sizeof(double2) * (size_t)(c->d.Ntheta + 1) * (size_t)c->cap, st), "zero wave");
@@ -736,19 +844,51 @@ int teuk_autotune(teuk_ctx *c, int trial_steps, void *stream, int *tile_rows_out
     return TEUK_OK;
 }
 
+int teuk_autotune(teuk_ctx *c, int trial_steps, void *stream, int *tile_rows_out)
+{
+    if (!c) return TEUK_E_STATE;
+    return autotune_impl(c, trial_steps, nullptr, 0, (cudaStream_t)stream, tile_rows_out);
+}
+
+int teuk_autotune_cold(teuk_ctx *c, int trial_steps, void *d_flush, size_t flush_bytes, void *stream,
+                       int *tile_rows_out)
+{
+    if (!c) return TEUK_E_STATE;
+    if (!d_flush || flush_bytes == 0) return set_err(c, TEUK_E_INVAL, "need a device flush buffer%s");
+    return autotune_impl(c, trial_steps, d_flush, flush_bytes, (cudaStream_t)stream, tile_rows_out);
+}
+
 int teuk_set_tiling(teuk_ctx *c, int tile_rows)
 {
     if (!c) return TEUK_E_STATE;
     if (c->d.scheme != TEUK_SCHEME_SPLIT) return TEUK_OK;
     if (tile_rows < 1 || tile_rows > 254) return set_err(c, TEUK_E_INVAL, "tile_rows out of range [1, 254]%s");
-    int N = (int)c->d.Ntheta;
-    bool f32 = c->d.precision == TEUK_FP32;
-    size_t sm = f32 ? split_smem_bytes<float>(tile_rows, N) : split_smem_bytes<double>(tile_rows, N);
-    int k = f32 ? split_blocks_per_sm<float>(N, c->threads, sm) : split_blocks_per_sm<double>(N, c->threads, sm);
-    if (sm > 227 * 1024 || k < 1) return set_err(c, TEUK_E_INVAL, "tile does not fit in shared memory%s");
+    TileCand t;
+    if (!tiled_cand(c, tile_rows, sm_count(), &t)) return set_err(c, TEUK_E_INVAL, "tile does not fit in shared memory%s");
     drop_graphs(c);
-    c->tile_rows = tile_rows;
-    c->smem = sm;
+    apply_cand(c, t);
+    return TEUK_OK;
+}
+
+int teuk_set_persistent(teuk_ctx *c, int tile_rows, int consumer_threads)
+{
+    if (!c) return TEUK_E_STATE;
+    if (c->d.scheme != TEUK_SCHEME_SPLIT) return set_err(c, TEUK_E_INVAL, "the persistent kernel is a split-scheme kernel%s");
+    if (tile_rows < 1 || tile_rows > 254) return set_err(c, TEUK_E_INVAL, "tile_rows out of range [1, 254]%s");
+    TileCand t;
+    if (!persist_cand(c, tile_rows, consumer_threads, sm_count(), &t)) {
+        const int N = (int)c->d.Ntheta;
+        const bool f32 = c->d.precision == TEUK_FP32;
+        size_t sm = f32 ? persist_smem_bytes<float>(tile_rows, N) : persist_smem_bytes<double>(tile_rows, N);
+        char why[320];
+        if (f32) persist_explain<float>(N, consumer_threads, sm, why, sizeof(why));
+        else persist_explain<double>(N, consumer_threads, sm, why, sizeof(why));
+        return set_err(c, TEUK_E_INVAL, "persistent kernel unavailable for this grid: %s", why);
+    }
+    TileCand tt;
+    if (!tiled_cand(c, tile_rows, sm_count(), &tt)) return set_err(c, TEUK_E_INVAL, "tile does not fit in shared memory%s");
+    drop_graphs(c);
+    apply_cand(c, t);
     return TEUK_OK;
 }
 

@@ -100,9 +100,12 @@ constexpr double kGamma = 0.29289321881345247559915563789515;
 constexpr double kPi = 3.14159265358979323846264338327950;
 
 // Shared-memory carve-up of the split kernel for R = tile_rows + 2 rows of
-// N theta points; every section starts on a 16-byte boundary.
+// N theta points; every section starts on a 16-byte boundary.  piv holds
+// the tile rows' Thomas pivots; rt holds the r-table entries of positions
+// 2(i0-1) .. 2(i0+TR) (nodes and half nodes interleaved, as in the global
+// table).
 struct SplitSmem {
-    unsigned phi, pi, sig, rn, rh, th, total;
+    unsigned phi, pi, piv, rt, th, total;
 };
 __host__ __device__ inline unsigned smem_align16(unsigned x) { return (x + 15u) & ~15u; }
 __host__ __device__ inline SplitSmem split_smem_plan(int R, int N, int tsize)
@@ -111,11 +114,34 @@ __host__ __device__ inline SplitSmem split_smem_plan(int R, int N, int tsize)
     const unsigned plane = (unsigned)R * (unsigned)N * 2u * (unsigned)tsize;
     s.phi = 0;
     s.pi = smem_align16(plane);
-    s.sig = smem_align16(s.pi + plane);
-    s.rn = smem_align16(s.sig + (unsigned)R * (unsigned)N * (unsigned)tsize);
-    s.rh = smem_align16(s.rn + (unsigned)R * NRF * (unsigned)tsize);
-    s.th = smem_align16(s.rh + (unsigned)(R - 1) * NRF * (unsigned)tsize);
+    s.piv = smem_align16(s.pi + plane);
+    s.rt = smem_align16(s.piv + plane);
+    s.th = smem_align16(s.rt + (unsigned)(2 * R - 1) * NRF * (unsigned)tsize);
     s.total = smem_align16(s.th + (unsigned)NTF * (unsigned)N * (unsigned)tsize);
+    return s;
+}
+
+// Shared-memory carve-up of the persistent split kernel: theta tables, a
+// copy of the extraction row (state and r-table entry) and two tile
+// buffers, each with the two state planes [R][N], the pivots [R][N] and the
+// interleaved r-table entries [2R-1][NRF].
+struct PersistSmem {
+    unsigned th, xphi, xpi, xf, buf, bpi, bpiv, brt, bsize, total;
+};
+__host__ __device__ inline PersistSmem persist_smem_plan(int R, int N, int tsize)
+{
+    PersistSmem s;
+    const unsigned c2 = 2u * (unsigned)tsize, plane = (unsigned)R * (unsigned)N * c2;
+    s.th = 0;
+    s.xphi = smem_align16((unsigned)NTF * (unsigned)N * (unsigned)tsize);
+    s.xpi = smem_align16(s.xphi + (unsigned)N * c2);
+    s.xf = smem_align16(s.xpi + (unsigned)N * c2);
+    s.buf = smem_align16(s.xf + NRF * (unsigned)tsize);
+    s.bpi = smem_align16(plane);
+    s.bpiv = smem_align16(s.bpi + plane);
+    s.brt = smem_align16(s.bpiv + plane);
+    s.bsize = smem_align16(s.brt + (unsigned)(2 * R - 1) * NRF * (unsigned)tsize);
+    s.total = s.buf + 2u * s.bsize;
     return s;
 }
 
@@ -148,6 +174,19 @@ cudaError_t launch_extract(const StepParams<T> &p, const typename V2<T>::t *u, l
                            cudaStream_t st);
 template <typename T>
 size_t split_smem_bytes(int tile_rows, int Nth);
+// Persistent split kernel (one producer warp moves tiles by TMA into two
+// buffers while nc consumer threads compute): available for the FP32 state
+// with Ntheta <= 128 and nc in {384, 480}.
+template <typename T>
+bool persist_available(int Nth, int nc);
+template <typename T>
+size_t persist_smem_bytes(int tile_rows, int Nth);
+template <typename T>
+int persist_blocks_per_sm(int Nth, int nc, size_t smem);   // 0 if the launch cannot fit
+template <typename T>
+void persist_explain(int Nth, int nc, size_t smem, char *buf, size_t len);   // why it cannot
+template <typename T>
+cudaError_t launch_split_persist(const StepParams<T> &p, int nc, int grid, size_t smem, cudaStream_t st);
 template <typename T>
 int split_blocks_per_sm(int Nth, int threads, size_t smem);   // 0 if the launch cannot fit
 int implicit_group(int Nth);            // threads per theta row

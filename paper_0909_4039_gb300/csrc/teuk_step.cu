@@ -23,6 +23,7 @@
 // Paper: Khanna & McKennon, arXiv:0909.4039, Sec. 2.2, Eqs. 9-14 and the
 // boundary conditions stated after Eq. 14.
 #include <math.h>
+#include <stdio.h>
 
 #include <mutex>
 
@@ -160,8 +161,9 @@ template <> struct ScanTol<float> { static constexpr float v = 1e-10f; };
 template <> struct ScanTol<double> { static constexpr double v = 1e-19; };
 
 // One implicit SDIRK2 step of length h (constants K) on one r* row held in
-// shared memory (phi, pi, sig = 1/Sigma: element j at [j]; f: the row's r table,
-// 16-byte aligned; th: theta tables), by a group of G consecutive lanes.
+// shared memory (phi, pi: element j at [j]; prow: the row's Thomas pivots,
+// shared or global; f: the row's r-table entry, 16-byte aligned; th: theta
+// tables), by a group of G consecutive lanes.
 // Lane g holds the contiguous theta segment [g S, g S + S) in registers;
 // with vec every segment is whole and 16-byte aligned and moves by vector
 // loads and stores.
@@ -183,7 +185,7 @@ template <> struct ScanTol<double> { static constexpr double v = 1e-19; };
 // the grid) take part in the shuffles with neutral data and write zeros.
 template <typename T, int S>
 __device__ void implicit_row_group(const ImpConst<T> &K, typename V2<T>::t *phi, typename V2<T>::t *pi,
-                                   const T *sig, const T *f, const T *th, int N, int gi, bool active,
+                                   const typename V2<T>::t *prow, const T *f, const T *th, int N, bool active,
                                    bool in_tile, int g, int G, bool vec)
 {
     typedef typename V2<T>::t c2;
@@ -204,34 +206,39 @@ __device__ void implicit_row_group(const ImpConst<T> &K, typename V2<T>::t *phi,
     T fr[NRF];
     vload<NRF>(fr, f);
     const T D = fr[RF_DELTA], ctr = fr[RF_CTR], cti = fr[RF_CTI], ctc = fr[RF_CTC], c0r = fr[RF_C0R],
-            c0i = fr[RF_C0I];
+            c0i = fr[RF_C0I], R2 = fr[RF_R2], AD = fr[RF_AD];
+    const T *S2t = th + TF_S2 * N;
     const T *Cc = th + TF_C * N;
     const T *Am = th + TF_AM * N;
     const T *A0 = th + TF_A0 * N;
     const T *Ap = th + TF_AP * N;
 
-    T sgv[S], ccv[S], am[S], a0[S], ap[S];
+    // rsv = 1/Sigma (zero for neutral elements)
+    T rsv[S], ccv[S], am[S], a0[S], ap[S];
     c2 e[S], w[S], y[S];
     if (vec && len == S) {
-        vload<S>(sgv, sig + j0);
+        T s2v[S];
+        vload<S>(s2v, S2t + j0);
         vload<S>(ccv, Cc + j0);
         vload<S>(am, Am + j0);
         vload<S>(a0, A0 + j0);
         vload<S>(ap, Ap + j0);
-        vload<S>(e, K.piv + (size_t)gi * N + j0);
+        vload<S>(e, prow + j0);
         vload<S>(w, phi + j0);
         vload<S>(y, pi + j0);
+#pragma unroll
+        for (int k = 0; k < S; ++k) rsv[k] = rsq_(fma(-AD, s2v[k], R2));
     } else {
 #pragma unroll
         for (int k = 0; k < S; ++k) {
             const bool real = k < len;
             const int j = real ? j0 + k : 0;
-            sgv[k] = real ? sig[j] : T(0);
+            rsv[k] = real ? rsq_(fma(-AD, S2t[j], R2)) : T(0);
             ccv[k] = real ? Cc[j] : T(0);
             am[k] = real ? Am[j] : T(0);
             a0[k] = real ? A0[j] : T(0);
             ap[k] = real ? Ap[j] : T(0);
-            e[k] = real ? K.piv[(size_t)gi * N + j] : one;
+            e[k] = real ? prow[j] : one;
             w[k] = real ? phi[j] : zero;
             y[k] = real ? pi[j] : zero;
         }
@@ -242,7 +249,7 @@ __device__ void implicit_row_group(const ImpConst<T> &K, typename V2<T>::t *phi,
     T qam[S], qap[S];
 #pragma unroll
     for (int k = 0; k < S; ++k) {
-        const T sg = sgv[k] * sgv[k];
+        const T sg = rsv[k] * rsv[k];
         const T q = D * sg;
         ct[k] = cmk<c2>(sg * ctr, sg * fma(ctc, ccv[k], cti));
         dg[k] = cmk<c2>(fma(q, a0[k], -sg * c0r), -sg * c0i);
@@ -296,7 +303,6 @@ __device__ void implicit_row_group(const ImpConst<T> &K, typename V2<T>::t *phi,
         c2 B = zero;
 #pragma unroll
         for (int k = 0; k < S; ++k) B = csub(w[k], cmul(m[k], B));
-#pragma unroll
         {
             c2 A = Af0;
 #pragma unroll
@@ -323,7 +329,6 @@ __device__ void implicit_row_group(const ImpConst<T> &K, typename V2<T>::t *phi,
         B = zero;
 #pragma unroll
         for (int k = S - 1; k >= 0; --k) B = csub(w[k], cmul(fk[k], B));
-#pragma unroll
         {
             c2 A = Ab0;
 #pragma unroll
@@ -437,10 +442,12 @@ static_assert(RF_R < 12 && RF_R2 < 12 && RF_AD < 12 && RF_CTR < 12 && RF_CTI < 1
 // Split-scheme Lax-Wendroff update (Eqs. 13-14 with S = F + K Phi_{r*}) of
 // tile rows [ra, rb) in theta column j, in place.  (pf, pg) is the old value
 // of row ra-1 and (nf, ng) the old value of row rb: both may belong to other
-// threads' segments, so the caller reads them before a barrier.
+// threads' segments, so the caller reads them before a barrier.  sRt holds
+// the r-table entries of the tile: node row lr at 2 lr, the half node
+// between rows k and k+1 at 2 k + 1.
 template <typename T>
 __device__ void lw_segment(const StepParams<T> &p, typename V2<T>::t *sPhi, typename V2<T>::t *sPi,
-                           const T *sSig, const T *sRn, const T *sRh, const T *sTh, int j, int ra, int rb,
+                           const T *sRt, const T *sTh, int j, int ra, int rb,
                            typename V2<T>::t pf, typename V2<T>::t pg, typename V2<T>::t nf,
                            typename V2<T>::t ng, int i0, typename V2<T>::t ph1, typename V2<T>::t ph2,
                            bool src)
@@ -460,7 +467,7 @@ __device__ void lw_segment(const StepParams<T> &p, typename V2<T>::t *sPhi, type
             return;
         }
         T f[12];   // fields R .. E3 of the half-node entry
-        vload<12>(f, sRh + k * NRF);
+        vload<12>(f, sRt + (2 * k + 1) * NRF);
         T rs = rsq_(fma(-f[RF_AD], S2, f[RF_R2]));
         T b;
         c2 K;
@@ -495,8 +502,8 @@ __device__ void lw_segment(const StepParams<T> &p, typename V2<T>::t *sPhi, type
         if (gi >= 1 && gi <= Nr - 2) {
             // Eq. 14 at node gi
             T f[12];   // fields R .. E3 of the node entry
-            vload<12>(f, sRn + lr * NRF);
-            T rs = sSig[lr * P + j];
+            vload<12>(f, sRt + 2 * lr * NRF);
+            T rs = rsq_(fma(-f[RF_AD], S2, f[RF_R2]));
             T b;
             c2 K;
             bK<T>(f, rs, S2, C, b, K);
@@ -530,6 +537,54 @@ template <typename T> __device__ __forceinline__ typename V2<T>::t from_d2(doubl
 {
     typedef typename V2<T>::t c2;
     return cmk<c2>((T)v.x, (T)v.y);
+}
+
+// Lax-Wendroff phase of one tile (output rows 1..TR of the R = TR + 2 held)
+// by NC threads with index ctid.  With N <= NC every column is cut into
+// NC / N row segments; the rows on either side of a segment are read before
+// bar() (a barrier over the NC threads), as the neighbouring segments
+// overwrite them.
+template <typename T, typename Bar>
+__device__ __forceinline__ void lw_phase(const StepParams<T> &p, typename V2<T>::t *sPhi, typename V2<T>::t *sPi,
+                                         const T *sRt, const T *sTh, int TR, int i0, int ctid,
+                                         int NC, bool src, typename V2<T>::t ph1, typename V2<T>::t ph2, Bar bar)
+{
+    typedef typename V2<T>::t c2;
+    const int N = p.Nth, P = p.pitch;
+    const c2 zero = cmk<c2>(T(0), T(0));
+    if (N <= NC) {
+        const int nseg = NC / N;
+        const int sl = (TR + nseg - 1) / nseg;
+        const int j = ctid % N, sgm = ctid / N;
+        int ra = 1 + sgm * sl, rb = 1 + (sgm + 1) * sl;
+        if (rb > TR + 1) rb = TR + 1;
+        const bool work = sgm < nseg && ra < rb;
+        c2 pf = zero, pg = zero, nf = zero, ng = zero;
+        if (work) {
+            pf = sPhi[(ra - 1) * P + j];
+            pg = sPi[(ra - 1) * P + j];
+            nf = sPhi[rb * P + j];
+            ng = sPi[rb * P + j];
+        }
+        bar();
+        if (work) lw_segment<T>(p, sPhi, sPi, sRt, sTh, j, ra, rb, pf, pg, nf, ng, i0, ph1, ph2, src);
+    } else {
+        for (int j = ctid; j < N; j += NC) {
+            c2 pf = sPhi[j], pg = sPi[j], nf = sPhi[(TR + 1) * P + j], ng = sPi[(TR + 1) * P + j];
+            lw_segment<T>(p, sPhi, sPi, sRt, sTh, j, 1, TR + 1, pf, pg, nf, ng, i0, ph1, ph2, src);
+        }
+    }
+}
+
+// Barrier over the first n threads of the CTA (named barrier id).
+__device__ __forceinline__ void named_sync(int id, int n) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
+// The same barrier; returns whether pred holds in all n threads.
+__device__ __forceinline__ int named_sync_and(int id, int n, int pred)
+{
+    int r;
+    asm volatile("{ .reg .pred p, q; setp.ne.s32 p, %1, 0; bar.red.and.pred q, %2, %3, p; selp.s32 %0, 1, 0, q; }"
+                 : "=r"(r) : "r"(pred), "r"(id), "r"(n) : "memory");
+    return r;
 }
 
 // ---- TMA bulk copies (1-D, global <-> shared) and the mbarrier that
@@ -615,10 +670,11 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && S <= 4) ? 2 : 1) k_spl
     const SplitSmem plan = split_smem_plan(R, N, (int)sizeof(T));
     c2 *sPhi = (c2 *)(smem_raw + plan.phi);
     c2 *sPi = (c2 *)(smem_raw + plan.pi);
-    T *sSig = (T *)(smem_raw + plan.sig);
-    T *sRn = (T *)(smem_raw + plan.rn);
-    T *sRh = (T *)(smem_raw + plan.rh);
+    c2 *sPiv = (c2 *)(smem_raw + plan.piv);
+    T *sRt = (T *)(smem_raw + plan.rt);
     T *sTh = (T *)(smem_raw + plan.th);
+    // implicit step of this launch: dt/2 for the first step and for the state output
+    const ImpConst<T> &K = (p.first || p.imp_only) ? p.half : p.full;
 
     const bool src = !p.imp_only && p.patch_np > 0 && i0 + TR >= p.patch_p0 &&
                      i0 - 1 <= p.patch_p0 + p.patch_np;
@@ -642,7 +698,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && S <= 4) ? 2 : 1) k_spl
             sph[1] = phase_at(p.mOmega, t + 0.5 * p.dt64);
         }
     }
-    // ---- A: tile rows i0-1 .. i0+TR, r and theta tables, 1/Sigma^2 at the nodes
+    // ---- A: tile rows i0-1 .. i0+TR (state and pivots), r and theta tables
     const c2 zero = cmk<c2>(T(0), T(0));
     // (row, column) walk of the tile without integer division in the loop
     const int t_lr = tid / N, t_j = tid - t_lr * N;
@@ -666,11 +722,12 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && S <= 4) ? 2 : 1) k_spl
                 if (r0 < la) r0 = la;
                 if (r1 > la + nrows) r1 = la + nrows;
                 unsigned bytes = r1 > r0 ? (unsigned)(r1 - r0) * (unsigned)N * (unsigned)sizeof(c2) : 0u;
-                mbar_expect_tx(&s_mbar[c], 2 * bytes);   // with no bytes this is a plain arrival
+                mbar_expect_tx(&s_mbar[c], 3 * bytes);   // with no bytes this is a plain arrival
                 if (bytes) {
                     const size_t g0 = (size_t)(ga + r0 - la);
                     bulk_g2s(sPhi + r0 * P, p.uin + g0 * N, bytes, &s_mbar[c]);
                     bulk_g2s(sPi + r0 * P, p.uin + ((size_t)Nr + g0) * N, bytes, &s_mbar[c]);
+                    bulk_g2s(sPiv + r0 * P, K.piv + g0 * N, bytes, &s_mbar[c]);
                 }
             }
         }
@@ -687,45 +744,35 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && S <= 4) ? 2 : 1) k_spl
     } else {
         for (int lr = t_lr, j = t_j; lr < R;) {
             int gi = i0 - 1 + lr;
-            c2 fv = zero, gv = zero;
+            c2 fv = zero, gv = zero, ev = zero;
             if (gi >= 0 && gi < Nr) {
                 fv = p.uin[(size_t)gi * N + j];
                 gv = p.uin[((size_t)Nr + gi) * N + j];
+                ev = K.piv[(size_t)gi * N + j];
             }
             sPhi[lr * P + j] = fv;
             sPi[lr * P + j] = gv;
+            sPiv[lr * P + j] = ev;
             lr += d_lr;
             j += d_j;
             if (j >= N) { j -= N; ++lr; }
         }
     }
-    for (int idx = tid; idx < R * NRF; idx += NT) {
-        int lr = idx / NRF, q = idx - lr * NRF;
-        int gi = i0 - 1 + lr;
-        sRn[idx] = (gi >= 0 && gi < Nr) ? p.rtab[(size_t)(2 * gi) * NRF + q] : T(0);
-    }
-    for (int idx = tid; idx < (R - 1) * NRF; idx += NT) {
-        int k = idx / NRF, q = idx - k * NRF;
-        int gi = i0 - 1 + k;
-        sRh[idx] = (gi >= 0 && gi <= Nr - 2) ? p.rtab[(size_t)(2 * gi + 1) * NRF + q] : T(0);
+    {
+        // r-table positions 2(i0-1) .. 2(i0+TR); those off the grid are zero
+        const long long pbase = 2LL * (i0 - 1);
+        const long long pmax = 2LL * Nr - 2;
+        for (int idx = tid; idx < (2 * R - 1) * NRF; idx += NT) {
+            int e = idx / NRF, q = idx - e * NRF;
+            long long pos = pbase + e;
+            sRt[idx] = (pos >= 0 && pos <= pmax) ? p.rtab[(size_t)pos * NRF + q] : T(0);
+        }
     }
     for (int idx = tid; idx < NTF * N; idx += NT) sTh[idx] = p.thtab[idx];
-    __syncthreads();
-    // 1/Sigma at the node rows, while the state tile is in flight
-    for (int lr = t_lr, j = t_j; lr < R;) {
-        int gi = i0 - 1 + lr;
-        T v = T(0);
-        if (gi >= 0 && gi < Nr) v = rsq_(fma(-sRn[lr * NRF + RF_AD], sTh[TF_S2 * N + j], sRn[lr * NRF + RF_R2]));
-        sSig[lr * P + j] = v;
-        lr += d_lr;
-        j += d_j;
-        if (j >= N) { j -= N; ++lr; }
-    }
     __syncthreads();
     // ---- B: implicit step on the tile rows (all R rows; only rows 1..TR with imp_only)
     int ok = 1;   // every bounded wait of this thread succeeded
     {
-        const ImpConst<T> &K = (p.first || p.imp_only) ? p.half : p.full;
         const int lo = p.imp_only ? 1 : 0, hi = p.imp_only ? TR + 1 : R;
         const int g = tid % G;
         const bool vec = p.vec != 0;
@@ -741,8 +788,8 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && S <= 4) ? 2 : 1) k_spl
             int gi = i0 - 1 + lr;
             bool active = in_tile && gi >= 1 && gi <= Nr - 2;
             int lrc = in_tile ? lr : lo;
-            implicit_row_group<T, S>(K, sPhi + lrc * P, sPi + lrc * P, sSig + lrc * P, sRn + lrc * NRF, sTh, N,
-                                     active ? gi : 1, active, in_tile, g, G, vec);
+            implicit_row_group<T, S>(K, sPhi + lrc * P, sPi + lrc * P, sPiv + lrc * P, sRt + 2 * lrc * NRF, sTh, N,
+                                     active, in_tile, g, G, vec);
         }
         // the remaining phases read every row of the tile
         if (p.bulk && ok)
@@ -758,34 +805,14 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && S <= 4) ? 2 : 1) k_spl
         return;
     }
     if (!p.imp_only) {
-        // ---- C: Lax-Wendroff on the output rows; NSEG row segments per column
+        // ---- C: Lax-Wendroff on the output rows
         c2 ph1 = zero, ph2 = zero;
         if (src) {
             ph1 = from_d2<T>(sph[0]);
             ph2 = from_d2<T>(sph[1]);
         }
-        if (N <= NT) {
-            const int nseg = NT / N;
-            const int sl = (TR + nseg - 1) / nseg;
-            const int j = tid % N, sgm = tid / N;
-            int ra = 1 + sgm * sl, rb = 1 + (sgm + 1) * sl;
-            if (rb > TR + 1) rb = TR + 1;
-            bool work = sgm < nseg && ra < rb;
-            c2 pf = zero, pg = zero, nf = zero, ng = zero;
-            if (work) {
-                pf = sPhi[(ra - 1) * P + j];
-                pg = sPi[(ra - 1) * P + j];
-                nf = sPhi[rb * P + j];
-                ng = sPi[rb * P + j];
-            }
-            __syncthreads();
-            if (work) lw_segment<T>(p, sPhi, sPi, sSig, sRn, sRh, sTh, j, ra, rb, pf, pg, nf, ng, i0, ph1, ph2, src);
-        } else {
-            for (int j = tid; j < N; j += NT) {
-                c2 pf = sPhi[j], pg = sPi[j], nf = sPhi[(TR + 1) * P + j], ng = sPi[(TR + 1) * P + j];
-                lw_segment<T>(p, sPhi, sPi, sSig, sRn, sRh, sTh, j, 1, TR + 1, pf, pg, nf, ng, i0, ph1, ph2, src);
-            }
-        }
+        auto sync_all = [] { __syncthreads(); };
+        lw_phase<T>(p, sPhi, sPi, sRt, sTh, TR, i0, tid, NT, src, ph1, ph2, sync_all);
         __syncthreads();
     }
     // ---- D: store the output rows
@@ -821,10 +848,221 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && S <= 4) ? 2 : 1) k_spl
         if (tid < 32) {
             bool mine = tid < G;
             bool active = mine && p.i_ext >= 1 && p.i_ext <= Nr - 2;
-            implicit_row_group<T, S>(p.half, sPhi + lr * P, sPi + lr * P, sSig + lr * P, sRn + lr * NRF, sTh, N,
-                                     active ? p.i_ext : 1, active, mine, tid % G, G, p.vec != 0);
+            implicit_row_group<T, S>(p.half, sPhi + lr * P, sPi + lr * P, p.half.piv + (size_t)p.i_ext * N,
+                                     sRt + 2 * lr * NRF, sTh, N, active, mine, tid % G, G, p.vec != 0);
             __syncwarp();
             extract_warp<T>(p, sPhi + lr * P, s_n + 1);
+        }
+    }
+}
+
+__device__ __forceinline__ void mbar_arrive(unsigned long long *m)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(m)) : "memory");
+}
+
+// Persistent form of k_split_step (same arithmetic, same output).  The CTA
+// keeps the theta tables and walks the tiles blockIdx.x, blockIdx.x +
+// gridDim.x, ...  Warp NC/32 is the producer: its lane 0 loads tile k+2 into
+// the buffer that tile k used as soon as tile k is stored, so tiles arrive
+// while the NC consumer threads compute the previous one.  Per buffer b:
+//   full[b]   completes when the tile's state rows and r-table entries are
+//             resident (transaction count);
+//   empty[b]  completes when every consumer warp has finished the tile and
+//             fenced its shared-memory writes for the bulk store.
+// Every wait is bounded; a lost copy sets FLAG_TIMEOUT and ends the CTA.
+// Registers per thread so that one CTA of NC + 32 threads fits an SM: its
+// warps are spread over the SM's four sub-partitions of 16K registers each.
+template <int NC> struct PersistRegs {
+    static constexpr int warps_per_quarter = (NC / 32 + 1 + 3) / 4;
+    static constexpr int raw = 16384 / (warps_per_quarter * 32);
+    static constexpr int v = (raw > 255 ? 255 : raw) / 8 * 8;
+};
+
+template <typename T, int S, int NC>
+__global__ void __maxnreg__(PersistRegs<NC>::v) k_split_persist(const StepParams<T> p)
+{
+    typedef typename V2<T>::t c2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double2 sph[2];
+    __shared__ long long s_n;
+    __shared__ __align__(8) unsigned long long s_full[2], s_empty[2];
+    const int Nr = p.Nr, N = p.Nth, TR = p.tile_rows, R = TR + 2, P = p.pitch;
+    const int tid = threadIdx.x;
+    const int G = p.group;
+    const PersistSmem plan = persist_smem_plan(R, N, (int)sizeof(T));
+    T *sTh = (T *)(smem_raw + plan.th);
+    c2 *xPhi = (c2 *)(smem_raw + plan.xphi);
+    c2 *xPi = (c2 *)(smem_raw + plan.xpi);
+    T *xF = (T *)(smem_raw + plan.xf);
+    auto bphi = [&](int b) { return (c2 *)(smem_raw + plan.buf + b * plan.bsize); };
+    auto bpi = [&](int b) { return (c2 *)(smem_raw + plan.buf + b * plan.bsize + plan.bpi); };
+    auto bpiv = [&](int b) { return (c2 *)(smem_raw + plan.buf + b * plan.bsize + plan.bpiv); };
+    auto brt = [&](int b) { return (T *)(smem_raw + plan.buf + b * plan.bsize + plan.brt); };
+    const ImpConst<T> &K = p.first ? p.half : p.full;
+    const int ntiles = (Nr + TR - 1) / TR;
+    const int nmine = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    // Geometry of tile number it of this CTA: on-grid rows [ga, gb] from tile
+    // row la (nrows of them), on-grid r-table positions from entry lp (npos).
+    struct Geo {
+        int i0, ga, la, nrows, pos0, lp, npos;
+    };
+    auto geo = [&](int it) {
+        Geo q;
+        q.i0 = ((int)blockIdx.x + it * (int)gridDim.x) * TR;
+        q.ga = q.i0 - 1 < 0 ? 0 : q.i0 - 1;
+        const int gb = q.i0 + TR > Nr - 1 ? Nr - 1 : q.i0 + TR;
+        q.la = q.ga - (q.i0 - 1);
+        q.nrows = gb - q.ga + 1;
+        const int pb = 2 * (q.i0 - 1), pe0 = 2 * (q.i0 + TR);
+        q.pos0 = pb < 0 ? 0 : pb;
+        const int pe = pe0 > 2 * Nr - 2 ? 2 * Nr - 2 : pe0;
+        q.lp = q.pos0 - pb;
+        q.npos = pe - q.pos0 + 1;
+        return q;
+    };
+
+    if (tid == 0) {
+        long long n = *((volatile long long *)&p.ctl->step);
+        s_n = n;
+        // the last CTA to read the step index advances it
+        __threadfence();
+        unsigned t = atomicAdd(&p.ctl->ticket, 1u);
+        if (t == gridDim.x - 1) {
+            p.ctl->ticket = 0u;
+            p.ctl->step = n + 1;
+        }
+        if (p.patch_np > 0) {
+            double tt = (double)n * p.dt64;
+            sph[0] = phase_at(p.mOmega, tt);
+            sph[1] = phase_at(p.mOmega, tt + 0.5 * p.dt64);
+        }
+        mbar_init(&s_full[0], 1);
+        mbar_init(&s_full[1], 1);
+        mbar_init(&s_empty[0], NC / 32);
+        mbar_init(&s_empty[1], NC / 32);
+    }
+    for (int idx = tid; idx < NTF * N; idx += blockDim.x) sTh[idx] = p.thtab[idx];
+    __syncthreads();
+
+    if (tid >= NC) {
+        // ---------------- producer
+        if (tid != NC) return;
+        auto load = [&](int it) {
+            const int b = it & 1;
+            const Geo q = geo(it);
+            const unsigned bs = (unsigned)q.nrows * (unsigned)N * (unsigned)sizeof(c2);
+            const unsigned br = (unsigned)q.npos * NRF * (unsigned)sizeof(T);
+            mbar_expect_tx(&s_full[b], 3 * bs + br);
+            bulk_g2s(bphi(b) + q.la * P, p.uin + (size_t)q.ga * N, bs, &s_full[b]);
+            bulk_g2s(bpi(b) + q.la * P, p.uin + ((size_t)Nr + q.ga) * N, bs, &s_full[b]);
+            bulk_g2s(bpiv(b) + q.la * P, K.piv + (size_t)q.ga * N, bs, &s_full[b]);
+            bulk_g2s(brt(b) + q.lp * NRF, p.rtab + (size_t)q.pos0 * NRF, br, &s_full[b]);
+        };
+        if (nmine > 0) load(0);
+        if (nmine > 1) load(1);
+        for (int it = 0; it < nmine; ++it) {
+            const int b = it & 1;
+            if (!mbar_wait(&s_empty[b], (unsigned)((it >> 1) & 1), kWaitLimit)) {
+                atomicOr(&p.ctl->flags, FLAG_TIMEOUT);
+                break;
+            }
+            const Geo q = geo(it);
+            const int nout = (Nr - q.i0) < TR ? (Nr - q.i0) : TR;
+            const unsigned bytes = (unsigned)nout * (unsigned)N * (unsigned)sizeof(c2);
+            bulk_s2g(p.uout + (size_t)q.i0 * N, bphi(b) + P, bytes);
+            bulk_s2g(p.uout + ((size_t)Nr + q.i0) * N, bpi(b) + P, bytes);
+            bulk_commit();
+            if (it + 2 < nmine) {
+                bulk_wait_read();   // buffer b is read out: refill it
+                load(it + 2);
+            }
+        }
+        bulk_wait_read();
+        return;
+    }
+
+    // ---------------- consumers (threads 0 .. NC-1)
+    const c2 zero = cmk<c2>(T(0), T(0));
+    const int rpp = NC / G;
+    const int g = tid % G;
+    const bool vec = p.vec != 0;
+    const int t_lr = tid / N, t_j = tid - t_lr * N;
+    const int d_lr = NC / N, d_j = NC - d_lr * N;
+    c2 ph1 = zero, ph2 = zero;
+    if (p.patch_np > 0) {
+        ph1 = from_d2<T>(sph[0]);
+        ph2 = from_d2<T>(sph[1]);
+    }
+    auto bar = [] { named_sync(1, NC); };
+    for (int it = 0; it < nmine; ++it) {
+        const int b = it & 1;
+        const Geo q = geo(it);
+        const int i0 = q.i0;
+        c2 *sPhi = bphi(b), *sPi = bpi(b);
+        const c2 *sPiv = bpiv(b);
+        T *sRt = brt(b);
+        const int ok = (int)mbar_wait(&s_full[b], (unsigned)((it >> 1) & 1), kWaitLimit);
+        if (!named_sync_and(1, NC, ok)) {
+            if (tid == 0) atomicOr(&p.ctl->flags, FLAG_TIMEOUT);
+            return;
+        }
+        // off-grid rows and r-table entries (first and last tile) are zero
+        if (q.la > 0 || q.la + q.nrows < R) {
+            for (int lr = t_lr, j = t_j; lr < R;) {
+                if (lr < q.la || lr >= q.la + q.nrows) {
+                    sPhi[lr * P + j] = zero;
+                    sPi[lr * P + j] = zero;
+                }
+                lr += d_lr;
+                j += d_j;
+                if (j >= N) { j -= N; ++lr; }
+            }
+        }
+        if (q.lp > 0 || q.lp + q.npos < 2 * R - 1) {
+            for (int idx = tid; idx < (2 * R - 1) * NRF; idx += NC) {
+                int e = idx / NRF;
+                if (e < q.lp || e >= q.lp + q.npos) sRt[idx] = T(0);
+            }
+        }
+        bar();
+        // implicit step on all R rows
+        for (int base = 0; base < R; base += rpp) {
+            int lr = base + tid / G;
+            bool in_tile = lr < R;
+            int gi = i0 - 1 + lr;
+            bool active = in_tile && gi >= 1 && gi <= Nr - 2;
+            int lrc = in_tile ? lr : 0;
+            implicit_row_group<T, S>(K, sPhi + lrc * P, sPi + lrc * P, sPiv + lrc * P, sRt + 2 * lrc * NRF, sTh, N,
+                                     active, in_tile, g, G, vec);
+        }
+        bar();
+        // The extraction row (its r-table entry and, after the Lax-Wendroff
+        // phase, its state) is copied out for the sample below: the buffer
+        // is refilled once it is handed back.
+        const bool ext = p.i_ext >= i0 && p.i_ext < i0 + TR && p.i_ext < Nr;
+        const int lx = p.i_ext - i0 + 1;
+        if (ext && tid < NRF) xF[tid] = sRt[2 * lx * NRF + tid];
+        const bool src = p.patch_np > 0 && i0 + TR >= p.patch_p0 && i0 - 1 <= p.patch_p0 + p.patch_np;
+        lw_phase<T>(p, sPhi, sPi, sRt, sTh, TR, i0, tid, NC, src, ph1, ph2, bar);
+        bar();
+        if (ext && tid < 32) {
+            for (int j = tid; j < N; j += 32) {
+                xPhi[j] = sPhi[lx * P + j];
+                xPi[j] = sPi[lx * P + j];
+            }
+        }
+        fence_proxy_async();   // this thread's shared-memory writes become visible to the bulk store
+        __syncwarp();
+        if ((tid & 31) == 0) mbar_arrive(&s_empty[b]);
+        // physical sample u_{n+1} = C_{dt/2} s_{n+1} on the extraction row
+        if (ext && tid < 32) {
+            bool mine = tid < G;
+            bool active = mine && p.i_ext >= 1 && p.i_ext <= Nr - 2;
+            implicit_row_group<T, S>(p.half, xPhi, xPi, p.half.piv + (size_t)p.i_ext * N, xF, sTh, N, active, mine,
+                                     tid % G, G, vec);
+            __syncwarp();
+            extract_warp<T>(p, xPhi, s_n + 1);
         }
     }
 }
@@ -1068,6 +1306,90 @@ cudaError_t launch_split_step(const StepParams<T> &p, int threads, size_t smem, 
 }
 
 template <typename T>
+bool persist_available(int Nth, int nc)
+{
+    return sizeof(T) == 4 && implicit_seg(Nth) == kSegNarrow && (nc == 384 || nc == 480);
+}
+
+template <typename T>
+size_t persist_smem_bytes(int tile_rows, int Nth)
+{
+    return persist_smem_plan(tile_rows + 2, Nth, (int)sizeof(T)).total;
+}
+
+// The persistent kernel for (T, nc), or nullptr.
+template <typename T>
+static void (*persist_fn(int Nth, int nc))(const StepParams<T>)
+{
+    if constexpr (sizeof(T) == 4) {
+        if (!persist_available<T>(Nth, nc)) return nullptr;
+        return nc == 384 ? k_split_persist<T, kSegNarrow, 384> : k_split_persist<T, kSegNarrow, 480>;
+    } else {
+        return nullptr;
+    }
+}
+
+template <typename T>
+int persist_blocks_per_sm(int Nth, int nc, size_t smem)
+{
+    auto fn = persist_fn<T>(Nth, nc);
+    if (!fn) return 0;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, nc + 32, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return nb;
+}
+
+template <typename T>
+void persist_explain(int Nth, int nc, size_t smem, char *buf, size_t len)
+{
+    auto fn = persist_fn<T>(Nth, nc);
+    if (!fn) {
+        snprintf(buf, len, "no persistent kernel for this precision, Ntheta and consumer count");
+        return;
+    }
+    cudaFuncAttributes a;
+    cudaError_t e = cudaFuncGetAttributes(&a, fn);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        snprintf(buf, len, "cudaFuncGetAttributes: %s", cudaGetErrorString(e));
+        return;
+    }
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaGetLastError();
+    int nb = -1;
+    cudaError_t e2 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, nc + 32, smem);
+    cudaGetLastError();
+    snprintf(buf, len,
+             "persistent kernel: %d registers/thread, max %d threads/block, %zu B static shared, %zu B local; "
+             "needs %d threads and %zu B dynamic shared (set: %s); blocks per SM %d (%s)",
+             a.numRegs, a.maxThreadsPerBlock, (size_t)a.sharedSizeBytes, (size_t)a.localSizeBytes, nc + 32, smem,
+             cudaGetErrorString(e), nb, cudaGetErrorString(e2));
+}
+
+template <typename T>
+cudaError_t launch_split_persist(const StepParams<T> &p, int nc, int grid, size_t smem, cudaStream_t st)
+{
+    static size_t configured[2] = {0, 0};
+    auto fn = persist_fn<T>(p.Nth, nc);
+    if (!fn || !p.bulk || grid < 1) return cudaErrorInvalidConfiguration;
+    const int v = nc == 384 ? 0 : 1;
+    if (smem > configured[v]) {
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        configured[v] = smem;
+    }
+    fn<<<grid, nc + 32, smem, st>>>(p);
+    return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_literal_step(const StepParams<T> &p, cudaStream_t st)
 {
     int nm = (p.Nr - 1) * p.Nth, nn = p.Nr * p.Nth;
@@ -1134,6 +1456,16 @@ cudaError_t launch_convert_from(int prec, const void *src, double2 *dst, size_t 
     return cudaGetLastError();
 }
 
+template bool persist_available<float>(int, int);
+template bool persist_available<double>(int, int);
+template size_t persist_smem_bytes<float>(int, int);
+template size_t persist_smem_bytes<double>(int, int);
+template void persist_explain<float>(int, int, size_t, char *, size_t);
+template void persist_explain<double>(int, int, size_t, char *, size_t);
+template int persist_blocks_per_sm<float>(int, int, size_t);
+template int persist_blocks_per_sm<double>(int, int, size_t);
+template cudaError_t launch_split_persist<float>(const StepParams<float> &, int, int, size_t, cudaStream_t);
+template cudaError_t launch_split_persist<double>(const StepParams<double> &, int, int, size_t, cudaStream_t);
 template int split_blocks_per_sm<float>(int, int, size_t);
 template int split_blocks_per_sm<double>(int, int, size_t);
 template size_t split_smem_bytes<float>(int, int);

@@ -38,6 +38,7 @@ EXPORTED = [
     "teuk_set_state", "teuk_get_state", "teuk_step", "teuk_extract_waveform",
     "teuk_current_step", "teuk_last_error", "teuk_status_string", "teuk_destroy",
     "teuk_tiling", "teuk_autotune", "teuk_set_tiling", "teuk_literal_step_static",
+    "teuk_kernel_config", "teuk_set_persistent", "teuk_autotune_cold",
 ]
 
 
@@ -105,9 +106,14 @@ def lib(load_only: bool = False):
     L.teuk_autotune.argtypes = [vp, ctypes.c_int, vp, ctypes.POINTER(ctypes.c_int)]
     L.teuk_set_tiling.argtypes = [vp, ctypes.c_int]
     L.teuk_literal_step_static.argtypes = [vp, vp, vp, i64, vp]
+    L.teuk_kernel_config.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                     ctypes.POINTER(ctypes.c_int)]
+    L.teuk_set_persistent.argtypes = [vp, ctypes.c_int, ctypes.c_int]
+    L.teuk_autotune_cold.argtypes = [vp, ctypes.c_int, vp, ctypes.c_size_t, vp, ctypes.POINTER(ctypes.c_int)]
     for name in ("teuk_workspace_bytes", "teuk_init_grid", "teuk_set_source", "teuk_set_weights",
                  "teuk_set_state", "teuk_get_state", "teuk_step", "teuk_extract_waveform", "teuk_destroy",
-                 "teuk_tiling", "teuk_autotune", "teuk_set_tiling", "teuk_literal_step_static"):
+                 "teuk_tiling", "teuk_autotune", "teuk_set_tiling", "teuk_literal_step_static",
+                 "teuk_kernel_config", "teuk_set_persistent", "teuk_autotune_cold"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -195,8 +201,24 @@ def teuk_autotune(ctx, trial_steps: int = 20, stream: int = 0) -> int:
     return tr.value
 
 
+def teuk_autotune_cold(ctx, trial_steps: int, d_flush: int, flush_bytes: int, stream: int = 0) -> int:
+    tr = ctypes.c_int()
+    _check(lib().teuk_autotune_cold(ctx, int(trial_steps), d_flush, int(flush_bytes), stream, ctypes.byref(tr)), ctx)
+    return tr.value
+
+
 def teuk_set_tiling(ctx, tile_rows: int):
     _check(lib().teuk_set_tiling(ctx, int(tile_rows)), ctx)
+
+
+def teuk_kernel_config(ctx) -> dict:
+    pe, nc, gr = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(lib().teuk_kernel_config(ctx, ctypes.byref(pe), ctypes.byref(nc), ctypes.byref(gr)), ctx)
+    return {"persistent": bool(pe.value), "consumer_threads": nc.value, "grid": gr.value}
+
+
+def teuk_set_persistent(ctx, tile_rows: int, consumer_threads: int = 480):
+    _check(lib().teuk_set_persistent(ctx, int(tile_rows), int(consumer_threads)), ctx)
 
 
 def teuk_literal_step_static(ctx, d_in: int, d_out: int, n: int, stream: int = 0):
@@ -243,14 +265,24 @@ class Stepper:
     def sh(self) -> int:
         return self.stream.cuda_stream
 
-    def autotune(self, trial_steps: int = 20) -> int:
-        return teuk_autotune(self.ctx, trial_steps, self.sh)
+    def autotune(self, trial_steps: int = 20, flush=None) -> int:
+        """Measured choice of kernel and tile height.  With flush (a device
+        tensor larger than the L2) every timed trial step starts cold."""
+        if flush is None:
+            return teuk_autotune(self.ctx, trial_steps, self.sh)
+        return teuk_autotune_cold(self.ctx, trial_steps, flush.data_ptr(), flush.numel() * flush.element_size(),
+                                  self.sh)
 
     def tiling(self) -> dict:
-        return teuk_tiling(self.ctx)
+        out = teuk_tiling(self.ctx)
+        out.update(teuk_kernel_config(self.ctx))
+        return out
 
     def set_tiling(self, tile_rows: int):
         teuk_set_tiling(self.ctx, tile_rows)
+
+    def set_persistent(self, tile_rows: int, consumer_threads: int = 480):
+        teuk_set_persistent(self.ctx, tile_rows, consumer_threads)
 
     def set_source(self, amp=1.0, r0=10.0, sigma_rstar=0.1, sigma_theta=0.1, Omega=float("nan")):
         teuk_set_source(self.ctx, amp, r0, sigma_rstar, sigma_theta, Omega)

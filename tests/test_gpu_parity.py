@@ -226,3 +226,62 @@ def test_result_independent_of_tiling_and_autotune(precision):
     st.step(w.steps)
     assert np.array_equal(st.get_state(), outs[0][0])
     st.close()
+
+
+PERSIST = [
+    # Nr, Ntheta, tile_rows, consumer threads
+    (700, 128, 28, 480),
+    (701, 128, 22, 384),
+    (333, 64, 21, 384),
+    (1000, 32, 46, 480),
+    (150, 16, 10, 384),
+]
+
+
+@pytest.mark.parametrize("Nr,Nth,tr,nc", PERSIST)
+def test_persistent_kernel_matches_tiled_and_oracle(Nr, Nth, tr, nc):
+    """The persistent kernel (producer warp + double-buffered tiles) runs the
+    same arithmetic as the tiled kernel: the same state and waveform bit for
+    bit, and the oracle within the FP32 tolerance.  Ragged last tiles, tiles
+    per CTA > 2 and a source patch spanning tile boundaries are covered."""
+    from oracle import oracle as O
+    w = inputs.Workload("persist", s=-2, m=2, a=0.9, Nr=Nr, Ntheta=Nth, rs_min=-60.0, rs_max=240.0, steps=24,
+                        r0=8.0, amp=0.8 + 0.3j, sig_r=0.9, sig_th=0.25, rs_ext=150.0)
+    u0 = inputs.random_state(w.Nr, w.Ntheta, seed=Nr + Nth)
+    outs = []
+    for persistent in (False, True):
+        st = gpu_stepper(w, "fp32", wave_capacity=64)
+        if persistent:
+            st.set_persistent(tr, nc)
+        else:
+            st.set_tiling(tr)
+        cfg = st.tiling()
+        assert cfg["persistent"] == persistent and cfg["tile_rows"] == tr
+        st.set_state(u0, 0)
+        st.step(w.steps)
+        outs.append((st.get_state(), st.waveform(0, w.steps + 1)))
+        st.close()
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+    uo, ho = O.run(oracle_problem(w), u0, w.steps)
+    assert rel_l2(outs[1][0], uo) <= FP32_TOL, rel_l2(outs[1][0], uo)
+    assert rel_l2(outs[1][1], ho) <= FP32_TOL, rel_l2(outs[1][1], ho)
+
+
+def test_persistent_kernel_rejected_where_unavailable():
+    """FP64 states and Ntheta > 128 have no persistent kernel: E_INVAL, and
+    the context keeps its previous (working) configuration."""
+    from paper_0909_4039_gb300 import teuk
+    w = inputs.Workload("nopersist", s=-2, m=2, a=0.5, Nr=200, Ntheta=32, rs_min=-50.0, rs_max=150.0, steps=4)
+    st = gpu_stepper(w, "fp64", wave_capacity=16)
+    before = st.tiling()
+    with pytest.raises(teuk.TeukError):
+        st.set_persistent(20, 480)
+    assert st.tiling() == before
+    st.close()
+    w2 = w.with_(Ntheta=256)
+    st = gpu_stepper(w2, "fp32", wave_capacity=16)
+    with pytest.raises(teuk.TeukError):
+        st.set_persistent(10, 384)
+    with pytest.raises(teuk.TeukError):
+        st.set_persistent(10, 256)
+    st.close()
