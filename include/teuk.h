@@ -241,6 +241,63 @@ const char *teuk_status_string(int status);
 /* Release the host context (the caller frees its device buffers). */
 int teuk_destroy(teuk_ctx *ctx);
 
+/* ---------------------------------------------------------------- batches
+ * Many independent instances -- each a split-scheme context with its own
+ * grid, spin, mode, source and buffers -- advanced together: one launch per
+ * step covers every tile of every instance (a flattened tile list of
+ * (instance, tile) entries), and long runs replay a captured CUDA graph.
+ * This is the data-parallel decomposition of the method over independent
+ * problems (Sec. 4); each instance computes exactly what teuk_step computes
+ * for it alone.  Instances must share the state precision and the theta
+ * segment class (Ntheta <= 128, <= 256 or <= 1024).  The batch holds
+ * pointers to the contexts, which must outlive it.  Every teuk_batch_step
+ * reads each instance's current level, step and phase, so between batched
+ * steps an instance may still be set, read, extracted or stepped alone. */
+typedef struct teuk_batch teuk_batch;
+
+/* Device workspace for a batch of `count` contexts (parameter tables and the
+ * tile list), in *bytes.  TEUK_E_INVAL for a NULL context or count < 1. */
+int teuk_batch_workspace_bytes(teuk_ctx *const *ctxs, int count, size_t *bytes);
+
+/* Group contexts into a batch.  d_ws: caller-owned device memory of at
+ * least teuk_batch_workspace_bytes, 256-byte aligned, for the lifetime of
+ * the batch.  Tile heights start from a shared-memory model (whole implicit
+ * passes, two CTAs per SM); teuk_batch_autotune measures them.
+ * TEUK_E_INVAL for mixed precision or segment class, a literal-scheme or
+ * repeated context.  Synchronous (uploads the tile list). */
+int teuk_batch_create(teuk_ctx *const *ctxs, int count, void *d_ws, size_t ws_bytes, teuk_batch **out);
+
+/* Advance every instance by nsteps (instances whose state is physical take
+ * the half implicit step first, as teuk_step does).  Asynchronous on
+ * `stream`; with a non-default stream and nsteps >= 128 chunks of 64 steps
+ * replay one captured graph.  Work queued for an instance on another stream
+ * (teuk_set_state, teuk_step) must be ordered before this call by the caller
+ * (an event the stream waits on), and later work on other streams after it. */
+int teuk_batch_step(teuk_batch *batch, int64_t nsteps, void *stream);
+
+/* Tile height per instance (tile_rows: count entries), number of CTAs per
+ * step and dynamic shared memory per CTA.  Any pointer may be NULL. */
+int teuk_batch_tiling(const teuk_batch *batch, int *tile_rows, int *total_tiles, size_t *smem_bytes);
+
+/* Set the tile height of every instance (count entries in [1, 254]);
+ * TEUK_E_INVAL (and the previous tiling kept) if a tile does not fit. */
+int teuk_batch_set_tiling(teuk_batch *batch, const int *tile_rows);
+
+/* Measured tile heights: coordinate descent over the batch's Ntheta
+ * classes, each class trying every whole number of implicit passes per tile
+ * that fits, timed over trial_steps batched steps (CUDA events on `stream`).
+ * The trials overwrite the states: afterwards every instance is zero at
+ * step 0 with an empty waveform buffer (sources and weights kept).
+ * Synchronous. */
+int teuk_batch_autotune(teuk_batch *batch, int trial_steps, void *stream);
+
+/* Message of the last error on the batch (or of the last failed create if
+ * batch is NULL). */
+const char *teuk_batch_last_error(const teuk_batch *batch);
+
+/* Release the batch (not its contexts or workspace). */
+int teuk_batch_destroy(teuk_batch *batch);
+
 #ifdef __cplusplus
 }
 #endif

@@ -195,8 +195,11 @@ double host_atheta_bound(const teuk_grid_desc &d)
 //
 // Persistent kernel (nc consumer threads + a producer warp, one CTA per SM,
 // tiles double-buffered): a CTA computes ceil(tiles / grid) tiles of
-// (0.6 Rpad + 0.4 R) (256 / nc) row-times each (Rpad in passes of nc / G
-// rows), plus the first tile's load.
+// (0.6 Rpad + 0.4 R) (256 / nc) + 2 row-times each (Rpad in passes of
+// nc / G rows; the 2 for its barriers), plus the first tile's load.  Its
+// consumers move in lockstep between barriers, which costs about a factor
+// of two per row-time against the tiled kernel's two independent CTAs per
+// SM (measured on 16384 x 128 at equal tile height).
 struct TileCand {
     double cost;
     int R;
@@ -256,8 +259,8 @@ static bool persist_cand(const teuk_ctx *c, int TR, int nc, int nsm, TileCand *o
     long long per = (tiles + grid - 1) / grid;
     int rpp = nc / implicit_group(N);
     int rpad = ((R + rpp - 1) / rpp) * rpp;
-    double rows = (0.6 * rpad + 0.4 * R) * 256.0 / nc;
-    out->cost = (double)per * k * rows + 4.0;
+    double rows = (0.6 * rpad + 0.4 * R) * 256.0 / nc + 2.0;
+    out->cost = 2.0 * (double)per * k * rows + 4.0;
     out->R = R;
     out->persist = 1;
     out->nc = nc;
@@ -410,6 +413,21 @@ void drop_graphs(teuk_ctx *c)
         c->graph[k] = nullptr;
         c->graph_stream[k] = nullptr;
     }
+}
+
+// Back to a clean state: zero field at step 0, empty ring buffer, cleared
+// flags (the source and weights are kept).
+int reset_state(teuk_ctx *c, cudaStream_t st)
+{
+    CK(cudaMemsetAsync(c->state, 0, 2 * c->level_bytes, st), "zero state");
+    CK(cudaMemsetAsync(c->wave, 0, sizeof(double2) * (size_t)(c->d.Ntheta + 1) * (size_t)c->cap, st), "zero wave");
+    CK(launch_set_ctl(c->coef, c->L, 0, 1, st), "control block");
+    c->cur = 0;
+    c->shifted = 0;
+    c->step = 0;
+    c->rec_lo = 0;
+    CK(extract_current(c, st), "extract");
+    return TEUK_OK;
 }
 
 }  // namespace
@@ -830,15 +848,8 @@ static int autotune_impl(teuk_ctx *c, int trial_steps, void *flush, size_t flush
     if (e != cudaSuccess) return cuda_err(c, e, "autotune trial");
     if (bestk < 0) return set_err(c, TEUK_E_CUDA, "no tile of the split kernel fits on this device%s");
     apply_cand(c, cand[bestk]);
-    // back to a clean state: zero field at step 0, empty ring buffer
-    CK(cudaMemsetAsync(c->state, 0, 2 * c->level_bytes, st), "zero state");
-    CK(cudaMemsetAsync(c->wave, 0, sizeof(double2) * (size_t)(c->d.Ntheta + 1) * (size_t)c->cap, st), "zero wave");
-    CK(launch_set_ctl(c->coef, c->L, 0, 1, st), "control block");
-    c->cur = 0;
-    c->shifted = 0;
-    c->step = 0;
-    c->rec_lo = 0;
-    CK(extract_current(c, st), "extract");
+    int rr = reset_state(c, st);
+    if (rr != TEUK_OK) return rr;
     CK(cudaStreamSynchronize(st), "autotune sync");
     if (tile_rows_out) *tile_rows_out = c->tile_rows;
     return TEUK_OK;
@@ -919,6 +930,398 @@ int teuk_literal_step_static(const teuk_ctx *c, const void *d_in, void *d_out, i
         e = launch_literal_step_static<double>(p, (long long)n, st);
     }
     if (e != cudaSuccess) return cuda_err(cm, e, "literal step (static scratch)");
+    return TEUK_OK;
+}
+
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ batches
+
+struct teuk_batch {
+    std::vector<teuk_ctx *> c;
+    std::vector<int> tr;             // tile height per instance
+    int prec, seg;
+    char *ws;                        // caller-owned device workspace
+    size_t ws_bytes, par_bytes;      // par_bytes: one parameter table
+    size_t off_par[3], off_tiles;    // tables: in = cur, in = cur ^ 1, first step; tile list
+    int ntot;
+    size_t smem;
+    cudaGraphExec_t graph;
+    cudaStream_t graph_stream;
+    std::vector<unsigned char> hpar;
+    std::vector<int2> htiles;
+    char err[512];
+};
+
+namespace {
+
+int bset_err(teuk_batch *b, int code, const char *fmt, const char *a = "", double x = 0.0)
+{
+    snprintf(b ? b->err : g_init_err, 512, fmt, a, x);
+    return code;
+}
+
+int bcuda_err(teuk_batch *b, cudaError_t e, const char *where)
+{
+    snprintf(b ? b->err : g_init_err, 512, "%s: %s", where, cudaGetErrorString(e));
+    return TEUK_E_CUDA;
+}
+
+#define BCK(call, where)                                      \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return bcuda_err(b, e_, where); \
+    } while (0)
+
+size_t params_size(int prec) { return prec == TEUK_FP32 ? sizeof(StepParams<float>) : sizeof(StepParams<double>); }
+
+size_t batch_ws_bytes(teuk_ctx *const *ctxs, int count, size_t *par_bytes, size_t *tiles_off)
+{
+    const size_t pb = align256(params_size(ctxs[0]->d.precision) * (size_t)count);
+    size_t rows = 0;
+    for (int i = 0; i < count; ++i) rows += (size_t)ctxs[i]->d.Nr;
+    if (par_bytes) *par_bytes = pb;
+    if (tiles_off) *tiles_off = 3 * pb;
+    return 3 * pb + align256(sizeof(int2) * rows);
+}
+
+// Rows of one implicit pass for Ntheta (256 threads / G).
+int batch_rpp(int N) { return 256 / implicit_group(N); }
+
+// Default tile height: the largest whole number of implicit passes whose
+// tile leaves room for two CTAs per SM.
+int batch_default_tr(const teuk_ctx *c)
+{
+    const int N = (int)c->d.Ntheta, rpp = batch_rpp(N);
+    const bool f32 = c->d.precision == TEUK_FP32;
+    int best = 1;
+    for (int R = rpp; R - 2 <= 254; R += rpp) {
+        size_t sm = f32 ? split_smem_bytes<float>(R - 2, N) : split_smem_bytes<double>(R - 2, N);
+        if (sm > 112 * 1024 && R > rpp) break;
+        if (R - 2 >= 1) best = R - 2;
+        if (R - 2 >= c->d.Nr) break;
+    }
+    return best;
+}
+
+// Tile list (instances interleaved tile by tile) and shared memory for the
+// current tile heights; drops the captured graph.
+int batch_layout(teuk_batch *b)
+{
+    const int n = (int)b->c.size();
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+    b->graph_stream = nullptr;
+    std::vector<int> nt(n);
+    int maxt = 0;
+    size_t smem = 0;
+    for (int i = 0; i < n; ++i) {
+        const teuk_ctx *c = b->c[i];
+        nt[i] = (int)((c->d.Nr + b->tr[i] - 1) / b->tr[i]);
+        maxt = nt[i] > maxt ? nt[i] : maxt;
+        const int N = (int)c->d.Ntheta;
+        size_t sm = b->prec == TEUK_FP32 ? split_smem_bytes<float>(b->tr[i], N) : split_smem_bytes<double>(b->tr[i], N);
+        smem = sm > smem ? sm : smem;
+    }
+    if (smem > 227 * 1024) return bset_err(b, TEUK_E_INVAL, "a tile of the batch does not fit in shared memory%s");
+    int k = b->prec == TEUK_FP32 ? split_batch_blocks_per_sm<float>(b->seg, smem)
+                                 : split_batch_blocks_per_sm<double>(b->seg, smem);
+    if (k < 1) return bset_err(b, TEUK_E_INVAL, "the batched kernel does not fit on this device with these tiles%s");
+    b->htiles.clear();
+    for (int t = 0; t < maxt; ++t)
+        for (int i = 0; i < n; ++i)
+            if (t < nt[i]) b->htiles.push_back(make_int2(i, t));
+    b->ntot = (int)b->htiles.size();
+    b->smem = smem;
+    if ((size_t)b->ntot * sizeof(int2) > b->ws_bytes - b->off_tiles)
+        return bset_err(b, TEUK_E_INVAL, "workspace too small for the tile list%s");
+    // launches in flight on any stream may still read the old list
+    BCK(cudaDeviceSynchronize(), "wait before the tile list changes");
+    BCK(cudaMemcpy(b->ws + b->off_tiles, b->htiles.data(), sizeof(int2) * b->htiles.size(), cudaMemcpyHostToDevice),
+        "tile list upload");
+    return TEUK_OK;
+}
+
+template <typename T>
+void batch_fill(teuk_batch *b)
+{
+    const int n = (int)b->c.size();
+    b->hpar.assign(3 * b->par_bytes, 0);
+    for (int k = 0; k < 3; ++k)
+        for (int i = 0; i < n; ++i) {
+            teuk_ctx *c = b->c[i];
+            StepParams<T> p = make_params<T>(c, k == 1 ? c->cur ^ 1 : c->cur);
+            p.tile_rows = b->tr[i];
+            p.first = k == 2 ? (c->shifted ? 0 : 1) : 0;
+            memcpy(b->hpar.data() + k * b->par_bytes + i * sizeof(StepParams<T>), &p, sizeof(p));
+        }
+}
+
+// Parameter tables for the instances' current levels, uploaded on `st`.
+int batch_tables(teuk_batch *b, cudaStream_t st)
+{
+    if (b->prec == TEUK_FP32) batch_fill<float>(b);
+    else batch_fill<double>(b);
+    BCK(cudaMemcpyAsync(b->ws, b->hpar.data(), b->hpar.size(), cudaMemcpyHostToDevice, st), "parameter upload");
+    return TEUK_OK;
+}
+
+cudaError_t batch_launch(teuk_batch *b, int table, cudaStream_t st)
+{
+    const int2 *tiles = (const int2 *)(b->ws + b->off_tiles);
+    if (b->prec == TEUK_FP32)
+        return launch_split_batch<float>((const StepParams<float> *)(b->ws + b->off_par[table]), tiles, b->ntot, b->seg,
+                                         b->smem, st);
+    return launch_split_batch<double>((const StepParams<double> *)(b->ws + b->off_par[table]), tiles, b->ntot, b->seg,
+                                      b->smem, st);
+}
+
+int batch_step_impl(teuk_batch *b, int64_t nsteps, cudaStream_t st)
+{
+    int64_t left = nsteps;
+    if (left <= 0) return TEUK_OK;
+    int r = batch_tables(b, st);
+    if (r != TEUK_OK) return r;
+    bool any_first = false;
+    for (teuk_ctx *c : b->c) any_first = any_first || !c->shifted;
+    if (any_first) {
+        // first step from physical states: s_{n+1} = LW C_{dt/2} u_n where needed
+        BCK(batch_launch(b, 2, st), "batched first step");
+        for (teuk_ctx *c : b->c) {
+            c->cur ^= 1;
+            c->shifted = 1;
+        }
+        left -= 1;
+        r = batch_tables(b, st);
+        if (r != TEUK_OK) return r;
+    }
+    if (st != nullptr && left >= 2 * kGraphChunk) {
+        if (b->graph && b->graph_stream != st) {
+            cudaGraphExecDestroy(b->graph);
+            b->graph = nullptr;
+        }
+        if (!b->graph) {
+            cudaGraph_t graph;
+            BCK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal), "begin capture");
+            cudaError_t le = cudaSuccess;
+            for (int k = 0; k < kGraphChunk && le == cudaSuccess; ++k) le = batch_launch(b, k & 1, st);
+            cudaError_t ee = cudaStreamEndCapture(st, &graph);
+            if (le != cudaSuccess) return bcuda_err(b, le, "captured batched launch");
+            if (ee != cudaSuccess) return bcuda_err(b, ee, "end capture");
+            cudaError_t ie = cudaGraphInstantiate(&b->graph, graph, 0);
+            cudaGraphDestroy(graph);
+            if (ie != cudaSuccess) {
+                b->graph = nullptr;
+                return bcuda_err(b, ie, "graph instantiate");
+            }
+            b->graph_stream = st;
+        }
+        while (left >= kGraphChunk) {
+            BCK(cudaGraphLaunch(b->graph, st), "graph launch");
+            left -= kGraphChunk;
+        }
+    }
+    for (int64_t k = 0; k < left; ++k) BCK(batch_launch(b, (int)(k & 1), st), "batched step");
+    for (teuk_ctx *c : b->c) {
+        c->cur ^= (int)(left & 1);
+        c->step += nsteps;
+    }
+    return TEUK_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int teuk_batch_workspace_bytes(teuk_ctx *const *ctxs, int count, size_t *bytes)
+{
+    if (!ctxs || count < 1 || !bytes) {
+        snprintf(g_init_err, sizeof(g_init_err), "need count >= 1 contexts and an output pointer");
+        return TEUK_E_INVAL;
+    }
+    for (int i = 0; i < count; ++i)
+        if (!ctxs[i]) {
+            snprintf(g_init_err, sizeof(g_init_err), "context %d is NULL", i);
+            return TEUK_E_INVAL;
+        }
+    *bytes = batch_ws_bytes(ctxs, count, nullptr, nullptr);
+    return TEUK_OK;
+}
+
+int teuk_batch_create(teuk_ctx *const *ctxs, int count, void *d_ws, size_t ws_bytes, teuk_batch **out)
+{
+    if (!out) return TEUK_E_INVAL;
+    *out = nullptr;
+    size_t need = 0;
+    int r = teuk_batch_workspace_bytes(ctxs, count, &need);
+    if (r != TEUK_OK) return r;
+    if (!d_ws || ws_bytes < need || ((uintptr_t)d_ws & 255u)) {
+        snprintf(g_init_err, sizeof(g_init_err), "workspace must be 256-byte aligned and at least %zu bytes", need);
+        return TEUK_E_INVAL;
+    }
+    const int prec = ctxs[0]->d.precision;
+    const int seg = implicit_seg((int)ctxs[0]->d.Ntheta);
+    for (int i = 0; i < count; ++i) {
+        const teuk_ctx *c = ctxs[i];
+        const char *why = nullptr;
+        if (c->d.scheme != TEUK_SCHEME_SPLIT) why = "is not a split-scheme context";
+        else if (c->d.precision != prec) why = "has another state precision than context 0";
+        else if (implicit_seg((int)c->d.Ntheta) != seg) why = "has an Ntheta of another theta-segment class";
+        for (int j = 0; j < i && !why; ++j)
+            if (ctxs[j] == c) why = "appears twice";
+        if (why) {
+            snprintf(g_init_err, sizeof(g_init_err), "context %d %s", i, why);
+            return TEUK_E_INVAL;
+        }
+    }
+    teuk_batch *b = new (std::nothrow) teuk_batch();
+    if (!b) return TEUK_E_INVAL;
+    b->c.assign(ctxs, ctxs + count);
+    b->prec = prec;
+    b->seg = seg;
+    b->ws = (char *)d_ws;
+    b->ws_bytes = ws_bytes;
+    batch_ws_bytes(ctxs, count, &b->par_bytes, &b->off_tiles);
+    for (int k = 0; k < 3; ++k) b->off_par[k] = (size_t)k * b->par_bytes;
+    b->tr.resize(count);
+    for (int i = 0; i < count; ++i) b->tr[i] = batch_default_tr(ctxs[i]);
+    r = batch_layout(b);
+    if (r != TEUK_OK) {
+        memcpy(g_init_err, b->err, sizeof(g_init_err));
+        delete b;
+        return r;
+    }
+    // the workspace holds valid parameter tables from the start
+    r = batch_tables(b, nullptr);
+    if (r == TEUK_OK && cudaStreamSynchronize(nullptr) != cudaSuccess) r = bcuda_err(b, cudaGetLastError(), "table upload");
+    if (r != TEUK_OK) {
+        memcpy(g_init_err, b->err, sizeof(g_init_err));
+        delete b;
+        return r;
+    }
+    for (teuk_ctx *c : b->c) drop_graphs(c);
+    *out = b;
+    return TEUK_OK;
+}
+
+int teuk_batch_step(teuk_batch *b, int64_t nsteps, void *stream)
+{
+    if (!b) return TEUK_E_STATE;
+    if (nsteps < 0) return bset_err(b, TEUK_E_INVAL, "nsteps must be >= 0%s");
+    return batch_step_impl(b, nsteps, (cudaStream_t)stream);
+}
+
+int teuk_batch_tiling(const teuk_batch *b, int *tile_rows, int *total_tiles, size_t *smem_bytes)
+{
+    if (!b) return TEUK_E_STATE;
+    if (tile_rows)
+        for (size_t i = 0; i < b->tr.size(); ++i) tile_rows[i] = b->tr[i];
+    if (total_tiles) *total_tiles = b->ntot;
+    if (smem_bytes) *smem_bytes = b->smem;
+    return TEUK_OK;
+}
+
+int teuk_batch_set_tiling(teuk_batch *b, const int *tile_rows)
+{
+    if (!b) return TEUK_E_STATE;
+    if (!tile_rows) return bset_err(b, TEUK_E_INVAL, "tile_rows is NULL%s");
+    std::vector<int> old = b->tr;
+    for (size_t i = 0; i < b->tr.size(); ++i) {
+        if (tile_rows[i] < 1 || tile_rows[i] > 254) return bset_err(b, TEUK_E_INVAL, "tile_rows out of range [1, 254]%s");
+        b->tr[i] = tile_rows[i];
+    }
+    int r = batch_layout(b);
+    if (r != TEUK_OK) {
+        b->tr = old;
+        char keep[512];
+        memcpy(keep, b->err, sizeof(keep));
+        batch_layout(b);
+        memcpy(b->err, keep, sizeof(keep));
+    }
+    return r;
+}
+
+int teuk_batch_autotune(teuk_batch *b, int trial_steps, void *stream)
+{
+    if (!b) return TEUK_E_STATE;
+    if (trial_steps < 1 || trial_steps > 100000) return bset_err(b, TEUK_E_INVAL, "trial_steps out of range%s");
+    cudaStream_t st = (cudaStream_t)stream;
+    // Coordinate descent over the Ntheta classes of the batch: for each
+    // class, every whole number of implicit passes per tile that fits is
+    // timed with the other classes fixed, and the fastest is kept.
+    std::vector<int> classes;
+    for (teuk_ctx *c : b->c) {
+        int N = (int)c->d.Ntheta;
+        bool seen = false;
+        for (int v : classes) seen = seen || v == N;
+        if (!seen) classes.push_back(N);
+    }
+    cudaEvent_t e0, e1;
+    BCK(cudaEventCreate(&e0), "event");
+    BCK(cudaEventCreate(&e1), "event");
+    int rc = TEUK_OK;
+    for (int N : classes) {
+        const int rpp = batch_rpp(N);
+        std::vector<int> keep = b->tr;
+        float best = 3.4e38f;
+        int best_tr = -1;
+        for (int R = rpp; R - 2 <= 254 && rc == TEUK_OK; R += rpp) {
+            if (R - 2 < 1) continue;
+            std::vector<int> trial = keep;
+            for (size_t i = 0; i < b->c.size(); ++i)
+                if ((int)b->c[i]->d.Ntheta == N) trial[i] = R - 2;
+            b->tr = trial;
+            if (batch_layout(b) != TEUK_OK) break;   // larger tiles do not fit either
+            for (teuk_ctx *c : b->c) c->shifted = 1;
+            rc = batch_tables(b, st);                 // parameters for these tile heights
+            if (rc != TEUK_OK) break;
+            cudaError_t e = cudaSuccess;
+            for (int w = 0; w < 2 && e == cudaSuccess; ++w) e = batch_launch(b, w & 1, st);
+            if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+            for (int w = 0; w < trial_steps && e == cudaSuccess; ++w) e = batch_launch(b, w & 1, st);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.0f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e != cudaSuccess) {
+                rc = bcuda_err(b, e, "batch autotune trial");
+                break;
+            }
+            if (ms < best) {
+                best = ms;
+                best_tr = R - 2;
+            }
+        }
+        b->tr = keep;
+        if (best_tr > 0)
+            for (size_t i = 0; i < b->c.size(); ++i)
+                if ((int)b->c[i]->d.Ntheta == N) b->tr[i] = best_tr;
+        if (rc != TEUK_OK) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != TEUK_OK) return rc;
+    int r = batch_layout(b);
+    if (r != TEUK_OK) return r;
+    for (teuk_ctx *c : b->c) {
+        r = reset_state(c, st);
+        if (r != TEUK_OK) {
+            snprintf(b->err, sizeof(b->err), "reset after autotune: %.400s", c->err);
+            return r;
+        }
+    }
+    BCK(cudaStreamSynchronize(st), "autotune sync");
+    return TEUK_OK;
+}
+
+const char *teuk_batch_last_error(const teuk_batch *b) { return b ? b->err : g_init_err; }
+
+int teuk_batch_destroy(teuk_batch *b)
+{
+    if (!b) return TEUK_OK;
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    delete b;
     return TEUK_OK;
 }
 

@@ -189,6 +189,14 @@ template <typename T>
 cudaError_t launch_split_persist(const StepParams<T> &p, int nc, int grid, size_t smem, cudaStream_t st);
 template <typename T>
 int split_blocks_per_sm(int Nth, int threads, size_t smem);   // 0 if the launch cannot fit
+// Batched split step: one CTA of 256 threads per entry of the tile list
+// (instance, tile); params[instance] describes the instance's step.  Every
+// instance must use the theta segment `seg` (implicit_seg of its Ntheta).
+template <typename T>
+int split_batch_blocks_per_sm(int seg, size_t smem);
+template <typename T>
+cudaError_t launch_split_batch(const StepParams<T> *d_params, const int2 *d_tiles, int ntiles, int seg, size_t smem,
+                               cudaStream_t st);
 int implicit_group(int Nth);            // threads per theta row
 int implicit_seg(int Nth);              // theta elements per thread
 constexpr int kSegNarrow = 4;           // theta elements per thread (Ntheta <= 128)

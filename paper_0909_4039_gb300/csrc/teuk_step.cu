@@ -26,6 +26,8 @@
 #include <stdio.h>
 
 #include <mutex>
+#include <utility>
+#include <vector>
 
 #include "teuk_internal.cuh"
 
@@ -270,27 +272,38 @@ __device__ void implicit_row_group(const ImpConst<T> &K, typename V2<T>::t *phi,
     // below ScanTol in magnitude the level adds nothing the state precision
     // can hold, and neither do the levels above it (their multipliers are
     // products of these), so the scans stop there: nf levels forward, nb
-    // backward (warp-uniform).  The data scans recompute the multipliers of
-    // the levels they use instead of keeping one per level in registers.
+    // backward.  The test is taken over this row's group of G lanes only, so
+    // a row's result does not depend on the rows that share its warp; the
+    // shuffles run for the levels any group of the warp needs (nfw, nbw).
+    // The data scans recompute the multipliers of the levels they use
+    // instead of keeping one per level in registers.
     c2 Af0 = one, Ab0 = one;
-    int nf = 0, nb = 0;
+    int nf = 0, nb = 0, nfw = 0, nbw = 0;
     {
 #pragma unroll
         for (int k = 0; k < S; ++k) Af0 = cmul(cmk<c2>(-m[k].x, -m[k].y), Af0);
 #pragma unroll
         for (int k = S - 1; k >= 0; --k) Ab0 = cmul(cmk<c2>(-fk[k].x, -fk[k].y), Ab0);
         const T tol2 = ScanTol<T>::v * ScanTol<T>::v;
+        const unsigned lane = threadIdx.x & 31u;
+        const unsigned gbase = lane - (unsigned)g;
+        const unsigned gmask = G >= 32 ? 0xffffffffu : ((1u << G) - 1u);
         c2 Af = Af0, Ab = Ab0;
         bool gf = true, gb = true;
 #pragma unroll
         for (int l = 0; l < LOGMAX; ++l) {
             const int d = 1 << l;
             if (d >= G) break;
-            gf = gf && __any_sync(0xffffffffu, g >= d && fma(Af.x, Af.x, Af.y * Af.y) > tol2);
-            gb = gb && __any_sync(0xffffffffu, g + d < G && fma(Ab.x, Ab.x, Ab.y * Ab.y) > tol2);
-            if (!gf && !gb) break;
+            const unsigned bf = __ballot_sync(0xffffffffu, g >= d && fma(Af.x, Af.x, Af.y * Af.y) > tol2);
+            const unsigned bb = __ballot_sync(0xffffffffu, g + d < G && fma(Ab.x, Ab.x, Ab.y * Ab.y) > tol2);
+            gf = gf && ((bf >> gbase) & gmask) != 0u;
+            gb = gb && ((bb >> gbase) & gmask) != 0u;
+            const bool wf = __any_sync(0xffffffffu, gf), wb = __any_sync(0xffffffffu, gb);
+            if (!wf && !wb) break;
             if (gf) nf = l + 1;
             if (gb) nb = l + 1;
+            if (wf) nfw = l + 1;
+            if (wb) nbw = l + 1;
             if (2 * d >= G) break;
             const c2 Ao = shfl_up_c(Af, d, G), Bo = shfl_down_c(Ab, d, G);
             if (gf && g >= d) Af = cmul(Af, Ao);
@@ -307,14 +320,13 @@ __device__ void implicit_row_group(const ImpConst<T> &K, typename V2<T>::t *phi,
             c2 A = Af0;
 #pragma unroll
             for (int l = 0; l < LOGMAX; ++l) {
-                if (l < nf) {
+                if (l < nfw) {
                     const int d = 1 << l;
-                    const bool more = l + 1 < nf;
                     c2 Bo = shfl_up_c(B, d, G), Ao = one;
-                    if (more) Ao = shfl_up_c(A, d, G);
-                    if (g >= d) {
+                    if (l + 1 < nfw) Ao = shfl_up_c(A, d, G);
+                    if (l < nf && g >= d) {
                         B = cadd(cmul(A, Bo), B);
-                        if (more) A = cmul(A, Ao);
+                        if (l + 1 < nf) A = cmul(A, Ao);
                     }
                 }
             }
@@ -333,14 +345,13 @@ __device__ void implicit_row_group(const ImpConst<T> &K, typename V2<T>::t *phi,
             c2 A = Ab0;
 #pragma unroll
             for (int l = 0; l < LOGMAX; ++l) {
-                if (l < nb) {
+                if (l < nbw) {
                     const int d = 1 << l;
-                    const bool more = l + 1 < nb;
                     c2 Bo = shfl_down_c(B, d, G), Ao = one;
-                    if (more) Ao = shfl_down_c(A, d, G);
-                    if (g + d < G) {
+                    if (l + 1 < nbw) Ao = shfl_down_c(A, d, G);
+                    if (l < nb && g + d < G) {
                         B = cadd(cmul(A, Bo), B);
-                        if (more) A = cmul(A, Ao);
+                        if (l + 1 < nb) A = cmul(A, Ao);
                     }
                 }
             }
@@ -653,8 +664,11 @@ __device__ void extract_warp(const StepParams<T> &p, const typename V2<T>::t *ro
 // and the physical sample u_{n+1} = C_{dt/2} s_{n+1} is taken on the
 // extraction row.  With p.imp_only the kernel only applies C_{dt/2} to the
 // tile rows (used to output the physical state).
+// The work of one CTA: tile number `tile` of the grid described by p, whose
+// step takes `ntiles` CTAs (the last of them to start advances the step
+// index).
 template <typename T, int S>
-__global__ void __launch_bounds__(256, (sizeof(T) == 4 && S <= 4) ? 2 : 1) k_split_step(const StepParams<T> p)
+__device__ __forceinline__ void split_tile(const StepParams<T> &p, int tile, int ntiles)
 {
     typedef typename V2<T>::t c2;
     constexpr int kMaxChunks = 8;
@@ -664,7 +678,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && S <= 4) ? 2 : 1) k_spl
     __shared__ __align__(8) unsigned long long s_mbar[kMaxChunks];
     const int Nr = p.Nr, N = p.Nth, TR = p.tile_rows, R = TR + 2, P = p.pitch;
     const int tid = threadIdx.x, NT = blockDim.x;
-    const int i0 = blockIdx.x * TR;
+    const int i0 = tile * TR;
     const int G = p.group;
 
     const SplitSmem plan = split_smem_plan(R, N, (int)sizeof(T));
@@ -687,7 +701,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && S <= 4) ? 2 : 1) k_spl
             // again, so no CTA has to wait for its own stores first.
             __threadfence();
             unsigned t = atomicAdd(&p.ctl->ticket, 1u);
-            if (t == gridDim.x - 1) {
+            if (t == (unsigned)ntiles - 1u) {
                 p.ctl->ticket = 0u;
                 p.ctl->step = n + 1;
             }
@@ -854,6 +868,31 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && S <= 4) ? 2 : 1) k_spl
             extract_warp<T>(p, sPhi + lr * P, s_n + 1);
         }
     }
+}
+
+template <typename T, int S>
+__global__ void __launch_bounds__(256, (sizeof(T) == 4 && S <= 4) ? 2 : 1) k_split_step(const StepParams<T> p)
+{
+    split_tile<T, S>(p, (int)blockIdx.x, (int)gridDim.x);
+}
+
+// Batched split step: every CTA takes entry blockIdx.x of the tile list,
+// (instance, tile), stages that instance's parameters in shared memory and
+// computes the tile.  One launch advances every instance of the batch by one
+// step; the instances may differ in every parameter (grid, spin, mode,
+// source, tile height) as long as they share the state precision and the
+// theta segment S.
+template <typename T, int S>
+__global__ void __launch_bounds__(256, (sizeof(T) == 4 && S <= 4) ? 2 : 1)
+    k_split_batch(const StepParams<T> *params, const int2 *tiles)
+{
+    __shared__ __align__(16) StepParams<T> sp;
+    static_assert(sizeof(StepParams<T>) % 4 == 0 && sizeof(StepParams<T>) <= 4 * 256, "parameter copy");
+    const int2 e = tiles[blockIdx.x];
+    if (threadIdx.x < sizeof(StepParams<T>) / 4)
+        reinterpret_cast<int *>(&sp)[threadIdx.x] = reinterpret_cast<const int *>(params + e.x)[threadIdx.x];
+    __syncthreads();
+    split_tile<T, S>(sp, e.y, (sp.Nr + sp.tile_rows - 1) / sp.tile_rows);
 }
 
 __device__ __forceinline__ void mbar_arrive(unsigned long long *m)
@@ -1252,6 +1291,31 @@ __global__ void k_from_f32(const float2 *src, double2 *dst, size_t n)
 
 }  // namespace
 
+// Raise a kernel's dynamic shared-memory limit to the device maximum, once
+// per kernel and device.  Occupancy queries and launches never lower it, so
+// a launch within the maximum is valid whatever was queried before it.
+static cudaError_t smem_limit_max(const void *fn)
+{
+    static std::mutex mu;
+    static std::vector<std::pair<const void *, int>> done;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    for (const auto &d : done)
+        if (d.first == fn && d.second == dev) return cudaSuccess;
+    int optin = 0;
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    cudaFuncAttributes a;
+    e = cudaFuncGetAttributes(&a, fn);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)a.sharedSizeBytes);
+    if (e != cudaSuccess) return e;
+    done.emplace_back(fn, dev);
+    return cudaSuccess;
+}
+
 template <typename T>
 size_t split_smem_bytes(int tile_rows, int Nth)
 {
@@ -1274,7 +1338,7 @@ int split_blocks_per_sm(int Nth, int threads, size_t smem)
 {
     const int seg = implicit_seg(Nth);
     auto fn = seg == kSegNarrow ? k_split_step<T, kSegNarrow> : (seg == kSeg ? k_split_step<T, kSeg> : k_split_step<T, kSegWide>);
-    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+    if (smem_limit_max((const void *)fn) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
@@ -1289,17 +1353,11 @@ int split_blocks_per_sm(int Nth, int threads, size_t smem)
 template <typename T>
 cudaError_t launch_split_step(const StepParams<T> &p, int threads, size_t smem, cudaStream_t st)
 {
-    // opt in to the dynamic shared memory this launch needs (once per size)
-    static size_t configured[2][3] = {{0, 0, 0}, {0, 0, 0}};
     const int seg = implicit_seg(p.Nth);
     const int v = seg == kSegNarrow ? 0 : (seg == kSeg ? 1 : 2);
-    int key = sizeof(T) == 4 ? 0 : 1;
     auto fn = v == 0 ? k_split_step<T, kSegNarrow> : (v == 1 ? k_split_step<T, kSeg> : k_split_step<T, kSegWide>);
-    if (smem > configured[key][v]) {
-        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        configured[key][v] = smem;
-    }
+    cudaError_t e = smem_limit_max((const void *)fn);
+    if (e != cudaSuccess) return e;
     int grid = (p.Nr + p.tile_rows - 1) / p.tile_rows;
     fn<<<grid, threads, smem, st>>>(p);
     return cudaGetLastError();
@@ -1334,7 +1392,7 @@ int persist_blocks_per_sm(int Nth, int nc, size_t smem)
 {
     auto fn = persist_fn<T>(Nth, nc);
     if (!fn) return 0;
-    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+    if (smem_limit_max((const void *)fn) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
@@ -1361,7 +1419,7 @@ void persist_explain(int Nth, int nc, size_t smem, char *buf, size_t len)
         snprintf(buf, len, "cudaFuncGetAttributes: %s", cudaGetErrorString(e));
         return;
     }
-    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = smem_limit_max((const void *)fn);
     cudaGetLastError();
     int nb = -1;
     cudaError_t e2 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, nc + 32, smem);
@@ -1376,16 +1434,46 @@ void persist_explain(int Nth, int nc, size_t smem, char *buf, size_t len)
 template <typename T>
 cudaError_t launch_split_persist(const StepParams<T> &p, int nc, int grid, size_t smem, cudaStream_t st)
 {
-    static size_t configured[2] = {0, 0};
     auto fn = persist_fn<T>(p.Nth, nc);
     if (!fn || !p.bulk || grid < 1) return cudaErrorInvalidConfiguration;
-    const int v = nc == 384 ? 0 : 1;
-    if (smem > configured[v]) {
-        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        configured[v] = smem;
-    }
+    cudaError_t e = smem_limit_max((const void *)fn);
+    if (e != cudaSuccess) return e;
     fn<<<grid, nc + 32, smem, st>>>(p);
+    return cudaGetLastError();
+}
+
+template <typename T>
+static void (*batch_fn(int seg))(const StepParams<T> *, const int2 *)
+{
+    return seg == kSegNarrow ? k_split_batch<T, kSegNarrow>
+                             : (seg == kSeg ? k_split_batch<T, kSeg> : k_split_batch<T, kSegWide>);
+}
+
+template <typename T>
+int split_batch_blocks_per_sm(int seg, size_t smem)
+{
+    auto fn = batch_fn<T>(seg);
+    if (smem_limit_max((const void *)fn) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, 256, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return nb;
+}
+
+template <typename T>
+cudaError_t launch_split_batch(const StepParams<T> *d_params, const int2 *d_tiles, int ntiles, int seg, size_t smem,
+                               cudaStream_t st)
+{
+    auto fn = batch_fn<T>(seg);
+    cudaError_t e = smem_limit_max((const void *)fn);
+    if (e != cudaSuccess) return e;
+    if (ntiles < 1) return cudaSuccess;
+    fn<<<ntiles, 256, smem, st>>>(d_params, d_tiles);
     return cudaGetLastError();
 }
 
@@ -1456,6 +1544,11 @@ cudaError_t launch_convert_from(int prec, const void *src, double2 *dst, size_t 
     return cudaGetLastError();
 }
 
+template int split_batch_blocks_per_sm<float>(int, size_t);
+template int split_batch_blocks_per_sm<double>(int, size_t);
+template cudaError_t launch_split_batch<float>(const StepParams<float> *, const int2 *, int, int, size_t, cudaStream_t);
+template cudaError_t launch_split_batch<double>(const StepParams<double> *, const int2 *, int, int, size_t,
+                                                cudaStream_t);
 template bool persist_available<float>(int, int);
 template bool persist_available<double>(int, int);
 template size_t persist_smem_bytes<float>(int, int);

@@ -39,6 +39,8 @@ EXPORTED = [
     "teuk_current_step", "teuk_last_error", "teuk_status_string", "teuk_destroy",
     "teuk_tiling", "teuk_autotune", "teuk_set_tiling", "teuk_literal_step_static",
     "teuk_kernel_config", "teuk_set_persistent", "teuk_autotune_cold",
+    "teuk_batch_workspace_bytes", "teuk_batch_create", "teuk_batch_step", "teuk_batch_tiling",
+    "teuk_batch_set_tiling", "teuk_batch_autotune", "teuk_batch_last_error", "teuk_batch_destroy",
 ]
 
 
@@ -114,6 +116,20 @@ def lib(load_only: bool = False):
                  "teuk_set_state", "teuk_get_state", "teuk_step", "teuk_extract_waveform", "teuk_destroy",
                  "teuk_tiling", "teuk_autotune", "teuk_set_tiling", "teuk_literal_step_static",
                  "teuk_kernel_config", "teuk_set_persistent", "teuk_autotune_cold"):
+        getattr(L, name).restype = ctypes.c_int
+    pvp = ctypes.POINTER(vp)
+    ip = ctypes.POINTER(ctypes.c_int)
+    L.teuk_batch_workspace_bytes.argtypes = [pvp, ctypes.c_int, sz]
+    L.teuk_batch_create.argtypes = [pvp, ctypes.c_int, vp, ctypes.c_size_t, pvp]
+    L.teuk_batch_step.argtypes = [vp, i64, vp]
+    L.teuk_batch_tiling.argtypes = [vp, ip, ip, sz]
+    L.teuk_batch_set_tiling.argtypes = [vp, ip]
+    L.teuk_batch_autotune.argtypes = [vp, ctypes.c_int, vp]
+    L.teuk_batch_last_error.argtypes = [vp]
+    L.teuk_batch_last_error.restype = ctypes.c_char_p
+    L.teuk_batch_destroy.argtypes = [vp]
+    for name in ("teuk_batch_workspace_bytes", "teuk_batch_create", "teuk_batch_step", "teuk_batch_tiling",
+                 "teuk_batch_set_tiling", "teuk_batch_autotune", "teuk_batch_destroy"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -323,6 +339,93 @@ class Stepper:
         if getattr(self, "ctx", None) is not None:
             teuk_destroy(self.ctx)
             self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _bcheck(rc: int, batch=None):
+    if rc != TEUK_OK:
+        msg = lib().teuk_batch_last_error(batch)
+        raise TeukError(rc, msg.decode() if msg else "")
+
+
+class Batch:
+    """Instances (Steppers of the split scheme) advanced together: one launch
+    per step over every tile of every instance (teuk_batch_* in the C ABI).
+    The steppers must outlive the batch and be stepped only through it."""
+
+    def __init__(self, steppers, stream=None):
+        import torch
+        self.torch = torch
+        self.steppers = list(steppers)
+        if not self.steppers:
+            raise ValueError("a batch needs at least one instance")
+        n = len(self.steppers)
+        self.device = self.steppers[0].device
+        self.stream = stream or self.steppers[0].stream
+        arr = (ctypes.c_void_p * n)(*[st.ctx for st in self.steppers])
+        nbytes = ctypes.c_size_t()
+        _bcheck(lib().teuk_batch_workspace_bytes(arr, n, ctypes.byref(nbytes)))
+        self.d_ws = torch.empty(int(nbytes.value) + 256, dtype=torch.uint8, device=self.device)
+        base = self.d_ws.data_ptr()
+        aligned = (base + 255) & ~255
+        out = ctypes.c_void_p()
+        _bcheck(lib().teuk_batch_create(arr, n, aligned, int(nbytes.value), ctypes.byref(out)))
+        self.batch = out
+
+    @property
+    def sh(self) -> int:
+        return self.stream.cuda_stream
+
+    def _after_instances(self):
+        # work queued on the instances' own streams comes first
+        for st in self.steppers:
+            if st.stream != self.stream:
+                self.stream.wait_stream(st.stream)
+
+    def _before_instances(self):
+        # later work on an instance's stream sees the batched steps
+        for st in self.steppers:
+            if st.stream != self.stream:
+                st.stream.wait_stream(self.stream)
+
+    def step(self, nsteps: int):
+        self._after_instances()
+        _bcheck(lib().teuk_batch_step(self.batch, int(nsteps), self.sh), self.batch)
+        self._before_instances()
+
+    def autotune(self, trial_steps: int = 10) -> list:
+        self._after_instances()
+        _bcheck(lib().teuk_batch_autotune(self.batch, int(trial_steps), self.sh), self.batch)
+        self._before_instances()
+        return self.tiling()["tile_rows"]
+
+    def tiling(self) -> dict:
+        n = len(self.steppers)
+        tr = (ctypes.c_int * n)()
+        tot = ctypes.c_int()
+        sm = ctypes.c_size_t()
+        _bcheck(lib().teuk_batch_tiling(self.batch, tr, ctypes.byref(tot), ctypes.byref(sm)), self.batch)
+        return {"tile_rows": list(tr), "total_tiles": tot.value, "smem_bytes": sm.value}
+
+    def set_tiling(self, tile_rows):
+        n = len(self.steppers)
+        if len(tile_rows) != n:
+            raise ValueError("one tile height per instance")
+        arr = (ctypes.c_int * n)(*[int(t) for t in tile_rows])
+        _bcheck(lib().teuk_batch_set_tiling(self.batch, arr), self.batch)
+
+    def synchronize(self):
+        self.stream.synchronize()
+
+    def close(self):
+        if getattr(self, "batch", None) is not None:
+            lib().teuk_batch_destroy(self.batch)
+            self.batch = None
 
     def __del__(self):
         try:
