@@ -10,11 +10,20 @@ kernel launch.  L2 is flushed (a 256 MB write) between timed steps, and each
 step is timed with CUDA events on the stepper's stream.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+                  [--workload single|batch64|long8]
 
 N > 1 runs as torchrun ranks, one independent replica per GPU (weak
 scaling; the single-instance stepper has no data-path collective).
 --impl reference times the FP64 CPU oracle on the host cores (bounded
 samples of the same workload) and prints the same JSON line.
+
+--workload batch64: the seeded uneven batch of 64 instances (a ~ U[0, 0.99],
+m ~ U{1..4}, r0 ~ U[6, 15], Nr ~ {2048, 4096, 8192, 16384}, Ntheta ~
+{32, 64, 128}, r* in [-100, 600]) advanced by one batched launch per step;
+--workload long8: eight 65536 x 256 instances (a = 0.999, r* in [-500, 4000],
+r0 = linspace(4, 20, 8)).  Their states (1.4 GB, 4.3 GB) exceed the L2, so no
+flush is needed.  With N > 1 the instances are split over the ranks
+(strong scaling; no collective while stepping).
 """
 from __future__ import annotations
 
@@ -368,6 +377,142 @@ def run_native(args):
     return 0
 
 
+def run_native_batch(args):
+    """Batched instances: one launch per step over every tile of every
+    instance this rank holds."""
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_0909_4039_gb300 import inputs, sharding, teuk
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if args.workload == "batch64":
+        allw = inputs.batched_instances(64, seed=0)
+        desc = ("batch64: 64 uneven instances (seed 0): a~U[0,0.99], m~U{1..4}, r0~U[6,15], "
+                "Nr~{2048,4096,8192,16384}, Ntheta~{32,64,128}, r* in [-100,600], dt=dr*/2")
+    else:
+        allw = inputs.long_run_batch(8)
+        desc = "long8: 8 x 65536x256, a=0.999, r* in [-500,4000], r0=linspace(4,20,8), dt=dr*/2"
+    pts_all = sum(w.points for w in allw)
+    mine = sharding.local_instances([w.points for w in allw], rank, ws)
+    prec = args.precision
+    stream = torch.cuda.Stream(device=dev)
+    sts = []
+    for k in mine:
+        w = allw[k]
+        drs = (w.rs_max - w.rs_min) / (w.Nr - 1)
+        st = teuk.Stepper(s=w.s, m=w.m, a=w.a, Nr=w.Nr, Ntheta=w.Ntheta, rstar_min=w.rs_min, rstar_max=w.rs_max,
+                          dt=w.cfl * drs, rstar_extract=w.rs_ext, precision=prec, device=dev, stream=stream,
+                          wave_capacity=args.steps + args.warmup + 8)
+        st.set_source(w.amp, w.r0, w.sig_r, w.sig_th)
+        sts.append(st)
+    pts = sum(allw[k].points for k in mine)
+    b = teuk.Batch(sts, stream=stream) if sts else None
+    tiling = {}
+    if b is not None:
+        b.autotune(5)
+        tiling = b.tiling()
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    with torch.cuda.stream(stream):
+        if b is not None:
+            b.step(args.warmup)
+    barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        barrier()
+        t_wall0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            for k in range(args.steps):
+                ev[k][0].record(stream)
+                if b is not None:
+                    b.step(1)
+                ev[k][1].record(stream)
+        barrier()
+        t_wall = time.perf_counter() - t_wall0
+    durs = [a.elapsed_time(c) for a, c in ev]
+    total_ms = sum(durs)
+    if ws > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = pts_all * args.steps / (total_ms * 1e-3) / 1e9
+    avg_s = statistics.fmean(durs) * 1e-3
+    bytes_per_pt = 32 if prec == "fp32" else 64
+    peak, peak_src = _peaks()
+    achieved = bytes_per_pt * pts / avg_s / 1e9
+
+    # end to end: every instance's state from pinned host, the batched steps,
+    # every state and waveform back to the host
+    hosts = [torch.zeros((2, st.Nr, st.Ntheta), dtype=torch.complex128, pin_memory=True) for st in sts]
+    outs = [torch.empty_like(h, pin_memory=True) for h in hosts]
+    k_e2e = args.steps
+    barrier()
+    t0 = time.perf_counter()
+    for st, h in zip(sts, hosts):
+        teuk.teuk_set_state(st.ctx, h.data_ptr(), st.current_step, st.sh)
+    if b is not None:
+        b.step(k_e2e)
+    waves = {}
+    for k, st, o in zip(mine, sts, outs):
+        teuk.teuk_get_state(st.ctx, o.data_ptr(), st.sh)
+        waves[k] = st.waveform(st.current_step - k_e2e + 1, k_e2e)
+    t_e2e = time.perf_counter() - t0
+    if ws > 1:
+        t = torch.tensor([t_e2e], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_e2e = float(t.item())
+    merged = sharding.gather_waveforms({k: v[-1] for k, v in waves.items()})
+    finite = bool(all(np.isfinite(o.numpy()).all() for o in outs)) and \
+        all(np.isfinite(np.asarray(v)).all() for v in merged.values())
+    state_bytes = sum(2 * allw[k].points * 16 for k in mine)
+    e2e = {"value": pts_all * k_e2e / t_e2e / 1e9, "unit": UNIT,
+           "h2d_bytes_per_step": state_bytes / k_e2e,
+           "d2h_bytes_per_step": (state_bytes + 16 * k_e2e * len(mine)) / k_e2e, "steps_per_call": k_e2e,
+           "note": "teuk_set_state of every instance from pinned host, teuk_batch_step, teuk_get_state and "
+                   "teuk_extract_waveform of every instance; wall clock; waveforms gathered over ranks"}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
+        "dtype": "f32" if prec == "fp32" else "f64", "data": "synthetic",
+        "config": {"workload": desc, "instances": len(allw), "points": pts_all,
+                   "l2": f"not flushed: the batch's states ({2 * pts_all * bytes_per_pt / 2 / 1e9:.1f} GB) "
+                         f"exceed the 129 MB L2",
+                   "parallelism": f"instances split over {ws} rank(s) by points", "tiling": tiling,
+                   "tiling_source": "teuk_batch_autotune (coordinate descent over the Ntheta classes, 5 steps)"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None, "kernel": "k_split_batch", "bytes_per_point": bytes_per_pt,
+                     "peak_source": f"{peak_src} hbm_gbs (copy, burst)"},
+        "e2e": e2e,
+        "clocks": clk.summary(),
+        "gpu_launches": args.steps,
+        "wall_s_timed": t_wall,
+        "finite": finite,
+    }
+    if ws == 1 and rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_oracle_rate(allw[int(np.argmax([w.points for w in allw]))])
+    if b is not None:
+        b.close()
+    for st in sts:
+        st.close()
+    if ws > 1:
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -380,11 +525,15 @@ def main():
                     help="auto: measured choice (cold-L2 autotune); otherwise the given kernel")
     ap.add_argument("--tile-rows", type=int, default=28, help="tile height for --kernel tiled/persistent")
     ap.add_argument("--consumers", type=int, default=480, help="consumer threads for --kernel persistent")
+    ap.add_argument("--workload", choices=["single", "batch64", "long8"], default="single",
+                    help="single: the 16384 x 128 instance; batch64 / long8: batched instances")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload != "single":
+        return run_native_batch(args)
     return run_native(args)
 
 

@@ -186,3 +186,33 @@ def test_uneven_batch_of_64_window():
     uo, ho = O.run(oracle_problem(ws[k]), u0[k], nsteps)
     assert rel_l2(got[k][0], uo) <= FP32_TOL
     assert rel_l2(got[k][1], ho) <= FP32_TOL
+
+
+def test_batch_wide_theta_class():
+    """Instances with 128 < Ntheta <= 256 (eight theta points per lane, the
+    long-run workload's class) batch together and equal their solo runs."""
+    ws = [inputs.Workload(f"wide{k}", s=-2, m=m, a=a, Nr=Nr, Ntheta=Nth, rs_min=-60.0, rs_max=240.0, steps=0,
+                          r0=r0, amp=1.0 + 0.1j * k, sig_r=0.9, sig_th=0.2, rs_ext=150.0)
+          for k, (Nr, Nth, a, m, r0) in enumerate([(400, 256, 0.999, 2, 5.0), (350, 200, 0.5, 3, 9.0),
+                                                     (300, 136, 0.9, 1, 7.0)])]
+    nsteps = 17
+    u0 = [inputs.random_state(w.Nr, w.Ntheta, seed=50 + k) for k, w in enumerate(ws)]
+    alone = []
+    for w, u in zip(ws, u0):
+        st = gpu_stepper(w, "fp32", wave_capacity=nsteps + 1)
+        st.set_state(u, 0)
+        st.step(nsteps)
+        alone.append((st.get_state(), st.waveform(0, nsteps + 1)))
+        st.close()
+    sts = [gpu_stepper(w, "fp32", wave_capacity=nsteps + 1) for w in ws]
+    for st, u in zip(sts, u0):
+        st.set_state(u, 0)
+    b = _batch(sts)
+    b.step(nsteps)
+    b.synchronize()
+    for k, st in enumerate(sts):
+        assert np.array_equal(st.get_state(), alone[k][0]), k
+        assert np.array_equal(st.waveform(0, nsteps + 1), alone[k][1]), k
+    b.close()
+    for st in sts:
+        st.close()
