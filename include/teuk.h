@@ -241,6 +241,48 @@ const char *teuk_status_string(int status);
 /* Release the host context (the caller frees its device buffers). */
 int teuk_destroy(teuk_ctx *ctx);
 
+/* ------------------------------------------------- operator and adjoint
+ * The step as an operator on caller buffers, and its Hermitian adjoint (for
+ * the inner product <x, y> = Re sum conj(x) y over both planes), for
+ * gradients of waveform losses.  Split scheme only.  With s_n the internal
+ * state (u_n = C_{dt/2} s_n the physical one, Sec. 2.2 split as described
+ * for teuk_step):
+ *   s_1 = M_0(u_0) = LW_0 C_{dt/2} u_0,   s_{n+1} = M_n(s_n) = LW_n C_dt s_n,
+ *   h_0 = E u_0,  h_n = E C_{dt/2} s_n,   E u = sum_j w_j Phi_{i_ext, j}.
+ * LW_n is affine (the source at t_n and t_n + dt/2); C_h is linear.  All
+ * buffers are device memory of [2][Nr][Ntheta] complex in the context's
+ * state precision, distinct from each other and from the context's own.
+ * The context's state, step counter and waveform are not touched.  All
+ * calls are asynchronous on `stream`. */
+
+/* d_out = M_n(d_in) (first = 1: the first step from a physical state). */
+int teuk_apply_step(teuk_ctx *ctx, const void *d_in, void *d_out, int64_t n, int first, void *stream);
+
+/* One waveform sample into d_h (one complex double, device): E d_s if
+ * physical, else E C_{dt/2} d_s; the same FP64 sum the steps write. */
+int teuk_apply_sample(teuk_ctx *ctx, const void *d_s, int physical, void *d_h, void *stream);
+
+/* Device workspace of teuk_adjoint_step and teuk_dot, in *bytes.  Its first
+ * four doubles accumulate the source derivatives (see teuk_adjoint_step);
+ * zero them before a backward sweep. */
+int teuk_adjoint_workspace_bytes(const teuk_ctx *ctx, size_t *bytes);
+
+/* One step of the backward (adjoint) sweep:
+ *   d_lam_out = M_n^H d_lam_in + C_{dt/2}^H E^H g_n   (E^H g_0 if first),
+ * where d_lam_in is the adjoint of s_{n+1}, d_lam_out that of s_n (of u_0
+ * if first), and d_gseed points to g_n = dL/dRe h_n + i dL/dIm h_n (one
+ * complex double on the device; NULL: no sample term).  The step's source
+ * derivatives are added to the workspace accumulators acc[0..3]:
+ *   dL/dRe A = acc[0],  dL/dIm A = -acc[1],  dL/dr0 = acc[2]
+ * (A the source amplitude, r0 the orbit radius through r0* and the Kepler
+ * frequency; sum over the backward sweep, in a fixed order). */
+int teuk_adjoint_step(teuk_ctx *ctx, const void *d_lam_in, void *d_lam_out, int64_t n, int first,
+                      const void *d_gseed, void *d_ws, void *stream);
+
+/* d_out (one complex double, device) = sum conj(x) y over both planes, in
+ * FP64 and a fixed order.  d_ws: the adjoint workspace. */
+int teuk_dot(teuk_ctx *ctx, const void *d_x, const void *d_y, void *d_ws, void *d_out, void *stream);
+
 /* ---------------------------------------------------------------- batches
  * Many independent instances -- each a split-scheme context with its own
  * grid, spin, mode, source and buffers -- advanced together: one launch per

@@ -40,9 +40,12 @@ struct teuk_ctx {
     int shifted;            // split scheme: the level holds s_n (u_n = C_{dt/2} s_n)
     int64_t step;           // host mirror of the device step counter
     int64_t rec_lo;         // oldest recorded waveform step
-    // source
-    int patch_p0, patch_np;
+    // source: patch rows of the forward source (patch_np = 0: off) and of
+    // the unit-amplitude patch, which exists whenever the orbit is valid
+    // (derivatives with respect to the amplitude and the orbit radius)
+    int patch_p0, patch_np, unit_p0, unit_np;
     double mOmega;
+    double amp_re, amp_im, rs0, sig_r, drs0_dr0, m_dOmega;
     // launch configuration: tiled kernel (tile_rows, threads, smem) or the
     // persistent kernel (persist = 1: nc consumer threads, grid CTAs,
     // persist_smem); the tiled kernel at the same tile height also serves
@@ -76,6 +79,7 @@ Layout make_layout(const teuk_grid_desc &d)
     L.piv = off; off = align256(off + c2 * N * Nr);
     L.pivh = off; off = align256(off + c2 * N * Nr);
     L.patch = off; off = align256(off + c2 * 2 * N * patch_rows);
+    L.patchu = off; off = align256(off + c2 * 2 * N * patch_rows);
     L.w = off; off = align256(off + sizeof(double) * N);
     L.ctl = off; off = align256(off + sizeof(Ctl));
     L.staging_elems = 0;
@@ -356,6 +360,18 @@ StepParams<T> make_params(const teuk_ctx *c, int in_level)
     p.rtab = (const T *)(c->coef + c->L.rtabT);
     p.thtab = (const T *)(c->coef + c->L.thT);
     p.patch = (const c2 *)(c->coef + c->L.patch);
+    p.nfix = -1;
+    p.patchu = (const c2 *)(c->coef + c->L.patchu);
+    p.unit_p0 = c->unit_p0;
+    p.unit_np = c->unit_np;
+    p.amp_re = c->amp_re;
+    p.amp_im = c->amp_im;
+    p.rs_min64 = d.rstar_min;
+    p.drs64 = c->drs;
+    p.rs0 = c->rs0;
+    p.inv_sig_r2 = c->sig_r > 0.0 ? 1.0 / (c->sig_r * c->sig_r) : 0.0;
+    p.drs0_dr0 = c->drs0_dr0;
+    p.m_dOmega = c->m_dOmega;
     p.w = (const double *)(c->coef + c->L.w);
     p.uin = (const c2 *)(c->state + (size_t)in_level * c->level_bytes);
     p.uout = (c2 *)(c->state + (size_t)(1 - in_level) * c->level_bytes);
@@ -560,15 +576,20 @@ int teuk_set_source(teuk_ctx *c, double amp_re, double amp_im, double r0, double
     const teuk_grid_desc &d = c->d;
     if (!isfinite(amp_re) || !isfinite(amp_im)) return set_err(c, TEUK_E_INVAL, "amplitude must be finite%s");
     drop_graphs(c);
-    if (amp_re == 0.0 && amp_im == 0.0) {
+    const bool off = amp_re == 0.0 && amp_im == 0.0;
+    double rp = d.M + sqrt(d.M * d.M - d.a * d.a);
+    const bool orbit_ok = r0 > rp && isfinite(r0) && sigma_rstar > 0.0 && sigma_theta > 0.0;
+    if (off && !orbit_ok) {
         c->patch_np = 0;
+        c->unit_np = 0;
         c->mOmega = 0.0;
+        c->amp_re = c->amp_im = 0.0;
         return TEUK_OK;
     }
-    double rp = d.M + sqrt(d.M * d.M - d.a * d.a);
     if (!(r0 > rp) || !isfinite(r0)) return set_err(c, TEUK_E_INVAL, "orbit radius must exceed r_+%s");
     if (!(sigma_rstar > 0.0) || !(sigma_theta > 0.0)) return set_err(c, TEUK_E_INVAL, "source widths must be positive%s");
-    double Om = isnan(Omega) ? sqrt(d.M) / (pow(r0, 1.5) + d.a * sqrt(d.M)) : Omega;
+    const bool kepler = isnan(Omega);
+    double Om = kepler ? sqrt(d.M) / (pow(r0, 1.5) + d.a * sqrt(d.M)) : Omega;
     if (!isfinite(Om)) return set_err(c, TEUK_E_INVAL, "Omega must be finite or NaN%s");
     double rs0 = host_rstar(d.M, d.a, r0);
     double lo = (rs0 - 9.0 * sigma_rstar - d.rstar_min) / c->drs;
@@ -586,8 +607,19 @@ int teuk_set_source(teuk_ctx *c, double amp_re, double amp_im, double r0, double
         CK(cudaStreamSynchronize(st), "source sync");
     }
     c->patch_p0 = (int)p0;
-    c->patch_np = np;
+    c->patch_np = off ? 0 : np;
+    c->unit_p0 = (int)p0;
+    c->unit_np = np;
     c->mOmega = (double)d.m * Om;
+    c->amp_re = amp_re;
+    c->amp_im = amp_im;
+    c->rs0 = rs0;
+    c->sig_r = sigma_rstar;
+    // d r0*/d r0 = (r0^2 + a^2)/Delta(r0); with the Kepler frequency
+    // Omega = M^(1/2)/(r0^(3/2) + a M^(1/2)), dOmega/dr0 = -(3/2) r0^(1/2) Omega^2 / M^(1/2)
+    const double Delta0 = r0 * r0 - 2.0 * d.M * r0 + d.a * d.a;
+    c->drs0_dr0 = (r0 * r0 + d.a * d.a) / Delta0;
+    c->m_dOmega = kepler ? (double)d.m * (-1.5 * sqrt(r0) * Om * Om / sqrt(d.M)) : 0.0;
     return TEUK_OK;
 }
 
@@ -933,6 +965,134 @@ int teuk_literal_step_static(const teuk_ctx *c, const void *d_in, void *d_out, i
     return TEUK_OK;
 }
 
+
+}  // extern "C"
+
+
+// ------------------------------------------------------ operator and adjoint
+
+namespace {
+
+// Tile height of the adjoint kernel: the largest up to 30 rows whose four
+// state planes fit in about 100 KB of shared memory.
+int adjoint_tile_rows(const teuk_ctx *c)
+{
+    const int N = (int)c->d.Ntheta;
+    const bool f32 = c->d.precision == TEUK_FP32;
+    int best = 1;
+    for (int tr = 1; tr <= 30; ++tr) {
+        size_t sm = f32 ? adjoint_smem_bytes<float>(tr, N) : adjoint_smem_bytes<double>(tr, N);
+        if (sm <= 100 * 1024) best = tr;
+    }
+    return best;
+}
+
+size_t adjoint_ws_doubles(const teuk_ctx *c)
+{
+    const int tr = adjoint_tile_rows(c);
+    const int grid = (int)((c->d.Nr + tr - 1) / tr);
+    return 8 + 4 * (size_t)grid + 2 * 256;   // accumulators, per-CTA parts, dot parts
+}
+
+}  // namespace
+
+extern "C" {
+
+int teuk_apply_step(teuk_ctx *c, const void *d_in, void *d_out, int64_t n, int first, void *stream)
+{
+    if (!c) return TEUK_E_STATE;
+    if (c->d.scheme != TEUK_SCHEME_SPLIT) return set_err(c, TEUK_E_INVAL, "teuk_apply_step needs the split scheme%s");
+    if (!d_in || !d_out || d_in == d_out || n < 0)
+        return set_err(c, TEUK_E_INVAL, "need distinct non-NULL device buffers and n >= 0%s");
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e;
+    if (c->d.precision == TEUK_FP32) {
+        StepParams<float> p = make_params<float>(c, 0);
+        p.uin = (const float2 *)d_in;
+        p.uout = (float2 *)d_out;
+        p.first = first ? 1 : 0;
+        p.nfix = n;
+        e = launch_apply_step<float>(p, c->threads, c->smem, st);
+    } else {
+        StepParams<double> p = make_params<double>(c, 0);
+        p.uin = (const double2 *)d_in;
+        p.uout = (double2 *)d_out;
+        p.first = first ? 1 : 0;
+        p.nfix = n;
+        e = launch_apply_step<double>(p, c->threads, c->smem, st);
+    }
+    if (e != cudaSuccess) return cuda_err(c, e, "apply step");
+    return TEUK_OK;
+}
+
+int teuk_apply_sample(teuk_ctx *c, const void *d_s, int physical, void *d_h, void *stream)
+{
+    if (!c) return TEUK_E_STATE;
+    if (!d_s || !d_h) return set_err(c, TEUK_E_INVAL, "need non-NULL device buffers%s");
+    if (c->d.scheme != TEUK_SCHEME_SPLIT && !physical)
+        return set_err(c, TEUK_E_INVAL, "the literal scheme has no internal state: pass physical = 1%s");
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e;
+    if (c->d.precision == TEUK_FP32)
+        e = launch_sample<float>(make_params<float>(c, 0), (const float2 *)d_s, physical, (double2 *)d_h, st);
+    else
+        e = launch_sample<double>(make_params<double>(c, 0), (const double2 *)d_s, physical, (double2 *)d_h, st);
+    if (e != cudaSuccess) return cuda_err(c, e, "sample");
+    return TEUK_OK;
+}
+
+int teuk_adjoint_workspace_bytes(const teuk_ctx *c, size_t *bytes)
+{
+    if (!c || !bytes) return TEUK_E_STATE;
+    *bytes = sizeof(double) * adjoint_ws_doubles(c);
+    return TEUK_OK;
+}
+
+int teuk_adjoint_step(teuk_ctx *c, const void *d_lam_in, void *d_lam_out, int64_t n, int first, const void *d_gseed,
+                      void *d_ws, void *stream)
+{
+    if (!c) return TEUK_E_STATE;
+    if (c->d.scheme != TEUK_SCHEME_SPLIT) return set_err(c, TEUK_E_INVAL, "the adjoint needs the split scheme%s");
+    if (!d_lam_in || !d_lam_out || d_lam_in == d_lam_out || !d_ws || n < 0)
+        return set_err(c, TEUK_E_INVAL, "need distinct non-NULL device buffers, a workspace and n >= 0%s");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int tr = adjoint_tile_rows(c);
+    double *acc = (double *)d_ws, *part = acc + 8;
+    cudaError_t e;
+    if (c->d.precision == TEUK_FP32) {
+        StepParams<float> p = make_params<float>(c, 0);
+        p.uin = (const float2 *)d_lam_in;
+        p.uout = (float2 *)d_lam_out;
+        p.first = first ? 1 : 0;
+        p.nfix = n;
+        e = launch_adjoint_step<float>(p, tr, (const double2 *)d_gseed, part, acc, st);
+    } else {
+        StepParams<double> p = make_params<double>(c, 0);
+        p.uin = (const double2 *)d_lam_in;
+        p.uout = (double2 *)d_lam_out;
+        p.first = first ? 1 : 0;
+        p.nfix = n;
+        e = launch_adjoint_step<double>(p, tr, (const double2 *)d_gseed, part, acc, st);
+    }
+    if (e != cudaSuccess) return cuda_err(c, e, "adjoint step");
+    return TEUK_OK;
+}
+
+int teuk_dot(teuk_ctx *c, const void *d_x, const void *d_y, void *d_ws, void *d_out, void *stream)
+{
+    if (!c) return TEUK_E_STATE;
+    if (!d_x || !d_y || !d_ws || !d_out) return set_err(c, TEUK_E_INVAL, "need non-NULL device buffers%s");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t n = 2 * (size_t)c->d.Nr * (size_t)c->d.Ntheta;
+    double *part = (double *)d_ws + adjoint_ws_doubles(c) - 2 * 256;
+    cudaError_t e;
+    if (c->d.precision == TEUK_FP32)
+        e = launch_dot<float>((const float2 *)d_x, (const float2 *)d_y, n, part, (double2 *)d_out, st);
+    else
+        e = launch_dot<double>((const double2 *)d_x, (const double2 *)d_y, n, part, (double2 *)d_out, st);
+    if (e != cudaSuccess) return cuda_err(c, e, "dot");
+    return TEUK_OK;
+}
 
 }  // extern "C"
 

@@ -216,11 +216,13 @@ struct PatchArgs {
     double rs_min, drs, dth;
     double amp_re, amp_im, rs0, sig_r, sig_th;
     const double *rtab64;
-    void *patch;
+    void *patch;    // A F_pref G (nullptr: not written)
+    void *patchu;   // F_pref G, the unit-amplitude patch
 };
 
 // Spatial part of the source, A F_pref G(r*, theta), at the nodes and half
 // nodes of patch rows; F_pref = 4 pi (r^2 + a^2 cos^2) Delta/(Sigma^2 r^3).
+// The unit-amplitude part F_pref G is kept as well (source derivatives).
 __global__ void k_patch(PatchArgs A)
 {
     int idx = blockIdx.x * blockDim.x + threadIdx.x;
@@ -243,11 +245,16 @@ __global__ void k_patch(PatchArgs A)
         double rs = pos ? A.rs_min + ((double)gi + 0.5) * A.drs : A.rs_min + (double)gi * A.drs;
         double dr = rs - A.rs0, dq = th - 0.5 * kPi;
         double G = exp(-dr * dr / (2.0 * A.sig_r * A.sig_r) - dq * dq / (2.0 * A.sig_th * A.sig_th));
-        vre = A.amp_re * pref * G;
-        vim = A.amp_im * pref * G;
+        vre = pref * G;
     }
-    if (A.prec == TEUK_FP32) ((float2 *)A.patch)[idx] = make_float2((float)vre, (float)vim);
-    else ((double2 *)A.patch)[idx] = make_double2(vre, vim);
+    if (A.prec == TEUK_FP32) ((float2 *)A.patchu)[idx] = make_float2((float)vre, 0.0f);
+    else ((double2 *)A.patchu)[idx] = make_double2(vre, 0.0);
+    if (A.patch) {
+        vim = A.amp_im * vre;
+        vre = A.amp_re * vre;
+        if (A.prec == TEUK_FP32) ((float2 *)A.patch)[idx] = make_float2((float)vre, (float)vim);
+        else ((double2 *)A.patch)[idx] = make_double2(vre, vim);
+    }
 }
 
 __global__ void k_set_ctl(Ctl *c, long long step, int clear_flags)
@@ -315,7 +322,8 @@ cudaError_t launch_patch(const teuk_grid_desc &d, double drs, void *coef, const 
     A.sig_r = sig_r;
     A.sig_th = sig_th;
     A.rtab64 = (const double *)((const char *)coef + L.rtab64);
-    A.patch = (char *)coef + L.patch;
+    A.patch = (amp_re != 0.0 || amp_im != 0.0) ? (void *)((char *)coef + L.patch) : nullptr;
+    A.patchu = (char *)coef + L.patchu;
     int total = np * 2 * A.Nth;
     k_patch<<<(total + 255) / 256, 256, 0, st>>>(A);
     return cudaGetLastError();

@@ -93,6 +93,15 @@ template <typename T> struct StepParams {
     c2 *mid;                 // literal scheme scratch [2][Nr-1][Nth]
     double2 *wave;           // [cap][1 + Nth]
     Ctl *ctl;
+    // Applying one step to caller buffers (nfix >= 0): the step index is
+    // nfix, the step counter is not touched and nothing is extracted.
+    long long nfix;
+    // Source-parameter derivatives (adjoint step): the unit-amplitude patch
+    // [np][2][Nth] (same rows as patch), the amplitude, the r* grid and the
+    // orbit's r0*, 1/sigma_r^2, d r0*/d r0 and m dOmega/d r0.
+    const c2 *patchu;
+    int unit_p0, unit_np;    // rows of the unit-amplitude patch (np = 0: none)
+    double amp_re, amp_im, rs_min64, drs64, rs0, inv_sig_r2, drs0_dr0, m_dOmega;
 };
 
 // SDIRK2 constant gamma = 1 - 1/sqrt(2) (Alexander 1977).
@@ -147,7 +156,7 @@ __host__ __device__ inline PersistSmem persist_smem_plan(int R, int N, int tsize
 
 // ---------------------------------------------------------------- host side
 struct Layout {
-    size_t rtab64, rtabT, th64, thT, piv, pivh, patch, w, ctl, staging, scratch, total;
+    size_t rtab64, rtabT, th64, thT, piv, pivh, patch, patchu, w, ctl, staging, scratch, total;
     size_t staging_elems;    // complex doubles that fit in the staging area
 };
 
@@ -161,6 +170,23 @@ cudaError_t launch_patch(const teuk_grid_desc &d, double drs, void *coef, const 
                          double sig_r, double sig_th, cudaStream_t st);
 cudaError_t launch_set_ctl(void *coef, const Layout &L, long long step, int clear_flags,
                            cudaStream_t st);
+
+// Adjoint and operator entry points (teuk_step.cu).
+template <typename T>
+cudaError_t launch_apply_step(const StepParams<T> &p, int threads, size_t smem, cudaStream_t st);
+template <typename T>
+cudaError_t launch_sample(const StepParams<T> &p, const typename V2<T>::t *s, int physical, double2 *h_out,
+                          cudaStream_t st);
+template <typename T>
+cudaError_t launch_adjoint_step(const StepParams<T> &p, int tile_rows, const double2 *gseed, double *part,
+                                double *acc, cudaStream_t st);
+template <typename T>
+size_t adjoint_smem_bytes(int tile_rows, int Nth);
+template <typename T>
+int adjoint_grid(int Nr, int tile_rows);
+template <typename T>
+cudaError_t launch_dot(const typename V2<T>::t *x, const typename V2<T>::t *y, size_t n, double *part,
+                       double2 *out, cudaStream_t st);
 
 template <typename T>
 cudaError_t launch_split_step(const StepParams<T> &p, int threads, size_t smem, cudaStream_t st);

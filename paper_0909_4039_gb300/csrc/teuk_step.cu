@@ -185,25 +185,30 @@ template <> struct ScanTol<double> { static constexpr double v = 1e-19; };
 // only on the matrix, so it is scanned once per call and both stages scan
 // only the additive part.  Rows with active == false (boundary or outside
 // the grid) take part in the shuffles with neutral data and write zeros.
+// Per-element coefficients of one row's implicit stage (lane segment of S
+// elements): LU pivots e, forward multipliers m_j = sub_j e_{j-1}, backward
+// multipliers fk_j = e_j sup_j, c_t, row j of B + c0rad as (qam, dg, qap),
+// and 1/(1 + gh c_t).  Loaded together with the lane's (Phi, Pi) segment.
+template <typename T, int S> struct RowCoef {
+    typedef typename V2<T>::t c2;
+    c2 e[S], m[S], fk[S], ct[S], dg[S], ia1[S];
+    T qam[S], qap[S];
+};
+
+// Elements past the end of the row (and every element of an inactive row)
+// are neutral: sigma = 0 (so q = c_t = c0rad = 0), zero data, e = 1, zero
+// angular row.  Padded elements only follow the real ones of a segment and
+// only feed lanes that hold no real element, so the recurrences need no
+// bounds tests, and a neutral row maps to zero.
 template <typename T, int S>
-__device__ void implicit_row_group(const ImpConst<T> &K, typename V2<T>::t *phi, typename V2<T>::t *pi,
-                                   const typename V2<T>::t *prow, const T *f, const T *th, int N, bool active,
-                                   bool in_tile, int g, int G, bool vec)
+__device__ __forceinline__ void row_load(const ImpConst<T> &K, const typename V2<T>::t *phi,
+                                         const typename V2<T>::t *pi, const typename V2<T>::t *prow, const T *f,
+                                         const T *th, int N, int len, int j0, int G, bool vec, RowCoef<T, S> &C,
+                                         typename V2<T>::t (&w)[S], typename V2<T>::t (&y)[S])
 {
     typedef typename V2<T>::t c2;
-    constexpr int LOGMAX = 5;
     const c2 zero = cmk<c2>(T(0), T(0));
     const c2 one = cmk<c2>(T(1), T(0));
-    // Elements past the end of the row (and every element of an inactive
-    // row) are neutral: sigma = 0 (so q = c_t = c0rad = 0), zero data, e = 1,
-    // zero angular row.  Padded elements only follow the real ones of a
-    // segment and only feed lanes that hold no real element, so the
-    // recurrences need no bounds tests, and a neutral row solves to zero.
-    const int j0 = g * S;
-    int len = N - j0;
-    len = len < 0 ? 0 : (len > S ? S : len);
-    const int lenw = len;          // real elements of the segment (written back)
-    if (!active) len = 0;
     const T gh = K.gh, gh2 = K.gh2;
     T fr[NRF];
     vload<NRF>(fr, f);
@@ -217,7 +222,6 @@ __device__ void implicit_row_group(const ImpConst<T> &K, typename V2<T>::t *phi,
 
     // rsv = 1/Sigma (zero for neutral elements)
     T rsv[S], ccv[S], am[S], a0[S], ap[S];
-    c2 e[S], w[S], y[S];
     if (vec && len == S) {
         T s2v[S];
         vload<S>(s2v, S2t + j0);
@@ -225,7 +229,7 @@ __device__ void implicit_row_group(const ImpConst<T> &K, typename V2<T>::t *phi,
         vload<S>(am, Am + j0);
         vload<S>(a0, A0 + j0);
         vload<S>(ap, Ap + j0);
-        vload<S>(e, prow + j0);
+        vload<S>(C.e, prow + j0);
         vload<S>(w, phi + j0);
         vload<S>(y, pi + j0);
 #pragma unroll
@@ -240,130 +244,194 @@ __device__ void implicit_row_group(const ImpConst<T> &K, typename V2<T>::t *phi,
             am[k] = real ? Am[j] : T(0);
             a0[k] = real ? A0[j] : T(0);
             ap[k] = real ? Ap[j] : T(0);
-            e[k] = real ? prow[j] : one;
+            C.e[k] = real ? prow[j] : one;
             w[k] = real ? phi[j] : zero;
             y[k] = real ? pi[j] : zero;
         }
     }
-    // per-element coefficients, computed once.  Row j of B + c0rad is
-    // (qam_j, dg_j, qap_j) = (q AM_j, q A0_j + c0rad_j, q AP_j).
-    c2 m[S], fk[S], ct[S], dg[S], ia1[S];
-    T qam[S], qap[S];
+    // Row j of B + c0rad is (qam_j, dg_j, qap_j) = (q AM_j, q A0_j + c0rad_j, q AP_j).
 #pragma unroll
     for (int k = 0; k < S; ++k) {
         const T sg = rsv[k] * rsv[k];
         const T q = D * sg;
-        ct[k] = cmk<c2>(sg * ctr, sg * fma(ctc, ccv[k], cti));
-        dg[k] = cmk<c2>(fma(q, a0[k], -sg * c0r), -sg * c0i);
-        qam[k] = q * am[k];
-        qap[k] = q * ap[k];
-        ia1[k] = cinv(cmk<c2>(fma(gh, ct[k].x, T(1)), gh * ct[k].y));
+        C.ct[k] = cmk<c2>(sg * ctr, sg * fma(ctc, ccv[k], cti));
+        C.dg[k] = cmk<c2>(fma(q, a0[k], -sg * c0r), -sg * c0i);
+        C.qam[k] = q * am[k];
+        C.qap[k] = q * ap[k];
+        C.ia1[k] = cinv(cmk<c2>(fma(gh, C.ct[k].x, T(1)), gh * C.ct[k].y));
     }
-    const c2 e_prev = shfl_up_c(e[S - 1], 1, G);   // e_{j0-1} (lane g-1 holds a full segment)
+    const c2 e_prev = shfl_up_c(C.e[S - 1], 1, G);   // e_{j0-1} (lane g-1 holds a full segment)
 #pragma unroll
     for (int k = 0; k < S; ++k) {
-        m[k] = cscale<c2>(gh2 * qam[k], k ? e[k - 1] : e_prev);
-        fk[k] = cscale<c2>(gh2 * qap[k], e[k]);
+        C.m[k] = cscale<c2>(gh2 * C.qam[k], k ? C.e[k - 1] : e_prev);
+        C.fk[k] = cscale<c2>(gh2 * C.qap[k], C.e[k]);
     }
-    // Multiplicative parts of the segment maps (matrix only): Af0, Ab0 for
-    // the lane's own segment.  Level l of a scan adds, to each lane's value,
-    // a neighbour's value times that level's multiplier (the product of the
-    // segment multipliers it spans).  Once every multiplier of a level is
-    // below ScanTol in magnitude the level adds nothing the state precision
-    // can hold, and neither do the levels above it (their multipliers are
-    // products of these), so the scans stop there: nf levels forward, nb
-    // backward.  The test is taken over this row's group of G lanes only, so
-    // a row's result does not depend on the rows that share its warp; the
-    // shuffles run for the levels any group of the warp needs (nfw, nbw).
-    // The data scans recompute the multipliers of the levels they use
-    // instead of keeping one per level in registers.
-    c2 Af0 = one, Ab0 = one;
-    int nf = 0, nb = 0, nfw = 0, nbw = 0;
+}
+
+// Scan plan of a pair of first-order affine recurrences over one row
+//   forward  t_j = r_j - fm_j t_{j-1},   backward  x_j = y_j - bm_j x_{j+1}:
+// Af0, Ab0 are the multiplicative parts of the lane's segment maps.  Level l
+// of a scan adds, to each lane's value, a neighbour's value times that
+// level's multiplier (the product of the segment multipliers it spans).
+// Once every multiplier of a level is below ScanTol in magnitude the level
+// adds nothing the state precision can hold, and neither do the levels
+// above it (their multipliers are products of these), so the scans stop
+// there: nf levels forward, nb backward.  The test is taken over this row's
+// group of G lanes only, so a row's result does not depend on the rows that
+// share its warp; the shuffles run for the levels any group of the warp
+// needs (nfw, nbw).  The data scans recompute the multipliers of the levels
+// they use instead of keeping one per level in registers.
+template <typename T> struct ScanPlan {
+    typename V2<T>::t Af0, Ab0;
+    int nf, nb, nfw, nbw;
+};
+
+template <typename T, int S>
+__device__ __forceinline__ ScanPlan<T> scan_plan(const typename V2<T>::t (&fm)[S], const typename V2<T>::t (&bm)[S],
+                                                 int g, int G)
+{
+    typedef typename V2<T>::t c2;
+    constexpr int LOGMAX = 5;
+    const c2 one = cmk<c2>(T(1), T(0));
+    ScanPlan<T> P;
+    P.Af0 = one;
+    P.Ab0 = one;
+    P.nf = P.nb = P.nfw = P.nbw = 0;
+#pragma unroll
+    for (int k = 0; k < S; ++k) P.Af0 = cmul(cmk<c2>(-fm[k].x, -fm[k].y), P.Af0);
+#pragma unroll
+    for (int k = S - 1; k >= 0; --k) P.Ab0 = cmul(cmk<c2>(-bm[k].x, -bm[k].y), P.Ab0);
+    const T tol2 = ScanTol<T>::v * ScanTol<T>::v;
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned gbase = lane - (unsigned)g;
+    const unsigned gmask = G >= 32 ? 0xffffffffu : ((1u << G) - 1u);
+    c2 Af = P.Af0, Ab = P.Ab0;
+    bool gf = true, gb = true;
+#pragma unroll
+    for (int l = 0; l < LOGMAX; ++l) {
+        const int d = 1 << l;
+        if (d >= G) break;
+        const unsigned bf = __ballot_sync(0xffffffffu, g >= d && fma(Af.x, Af.x, Af.y * Af.y) > tol2);
+        const unsigned bb = __ballot_sync(0xffffffffu, g + d < G && fma(Ab.x, Ab.x, Ab.y * Ab.y) > tol2);
+        gf = gf && ((bf >> gbase) & gmask) != 0u;
+        gb = gb && ((bb >> gbase) & gmask) != 0u;
+        const bool wf = __any_sync(0xffffffffu, gf), wb = __any_sync(0xffffffffu, gb);
+        if (!wf && !wb) break;
+        if (gf) P.nf = l + 1;
+        if (gb) P.nb = l + 1;
+        if (wf) P.nfw = l + 1;
+        if (wb) P.nbw = l + 1;
+        if (2 * d >= G) break;
+        const c2 Ao = shfl_up_c(Af, d, G), Bo = shfl_down_c(Ab, d, G);
+        if (gf && g >= d) Af = cmul(Af, Ao);
+        if (gb && g + d < G) Ab = cmul(Ab, Bo);
+    }
+    return P;
+}
+
+// w <- x with forward t_j = w_j - fm_j t_{j-1} (t_{-1} = 0), y_j = pm_j t_j,
+// backward x_j = y_j - bm_j x_{j+1} (x_N = 0), each affine recurrence as a
+// segmented scan over the G lanes of the row.
+template <typename T, int S>
+__device__ __forceinline__ void seg_solve(typename V2<T>::t (&w)[S], const typename V2<T>::t (&fm)[S],
+                                          const typename V2<T>::t (&pm)[S], const typename V2<T>::t (&bm)[S],
+                                          const ScanPlan<T> &P, int g, int G)
+{
+    typedef typename V2<T>::t c2;
+    constexpr int LOGMAX = 5;
+    const c2 zero = cmk<c2>(T(0), T(0));
+    const c2 one = cmk<c2>(T(1), T(0));
+    c2 B = zero;
+#pragma unroll
+    for (int k = 0; k < S; ++k) B = csub(w[k], cmul(fm[k], B));
     {
-#pragma unroll
-        for (int k = 0; k < S; ++k) Af0 = cmul(cmk<c2>(-m[k].x, -m[k].y), Af0);
-#pragma unroll
-        for (int k = S - 1; k >= 0; --k) Ab0 = cmul(cmk<c2>(-fk[k].x, -fk[k].y), Ab0);
-        const T tol2 = ScanTol<T>::v * ScanTol<T>::v;
-        const unsigned lane = threadIdx.x & 31u;
-        const unsigned gbase = lane - (unsigned)g;
-        const unsigned gmask = G >= 32 ? 0xffffffffu : ((1u << G) - 1u);
-        c2 Af = Af0, Ab = Ab0;
-        bool gf = true, gb = true;
+        c2 A = P.Af0;
 #pragma unroll
         for (int l = 0; l < LOGMAX; ++l) {
-            const int d = 1 << l;
-            if (d >= G) break;
-            const unsigned bf = __ballot_sync(0xffffffffu, g >= d && fma(Af.x, Af.x, Af.y * Af.y) > tol2);
-            const unsigned bb = __ballot_sync(0xffffffffu, g + d < G && fma(Ab.x, Ab.x, Ab.y * Ab.y) > tol2);
-            gf = gf && ((bf >> gbase) & gmask) != 0u;
-            gb = gb && ((bb >> gbase) & gmask) != 0u;
-            const bool wf = __any_sync(0xffffffffu, gf), wb = __any_sync(0xffffffffu, gb);
-            if (!wf && !wb) break;
-            if (gf) nf = l + 1;
-            if (gb) nb = l + 1;
-            if (wf) nfw = l + 1;
-            if (wb) nbw = l + 1;
-            if (2 * d >= G) break;
-            const c2 Ao = shfl_up_c(Af, d, G), Bo = shfl_down_c(Ab, d, G);
-            if (gf && g >= d) Af = cmul(Af, Ao);
-            if (gb && g + d < G) Ab = cmul(Ab, Bo);
+            if (l < P.nfw) {
+                const int d = 1 << l;
+                c2 Bo = shfl_up_c(B, d, G), Ao = one;
+                if (l + 1 < P.nfw) Ao = shfl_up_c(A, d, G);
+                if (l < P.nf && g >= d) {
+                    B = cadd(cmul(A, Bo), B);
+                    if (l + 1 < P.nf) A = cmul(A, Ao);
+                }
+            }
         }
     }
-
-    // tridiagonal solve of w in place (stage right side -> U_Phi)
-    auto solve = [&]() {
-        c2 B = zero;
+    c2 z = shfl_up_c(B, 1, G);
+    if (g == 0) z = zero;
 #pragma unroll
-        for (int k = 0; k < S; ++k) B = csub(w[k], cmul(m[k], B));
-        {
-            c2 A = Af0;
+    for (int k = 0; k < S; ++k) {
+        z = csub(w[k], cmul(fm[k], z));
+        w[k] = cmul(pm[k], z);
+    }
+    B = zero;
 #pragma unroll
-            for (int l = 0; l < LOGMAX; ++l) {
-                if (l < nfw) {
-                    const int d = 1 << l;
-                    c2 Bo = shfl_up_c(B, d, G), Ao = one;
-                    if (l + 1 < nfw) Ao = shfl_up_c(A, d, G);
-                    if (l < nf && g >= d) {
-                        B = cadd(cmul(A, Bo), B);
-                        if (l + 1 < nf) A = cmul(A, Ao);
-                    }
+    for (int k = S - 1; k >= 0; --k) B = csub(w[k], cmul(bm[k], B));
+    {
+        c2 A = P.Ab0;
+#pragma unroll
+        for (int l = 0; l < LOGMAX; ++l) {
+            if (l < P.nbw) {
+                const int d = 1 << l;
+                c2 Bo = shfl_down_c(B, d, G), Ao = one;
+                if (l + 1 < P.nbw) Ao = shfl_down_c(A, d, G);
+                if (l < P.nb && g + d < G) {
+                    B = cadd(cmul(A, Bo), B);
+                    if (l + 1 < P.nb) A = cmul(A, Ao);
                 }
             }
         }
-        c2 z = shfl_up_c(B, 1, G);
-        if (g == 0) z = zero;
+    }
+    c2 x = shfl_down_c(B, 1, G);
+    if (g == G - 1) x = zero;
+#pragma unroll
+    for (int k = S - 1; k >= 0; --k) {
+        x = csub(w[k], cmul(bm[k], x));
+        w[k] = x;
+    }
+}
+
+// Writes a lane's segment back (real elements only).
+template <typename T, int S>
+__device__ __forceinline__ void row_store(typename V2<T>::t *phi, typename V2<T>::t *pi,
+                                          const typename V2<T>::t (&w)[S], const typename V2<T>::t (&y)[S], int j0,
+                                          int lenw, bool vec)
+{
+    if (lenw <= 0) return;
+    if (vec) {
+        vstore<S>(phi + j0, w);
+        vstore<S>(pi + j0, y);
+    } else {
 #pragma unroll
         for (int k = 0; k < S; ++k) {
-            z = csub(w[k], cmul(m[k], z));
-            w[k] = cmul(e[k], z);          // b_k = e_k z_k
-        }
-        B = zero;
-#pragma unroll
-        for (int k = S - 1; k >= 0; --k) B = csub(w[k], cmul(fk[k], B));
-        {
-            c2 A = Ab0;
-#pragma unroll
-            for (int l = 0; l < LOGMAX; ++l) {
-                if (l < nbw) {
-                    const int d = 1 << l;
-                    c2 Bo = shfl_down_c(B, d, G), Ao = one;
-                    if (l + 1 < nbw) Ao = shfl_down_c(A, d, G);
-                    if (l < nb && g + d < G) {
-                        B = cadd(cmul(A, Bo), B);
-                        if (l + 1 < nb) A = cmul(A, Ao);
-                    }
-                }
+            if (k < lenw) {
+                phi[j0 + k] = w[k];
+                pi[j0 + k] = y[k];
             }
         }
-        c2 x = shfl_down_c(B, 1, G);
-        if (g == G - 1) x = zero;
-#pragma unroll
-        for (int k = S - 1; k >= 0; --k) {
-            x = csub(w[k], cmul(fk[k], x));
-            w[k] = x;
-        }
-    };
+    }
+}
+
+template <typename T, int S>
+__device__ void implicit_row_group(const ImpConst<T> &K, typename V2<T>::t *phi, typename V2<T>::t *pi,
+                                   const typename V2<T>::t *prow, const T *f, const T *th, int N, bool active,
+                                   bool in_tile, int g, int G, bool vec)
+{
+    typedef typename V2<T>::t c2;
+    const c2 zero = cmk<c2>(T(0), T(0));
+    const int j0 = g * S;
+    int len = N - j0;
+    len = len < 0 ? 0 : (len > S ? S : len);
+    const int lenw = len;          // real elements of the segment (written back)
+    if (!active) len = 0;
+    const T gh = K.gh;
+    RowCoef<T, S> C;
+    c2 w[S], y[S];
+    row_load<T, S>(K, phi, pi, prow, f, th, N, len, j0, G, vec, C, w, y);
+    const ScanPlan<T> P = scan_plan<T, S>(C.m, C.fk, g, G);
+
     // (B + c0rad) U_Phi for the whole segment
     auto apply_B = [&](c2 *bf) {
         c2 xl = shfl_up_c(w[S - 1], 1, G), xr = shfl_down_c(w[0], 1, G);
@@ -373,52 +441,145 @@ __device__ void implicit_row_group(const ImpConst<T> &K, typename V2<T>::t *phi,
         for (int k = 0; k < S; ++k) {
             c2 xm = k ? w[k - 1] : xl;
             c2 xp = (k + 1 < S) ? w[(k + 1) < S ? k + 1 : S - 1] : xr;
-            bf[k] = cadd(cmul(dg[k], w[k]), caxpy(qap[k], xp, cscale<c2>(qam[k], xm)));
+            bf[k] = cadd(cmul(C.dg[k], w[k]), caxpy(C.qap[k], xp, cscale<c2>(C.qam[k], xm)));
         }
     };
 
     // ---- stage 1: r = (1 + gh c_t) Phi + gh Pi
 #pragma unroll
     for (int k = 0; k < S; ++k) {
-        c2 a1 = cmk<c2>(fma(gh, ct[k].x, T(1)), gh * ct[k].y);
+        c2 a1 = cmk<c2>(fma(gh, C.ct[k].x, T(1)), gh * C.ct[k].y);
         w[k] = caxpy(gh, y[k], cmul(a1, w[k]));
     }
-    solve();
+    seg_solve<T, S>(w, C.m, C.e, C.fk, P, g, G);
     {
         c2 bf[S];
         apply_B(bf);
 #pragma unroll
         for (int k = 0; k < S; ++k) {
-            c2 a1 = cmk<c2>(fma(gh, ct[k].x, T(1)), gh * ct[k].y);
-            c2 P1 = cmul(csub(y[k], cscale<c2>(gh, bf[k])), ia1[k]);
-            c2 rphi = caxpy(K.h12g, P1, w[k]);                     // u_Phi + (1-gamma) h U1_Pi
-            c2 rpi = csub(y[k], cscale<c2>(K.h1g, cadd(bf[k], cmul(ct[k], P1))));
+            c2 a1 = cmk<c2>(fma(gh, C.ct[k].x, T(1)), gh * C.ct[k].y);
+            c2 P1 = cmul(csub(y[k], cscale<c2>(gh, bf[k])), C.ia1[k]);
+            c2 rphi = caxpy(K.h12g, P1, w[k]);                     // U1_Phi + (1 - 2 gamma) h U1_Pi
+            c2 rpi = csub(y[k], cscale<c2>(K.h1g, cadd(bf[k], cmul(C.ct[k], P1))));
             w[k] = caxpy(gh, rpi, cmul(a1, rphi));
             y[k] = rpi;
         }
     }
     // ---- stage 2
-    solve();
+    seg_solve<T, S>(w, C.m, C.e, C.fk, P, g, G);
     {
         c2 bf[S];
         apply_B(bf);
 #pragma unroll
-        for (int k = 0; k < S; ++k) y[k] = cmul(csub(y[k], cscale<c2>(gh, bf[k])), ia1[k]);
+        for (int k = 0; k < S; ++k) y[k] = cmul(csub(y[k], cscale<c2>(gh, bf[k])), C.ia1[k]);
     }
-    if (in_tile && lenw > 0) {
-        if (vec) {
-            vstore<S>(phi + j0, w);
-            vstore<S>(pi + j0, y);
-        } else {
+    if (in_tile) row_store<T, S>(phi, pi, w, y, j0, lenw, vec);
+}
+
+template <typename C> __device__ __forceinline__ C conj_c(C a) { return cmk<C>(a.x, -a.y); }
+
+// Hermitian adjoint (for <x, y> = Re sum conj(x) y) of implicit_row_group's
+// map on one row: the SDIRK2 stages in reverse order with conjugated
+// coefficients.  The stage matrix M = (1 + gh c_t) + gh^2 (B + c0rad) = L U
+// gives M^H = U^H L^H, solved as t_j = r_j - conj(fk_{j-1}) t_{j-1},
+// y_j = conj(e_j) t_j, x_j = y_j - conj(m_{j+1}) x_{j+1}; (B + c0rad)^H has
+// rows (qap_{j-1}, conj(dg_j), qam_{j+1}).  (phi, pi) hold the adjoint of
+// the output on entry and the adjoint of the input on exit.
+template <typename T, int S>
+__device__ void implicit_row_adjoint(const ImpConst<T> &K, typename V2<T>::t *phi, typename V2<T>::t *pi,
+                                     const typename V2<T>::t *prow, const T *f, const T *th, int N, bool active,
+                                     bool in_tile, int g, int G, bool vec)
+{
+    typedef typename V2<T>::t c2;
+    const c2 zero = cmk<c2>(T(0), T(0));
+    const int j0 = g * S;
+    int len = N - j0;
+    len = len < 0 ? 0 : (len > S ? S : len);
+    const int lenw = len;
+    if (!active) len = 0;
+    const T gh = K.gh;
+    RowCoef<T, S> C;
+    c2 w[S], y[S];
+    row_load<T, S>(K, phi, pi, prow, f, th, N, len, j0, G, vec, C, w, y);
+    // multipliers of M^H and the shifted angular rows of (B + c0rad)^H
+    c2 fm[S], pm[S], bm[S];
+    T qapp[S], qamn[S];
+    {
+        const c2 fk_prev = shfl_up_c(C.fk[S - 1], 1, G);
+        const c2 m_next = shfl_down_c(C.m[0], 1, G);
+        T qap_prev = __shfl_up_sync(0xffffffffu, C.qap[S - 1], 1, G);
+        T qam_next = __shfl_down_sync(0xffffffffu, C.qam[0], 1, G);
+        if (g == 0) qap_prev = T(0);
+        if (g == G - 1) qam_next = T(0);
 #pragma unroll
-            for (int k = 0; k < S; ++k) {
-                if (k < lenw) {
-                    phi[j0 + k] = w[k];
-                    pi[j0 + k] = y[k];
-                }
-            }
+        for (int k = 0; k < S; ++k) {
+            const c2 fkp = k ? C.fk[k - 1] : fk_prev;
+            const c2 mn = (k + 1 < S) ? C.m[(k + 1) < S ? k + 1 : S - 1] : m_next;
+            fm[k] = (g == 0 && k == 0) ? zero : conj_c(fkp);
+            pm[k] = conj_c(C.e[k]);
+            bm[k] = (g == G - 1 && k == S - 1) ? zero : conj_c(mn);   // m_N = 0
+            qapp[k] = k ? C.qap[k - 1] : qap_prev;
+            qamn[k] = (k + 1 < S) ? C.qam[(k + 1) < S ? k + 1 : S - 1] : qam_next;
         }
     }
+    const ScanPlan<T> P = scan_plan<T, S>(fm, bm, g, G);
+    // (B + c0rad)^H v for the whole segment, v held in v[]
+    auto apply_BH = [&](const c2 *v, c2 *out) {
+        c2 vl = shfl_up_c(v[S - 1], 1, G), vr = shfl_down_c(v[0], 1, G);
+        if (g == 0) vl = zero;
+        if (g == G - 1) vr = zero;
+#pragma unroll
+        for (int k = 0; k < S; ++k) {
+            c2 vm = k ? v[k - 1] : vl;
+            c2 vp = (k + 1 < S) ? v[(k + 1) < S ? k + 1 : S - 1] : vr;
+            out[k] = cadd(cmul(conj_c(C.dg[k]), v[k]), caxpy(qamn[k], vp, cscale<c2>(qapp[k], vm)));
+        }
+    };
+    // w = adjoint of U2_Phi, y = adjoint of U2_Pi
+    c2 r2p[S], ub[S];
+    {
+        c2 bf[S];
+#pragma unroll
+        for (int k = 0; k < S; ++k) {
+            const c2 iac = conj_c(C.ia1[k]);
+            r2p[k] = cmul(iac, y[k]);                   // adjoint of r2_Pi
+            bf[k] = cscale<c2>(-gh, r2p[k]);            // adjoint of bf2
+        }
+        apply_BH(bf, ub);
+#pragma unroll
+        for (int k = 0; k < S; ++k) w[k] = cadd(w[k], ub[k]);
+    }
+    seg_solve<T, S>(w, fm, pm, bm, P, g, G);       // adjoint of w2
+#pragma unroll
+    for (int k = 0; k < S; ++k) {
+        const c2 a1c = cmk<c2>(fma(gh, C.ct[k].x, T(1)), -gh * C.ct[k].y);
+        const c2 w2b = w[k];
+        r2p[k] = caxpy(gh, w2b, r2p[k]);                     // adjoint of r2_Pi
+        const c2 r2f = cmul(a1c, w2b);                       // adjoint of r2_Phi
+        y[k] = r2p[k];                                       // adjoint of u_Pi (so far)
+        // U1_Pi adjoint: from r2_Pi (-h1g conj(c_t)) and r2_Phi (h12g)
+        c2 u1p = caxpy(K.h12g, r2f, cscale<c2>(-K.h1g, cmul(conj_c(C.ct[k]), r2p[k])));
+        const c2 iac = conj_c(C.ia1[k]);
+        const c2 t = cmul(iac, u1p);
+        y[k] = cadd(y[k], t);                                // adjoint of u_Pi through U1_Pi
+        ub[k] = cadd(cscale<c2>(-K.h1g, r2p[k]), cscale<c2>(-gh, t));   // adjoint of bf1
+        w[k] = r2f;                                          // adjoint of U1_Phi (so far)
+    }
+    {
+        c2 bh[S];
+        apply_BH(ub, bh);
+#pragma unroll
+        for (int k = 0; k < S; ++k) w[k] = cadd(w[k], bh[k]);
+    }
+    seg_solve<T, S>(w, fm, pm, bm, P, g, G);       // adjoint of w0
+#pragma unroll
+    for (int k = 0; k < S; ++k) {
+        const c2 a1c = cmk<c2>(fma(gh, C.ct[k].x, T(1)), -gh * C.ct[k].y);
+        const c2 w0b = w[k];
+        y[k] = caxpy(gh, w0b, y[k]);
+        w[k] = cmul(a1c, w0b);
+    }
+    if (in_tile) row_store<T, S>(phi, pi, w, y, j0, lenw, vec);
 }
 
 // b and K at one point from the r table f, rs = 1/Sigma and the theta
@@ -693,9 +854,9 @@ __device__ __forceinline__ void split_tile(const StepParams<T> &p, int tile, int
     const bool src = !p.imp_only && p.patch_np > 0 && i0 + TR >= p.patch_p0 &&
                      i0 - 1 <= p.patch_p0 + p.patch_np;
     if (tid == 0) {
-        long long n = *((volatile long long *)&p.ctl->step);
+        long long n = p.nfix >= 0 ? p.nfix : *((volatile long long *)&p.ctl->step);
         s_n = n;
-        if (!p.imp_only) {
+        if (!p.imp_only && p.nfix < 0) {
             // The last CTA to read the step index advances it.  Later kernels
             // on the stream see the new value; no CTA of this launch reads it
             // again, so no CTA has to wait for its own stores first.
@@ -855,7 +1016,7 @@ __device__ __forceinline__ void split_tile(const StepParams<T> &p, int tile, int
     }
     if (p.imp_only) return;
     // ---- E: physical sample u_{n+1} = C_{dt/2} s_{n+1} on the extraction row
-    const bool ext = p.i_ext >= i0 && p.i_ext < i0 + TR && p.i_ext < Nr;
+    const bool ext = p.nfix < 0 && p.i_ext >= i0 && p.i_ext < i0 + TR && p.i_ext < Nr;
     if (ext) {
         __syncthreads();
         int lr = p.i_ext - i0 + 1;
@@ -1104,6 +1265,367 @@ __global__ void __maxnreg__(PersistRegs<NC>::v) k_split_persist(const StepParams
             extract_warp<T>(p, xPhi, s_n + 1);
         }
     }
+}
+
+// ---------------------------------------------------------------- adjoint
+
+// FP64 weighted sum h = sum_j w_j row_j in the order extract_warp uses; lane 0
+// of the calling warp returns it.
+template <typename T>
+__device__ double2 sample_warp(const StepParams<T> &p, const typename V2<T>::t *row)
+{
+    const int lane = threadIdx.x & 31;
+    double sre = 0.0, sim = 0.0;
+    for (int j = lane; j < p.Nth; j += 32) {
+        double w = p.w[j];
+        sre = fma(w, (double)row[j].x, sre);
+        sim = fma(w, (double)row[j].y, sim);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        sre += __shfl_xor_sync(0xffffffffu, sre, o);
+        sim += __shfl_xor_sync(0xffffffffu, sim, o);
+    }
+    return make_double2(sre, sim);
+}
+
+// h = E u with u = s (physical) or u = C_{dt/2} s on the extraction row; one
+// warp.  The sum is the one the step kernels write to the waveform buffer.
+template <typename T, int S>
+__global__ void __launch_bounds__(32) k_sample(const StepParams<T> p, const typename V2<T>::t *s, int physical,
+                                               double2 *h_out)
+{
+    typedef typename V2<T>::t c2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int N = p.Nth, Nr = p.Nr, i = p.i_ext, tid = threadIdx.x;
+    c2 *xPhi = (c2 *)smem_raw;
+    c2 *xPi = xPhi + ((N + 1) & ~1);
+    T *xF = (T *)(xPi + ((N + 1) & ~1));
+    T *xTh = xF + NRF;
+    for (int j = tid; j < N; j += 32) {
+        xPhi[j] = s[(size_t)i * N + j];
+        xPi[j] = s[((size_t)Nr + i) * N + j];
+    }
+    if (tid < NRF) xF[tid] = p.rtab[(size_t)(2 * i) * NRF + tid];
+    for (int k = tid; k < NTF * N; k += 32) xTh[k] = p.thtab[k];
+    __syncwarp();
+    if (!physical) {
+        const int G = p.group;
+        const bool mine = tid < G;
+        const bool active = mine && i >= 1 && i <= Nr - 2;
+        implicit_row_group<T, S>(p.half, xPhi, xPi, p.half.piv + (size_t)i * N, xF, xTh, N, active, mine, tid % G, G,
+                                 p.vec != 0);
+        __syncwarp();
+    }
+    double2 h = sample_warp<T>(p, xPhi);
+    if (tid == 0) *h_out = h;
+}
+
+// Adds conj(lam) * coef * (unit source) * phase to the amplitude sum cA and
+// conj(lam) * coef * (source) * (rho d r0*/d r0 - i m Omega' t) to the orbit
+// sum cr (rho = (r* - r0*)/sigma_r^2): the derivatives of the source term
+// A F_pref G(r*, theta) e^{-i m Omega t} with respect to A and r0.
+template <typename T>
+__device__ __forceinline__ void source_grad(const StepParams<T> &p, typename V2<T>::t lam, double coef,
+                                            typename V2<T>::t u, double2 ph, double rs, double t, double2 &cA,
+                                            double2 &cr)
+{
+    const double lr = (double)lam.x, li = -(double)lam.y;             // conj(lam)
+    const double ur = (double)u.x * ph.x - (double)u.y * ph.y, ui = (double)u.x * ph.y + (double)u.y * ph.x;
+    const double vr = coef * (lr * ur - li * ui), vi = coef * (lr * ui + li * ur);   // conj(lam) coef U ph
+    cA.x += vr;
+    cA.y += vi;
+    const double fr = p.amp_re * vr - p.amp_im * vi, fi = p.amp_re * vi + p.amp_im * vr;   // times A
+    const double zr = (rs - p.rs0) * p.inv_sig_r2 * p.drs0_dr0, zi = -p.m_dOmega * t;
+    cr.x += fr * zr - fi * zi;
+    cr.y += fr * zi + fi * zr;
+}
+
+// Hermitian adjoint of one split step s_n -> s_{n+1} = LW_n C_h s_n (h = dt;
+// h = dt/2 and a physical input when p.first), plus the extraction seed:
+//   lam_n = C_h^H LW^H lam_{n+1} + C_{dt/2}^H E^H g_n     (E^H g_0 when first)
+// where LW is the linear part of the two Lax-Wendroff stages (Eqs. 13-14)
+// and E u = sum_j w_j Phi_{i_ext, j}.  p.uin holds lam_{n+1}, p.uout gets
+// lam_n, p.nfix = n.  Each CTA owns TR output rows and reads one halo row on
+// either side.  The transposed stages are written in gather form: every
+// midpoint adjoint (mF, mG) from its two nodes, then every node from its two
+// midpoints.  The CTA's contributions to the source derivatives
+// (sum over steps of <lam_{n+1}, dF_n/dp> for p = Re A, Im A, r0) go to
+// part[4 blockIdx.x + (0..3)] = (Re cA, Im cA, Re cr, Im cr).
+template <typename T, int S>
+__global__ void __launch_bounds__(256, 1) k_adjoint_step(const StepParams<T> p, const double2 *gseed, double *part)
+{
+    typedef typename V2<T>::t c2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double s_red[8][4];
+    const int Nr = p.Nr, N = p.Nth, TR = p.tile_rows, R = TR + 2, P = N;
+    const int tid = threadIdx.x, NT = blockDim.x;
+    const int i0 = blockIdx.x * TR;
+    const int G = p.group;
+    const bool first = p.first != 0;
+    const ImpConst<T> &K = first ? p.half : p.full;
+    const long long n = p.nfix;
+    const T hdt = p.half_dt, dt = p.dt, ri = p.drs_inv;
+    const c2 zero = cmk<c2>(T(0), T(0));
+
+    const unsigned plane = (unsigned)R * (unsigned)N;
+    c2 *lF = (c2 *)smem_raw;
+    c2 *lG = lF + plane;
+    c2 *mF = lG + plane;
+    c2 *mG = mF + plane;
+    T *sRt = (T *)(mG + plane);
+    T *sTh = sRt + (2 * R - 1) * NRF;
+
+    // ---- load lam_{n+1} on rows i0-1 .. i0+TR, the r and theta tables
+    for (int idx = tid; idx < R * N; idx += NT) {
+        int lr = idx / N, j = idx - lr * N;
+        int gi = i0 - 1 + lr;
+        c2 f = zero, g = zero;
+        if (gi >= 0 && gi < Nr) {
+            f = p.uin[(size_t)gi * N + j];
+            g = p.uin[((size_t)Nr + gi) * N + j];
+        }
+        lF[idx] = f;
+        lG[idx] = g;
+    }
+    {
+        const long long pbase = 2LL * (i0 - 1), pmax = 2LL * Nr - 2;
+        for (int idx = tid; idx < (2 * R - 1) * NRF; idx += NT) {
+            int e = idx / NRF, q = idx - e * NRF;
+            long long pos = pbase + e;
+            sRt[idx] = (pos >= 0 && pos <= pmax) ? p.rtab[(size_t)pos * NRF + q] : T(0);
+        }
+    }
+    for (int idx = tid; idx < NTF * N; idx += NT) sTh[idx] = p.thtab[idx];
+    __syncthreads();
+
+    const bool src = p.unit_np > 0 && i0 + TR >= p.unit_p0 && i0 - 1 <= p.unit_p0 + p.unit_np;
+    double2 ph1 = make_double2(0.0, 0.0), ph2 = ph1;
+    const double t1 = (double)n * p.dt64, t2 = t1 + 0.5 * p.dt64;
+    if (src) {
+        ph1 = phase_at(p.mOmega, t1);
+        ph2 = phase_at(p.mOmega, t2);
+    }
+    double2 cA = make_double2(0.0, 0.0), cr = cA;
+    auto node_bK = [&](int lr, int j, T &b, c2 &Kc) {
+        T f[12];
+        vload<12>(f, sRt + 2 * lr * NRF);
+        const T S2 = sTh[TF_S2 * N + j], C = sTh[TF_C * N + j];
+        bK<T>(f, rsq_(fma(-f[RF_AD], S2, f[RF_R2])), S2, C, b, Kc);
+    };
+    auto half_bK = [&](int k, int j, T &b, c2 &Kc) {
+        T f[12];
+        vload<12>(f, sRt + (2 * k + 1) * NRF);
+        const T S2 = sTh[TF_S2 * N + j], C = sTh[TF_C * N + j];
+        bK<T>(f, rsq_(fma(-f[RF_AD], S2, f[RF_R2])), S2, C, b, Kc);
+    };
+
+    // ---- adjoints of the midpoints k = 0 .. R-2 (between tile rows k, k+1)
+    for (int idx = tid; idx < (R - 1) * N; idx += NT) {
+        int k = idx / N, j = idx - k * N;
+        int gl = i0 - 1 + k;
+        c2 vF = zero, vG = zero;
+        if (gl >= 0 && gl <= Nr - 2) {
+            if (gl >= 1) {   // lower node interior (gl <= Nr - 2 holds)
+                T b;
+                c2 Kc;
+                node_bK(k, j, b, Kc);
+                const c2 lf = lF[k * P + j], lg = lG[k * P + j];
+                const T cb = dt * b * ri;
+                const c2 cK = cscale<c2>(dt * ri, Kc);
+                vF = csub(cmul(conj_c(cK), lg), cscale<c2>(cb, lf));
+                vG = cscale<c2>(cb, lg);
+            }
+            if (gl + 1 <= Nr - 2) {   // upper node interior (gl + 1 >= 1 holds)
+                T b;
+                c2 Kc;
+                node_bK(k + 1, j, b, Kc);
+                const c2 lf = lF[(k + 1) * P + j], lg = lG[(k + 1) * P + j];
+                const T cb = dt * b * ri;
+                const c2 cK = cscale<c2>(dt * ri, Kc);
+                vF = cadd(vF, csub(cscale<c2>(cb, lf), cmul(conj_c(cK), lg)));
+                vG = csub(vG, cscale<c2>(cb, lg));
+            }
+            // stage-1 source at this midpoint (owned by the tile of its lower node)
+            if (src && k >= 1 && k <= TR) {
+                int pr = gl - p.unit_p0;
+                if (pr >= 0 && pr < p.unit_np)
+                    source_grad<T>(p, vG, (double)hdt, p.patchu[((size_t)pr * 2 + 1) * N + j], ph1,
+                                   p.rs_min64 + ((double)gl + 0.5) * p.drs64, t1, cA, cr);
+            }
+        }
+        mF[idx] = vF;
+        mG[idx] = vG;
+    }
+    __syncthreads();
+
+    // ---- adjoints of the nodes (inputs of the Lax-Wendroff stages), rows 1..TR
+    for (int idx = tid; idx < TR * N; idx += NT) {
+        int lr = 1 + idx / N, j = idx - (lr - 1) * N;
+        int gi = i0 - 1 + lr;
+        if (gi >= Nr) continue;
+        const c2 lf = lF[lr * P + j], lg = lG[lr * P + j];
+        const bool interior = gi >= 1 && gi <= Nr - 2;
+        c2 vF = interior ? lf : zero, vG = interior ? lg : zero;
+        if (gi <= Nr - 2) {   // midpoint lr (to the next row)
+            T b;
+            c2 Kc;
+            half_bK(lr, j, b, Kc);
+            const T c = hdt * b * ri;
+            const c2 kap = cscale<c2>(hdt * ri, Kc);
+            const c2 mf = mF[lr * P + j], mg = mG[lr * P + j];
+            vF = cadd(vF, csub(cscale<c2>(T(0.5) + c, mf), cmul(conj_c(kap), mg)));
+            vG = cadd(vG, cscale<c2>(T(0.5) - c, mg));
+        }
+        if (gi >= 1) {   // midpoint lr - 1 (to the previous row)
+            T b;
+            c2 Kc;
+            half_bK(lr - 1, j, b, Kc);
+            const T c = hdt * b * ri;
+            const c2 kap = cscale<c2>(hdt * ri, Kc);
+            const c2 mf = mF[(lr - 1) * P + j], mg = mG[(lr - 1) * P + j];
+            vF = cadd(vF, cadd(cscale<c2>(T(0.5) - c, mf), cmul(conj_c(kap), mg)));
+            vG = cadd(vG, cscale<c2>(T(0.5) + c, mg));
+        }
+        // stage-2 source at this node
+        if (src && interior) {
+            int pr = gi - p.unit_p0;
+            if (pr >= 0 && pr < p.unit_np)
+                source_grad<T>(p, lg, (double)dt, p.patchu[((size_t)pr * 2) * N + j], ph2,
+                               p.rs_min64 + (double)gi * p.drs64, t2, cA, cr);
+        }
+        lF[lr * P + j] = vF;
+        lG[lr * P + j] = vG;
+    }
+    __syncthreads();
+
+    // ---- C_h^H on the output rows
+    {
+        const int rpp = NT / G;
+        const int g = tid % G;
+        const bool vec = p.vec != 0;
+        for (int base = 1; base <= TR; base += rpp) {
+            int lr = base + tid / G;
+            bool in_tile = lr <= TR && i0 - 1 + lr < Nr;
+            int gi = i0 - 1 + lr;
+            bool active = in_tile && gi >= 1 && gi <= Nr - 2;
+            int lrc = in_tile ? lr : 1;
+            implicit_row_adjoint<T, S>(K, lF + lrc * P, lG + lrc * P, K.piv + (size_t)(active ? gi : 1) * N,
+                                       sRt + 2 * lrc * NRF, sTh, N, active, in_tile, g, G, vec);
+        }
+    }
+    __syncthreads();
+
+    // ---- extraction seed: C_{dt/2}^H E^H g_n (E^H g_0 for a physical input)
+    const bool ext = gseed != nullptr && p.i_ext >= i0 && p.i_ext < i0 + TR && p.i_ext < Nr;
+    if (ext) {
+        const int lx = p.i_ext - i0 + 1;
+        c2 *xF = mF, *xG = mG;
+        if (tid < 32) {
+            const double2 gv = *gseed;
+            for (int j = tid; j < N; j += 32) {
+                const double w = p.w[j];
+                xF[j] = cmk<c2>((T)(w * gv.x), (T)(w * gv.y));
+                xG[j] = zero;
+            }
+            __syncwarp();
+            if (!first) {
+                const bool mine = tid < G;
+                const bool active = mine && p.i_ext >= 1 && p.i_ext <= Nr - 2;
+                implicit_row_adjoint<T, S>(p.half, xF, xG, p.half.piv + (size_t)p.i_ext * N, sRt + 2 * lx * NRF, sTh,
+                                           N, active, mine, tid % G, G, p.vec != 0);
+                __syncwarp();
+            }
+            for (int j = tid; j < N; j += 32) {
+                lF[lx * P + j] = cadd(lF[lx * P + j], xF[j]);
+                lG[lx * P + j] = cadd(lG[lx * P + j], xG[j]);
+            }
+        }
+        __syncthreads();
+    }
+
+    // ---- store lam_n
+    for (int idx = tid; idx < TR * N; idx += NT) {
+        int lr = 1 + idx / N, j = idx - (lr - 1) * N;
+        int gi = i0 - 1 + lr;
+        if (gi >= Nr) continue;
+        p.uout[(size_t)gi * N + j] = lF[lr * P + j];
+        p.uout[((size_t)Nr + gi) * N + j] = lG[lr * P + j];
+    }
+
+    // ---- this CTA's source-derivative sums (fixed-order reduction)
+    double v[4] = {cA.x, cA.y, cr.x, cr.y};
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+        for (int o = 16; o > 0; o >>= 1) v[c] += __shfl_xor_sync(0xffffffffu, v[c], o);
+    if ((tid & 31) == 0)
+        for (int c = 0; c < 4; ++c) s_red[tid >> 5][c] = v[c];
+    __syncthreads();
+    if (tid < 4) {
+        double acc = 0.0;
+        for (int w = 0; w < NT / 32; ++w) acc += s_red[w][tid];
+        part[4 * blockIdx.x + tid] = acc;
+    }
+}
+
+// acc[c] += sum over the nblk CTAs of part[4 b + c], in a fixed order.
+__global__ void __launch_bounds__(32) k_part_reduce(const double *part, int nblk, double *acc)
+{
+    const int lane = threadIdx.x;
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int b = lane; b < nblk; b += 32)
+        for (int c = 0; c < 4; ++c) v[c] += part[4 * b + c];
+    for (int c = 0; c < 4; ++c)
+        for (int o = 16; o > 0; o >>= 1) v[c] += __shfl_xor_sync(0xffffffffu, v[c], o);
+    if (lane == 0)
+        for (int c = 0; c < 4; ++c) acc[c] += v[c];
+}
+
+// Deterministic <x, y> = sum conj(x_k) y_k in FP64: per-CTA partial sums
+// over a fixed grid, then one warp adds them in a fixed order.
+constexpr int kDotBlocks = 256;
+template <typename T>
+__global__ void __launch_bounds__(256) k_dot_part(const typename V2<T>::t *x, const typename V2<T>::t *y, size_t n,
+                                                  double *part)
+{
+    __shared__ double red[8][2];
+    double re = 0.0, im = 0.0;
+    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
+        const double xr = x[k].x, xi = x[k].y, yr = y[k].x, yi = y[k].y;
+        re = fma(xr, yr, fma(xi, yi, re));
+        im = fma(xr, yi, fma(-xi, yr, im));
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        re += __shfl_xor_sync(0xffffffffu, re, o);
+        im += __shfl_xor_sync(0xffffffffu, im, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        red[threadIdx.x >> 5][0] = re;
+        red[threadIdx.x >> 5][1] = im;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            a += red[w][0];
+            b += red[w][1];
+        }
+        part[2 * blockIdx.x] = a;
+        part[2 * blockIdx.x + 1] = b;
+    }
+}
+
+__global__ void __launch_bounds__(32) k_dot_final(const double *part, int nblk, double2 *out)
+{
+    double re = 0.0, im = 0.0;
+    for (int b = threadIdx.x; b < nblk; b += 32) {
+        re += part[2 * b];
+        im += part[2 * b + 1];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        re += __shfl_xor_sync(0xffffffffu, re, o);
+        im += __shfl_xor_sync(0xffffffffu, im, o);
+    }
+    if (threadIdx.x == 0) *out = make_double2(re, im);
 }
 
 // ------------------------------------------------------------ literal scheme
@@ -1478,6 +2000,71 @@ cudaError_t launch_split_batch(const StepParams<T> *d_params, const int2 *d_tile
 }
 
 template <typename T>
+cudaError_t launch_apply_step(const StepParams<T> &p, int threads, size_t smem, cudaStream_t st)
+{
+    if (p.nfix < 0) return cudaErrorInvalidValue;
+    return launch_split_step<T>(p, threads, smem, st);
+}
+
+template <typename T>
+cudaError_t launch_sample(const StepParams<T> &p, const typename V2<T>::t *s, int physical, double2 *h_out,
+                          cudaStream_t st)
+{
+    typedef typename V2<T>::t c2;
+    const int seg = implicit_seg(p.Nth);
+    auto fn = seg == kSegNarrow ? k_sample<T, kSegNarrow> : (seg == kSeg ? k_sample<T, kSeg> : k_sample<T, kSegWide>);
+    cudaError_t e = smem_limit_max((const void *)fn);
+    if (e != cudaSuccess) return e;
+    const size_t row = (size_t)((p.Nth + 1) & ~1);
+    const size_t smem = 2 * row * sizeof(c2) + ((size_t)NRF + (size_t)NTF * p.Nth) * sizeof(T);
+    fn<<<1, 32, smem, st>>>(p, s, physical, h_out);
+    return cudaGetLastError();
+}
+
+template <typename T>
+size_t adjoint_smem_bytes(int tile_rows, int Nth)
+{
+    const size_t R = (size_t)tile_rows + 2;
+    return 4 * R * Nth * sizeof(typename V2<T>::t) + ((2 * R - 1) * NRF + (size_t)NTF * Nth) * sizeof(T);
+}
+
+template <typename T>
+int adjoint_grid(int Nr, int tile_rows)
+{
+    return (Nr + tile_rows - 1) / tile_rows;
+}
+
+template <typename T>
+cudaError_t launch_adjoint_step(const StepParams<T> &p, int tile_rows, const double2 *gseed, double *part,
+                                double *acc, cudaStream_t st)
+{
+    const int seg = implicit_seg(p.Nth);
+    auto fn = seg == kSegNarrow ? k_adjoint_step<T, kSegNarrow>
+                                : (seg == kSeg ? k_adjoint_step<T, kSeg> : k_adjoint_step<T, kSegWide>);
+    cudaError_t e = smem_limit_max((const void *)fn);
+    if (e != cudaSuccess) return e;
+    StepParams<T> q = p;
+    q.tile_rows = tile_rows;
+    const int grid = adjoint_grid<T>(p.Nr, tile_rows);
+    fn<<<grid, 256, adjoint_smem_bytes<T>(tile_rows, p.Nth), st>>>(q, gseed, part);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_part_reduce<<<1, 32, 0, st>>>(part, grid, acc);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_dot(const typename V2<T>::t *x, const typename V2<T>::t *y, size_t n, double *part,
+                       double2 *out, cudaStream_t st)
+{
+    k_dot_part<T><<<kDotBlocks, 256, 0, st>>>(x, y, n, part);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_dot_final<<<1, 32, 0, st>>>(part, kDotBlocks, out);
+    return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_literal_step(const StepParams<T> &p, cudaStream_t st)
 {
     int nm = (p.Nr - 1) * p.Nth, nn = p.Nr * p.Nth;
@@ -1544,6 +2131,20 @@ cudaError_t launch_convert_from(int prec, const void *src, double2 *dst, size_t 
     return cudaGetLastError();
 }
 
+template cudaError_t launch_apply_step<float>(const StepParams<float> &, int, size_t, cudaStream_t);
+template cudaError_t launch_apply_step<double>(const StepParams<double> &, int, size_t, cudaStream_t);
+template cudaError_t launch_sample<float>(const StepParams<float> &, const float2 *, int, double2 *, cudaStream_t);
+template cudaError_t launch_sample<double>(const StepParams<double> &, const double2 *, int, double2 *, cudaStream_t);
+template size_t adjoint_smem_bytes<float>(int, int);
+template size_t adjoint_smem_bytes<double>(int, int);
+template int adjoint_grid<float>(int, int);
+template int adjoint_grid<double>(int, int);
+template cudaError_t launch_adjoint_step<float>(const StepParams<float> &, int, const double2 *, double *, double *,
+                                                cudaStream_t);
+template cudaError_t launch_adjoint_step<double>(const StepParams<double> &, int, const double2 *, double *, double *,
+                                                 cudaStream_t);
+template cudaError_t launch_dot<float>(const float2 *, const float2 *, size_t, double *, double2 *, cudaStream_t);
+template cudaError_t launch_dot<double>(const double2 *, const double2 *, size_t, double *, double2 *, cudaStream_t);
 template int split_batch_blocks_per_sm<float>(int, size_t);
 template int split_batch_blocks_per_sm<double>(int, size_t);
 template cudaError_t launch_split_batch<float>(const StepParams<float> *, const int2 *, int, int, size_t, cudaStream_t);

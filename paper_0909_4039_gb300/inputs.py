@@ -105,3 +105,15 @@ def gaussian_pulse(Nr: int, Ntheta: int, rs_min: float, rs_max: float, center: f
     u[:, 0, :] = 0.0
     u[:, -1, :] = 0.0
     return u
+
+
+def adjoint_target(nsamples: int, dt: float, seed: int = 1, omega_max: float = 0.5) -> np.ndarray:
+    """Synthetic target waveform for the adjoint workload: complex Gaussian
+    noise (numpy PCG64, `seed`) of `nsamples` samples spaced dt, low-passed
+    to |omega| < omega_max (1/M) by zeroing the higher FFT bins."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    z = rng.standard_normal(nsamples) + 1j * rng.standard_normal(nsamples)
+    spec = np.fft.fft(z)
+    omega = 2.0 * np.pi * np.fft.fftfreq(nsamples, d=dt)
+    spec[np.abs(omega) >= omega_max] = 0.0
+    return np.fft.ifft(spec)

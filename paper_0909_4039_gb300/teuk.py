@@ -41,6 +41,7 @@ EXPORTED = [
     "teuk_kernel_config", "teuk_set_persistent", "teuk_autotune_cold",
     "teuk_batch_workspace_bytes", "teuk_batch_create", "teuk_batch_step", "teuk_batch_tiling",
     "teuk_batch_set_tiling", "teuk_batch_autotune", "teuk_batch_last_error", "teuk_batch_destroy",
+    "teuk_apply_step", "teuk_apply_sample", "teuk_adjoint_workspace_bytes", "teuk_adjoint_step", "teuk_dot",
 ]
 
 
@@ -116,6 +117,14 @@ def lib(load_only: bool = False):
                  "teuk_set_state", "teuk_get_state", "teuk_step", "teuk_extract_waveform", "teuk_destroy",
                  "teuk_tiling", "teuk_autotune", "teuk_set_tiling", "teuk_literal_step_static",
                  "teuk_kernel_config", "teuk_set_persistent", "teuk_autotune_cold"):
+        getattr(L, name).restype = ctypes.c_int
+    L.teuk_apply_step.argtypes = [vp, vp, vp, i64, ctypes.c_int, vp]
+    L.teuk_apply_sample.argtypes = [vp, vp, ctypes.c_int, vp, vp]
+    L.teuk_adjoint_workspace_bytes.argtypes = [vp, sz]
+    L.teuk_adjoint_step.argtypes = [vp, vp, vp, i64, ctypes.c_int, vp, vp, vp]
+    L.teuk_dot.argtypes = [vp, vp, vp, vp, vp, vp]
+    for name in ("teuk_apply_step", "teuk_apply_sample", "teuk_adjoint_workspace_bytes", "teuk_adjoint_step",
+                 "teuk_dot"):
         getattr(L, name).restype = ctypes.c_int
     pvp = ctypes.POINTER(vp)
     ip = ctypes.POINTER(ctypes.c_int)

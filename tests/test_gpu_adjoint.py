@@ -1,0 +1,209 @@
+"""Adjoint (transposed) stepper and waveform-loss gradients.
+
+Pins, none of which uses the adjoint to check itself:
+  * dot-product identities <y, M x> = <M^H y, x> for one step (regular and
+    first), for the sample operator E C_{dt/2}, and for the whole map from
+    the initial state to the waveform, to 1e-13 relative in FP64;
+  * gradients of L = sum_n dt |h_n - target_n|^2 with respect to the source
+    amplitude (Re A, Im A), the orbit radius r0 and the spin a against
+    central finite differences of L computed by independent forward runs,
+    on the GPU and with the FP64 oracle;
+  * the torch.autograd.Function gives the same gradient as the sweep;
+  * the adjoint workload (4096 x 64, a = 0.7, 8000 steps, low-passed noise
+    target) at full size against central differences.
+"""
+import time
+
+import numpy as np
+import pytest
+
+from paper_0909_4039_gb300 import inputs
+from tests._common import oracle_problem, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+def _w(Nr=90, Nth=16, a=0.7, m=2, steps=0, amp=0.0, r0=7.0, sig_r=0.6, sig_th=0.3):
+    return inputs.Workload("adj", s=-2, m=m, a=a, Nr=Nr, Ntheta=Nth, rs_min=-40.0, rs_max=120.0, steps=steps,
+                           r0=r0, amp=amp, sig_r=sig_r, sig_th=sig_th, rs_ext=80.0)
+
+
+def _rand(shape, seed, device, dtype, zero_boundary=False):
+    import torch
+    u = inputs.random_state(shape[1], shape[2], seed=seed, zero_boundary=zero_boundary)
+    return torch.as_tensor(u).to(device=device, dtype=dtype)
+
+
+def _cdot(op, x, y):
+    import torch
+    out = torch.zeros(1, dtype=torch.complex128, device=x.device)
+    op.dot(x, y, out.data_ptr())
+    op.st.synchronize()
+    return complex(out.item())
+
+
+@pytest.mark.parametrize("Nr,Nth,m,first", [(90, 16, 2, False), (90, 16, 2, True), (70, 33, 3, False),
+                                             (64, 128, 1, False), (50, 64, 4, True)])
+def test_one_step_dot_product(Nr, Nth, m, first):
+    """<y, M_n x> = <M_n^H y, x> with the source off (M_n linear)."""
+    import torch
+    from paper_0909_4039_gb300 import adjoint as A
+    op = A.Operator(_w(Nr, Nth, m=m), A.Params(0.0, 7.0, 0.7), "fp64")
+    with torch.cuda.stream(op.st.stream):
+        x = _rand(op.shape, 1, op.st.device, op.ctype)
+        y = _rand(op.shape, 2, op.st.device, op.ctype)
+        Mx, MHy = op.empty(), op.empty()
+        op.step(x, Mx, 5, first)
+        op.adjoint(y, MHy, 5, first, None)
+        lhs, rhs = _cdot(op, y, Mx), _cdot(op, MHy, x)
+    scale = float(torch.linalg.vector_norm(y).item() * torch.linalg.vector_norm(Mx).item())
+    assert abs(lhs - rhs) <= 1e-13 * scale, (lhs, rhs, scale)
+    op.close()
+
+
+def test_sample_dot_product():
+    """<g, E C_{dt/2} x> = <C_{dt/2}^H E^H g, x>: the adjoint step with a
+    zero incoming adjoint returns the sample's adjoint."""
+    import torch
+    from paper_0909_4039_gb300 import adjoint as A
+    op = A.Operator(_w(80, 32, m=2), A.Params(0.0, 7.0, 0.5), "fp64")
+    with torch.cuda.stream(op.st.stream):
+        x = _rand(op.shape, 3, op.st.device, op.ctype)
+        h = torch.zeros(1, dtype=torch.complex128, device=op.st.device)
+        g = torch.tensor([0.3 - 1.7j], dtype=torch.complex128, device=op.st.device)
+        op.sample(x, False, h.data_ptr())
+        lam = op.empty()
+        op.adjoint(op.zeros(), lam, 9, False, g.data_ptr())
+        lhs = complex(np.conj(g.item()) * h.item())
+        rhs = _cdot(op, lam, x)
+    assert abs(lhs - rhs) <= 1e-13 * abs(lhs), (lhs, rhs)
+    op.close()
+
+
+def test_whole_map_dot_product_initial_state():
+    """G maps u_0 to (h_0..h_N) with the source off: <g, G u_0> equals
+    <G^H g, u_0> where G^H g is the backward sweep's adjoint of u_0."""
+    import torch
+    from paper_0909_4039_gb300 import adjoint as A
+    w = _w(100, 16, m=2)
+    N = 60
+    u0 = inputs.random_state(w.Nr, w.Ntheta, seed=11)
+    prm = A.Params(0.0, 7.0, 0.7)
+    h = A.waveform(w, prm, N, u0=u0).cpu().numpy()
+    rng = np.random.Generator(np.random.PCG64(5))
+    g = rng.standard_normal(N + 1) + 1j * rng.standard_normal(N + 1)
+    r = A.gradients(w, prm, N, torch.as_tensor(g), u0=u0, wrt_a=False, every=7)
+    lhs = np.vdot(g, h)
+    rhs = np.vdot(r["du0"].cpu().numpy().ravel(), u0.ravel())
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs), (lhs, rhs)
+
+
+def _loss(h, target, dt):
+    return float(dt * np.sum(np.abs(h - target) ** 2))
+
+
+def _fd_gradients(loss_of, prm, rel=1e-6):
+    """Central differences of the loss in (Re A, Im A, r0, a).  L is
+    quadratic in A, so its differences are exact there for any step."""
+    from paper_0909_4039_gb300 import adjoint as A
+    out = []
+    for k, (name, h) in enumerate([("Ar", 1e-3), ("Ai", 1e-3), ("r0", rel * prm.r0), ("a", rel * max(prm.a, 0.1))]):
+        def shifted(d):
+            amp, r0, a = prm.amp, prm.r0, prm.a
+            if k == 0:
+                amp = amp + d
+            elif k == 1:
+                amp = amp + 1j * d
+            elif k == 2:
+                r0 = r0 + d
+            else:
+                a = a + d
+            return loss_of(A.Params(amp, r0, a))
+        out.append((shifted(h) - shifted(-h)) / (2 * h))
+    return np.array(out)
+
+
+def test_source_and_spin_gradients_against_gpu_differences():
+    import torch
+    from paper_0909_4039_gb300 import adjoint as A
+    w = _w(220, 16, a=0.6, m=2, sig_r=0.8)
+    N = 300
+    dt = 0.5 * (w.rs_max - w.rs_min) / (w.Nr - 1)
+    prm = A.Params(0.7 - 0.2j, 7.0, 0.6)
+    target = 1e-3 * inputs.adjoint_target(N + 1, dt, seed=3)
+    h = A.waveform(w, prm, N).cpu().numpy()
+    r = A.gradients(w, prm, N, torch.as_tensor(2.0 * dt * (h - target)))
+    got = np.array([r["dA_re"], r["dA_im"], r["dr0"], r["da"]])
+    fd = _fd_gradients(lambda q: _loss(A.waveform(w, q, N).cpu().numpy(), target, dt), prm)
+    assert np.all(np.abs(got - fd) <= 1e-6 * np.abs(fd) + 1e-12 * np.abs(fd).max()), (got, fd)
+
+
+def test_gradients_against_oracle_differences():
+    """The FP64 oracle's loss, differenced in each parameter, against the
+    GPU adjoint gradient (small grid)."""
+    import torch
+    from oracle import oracle as O
+    from paper_0909_4039_gb300 import adjoint as A
+    w = _w(140, 8, a=0.5, m=2, sig_r=0.8)
+    N = 160
+    dt = 0.5 * (w.rs_max - w.rs_min) / (w.Nr - 1)
+    prm = A.Params(0.9 + 0.4j, 6.5, 0.5)
+    target = 1e-3 * inputs.adjoint_target(N + 1, dt, seed=4)
+    h = A.waveform(w, prm, N).cpu().numpy()
+    r = A.gradients(w, prm, N, torch.as_tensor(2.0 * dt * (h - target)))
+    got = np.array([r["dA_re"], r["dA_im"], r["dr0"], r["da"]])
+
+    def oracle_loss(q):
+        wq = w.with_(a=q.a, r0=q.r0, amp=q.amp)
+        _, ho = O.run(oracle_problem(wq), None, N)
+        return _loss(ho, target, dt)
+
+    fd = _fd_gradients(oracle_loss, prm)
+    assert np.all(np.abs(got - fd) <= 1e-6 * np.abs(fd) + 1e-12 * np.abs(fd).max()), (got, fd)
+    # the waveforms themselves agree at the FP64 parity tolerance
+    _, ho = O.run(oracle_problem(w.with_(a=prm.a, r0=prm.r0, amp=prm.amp)), None, N)
+    assert rel_l2(h, ho) <= 1e-12
+
+
+def test_autograd_function_matches_sweep():
+    import torch
+    from paper_0909_4039_gb300 import adjoint as A
+    w = _w(120, 16, a=0.4, m=2, sig_r=0.8)
+    N = 90
+    dt = 0.5 * (w.rs_max - w.rs_min) / (w.Nr - 1)
+    target = torch.as_tensor(1e-3 * inputs.adjoint_target(N + 1, dt, seed=6), device="cuda")
+    params = torch.tensor([0.5, -0.3, 8.0, 0.4], dtype=torch.float64, device="cuda", requires_grad=True)
+    h = A.waveform_fn(params, w, N)
+    loss = dt * torch.sum(torch.abs(h - target) ** 2)
+    loss.backward()
+    hn = h.detach().cpu().numpy()
+    r = A.gradients(w, A.Params(0.5 - 0.3j, 8.0, 0.4), N, torch.as_tensor(2.0 * dt * (hn - target.cpu().numpy())))
+    ref = np.array([r["dA_re"], r["dA_im"], r["dr0"], r["da"]])
+    assert np.allclose(params.grad.cpu().numpy(), ref, rtol=1e-12, atol=0.0)
+
+
+def test_adjoint_workload_4096x64_full_size():
+    """The adjoint workload: 4096 x 64, a = 0.7, orbit r0 = 10, 8000 steps,
+    target = low-passed complex noise (seed 1, |omega| < 0.5/M).  Gradient
+    with respect to (Re A, Im A, r0, a) against central differences of GPU
+    forward runs; prints the adjoint cost in forward-run units."""
+    import torch
+    from paper_0909_4039_gb300 import adjoint as A
+    w = inputs.ADJOINT_4096x64
+    N = w.steps
+    dt = 0.5 * (w.rs_max - w.rs_min) / (w.Nr - 1)
+    prm = A.Params(complex(w.amp), w.r0, w.a)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    h = A.waveform(w, prm, N).cpu().numpy()
+    t_fwd = time.perf_counter() - t0
+    scale = np.abs(h).max()
+    target = scale * inputs.adjoint_target(N + 1, dt, seed=1)
+    t0 = time.perf_counter()
+    r = A.gradients(w, prm, N, torch.as_tensor(2.0 * dt * (h - target)))
+    t_adj = time.perf_counter() - t0
+    got = np.array([r["dA_re"], r["dA_im"], r["dr0"], r["da"]])
+    fd = _fd_gradients(lambda q: _loss(A.waveform(w, q, N).cpu().numpy(), target, dt), prm)
+    print(f"\nadjoint 4096x64x8000: grad {got}, central differences {fd}, "
+          f"forward {t_fwd:.2f} s, gradient sweep {t_adj:.2f} s ({t_adj / t_fwd:.2f} forward runs)")
+    assert np.all(np.abs(got - fd) <= 1e-5 * np.abs(fd) + 1e-10 * np.abs(fd).max()), (got, fd)
