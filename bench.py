@@ -10,7 +10,7 @@ kernel launch.  L2 is flushed (a 256 MB write) between timed steps, and each
 step is timed with CUDA events on the stepper's stream.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
-                  [--workload single|batch64|long8]
+                  [--workload single|batch64|long8|adjoint4096]
 
 N > 1 runs as torchrun ranks, one independent replica per GPU (weak
 scaling; the single-instance stepper has no data-path collective).
@@ -513,25 +513,118 @@ def run_native_batch(args):
     return 0
 
 
+def run_native_adjoint(args):
+    """Gradient of the waveform loss L = sum_n dt |h_n - target_n|^2 with
+    respect to (Re A, Im A, r0, a) on the adjoint workload; one bench step is
+    one gradient evaluation (forward run + backward sweep over all time
+    steps)."""
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_0909_4039_gb300 import adjoint as A
+    from paper_0909_4039_gb300 import inputs
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    w = inputs.ADJOINT_4096x64
+    N = args.time_steps or w.steps
+    dt = w.cfl * (w.rs_max - w.rs_min) / (w.Nr - 1)
+    prm = A.Params(complex(w.amp), w.r0, w.a)
+    prec = args.precision or "fp64"
+    h = A.waveform(w, prm, N, precision=prec).cpu().numpy()
+    target = np.abs(h).max() * inputs.adjoint_target(N + 1, dt, seed=1)
+
+    def grad(wrt_a=True):
+        # forward run keeping sqrt(N) checkpoints, loss gradient on the host,
+        # backward sweep over the checkpoints
+        fw = A.forward(w, prm, N, precision=prec)
+        try:
+            hh = fw.h.cpu().numpy()
+            return A.backward(fw, torch.as_tensor(2.0 * dt * (hh - target)), wrt_a=wrt_a)
+        finally:
+            fw.close()
+
+    for _ in range(args.warmup):
+        grad()
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    with ClockSampler(local) as clk:
+        l0 = A.LAUNCHES[0]
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            r = grad()
+        torch.cuda.synchronize()
+        t = time.perf_counter() - t0
+        launches = A.LAUNCHES[0] - l0
+    tf0 = time.perf_counter()
+    A.waveform(w, prm, N, precision=prec)
+    t_fwd = time.perf_counter() - tf0
+    tg0 = time.perf_counter()
+    grad(wrt_a=False)
+    t_src = time.perf_counter() - tg0 - t_fwd
+    if ws > 1:
+        tt = torch.tensor([t], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt.item())
+    per = t / args.steps
+    line = {
+        "metric": "adjoint gradient evaluations/s", "value": ws * args.steps / t, "unit": "grad/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "f64", "data": "synthetic",
+        "config": {"workload": f"adjoint: {w.Nr}x{w.Ntheta}, a={w.a}, r0={w.r0}, {N} time steps, target = "
+                               "low-passed complex noise (seed 1, |omega| < 0.5/M); gradient of "
+                               "sum dt |h - target|^2 w.r.t. (Re A, Im A, r0, a); sqrt(N) checkpointing",
+                   "l2": "not flushed (each gradient streams 8000 steps of state)",
+                   "parallelism": f"replicas x{ws}"},
+        "gradient": [r["dA_re"], r["dA_im"], r["dr0"], r["da"]],
+        "adjoint_cost": {"forward_s": t_fwd, "gradient_s": per,
+                         "ratio_all_params": per / t_fwd,
+                         "ratio_source_params": (t_src + t_fwd) / t_fwd,
+                         "note": "gradient evaluation (forward waveform + sweep) in forward-run units; "
+                                 "source_params = amplitude and r0 only (no spin term)"},
+        "e2e": {"value": ws * args.steps / t, "unit": "grad/s", "h2d_bytes_per_step": 16 * (N + 1),
+                "d2h_bytes_per_step": 16 * (N + 1) + 32},
+        "clocks": clk.summary(),
+        "gpu_launches": launches,
+    }
+    if ws > 1:
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20000)
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
-    ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
+    ap.add_argument("--precision", choices=["fp32", "fp64"], default=None,
+                    help="state precision (default: fp32; fp64 for adjoint4096)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kernel", choices=["auto", "tiled", "persistent"], default="auto",
                     help="auto: measured choice (cold-L2 autotune); otherwise the given kernel")
     ap.add_argument("--tile-rows", type=int, default=28, help="tile height for --kernel tiled/persistent")
     ap.add_argument("--consumers", type=int, default=480, help="consumer threads for --kernel persistent")
-    ap.add_argument("--workload", choices=["single", "batch64", "long8"], default="single",
-                    help="single: the 16384 x 128 instance; batch64 / long8: batched instances")
+    ap.add_argument("--time-steps", type=int, default=0,
+                    help="adjoint4096: time steps per gradient (default: the workload's 8000)")
+    ap.add_argument("--workload", choices=["single", "batch64", "long8", "adjoint4096"], default="single",
+                    help="single: the 16384 x 128 instance; batch64 / long8: batched instances; "
+                         "adjoint4096: gradient evaluations of the waveform loss")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
+        args.precision = args.precision or "fp32"
         return run_reference(args)
+    if args.workload == "adjoint4096":
+        return run_native_adjoint(args)
+    args.precision = args.precision or "fp32"
     if args.workload != "single":
         return run_native_batch(args)
     return run_native(args)

@@ -279,9 +279,11 @@ int teuk_adjoint_workspace_bytes(const teuk_ctx *ctx, size_t *bytes);
 int teuk_adjoint_step(teuk_ctx *ctx, const void *d_lam_in, void *d_lam_out, int64_t n, int first,
                       const void *d_gseed, void *d_ws, void *stream);
 
-/* d_out (one complex double, device) = sum conj(x) y over both planes, in
- * FP64 and a fixed order.  d_ws: the adjoint workspace. */
-int teuk_dot(teuk_ctx *ctx, const void *d_x, const void *d_y, void *d_ws, void *d_out, void *stream);
+/* d_out (one complex double, device) = sum conj(x) (y - z) over both
+ * planes (z may be NULL: sum conj(x) y), in FP64 and a fixed order; the
+ * difference is taken in FP64.  d_ws: the adjoint workspace. */
+int teuk_dot(teuk_ctx *ctx, const void *d_x, const void *d_y, const void *d_z, void *d_ws, void *d_out,
+             void *stream);
 
 /* ---------------------------------------------------------------- batches
  * Many independent instances -- each a split-scheme context with its own

@@ -41,6 +41,10 @@ class Params:
     a: float
 
 
+# kernel launches issued through Operator (for launch accounting)
+LAUNCHES = [0]
+
+
 class Operator:
     """The step, sample and adjoint operators of one parameter set, on
     caller buffers.  `w` fixes the grid, mode and source widths; `prm` the
@@ -60,6 +64,10 @@ class Operator:
         nb = ctypes_size(lambda sz: teuk.lib().teuk_adjoint_workspace_bytes(self.st.ctx, sz))
         self.ws = torch.zeros(nb // 8, dtype=torch.float64, device=self.st.device)
         self.sh = self.st.sh
+        L = teuk.lib()
+        self._step, self._sample = L.teuk_apply_step, L.teuk_apply_sample
+        self._adj, self._dot = L.teuk_adjoint_step, L.teuk_dot
+        self._ctx, self._ws = self.st.ctx, self.ws.data_ptr()
 
     def empty(self):
         return self.torch.empty(self.shape, dtype=self.ctype, device=self.st.device)
@@ -67,21 +75,28 @@ class Operator:
     def zeros(self):
         return self.torch.zeros(self.shape, dtype=self.ctype, device=self.st.device)
 
+    def _ok(self, rc):
+        if rc != 0:
+            teuk._check(rc, self._ctx)
+
     def step(self, s_in, s_out, n: int, first: bool):
-        teuk._check(teuk.lib().teuk_apply_step(self.st.ctx, s_in.data_ptr(), s_out.data_ptr(), int(n), int(first),
-                                               self.sh), self.st.ctx)
+        LAUNCHES[0] += 1
+        self._ok(self._step(self._ctx, s_in.data_ptr(), s_out.data_ptr(), int(n), int(first), self.sh))
 
     def sample(self, s, physical: bool, out_ptr: int):
-        teuk._check(teuk.lib().teuk_apply_sample(self.st.ctx, s.data_ptr(), int(physical), out_ptr, self.sh),
-                    self.st.ctx)
+        LAUNCHES[0] += 1
+        self._ok(self._sample(self._ctx, s.data_ptr(), int(physical), out_ptr, self.sh))
 
     def adjoint(self, lam_in, lam_out, n: int, first: bool, gseed_ptr):
-        teuk._check(teuk.lib().teuk_adjoint_step(self.st.ctx, lam_in.data_ptr(), lam_out.data_ptr(), int(n),
-                                                 int(first), gseed_ptr, self.ws.data_ptr(), self.sh), self.st.ctx)
+        LAUNCHES[0] += 2     # the adjoint step and the reduction of its partial sums
+        self._ok(self._adj(self._ctx, lam_in.data_ptr(), lam_out.data_ptr(), int(n), int(first), gseed_ptr,
+                           self._ws, self.sh))
 
-    def dot(self, x, y, out_ptr: int):
-        teuk._check(teuk.lib().teuk_dot(self.st.ctx, x.data_ptr(), y.data_ptr(), self.ws.data_ptr(), out_ptr,
-                                        self.sh), self.st.ctx)
+    def dot(self, x, y, out_ptr: int, z=None):
+        """out = <x, y - z> (z None: <x, y>)."""
+        LAUNCHES[0] += 2     # per-CTA partial sums and their fixed-order reduction
+        self._ok(self._dot(self._ctx, x.data_ptr(), y.data_ptr(), None if z is None else z.data_ptr(), self._ws,
+                           out_ptr, self.sh))
 
     def close(self):
         self.st.close()
@@ -125,34 +140,69 @@ def run_forward(op: Operator, nsteps: int, u0=None, every: int | None = None):
     return h, ck
 
 
-def gradients(w: inputs.Workload, prm: Params, nsteps: int, grad_h, u0=None, precision: str = "fp64",
-              every: int | None = None, wrt_a: bool = True, eps_a: float | None = None, device=None):
-    """Reverse-mode derivatives of a loss whose gradient with respect to the
-    waveform h_0..h_N is grad_h (complex, dL/dRe h + i dL/dIm h).  Returns
-    dL/dRe A, dL/dIm A, dL/dr0, dL/da (None unless wrt_a) and the adjoint of
-    the initial state (dL/dRe u_0 + i dL/dIm u_0), plus the waveform."""
+class Forward:
+    """A forward run kept for a backward sweep: the operator, the waveform
+    and the checkpoints (sqrt(N) states)."""
+
+    def __init__(self, op, nsteps, h, ck, every):
+        self.op, self.nsteps, self.h, self.ck, self.every = op, nsteps, h, ck, every
+
+    def close(self):
+        if self.op is not None:
+            self.op.close()
+            self.op = None
+        self.ck = None
+
+
+def forward(w: inputs.Workload, prm: Params, nsteps: int, u0=None, precision: str = "fp64",
+            every: int | None = None, device=None) -> Forward:
+    """Forward run that keeps a state every `every` steps (default ~sqrt(N))."""
     import torch
     op = Operator(w, prm, precision, device=device)
     every = every or max(1, int(round(math.sqrt(max(nsteps, 1)))))
-    try:
-        with torch.cuda.stream(op.st.stream):
-            return _sweep(op, w, prm, nsteps, grad_h, u0, precision, every, wrt_a, eps_a, device)
-    finally:
-        op.close()
+    with torch.cuda.stream(op.st.stream):
+        h, ck = run_forward(op, nsteps, u0, every)
+    return Forward(op, nsteps, h, ck, every)
 
 
-def _sweep(op, w, prm, nsteps, grad_h, u0, precision, every, wrt_a, eps_a, device):
+def backward(fw: Forward, grad_h, wrt_a: bool = True, eps_a: float | None = None) -> dict:
+    """Reverse-mode derivatives of a loss whose gradient with respect to the
+    waveform h_0..h_N of the forward run is grad_h (complex, dL/dRe h +
+    i dL/dIm h): dL/dRe A, dL/dIm A, dL/dr0, dL/da (None unless wrt_a) and
+    the adjoint of the initial state (dL/dRe u_0 + i dL/dIm u_0)."""
     import torch
-    h, ck = run_forward(op, nsteps, u0, every)
-    g = grad_h.to(device=op.st.device, dtype=torch.complex128).contiguous()
+    op = fw.op
+    with torch.cuda.stream(op.st.stream):
+        return _sweep(fw, grad_h, wrt_a, eps_a)
+
+
+def gradients(w: inputs.Workload, prm: Params, nsteps: int, grad_h, u0=None, precision: str = "fp64",
+              every: int | None = None, wrt_a: bool = True, eps_a: float | None = None, device=None):
+    """forward() followed by backward(); returns backward's dictionary plus
+    the waveform under "h"."""
+    fw = forward(w, prm, nsteps, u0, precision, every, device)
+    try:
+        out = backward(fw, grad_h, wrt_a, eps_a)
+        out["h"] = fw.h
+        return out
+    finally:
+        fw.close()
+
+
+def _sweep(fw: Forward, grad_h, wrt_a, eps_a):
+    import torch
+    op, nsteps, ck = fw.op, fw.nsteps, fw.ck
+    w, prm, precision = op.w, op.prm, op.precision
+    g = torch.as_tensor(grad_h).to(device=op.st.device, dtype=torch.complex128).contiguous()
     if g.numel() != nsteps + 1:
         raise ValueError("grad_h needs one entry per sample h_0..h_N")
     if wrt_a:
         eps = eps_a if eps_a is not None else (1e-4 if precision == "fp64" else 1e-3)
-        opp = Operator(w, Params(prm.amp, prm.r0, prm.a + eps), precision, device=device, stream=op.st.stream)
-        opm = Operator(w, Params(prm.amp, prm.r0, prm.a - eps), precision, device=device, stream=op.st.stream)
-        dots = torch.zeros((nsteps + 1, 2), dtype=torch.complex128, device=op.st.device)
-        samp = torch.zeros((nsteps + 1, 2), dtype=torch.complex128, device=op.st.device)
+        dev = op.st.device
+        opp = Operator(w, Params(prm.amp, prm.r0, prm.a + eps), precision, device=dev, stream=op.st.stream)
+        opm = Operator(w, Params(prm.amp, prm.r0, prm.a - eps), precision, device=dev, stream=op.st.stream)
+        dots = torch.zeros(nsteps + 1, dtype=torch.complex128, device=dev)
+        samp = torch.zeros((nsteps + 1, 2), dtype=torch.complex128, device=dev)
         tp, tm = op.empty(), op.empty()
     op.ws.zero_()
     lam, lam2 = op.zeros(), op.empty()
@@ -175,21 +225,20 @@ def _sweep(op, w, prm, nsteps, grad_h, u0, precision, every, wrt_a, eps_a, devic
         for n in range(b - 1, a - 1, -1):
             sn = states[n - a]
             if wrt_a:
-                # <lam_{n+1}, M_n(a +- e) s_n>
+                # <lam_{n+1}, (M_n(a + e) - M_n(a - e)) s_n>
                 opp.step(sn, tp, n, n == 0)
                 opm.step(sn, tm, n, n == 0)
-                op.dot(lam, tp, _ptr(dots, 2 * n))
-                op.dot(lam, tm, _ptr(dots, 2 * n + 1))
+                op.dot(lam, tp, _ptr(dots, n), z=tm)
             op.adjoint(lam, lam2, n, n == 0, _ptr(g, n))
             lam, lam2 = lam2, lam
         del states
     acc = op.ws[:4].cpu().numpy()
-    out = {"dA_re": float(acc[0]), "dA_im": float(-acc[1]), "dr0": float(acc[2]), "du0": lam.clone(), "h": h}
+    out = {"dA_re": float(acc[0]), "dA_im": float(-acc[1]), "dr0": float(acc[2]), "du0": lam.clone()}
     if wrt_a:
         d = dots.cpu().numpy()
         sp = samp.cpu().numpy()
         gn = g.cpu().numpy()
-        step_term = np.sum((d[:nsteps, 0] - d[:nsteps, 1]).real)
+        step_term = np.sum(d[:nsteps].real)
         samp_term = np.sum((np.conj(gn[1:]) * (sp[1:, 0] - sp[1:, 1])).real)
         out["da"] = float((step_term + samp_term) / (2.0 * eps))
         opp.close()
@@ -218,21 +267,24 @@ def _make_function():
 
     class WaveformFunction(torch.autograd.Function):
         """h = waveform(A, r0, a) at the extraction node; params is a float64
-        tensor (Re A, Im A, r0, a).  The backward pass runs the adjoint sweep
-        with sqrt(N) checkpointing."""
+        tensor (Re A, Im A, r0, a).  The forward pass keeps sqrt(N)
+        checkpoints; the backward pass sweeps the adjoint over them."""
 
         @staticmethod
         def forward(ctx, params, w, nsteps, precision):
             p = params.detach().cpu().numpy().astype(np.float64)
             prm = Params(complex(p[0], p[1]), float(p[2]), float(p[3]))
-            ctx.w, ctx.nsteps, ctx.precision, ctx.prm = w, int(nsteps), precision, prm
             ctx.device = params.device
-            h = waveform(w, prm, int(nsteps), precision=precision)
-            return h.to(params.device)
+            ctx.fw = forward(w, prm, int(nsteps), precision=precision)
+            ctx.fw.op.st.synchronize()
+            return ctx.fw.h.to(params.device)
 
         @staticmethod
         def backward(ctx, grad_h):
-            r = gradients(ctx.w, ctx.prm, ctx.nsteps, grad_h, precision=ctx.precision)
+            try:
+                r = backward(ctx.fw, grad_h)
+            finally:
+                ctx.fw.close()
             gp = torch.tensor([r["dA_re"], r["dA_im"], r["dr0"], r["da"]], dtype=torch.float64,
                               device=ctx.device)
             return gp, None, None, None

@@ -973,17 +973,20 @@ int teuk_literal_step_static(const teuk_ctx *c, const void *d_in, void *d_out, i
 
 namespace {
 
-// Tile height of the adjoint kernel: the largest up to 30 rows whose four
-// state planes fit in about 100 KB of shared memory.
+// Tile height of the adjoint kernel (one CTA per SM): enough tiles for two
+// waves over the SMs where the grid allows, at most 30 rows and about 100 KB
+// of shared memory (four state planes) per tile.
 int adjoint_tile_rows(const teuk_ctx *c)
 {
     const int N = (int)c->d.Ntheta;
     const bool f32 = c->d.precision == TEUK_FP32;
+    const long long want = (c->d.Nr + 2LL * sm_count() - 1) / (2LL * sm_count());
     int best = 1;
     for (int tr = 1; tr <= 30; ++tr) {
         size_t sm = f32 ? adjoint_smem_bytes<float>(tr, N) : adjoint_smem_bytes<double>(tr, N);
         if (sm <= 100 * 1024) best = tr;
     }
+    if (want >= 4 && want < best) best = (int)want;
     return best;
 }
 
@@ -1078,7 +1081,7 @@ int teuk_adjoint_step(teuk_ctx *c, const void *d_lam_in, void *d_lam_out, int64_
     return TEUK_OK;
 }
 
-int teuk_dot(teuk_ctx *c, const void *d_x, const void *d_y, void *d_ws, void *d_out, void *stream)
+int teuk_dot(teuk_ctx *c, const void *d_x, const void *d_y, const void *d_z, void *d_ws, void *d_out, void *stream)
 {
     if (!c) return TEUK_E_STATE;
     if (!d_x || !d_y || !d_ws || !d_out) return set_err(c, TEUK_E_INVAL, "need non-NULL device buffers%s");
@@ -1087,9 +1090,11 @@ int teuk_dot(teuk_ctx *c, const void *d_x, const void *d_y, void *d_ws, void *d_
     double *part = (double *)d_ws + adjoint_ws_doubles(c) - 2 * 256;
     cudaError_t e;
     if (c->d.precision == TEUK_FP32)
-        e = launch_dot<float>((const float2 *)d_x, (const float2 *)d_y, n, part, (double2 *)d_out, st);
+        e = launch_dot<float>((const float2 *)d_x, (const float2 *)d_y, (const float2 *)d_z, n, part,
+                              (double2 *)d_out, st);
     else
-        e = launch_dot<double>((const double2 *)d_x, (const double2 *)d_y, n, part, (double2 *)d_out, st);
+        e = launch_dot<double>((const double2 *)d_x, (const double2 *)d_y, (const double2 *)d_z, n, part,
+                               (double2 *)d_out, st);
     if (e != cudaSuccess) return cuda_err(c, e, "dot");
     return TEUK_OK;
 }

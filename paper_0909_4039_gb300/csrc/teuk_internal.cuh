@@ -185,8 +185,8 @@ size_t adjoint_smem_bytes(int tile_rows, int Nth);
 template <typename T>
 int adjoint_grid(int Nr, int tile_rows);
 template <typename T>
-cudaError_t launch_dot(const typename V2<T>::t *x, const typename V2<T>::t *y, size_t n, double *part,
-                       double2 *out, cudaStream_t st);
+cudaError_t launch_dot(const typename V2<T>::t *x, const typename V2<T>::t *y, const typename V2<T>::t *z,
+                       size_t n, double *part, double2 *out, cudaStream_t st);
 
 template <typename T>
 cudaError_t launch_split_step(const StepParams<T> &p, int threads, size_t smem, cudaStream_t st);

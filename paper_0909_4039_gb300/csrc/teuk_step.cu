@@ -1580,17 +1580,23 @@ __global__ void __launch_bounds__(32) k_part_reduce(const double *part, int nblk
         for (int c = 0; c < 4; ++c) acc[c] += v[c];
 }
 
-// Deterministic <x, y> = sum conj(x_k) y_k in FP64: per-CTA partial sums
-// over a fixed grid, then one warp adds them in a fixed order.
+// Deterministic <x, y - z> = sum conj(x_k) (y_k - z_k) in FP64 (z may be
+// null): per-CTA partial sums over a fixed grid, then one warp adds them in
+// a fixed order.
 constexpr int kDotBlocks = 256;
 template <typename T>
-__global__ void __launch_bounds__(256) k_dot_part(const typename V2<T>::t *x, const typename V2<T>::t *y, size_t n,
-                                                  double *part)
+__global__ void __launch_bounds__(256) k_dot_part(const typename V2<T>::t *x, const typename V2<T>::t *y,
+                                                  const typename V2<T>::t *z, size_t n, double *part)
 {
     __shared__ double red[8][2];
     double re = 0.0, im = 0.0;
     for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
-        const double xr = x[k].x, xi = x[k].y, yr = y[k].x, yi = y[k].y;
+        const double xr = x[k].x, xi = x[k].y;
+        double yr = y[k].x, yi = y[k].y;
+        if (z) {   // y - z, exact in FP64 for FP32 data
+            yr -= (double)z[k].x;
+            yi -= (double)z[k].y;
+        }
         re = fma(xr, yr, fma(xi, yi, re));
         im = fma(xr, yi, fma(-xi, yr, im));
     }
@@ -2054,10 +2060,10 @@ cudaError_t launch_adjoint_step(const StepParams<T> &p, int tile_rows, const dou
 }
 
 template <typename T>
-cudaError_t launch_dot(const typename V2<T>::t *x, const typename V2<T>::t *y, size_t n, double *part,
-                       double2 *out, cudaStream_t st)
+cudaError_t launch_dot(const typename V2<T>::t *x, const typename V2<T>::t *y, const typename V2<T>::t *z,
+                       size_t n, double *part, double2 *out, cudaStream_t st)
 {
-    k_dot_part<T><<<kDotBlocks, 256, 0, st>>>(x, y, n, part);
+    k_dot_part<T><<<kDotBlocks, 256, 0, st>>>(x, y, z, n, part);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_dot_final<<<1, 32, 0, st>>>(part, kDotBlocks, out);
@@ -2143,8 +2149,10 @@ template cudaError_t launch_adjoint_step<float>(const StepParams<float> &, int, 
                                                 cudaStream_t);
 template cudaError_t launch_adjoint_step<double>(const StepParams<double> &, int, const double2 *, double *, double *,
                                                  cudaStream_t);
-template cudaError_t launch_dot<float>(const float2 *, const float2 *, size_t, double *, double2 *, cudaStream_t);
-template cudaError_t launch_dot<double>(const double2 *, const double2 *, size_t, double *, double2 *, cudaStream_t);
+template cudaError_t launch_dot<float>(const float2 *, const float2 *, const float2 *, size_t, double *, double2 *,
+                                       cudaStream_t);
+template cudaError_t launch_dot<double>(const double2 *, const double2 *, const double2 *, size_t, double *,
+                                        double2 *, cudaStream_t);
 template int split_batch_blocks_per_sm<float>(int, size_t);
 template int split_batch_blocks_per_sm<double>(int, size_t);
 template cudaError_t launch_split_batch<float>(const StepParams<float> *, const int2 *, int, int, size_t, cudaStream_t);

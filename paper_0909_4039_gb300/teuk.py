@@ -122,7 +122,7 @@ def lib(load_only: bool = False):
     L.teuk_apply_sample.argtypes = [vp, vp, ctypes.c_int, vp, vp]
     L.teuk_adjoint_workspace_bytes.argtypes = [vp, sz]
     L.teuk_adjoint_step.argtypes = [vp, vp, vp, i64, ctypes.c_int, vp, vp, vp]
-    L.teuk_dot.argtypes = [vp, vp, vp, vp, vp, vp]
+    L.teuk_dot.argtypes = [vp, vp, vp, vp, vp, vp, vp]
     for name in ("teuk_apply_step", "teuk_apply_sample", "teuk_adjoint_workspace_bytes", "teuk_adjoint_step",
                  "teuk_dot"):
         getattr(L, name).restype = ctypes.c_int
