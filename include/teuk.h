@@ -167,15 +167,20 @@ int teuk_tiling(const teuk_ctx *ctx, int *tile_rows, int *threads, size_t *smem_
  * persistent kernel (one CTA per SM walks the tiles; a producer warp moves
  * them by TMA into two shared-memory buffers while *consumer_threads threads
  * compute, so tile loads and stores overlap the arithmetic); 0: the tiled
- * kernel (one CTA per tile).  *grid is the number of CTAs per step.  Any
- * pointer may be NULL.  For the literal scheme *persistent = 0. */
-int teuk_kernel_config(const teuk_ctx *ctx, int *persistent, int *consumer_threads, int *grid);
+ * kernel (one CTA per tile).  *grid is the number of CTAs per launch.
+ * *steps_per_launch is 2 when the tiled kernel advances two time steps per
+ * launch (temporal blocking: two halo rows on either side, one state read
+ * and write per two steps), else 1.  Any pointer may be NULL.  For the
+ * literal scheme *persistent = 0 and *steps_per_launch = 1. */
+int teuk_kernel_config(const teuk_ctx *ctx, int *persistent, int *consumer_threads, int *grid,
+                       int *steps_per_launch);
 
 /* Measured tile autotuner.  Ranks the launch configurations that fit on the
- * device (tile heights of the tiled kernel and tile height x consumer count
- * of the persistent kernel) by a wave-quantisation cost model, times the
- * best four of each kernel for trial_steps steps each on this grid (CUDA
- * events on `stream`), and keeps the fastest.  The trials overwrite the
+ * device (tile heights of the tiled kernel with one or two steps per launch,
+ * and tile height x consumer count of the persistent kernel) by a
+ * wave-quantisation cost model, times the best four of each kind for
+ * trial_steps launches each on this grid (CUDA events on `stream`), and keeps
+ * the fastest per time step.  The trials overwrite the
  * state: afterwards the field is zero at step 0 and the waveform ring buffer
  * is empty (the source and weights are kept).  Call it right after
  * teuk_init_grid / teuk_set_source.  Synchronous.  *tile_rows_out (may be
@@ -194,6 +199,13 @@ int teuk_autotune_cold(teuk_ctx *ctx, int trial_steps, void *d_flush, size_t flu
  * shared memory.  The result of a step depends on neither the kernel nor
  * the tile height. */
 int teuk_set_tiling(teuk_ctx *ctx, int tile_rows);
+
+/* Select the tiled split-scheme kernel with the given tile height and
+ * steps_per_launch = 1 (as teuk_set_tiling) or 2 (two time steps per launch;
+ * the first step of a run and an odd last step still take one).  The
+ * result does not depend on the choice.  TEUK_E_INVAL if the tile does not
+ * fit or steps_per_launch is not 1 or 2. */
+int teuk_set_tiling_steps(teuk_ctx *ctx, int tile_rows, int steps_per_launch);
 
 /* Select the persistent split-scheme kernel with the given tile height and
  * consumer_threads in {384, 480}.  It exists for the FP32 state with

@@ -54,6 +54,8 @@ struct teuk_ctx {
     size_t smem;
     int persist, nc, grid;
     size_t persist_smem;
+    int ks;                  // time steps per launch of the tiled kernel (1 or 2)
+    size_t smem2;            // shared memory of the two-step kernel
     // graphs, one per starting level
     cudaGraphExec_t graph[2];
     cudaStream_t graph_stream[2];
@@ -205,9 +207,10 @@ double host_atheta_bound(const teuk_grid_desc &d)
 // of two per row-time against the tiled kernel's two independent CTAs per
 // SM (measured on 16384 x 128 at equal tile height).
 struct TileCand {
-    double cost;
-    int R;
+    double cost;             // model cost per time step
+    int R;                   // tile_rows + 2
     int persist, nc, grid;
+    int ks;                  // time steps per launch (tiled kernel)
     size_t smem;
 };
 
@@ -240,6 +243,35 @@ static bool tiled_cand(const teuk_ctx *c, int TR, int nsm, TileCand *out)
     out->persist = 0;
     out->nc = 0;
     out->grid = (int)tiles;
+    out->ks = 1;
+    out->smem = sm;
+    return true;
+}
+
+// A two-steps-per-launch candidate of height TR: per step, half of a tile
+// whose first step covers TR + 4 rows (implicit) and TR + 2 (LW) and whose
+// second covers TR + 2 and TR, with one load latency per two steps.
+static bool tiled2_cand(const teuk_ctx *c, int TR, int nsm, TileCand *out)
+{
+    const int N = (int)c->d.Ntheta;
+    const bool f32 = c->d.precision == TEUK_FP32;
+    const int threads = 256;
+    size_t sm = f32 ? split2_smem_bytes<float>(TR, N) : split2_smem_bytes<double>(TR, N);
+    if (sm > 227 * 1024) return false;
+    int k = f32 ? split2_blocks_per_sm<float>(N, threads, sm) : split2_blocks_per_sm<double>(N, threads, sm);
+    if (k < 1) return false;
+    const long long Nr = c->d.Nr;
+    long long tiles = (Nr + TR - 1) / TR;
+    long long waves = (tiles + (long long)k * nsm - 1) / ((long long)k * nsm);
+    int rpp = threads / implicit_group(N);
+    auto rpad = [&](int r) { return ((r + rpp - 1) / rpp) * rpp; };
+    double rows = 0.6 * (rpad(TR + 4) + rpad(TR + 2)) + 0.4 * (2.0 * TR + 6.0) + 4.0;
+    out->cost = 0.5 * (double)waves * k * rows * (k == 1 ? 1.2 : 1.0);
+    out->R = TR + 2;
+    out->persist = 0;
+    out->nc = 0;
+    out->grid = (int)tiles;
+    out->ks = 2;
     out->smem = sm;
     return true;
 }
@@ -269,6 +301,7 @@ static bool persist_cand(const teuk_ctx *c, int TR, int nc, int nsm, TileCand *o
     out->persist = 1;
     out->nc = nc;
     out->grid = (int)grid;
+    out->ks = 1;
     out->smem = sm;
     return true;
 }
@@ -281,6 +314,7 @@ int tile_candidates(teuk_ctx *c, TileCand *out, int maxn)
     int n = 0;
     for (int TR = 2; TR <= 254 && n < maxn; ++TR) {
         if (tiled_cand(c, TR, nsm, &out[n])) ++n;
+        if (n < maxn && c->d.scheme == TEUK_SCHEME_SPLIT && tiled2_cand(c, TR, nsm, &out[n])) ++n;
         for (int nc : {384, 480})
             if (n < maxn && persist_cand(c, TR, nc, nsm, &out[n])) ++n;
         if (TR >= Nr) break;
@@ -309,6 +343,8 @@ static bool apply_cand(teuk_ctx *c, const TileCand &k)
     c->nc = k.persist ? k.nc : 0;
     c->grid = k.persist ? k.grid : 0;
     c->persist_smem = k.persist ? k.smem : 0;
+    c->ks = k.persist ? 1 : k.ks;
+    c->smem2 = (!k.persist && k.ks == 2) ? k.smem : 0;
     return true;
 }
 
@@ -396,6 +432,24 @@ cudaError_t launch_one(teuk_ctx *c, int in_level, cudaStream_t st)
     }
     StepParams<double> p = make_params<double>(c, in_level);
     return c->d.scheme == TEUK_SCHEME_SPLIT ? launch_split<double>(c, p, st) : launch_literal_step<double>(p, st);
+}
+
+// One launch of the configured kernel from level in_level: two steps when
+// the tiled kernel takes two per launch and the state is shifted (a full
+// step follows), else one; *steps receives the count.
+cudaError_t launch_unit(teuk_ctx *c, int in_level, cudaStream_t st, int *steps)
+{
+    if (c->d.scheme == TEUK_SCHEME_SPLIT && c->ks == 2 && c->shifted) {
+        *steps = 2;
+        if (c->d.precision == TEUK_FP32) {
+            StepParams<float> p = make_params<float>(c, in_level);
+            return launch_split_step2<float>(p, c->threads, c->smem2, st);
+        }
+        StepParams<double> p = make_params<double>(c, in_level);
+        return launch_split_step2<double>(p, c->threads, c->smem2, st);
+    }
+    *steps = 1;
+    return launch_one(c, in_level, st);
 }
 
 // Physical state u_n = C_{dt/2} s_n of a shifted split-scheme state, written
@@ -715,6 +769,8 @@ int teuk_step(teuk_ctx *c, int64_t nsteps, void *stream)
         c->shifted = 1;
         left -= 1;
     }
+    // steps per launch from here on (the state is shifted)
+    const int ks = (c->d.scheme == TEUK_SCHEME_SPLIT && c->ks == 2) ? 2 : 1;
     bool use_graph = st != nullptr && c->d.scheme == TEUK_SCHEME_SPLIT && left >= 2 * kGraphChunk;
     if (use_graph) {
         int g = c->cur;
@@ -725,10 +781,12 @@ int teuk_step(teuk_ctx *c, int64_t nsteps, void *stream)
         if (!c->graph[g]) {
             cudaGraph_t graph;
             CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal), "begin capture");
-            int lev = g;
+            int lev = g, done = 0;
             cudaError_t le = cudaSuccess;
-            for (int k = 0; k < kGraphChunk && le == cudaSuccess; ++k) {
-                le = launch_one(c, lev, st);
+            while (done < kGraphChunk && le == cudaSuccess) {
+                int k = 0;
+                le = launch_unit(c, lev, st, &k);
+                done += k;
                 lev ^= 1;
             }
             cudaError_t ee = cudaStreamEndCapture(st, &graph);
@@ -747,9 +805,16 @@ int teuk_step(teuk_ctx *c, int64_t nsteps, void *stream)
             left -= kGraphChunk;
         }
     }
-    for (int64_t k = 0; k < left; ++k) {
+    while (left >= ks) {
+        int k = 0;
+        CK(launch_unit(c, c->cur, st, &k), "step launch");
+        c->cur ^= 1;
+        left -= k;
+    }
+    while (left > 0) {
         CK(launch_one(c, c->cur, st), "step launch");
         c->cur ^= 1;
+        left -= 1;
     }
     c->step += nsteps;
     return TEUK_OK;
@@ -806,12 +871,13 @@ int teuk_tiling(const teuk_ctx *c, int *tile_rows, int *threads, size_t *smem_by
     return TEUK_OK;
 }
 
-int teuk_kernel_config(const teuk_ctx *c, int *persistent, int *consumer_threads, int *grid)
+int teuk_kernel_config(const teuk_ctx *c, int *persistent, int *consumer_threads, int *grid, int *steps_per_launch)
 {
     if (!c) return TEUK_E_STATE;
     if (persistent) *persistent = c->persist;
     if (consumer_threads) *consumer_threads = c->persist ? c->nc : c->threads;
     if (grid) *grid = c->persist ? c->grid : (int)((c->d.Nr + c->tile_rows - 1) / c->tile_rows);
+    if (steps_per_launch) *steps_per_launch = c->d.scheme == TEUK_SCHEME_SPLIT ? c->ks : 1;
     return TEUK_OK;
 }
 
@@ -830,13 +896,15 @@ static int autotune_impl(teuk_ctx *c, int trial_steps, void *flush, size_t flush
     int n = tile_candidates(c, all.data(), (int)all.size());
     // the best few of each kernel by the model
     std::vector<TileCand> cand;
-    for (int kind = 0; kind < 2; ++kind) {
+    for (int kind = 0; kind < 3; ++kind) {   // tiled, tiled two steps per launch, persistent
         int taken = 0;
-        for (int k = 0; k < n && taken < 4; ++k)
-            if (all[k].persist == kind) {
+        for (int k = 0; k < n && taken < 4; ++k) {
+            const int kk = all[k].persist ? 2 : (all[k].ks == 2 ? 1 : 0);
+            if (kk == kind) {
                 cand.push_back(all[k]);
                 ++taken;
             }
+        }
     }
     if (cand.empty()) return set_err(c, TEUK_E_CUDA, "no tile of the split kernel fits on this device%s");
     drop_graphs(c);
@@ -849,27 +917,32 @@ static int autotune_impl(teuk_ctx *c, int trial_steps, void *flush, size_t flush
     for (size_t k = 0; k < cand.size() && e == cudaSuccess; ++k) {
         if (!apply_cand(c, cand[k])) continue;
         c->shifted = 1;
-        int lev = c->cur;
-        for (int w = 0; w < 3 && e == cudaSuccess; ++w, lev ^= 1) e = launch_one(c, lev, st);
+        int lev = c->cur, ku = 0, steps = 0;
+        for (int w = 0; w < 3 && e == cudaSuccess; ++w, lev ^= 1) e = launch_unit(c, lev, st, &ku);
         float total = 0.0f;
         if (flush) {
             for (int w = 0; w < trial_steps && e == cudaSuccess; ++w, lev ^= 1) {
                 float ms = 0.0f;
                 e = cudaMemsetAsync(flush, w & 0xff, flush_bytes, st);
                 if (e == cudaSuccess) e = cudaEventRecord(e0, st);
-                if (e == cudaSuccess) e = launch_one(c, lev, st);
+                if (e == cudaSuccess) e = launch_unit(c, lev, st, &ku);
                 if (e == cudaSuccess) e = cudaEventRecord(e1, st);
                 if (e == cudaSuccess) e = cudaEventSynchronize(e1);
                 if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
                 total += ms;
+                steps += ku;
             }
         } else {
             if (e == cudaSuccess) e = cudaEventRecord(e0, st);
-            for (int w = 0; w < trial_steps && e == cudaSuccess; ++w, lev ^= 1) e = launch_one(c, lev, st);
+            for (int w = 0; w < trial_steps && e == cudaSuccess; ++w, lev ^= 1) {
+                e = launch_unit(c, lev, st, &ku);
+                steps += ku;
+            }
             if (e == cudaSuccess) e = cudaEventRecord(e1, st);
             if (e == cudaSuccess) e = cudaEventSynchronize(e1);
             if (e == cudaSuccess) e = cudaEventElapsedTime(&total, e0, e1);
         }
+        if (steps > 0) total /= (float)steps;   // time per step
         if (e == cudaSuccess && total < best) {
             best = total;
             bestk = (int)k;
@@ -908,6 +981,23 @@ int teuk_set_tiling(teuk_ctx *c, int tile_rows)
     if (tile_rows < 1 || tile_rows > 254) return set_err(c, TEUK_E_INVAL, "tile_rows out of range [1, 254]%s");
     TileCand t;
     if (!tiled_cand(c, tile_rows, sm_count(), &t)) return set_err(c, TEUK_E_INVAL, "tile does not fit in shared memory%s");
+    drop_graphs(c);
+    apply_cand(c, t);
+    return TEUK_OK;
+}
+
+int teuk_set_tiling_steps(teuk_ctx *c, int tile_rows, int steps_per_launch)
+{
+    if (!c) return TEUK_E_STATE;
+    if (steps_per_launch == 1) return teuk_set_tiling(c, tile_rows);
+    if (steps_per_launch != 2) return set_err(c, TEUK_E_INVAL, "steps_per_launch must be 1 or 2%s");
+    if (c->d.scheme != TEUK_SCHEME_SPLIT) return set_err(c, TEUK_E_INVAL, "two steps per launch need the split scheme%s");
+    if (tile_rows < 1 || tile_rows > 250) return set_err(c, TEUK_E_INVAL, "tile_rows out of range [1, 250]%s");
+    TileCand t;
+    if (!tiled2_cand(c, tile_rows, sm_count(), &t))
+        return set_err(c, TEUK_E_INVAL, "tile does not fit in shared memory%s");
+    TileCand tt;
+    if (!tiled_cand(c, tile_rows, sm_count(), &tt)) return set_err(c, TEUK_E_INVAL, "tile does not fit in shared memory%s");
     drop_graphs(c);
     apply_cand(c, t);
     return TEUK_OK;

@@ -215,6 +215,15 @@ template <typename T>
 cudaError_t launch_split_persist(const StepParams<T> &p, int nc, int grid, size_t smem, cudaStream_t st);
 template <typename T>
 int split_blocks_per_sm(int Nth, int threads, size_t smem);   // 0 if the launch cannot fit
+// Two time steps per launch (k_split_step2): tile of tile_rows output rows
+// with two halo rows on either side.  Full steps only (not the first step
+// from a physical state, not the state output).
+template <typename T>
+size_t split2_smem_bytes(int tile_rows, int Nth);
+template <typename T>
+int split2_blocks_per_sm(int Nth, int threads, size_t smem);
+template <typename T>
+cudaError_t launch_split_step2(const StepParams<T> &p, int threads, size_t smem, cudaStream_t st);
 // Batched split step: one CTA of 256 threads per entry of the tile list
 // (instance, tile); params[instance] describes the instance's step.  Every
 // instance must use the theta segment `seg` (implicit_seg of its Ntheta).

@@ -616,12 +616,12 @@ static_assert(RF_R < 12 && RF_R2 < 12 && RF_AD < 12 && RF_CTR < 12 && RF_CTI < 1
 // of row ra-1 and (nf, ng) the old value of row rb: both may belong to other
 // threads' segments, so the caller reads them before a barrier.  sRt holds
 // the r-table entries of the tile: node row lr at 2 lr, the half node
-// between rows k and k+1 at 2 k + 1.
+// between rows k and k+1 at 2 k + 1.  Tile row lr is global row g0 + lr.
 template <typename T>
 __device__ void lw_segment(const StepParams<T> &p, typename V2<T>::t *sPhi, typename V2<T>::t *sPi,
                            const T *sRt, const T *sTh, int j, int ra, int rb,
                            typename V2<T>::t pf, typename V2<T>::t pg, typename V2<T>::t nf,
-                           typename V2<T>::t ng, int i0, typename V2<T>::t ph1, typename V2<T>::t ph2,
+                           typename V2<T>::t ng, int g0, typename V2<T>::t ph1, typename V2<T>::t ph2,
                            bool src)
 {
     typedef typename V2<T>::t c2;
@@ -632,7 +632,7 @@ __device__ void lw_segment(const StepParams<T> &p, typename V2<T>::t *sPhi, type
 
     // u*_{k+1/2} between tile rows k and k+1 (Eq. 13)
     auto midpoint = [&](int k, c2 fa, c2 ga, c2 fb, c2 gb, c2 &mf, c2 &mg) {
-        int gl = i0 - 1 + k;   // global index of the lower node
+        int gl = g0 + k;   // global index of the lower node
         if (gl < 0 || gl > Nr - 2) {
             mf = zero;
             mg = zero;
@@ -658,7 +658,7 @@ __device__ void lw_segment(const StepParams<T> &p, typename V2<T>::t *sPhi, type
     c2 mfp, mgp;
     midpoint(ra - 1, pf, pg, fb, gb, mfp, mgp);
     for (int lr = ra; lr < rb; ++lr) {
-        int gi = i0 + lr - 1;
+        int gi = g0 + lr;
         if (gi >= Nr) break;
         c2 fc, gc;
         if (lr + 1 < rb) {
@@ -711,25 +711,26 @@ template <typename T> __device__ __forceinline__ typename V2<T>::t from_d2(doubl
     return cmk<c2>((T)v.x, (T)v.y);
 }
 
-// Lax-Wendroff phase of one tile (output rows 1..TR of the R = TR + 2 held)
-// by NC threads with index ctid.  With N <= NC every column is cut into
+// Lax-Wendroff phase of tile rows r0 .. r0+nr-1 (tile row lr is global row
+// g0 + lr; rows r0-1 and r0+nr are read as neighbours) by NC threads with
+// index ctid.  With N <= NC every column is cut into
 // NC / N row segments; the rows on either side of a segment are read before
 // bar() (a barrier over the NC threads), as the neighbouring segments
 // overwrite them.
 template <typename T, typename Bar>
 __device__ __forceinline__ void lw_phase(const StepParams<T> &p, typename V2<T>::t *sPhi, typename V2<T>::t *sPi,
-                                         const T *sRt, const T *sTh, int TR, int i0, int ctid,
-                                         int NC, bool src, typename V2<T>::t ph1, typename V2<T>::t ph2, Bar bar)
+                                         const T *sRt, const T *sTh, int r0, int nr, int g0, int ctid, int NC,
+                                         bool src, typename V2<T>::t ph1, typename V2<T>::t ph2, Bar bar)
 {
     typedef typename V2<T>::t c2;
     const int N = p.Nth, P = p.pitch;
     const c2 zero = cmk<c2>(T(0), T(0));
     if (N <= NC) {
         const int nseg = NC / N;
-        const int sl = (TR + nseg - 1) / nseg;
+        const int sl = (nr + nseg - 1) / nseg;
         const int j = ctid % N, sgm = ctid / N;
-        int ra = 1 + sgm * sl, rb = 1 + (sgm + 1) * sl;
-        if (rb > TR + 1) rb = TR + 1;
+        int ra = r0 + sgm * sl, rb = r0 + (sgm + 1) * sl;
+        if (rb > r0 + nr) rb = r0 + nr;
         const bool work = sgm < nseg && ra < rb;
         c2 pf = zero, pg = zero, nf = zero, ng = zero;
         if (work) {
@@ -739,11 +740,13 @@ __device__ __forceinline__ void lw_phase(const StepParams<T> &p, typename V2<T>:
             ng = sPi[rb * P + j];
         }
         bar();
-        if (work) lw_segment<T>(p, sPhi, sPi, sRt, sTh, j, ra, rb, pf, pg, nf, ng, i0, ph1, ph2, src);
+        if (work) lw_segment<T>(p, sPhi, sPi, sRt, sTh, j, ra, rb, pf, pg, nf, ng, g0, ph1, ph2, src);
     } else {
+        // each thread owns whole columns: rows r0-1 and r0+nr are read before any write
         for (int j = ctid; j < N; j += NC) {
-            c2 pf = sPhi[j], pg = sPi[j], nf = sPhi[(TR + 1) * P + j], ng = sPi[(TR + 1) * P + j];
-            lw_segment<T>(p, sPhi, sPi, sRt, sTh, j, 1, TR + 1, pf, pg, nf, ng, i0, ph1, ph2, src);
+            c2 pf = sPhi[(r0 - 1) * P + j], pg = sPi[(r0 - 1) * P + j];
+            c2 nf = sPhi[(r0 + nr) * P + j], ng = sPi[(r0 + nr) * P + j];
+            lw_segment<T>(p, sPhi, sPi, sRt, sTh, j, r0, r0 + nr, pf, pg, nf, ng, g0, ph1, ph2, src);
         }
     }
 }
@@ -827,19 +830,25 @@ __device__ void extract_warp(const StepParams<T> &p, const typename V2<T>::t *ro
 // tile rows (used to output the physical state).
 // The work of one CTA: tile number `tile` of the grid described by p, whose
 // step takes `ntiles` CTAs (the last of them to start advances the step
-// index).
-template <typename T, int S>
+// index), for KS = 1 or 2 time steps per launch.  The tile holds its TR output
+// rows plus KS halo rows on either side (R = TR + 2 KS; tile row lr is global
+// row g0 + lr, g0 = i0 - KS).  With KS = 2 the first step updates rows
+// 1 .. R-2 and the second the TR output rows; the state read and written per
+// step halves at the cost of recomputing the extra halo rows.  The result is
+// bitwise that of KS single steps.
+template <typename T, int S, int KS>
 __device__ __forceinline__ void split_tile(const StepParams<T> &p, int tile, int ntiles)
 {
     typedef typename V2<T>::t c2;
     constexpr int kMaxChunks = 8;
+    static_assert(KS == 1 || KS == 2, "one or two steps per launch");
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ double2 sph[2];
+    __shared__ double2 sph[2 * KS];
     __shared__ long long s_n;
     __shared__ __align__(8) unsigned long long s_mbar[kMaxChunks];
-    const int Nr = p.Nr, N = p.Nth, TR = p.tile_rows, R = TR + 2, P = p.pitch;
+    const int Nr = p.Nr, N = p.Nth, TR = p.tile_rows, R = TR + 2 * KS, P = p.pitch;
     const int tid = threadIdx.x, NT = blockDim.x;
-    const int i0 = tile * TR;
+    const int i0 = tile * TR, g0 = i0 - KS;
     const int G = p.group;
 
     const SplitSmem plan = split_smem_plan(R, N, (int)sizeof(T));
@@ -848,11 +857,13 @@ __device__ __forceinline__ void split_tile(const StepParams<T> &p, int tile, int
     c2 *sPiv = (c2 *)(smem_raw + plan.piv);
     T *sRt = (T *)(smem_raw + plan.rt);
     T *sTh = (T *)(smem_raw + plan.th);
+    c2 *xPhi = (c2 *)(smem_raw + plan.total);   // KS = 2: copy of the extraction row
+    c2 *xPi = xPhi + N;
     // implicit step of this launch: dt/2 for the first step and for the state output
     const ImpConst<T> &K = (p.first || p.imp_only) ? p.half : p.full;
 
-    const bool src = !p.imp_only && p.patch_np > 0 && i0 + TR >= p.patch_p0 &&
-                     i0 - 1 <= p.patch_p0 + p.patch_np;
+    const bool src = !p.imp_only && p.patch_np > 0 && i0 + TR + KS - 1 >= p.patch_p0 &&
+                     g0 <= p.patch_p0 + p.patch_np;
     if (tid == 0) {
         long long n = p.nfix >= 0 ? p.nfix : *((volatile long long *)&p.ctl->step);
         s_n = n;
@@ -864,24 +875,25 @@ __device__ __forceinline__ void split_tile(const StepParams<T> &p, int tile, int
             unsigned t = atomicAdd(&p.ctl->ticket, 1u);
             if (t == (unsigned)ntiles - 1u) {
                 p.ctl->ticket = 0u;
-                p.ctl->step = n + 1;
+                p.ctl->step = n + KS;
             }
         }
-        if (src) {
-            double t = (double)n * p.dt64;
-            sph[0] = phase_at(p.mOmega, t);
-            sph[1] = phase_at(p.mOmega, t + 0.5 * p.dt64);
-        }
+        if (src)
+            for (int k = 0; k < KS; ++k) {
+                double t = (double)(n + k) * p.dt64;
+                sph[2 * k] = phase_at(p.mOmega, t);
+                sph[2 * k + 1] = phase_at(p.mOmega, t + 0.5 * p.dt64);
+            }
     }
-    // ---- A: tile rows i0-1 .. i0+TR (state and pivots), r and theta tables
+    // ---- A: tile rows g0 .. g0+R-1 (state and pivots), r and theta tables
     const c2 zero = cmk<c2>(T(0), T(0));
     // (row, column) walk of the tile without integer division in the loop
     const int t_lr = tid / N, t_j = tid - t_lr * N;
     const int d_lr = NT / N, d_j = NT - d_lr * N;
     // rows of the tile that exist on the grid: [ga, gb] globally, from tile row la
-    const int ga = i0 - 1 < 0 ? 0 : i0 - 1;
-    const int gb = i0 + TR > Nr - 1 ? Nr - 1 : i0 + TR;
-    const int la = ga - (i0 - 1), nrows = gb - ga + 1;
+    const int ga = g0 < 0 ? 0 : g0;
+    const int gb = g0 + R - 1 > Nr - 1 ? Nr - 1 : g0 + R - 1;
+    const int la = ga - g0, nrows = gb - ga + 1;
     // The state tile arrives in chunks of whole implicit passes, one mbarrier
     // each, so that the first pass can start while later rows are in flight.
     const int rpp = NT / G;   // theta rows per implicit pass
@@ -899,14 +911,14 @@ __device__ __forceinline__ void split_tile(const StepParams<T> &p, int tile, int
                 unsigned bytes = r1 > r0 ? (unsigned)(r1 - r0) * (unsigned)N * (unsigned)sizeof(c2) : 0u;
                 mbar_expect_tx(&s_mbar[c], 3 * bytes);   // with no bytes this is a plain arrival
                 if (bytes) {
-                    const size_t g0 = (size_t)(ga + r0 - la);
-                    bulk_g2s(sPhi + r0 * P, p.uin + g0 * N, bytes, &s_mbar[c]);
-                    bulk_g2s(sPi + r0 * P, p.uin + ((size_t)Nr + g0) * N, bytes, &s_mbar[c]);
-                    bulk_g2s(sPiv + r0 * P, K.piv + g0 * N, bytes, &s_mbar[c]);
+                    const size_t gr = (size_t)(ga + r0 - la);
+                    bulk_g2s(sPhi + r0 * P, p.uin + gr * N, bytes, &s_mbar[c]);
+                    bulk_g2s(sPi + r0 * P, p.uin + ((size_t)Nr + gr) * N, bytes, &s_mbar[c]);
+                    bulk_g2s(sPiv + r0 * P, K.piv + gr * N, bytes, &s_mbar[c]);
                 }
             }
         }
-        // rows off the grid (first and last tile only) are zero
+        // rows off the grid (first and last tiles only) are zero
         for (int lr = t_lr, j = t_j; lr < R;) {
             if (lr < la || lr >= la + nrows) {
                 sPhi[lr * P + j] = zero;
@@ -918,7 +930,7 @@ __device__ __forceinline__ void split_tile(const StepParams<T> &p, int tile, int
         }
     } else {
         for (int lr = t_lr, j = t_j; lr < R;) {
-            int gi = i0 - 1 + lr;
+            int gi = g0 + lr;
             c2 fv = zero, gv = zero, ev = zero;
             if (gi >= 0 && gi < Nr) {
                 fv = p.uin[(size_t)gi * N + j];
@@ -934,8 +946,8 @@ __device__ __forceinline__ void split_tile(const StepParams<T> &p, int tile, int
         }
     }
     {
-        // r-table positions 2(i0-1) .. 2(i0+TR); those off the grid are zero
-        const long long pbase = 2LL * (i0 - 1);
+        // r-table positions 2 g0 .. 2(g0+R-1); those off the grid are zero
+        const long long pbase = 2LL * g0;
         const long long pmax = 2LL * Nr - 2;
         for (int idx = tid; idx < (2 * R - 1) * NRF; idx += NT) {
             int e = idx / NRF, q = idx - e * NRF;
@@ -945,14 +957,12 @@ __device__ __forceinline__ void split_tile(const StepParams<T> &p, int tile, int
     }
     for (int idx = tid; idx < NTF * N; idx += NT) sTh[idx] = p.thtab[idx];
     __syncthreads();
-    // ---- B: implicit step on the tile rows (all R rows; only rows 1..TR with imp_only)
-    int ok = 1;   // every bounded wait of this thread succeeded
-    {
-        const int lo = p.imp_only ? 1 : 0, hi = p.imp_only ? TR + 1 : R;
-        const int g = tid % G;
-        const bool vec = p.vec != 0;
+    const int g = tid % G;
+    const bool vec = p.vec != 0;
+    // implicit step on tile rows [lo, hi)
+    auto implicit_rows = [&](const ImpConst<T> &Ki, int lo, int hi, bool wait_chunks, int &ok) {
         for (int base = lo; base < hi; base += rpp) {
-            if (p.bulk && ok) {
+            if (wait_chunks && p.bulk && ok) {
                 // the chunks that hold this pass's rows
                 int last = base + rpp - 1;
                 if (last > hi - 1) last = hi - 1;
@@ -960,12 +970,32 @@ __device__ __forceinline__ void split_tile(const StepParams<T> &p, int tile, int
             }
             int lr = base + tid / G;
             bool in_tile = lr < hi;
-            int gi = i0 - 1 + lr;
+            int gi = g0 + lr;
             bool active = in_tile && gi >= 1 && gi <= Nr - 2;
             int lrc = in_tile ? lr : lo;
-            implicit_row_group<T, S>(K, sPhi + lrc * P, sPi + lrc * P, sPiv + lrc * P, sRt + 2 * lrc * NRF, sTh, N,
+            implicit_row_group<T, S>(Ki, sPhi + lrc * P, sPi + lrc * P, sPiv + lrc * P, sRt + 2 * lrc * NRF, sTh, N,
                                      active, in_tile, g, G, vec);
         }
+    };
+    // physical sample u = C_{dt/2} s of the extraction row (tile row lx) in
+    // place, or of its copy in (xPhi, xPi); warp 0
+    auto extract_row = [&](int lx, long long slot, bool copy) {
+        if (tid < 32) {
+            c2 *rf = copy ? xPhi : sPhi + lx * P, *rg = copy ? xPi : sPi + lx * P;
+            bool mine = tid < G;
+            bool active = mine && p.i_ext >= 1 && p.i_ext <= Nr - 2;
+            implicit_row_group<T, S>(p.half, rf, rg, p.half.piv + (size_t)p.i_ext * N, sRt + 2 * lx * NRF, sTh, N,
+                                     active, mine, tid % G, G, vec);
+            __syncwarp();
+            extract_warp<T>(p, rf, slot);
+        }
+    };
+    const bool ext = !p.imp_only && p.nfix < 0 && p.i_ext >= i0 && p.i_ext < i0 + TR && p.i_ext < Nr;
+    // ---- B: implicit step on the tile rows (all R rows; only the output rows with imp_only)
+    int ok = 1;   // every bounded wait of this thread succeeded
+    {
+        const int lo = p.imp_only ? KS : 0, hi = p.imp_only ? TR + KS : R;
+        implicit_rows(K, lo, hi, true, ok);
         // the remaining phases read every row of the tile
         if (p.bulk && ok)
             for (int c = 0; c < nch; ++c) ok &= (int)mbar_wait(&s_mbar[c], 0, kWaitLimit);
@@ -980,25 +1010,48 @@ __device__ __forceinline__ void split_tile(const StepParams<T> &p, int tile, int
         return;
     }
     if (!p.imp_only) {
-        // ---- C: Lax-Wendroff on the output rows
+        auto sync_all = [] { __syncthreads(); };
+        // ---- C: Lax-Wendroff (first step: rows 1 .. R-2)
         c2 ph1 = zero, ph2 = zero;
         if (src) {
             ph1 = from_d2<T>(sph[0]);
             ph2 = from_d2<T>(sph[1]);
         }
-        auto sync_all = [] { __syncthreads(); };
-        lw_phase<T>(p, sPhi, sPi, sRt, sTh, TR, i0, tid, NT, src, ph1, ph2, sync_all);
+        lw_phase<T>(p, sPhi, sPi, sRt, sTh, 1, R - 2, g0, tid, NT, src, ph1, ph2, sync_all);
         __syncthreads();
+        if constexpr (KS == 2) {
+            // sample of step n+1 from a copy of the extraction row (the row
+            // itself goes on into the second step), then the second step on
+            // rows 1 .. R-2 (implicit) and 2 .. R-3 (Lax-Wendroff)
+            if (ext && tid < 32) {
+                const int lx = p.i_ext - g0;
+                for (int j = tid; j < N; j += 32) {
+                    xPhi[j] = sPhi[lx * P + j];
+                    xPi[j] = sPi[lx * P + j];
+                }
+            }
+            __syncthreads();
+            if (ext) extract_row(p.i_ext - g0, s_n + 1, true);
+            int ok2 = 1;
+            implicit_rows(p.full, 1, R - 1, false, ok2);
+            __syncthreads();
+            if (src) {
+                ph1 = from_d2<T>(sph[2]);
+                ph2 = from_d2<T>(sph[3]);
+            }
+            lw_phase<T>(p, sPhi, sPi, sRt, sTh, 2, R - 4, g0, tid, NT, src, ph1, ph2, sync_all);
+            __syncthreads();
+        }
     }
-    // ---- D: store the output rows
+    // ---- D: store the output rows (tile rows KS .. KS+TR-1)
     const int nout = (Nr - i0) < TR ? (Nr - i0) : TR;
     if (p.bulk) {
         fence_proxy_async();      // shared-memory writes become visible to the bulk copy
         __syncthreads();
         if (tid == 0) {
             unsigned bytes = (unsigned)nout * (unsigned)N * (unsigned)sizeof(c2);
-            bulk_s2g(p.uout + (size_t)i0 * N, sPhi + P, bytes);
-            bulk_s2g(p.uout + ((size_t)Nr + i0) * N, sPi + P, bytes);
+            bulk_s2g(p.uout + (size_t)i0 * N, sPhi + KS * P, bytes);
+            bulk_s2g(p.uout + ((size_t)Nr + i0) * N, sPi + KS * P, bytes);
             bulk_commit();
             bulk_wait_read();     // the tile may be reused (extraction) and the CTA may exit
         }
@@ -1006,8 +1059,8 @@ __device__ __forceinline__ void split_tile(const StepParams<T> &p, int tile, int
         for (int k = t_lr, j = t_j; k < TR;) {
             int gi = i0 + k;
             if (gi < Nr) {
-                p.uout[(size_t)gi * N + j] = sPhi[(k + 1) * P + j];
-                p.uout[((size_t)Nr + gi) * N + j] = sPi[(k + 1) * P + j];
+                p.uout[(size_t)gi * N + j] = sPhi[(k + KS) * P + j];
+                p.uout[((size_t)Nr + gi) * N + j] = sPi[(k + KS) * P + j];
             }
             k += d_lr;
             j += d_j;
@@ -1015,26 +1068,24 @@ __device__ __forceinline__ void split_tile(const StepParams<T> &p, int tile, int
         }
     }
     if (p.imp_only) return;
-    // ---- E: physical sample u_{n+1} = C_{dt/2} s_{n+1} on the extraction row
-    const bool ext = p.nfix < 0 && p.i_ext >= i0 && p.i_ext < i0 + TR && p.i_ext < Nr;
+    // ---- E: physical sample u_{n+KS} = C_{dt/2} s_{n+KS} on the extraction row
     if (ext) {
         __syncthreads();
-        int lr = p.i_ext - i0 + 1;
-        if (tid < 32) {
-            bool mine = tid < G;
-            bool active = mine && p.i_ext >= 1 && p.i_ext <= Nr - 2;
-            implicit_row_group<T, S>(p.half, sPhi + lr * P, sPi + lr * P, p.half.piv + (size_t)p.i_ext * N,
-                                     sRt + 2 * lr * NRF, sTh, N, active, mine, tid % G, G, p.vec != 0);
-            __syncwarp();
-            extract_warp<T>(p, sPhi + lr * P, s_n + 1);
-        }
+        extract_row(p.i_ext - g0, s_n + KS, false);
     }
 }
 
 template <typename T, int S>
 __global__ void __launch_bounds__(256, (sizeof(T) == 4 && S <= 4) ? 2 : 1) k_split_step(const StepParams<T> p)
 {
-    split_tile<T, S>(p, (int)blockIdx.x, (int)gridDim.x);
+    split_tile<T, S, 1>(p, (int)blockIdx.x, (int)gridDim.x);
+}
+
+// Two time steps per launch (temporal blocking): see split_tile.
+template <typename T, int S>
+__global__ void __launch_bounds__(256, (sizeof(T) == 4 && S <= 4) ? 2 : 1) k_split_step2(const StepParams<T> p)
+{
+    split_tile<T, S, 2>(p, (int)blockIdx.x, (int)gridDim.x);
 }
 
 // Batched split step: every CTA takes entry blockIdx.x of the tile list,
@@ -1053,7 +1104,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && S <= 4) ? 2 : 1)
     if (threadIdx.x < sizeof(StepParams<T>) / 4)
         reinterpret_cast<int *>(&sp)[threadIdx.x] = reinterpret_cast<const int *>(params + e.x)[threadIdx.x];
     __syncthreads();
-    split_tile<T, S>(sp, e.y, (sp.Nr + sp.tile_rows - 1) / sp.tile_rows);
+    split_tile<T, S, 1>(sp, e.y, (sp.Nr + sp.tile_rows - 1) / sp.tile_rows);
 }
 
 __device__ __forceinline__ void mbar_arrive(unsigned long long *m)
@@ -1244,7 +1295,7 @@ __global__ void __maxnreg__(PersistRegs<NC>::v) k_split_persist(const StepParams
         const int lx = p.i_ext - i0 + 1;
         if (ext && tid < NRF) xF[tid] = sRt[2 * lx * NRF + tid];
         const bool src = p.patch_np > 0 && i0 + TR >= p.patch_p0 && i0 - 1 <= p.patch_p0 + p.patch_np;
-        lw_phase<T>(p, sPhi, sPi, sRt, sTh, TR, i0, tid, NC, src, ph1, ph2, bar);
+        lw_phase<T>(p, sPhi, sPi, sRt, sTh, 1, TR, i0 - 1, tid, NC, src, ph1, ph2, bar);
         bar();
         if (ext && tid < 32) {
             for (int j = tid; j < N; j += 32) {
@@ -1850,6 +1901,13 @@ size_t split_smem_bytes(int tile_rows, int Nth)
     return split_smem_plan(tile_rows + 2, Nth, (int)sizeof(T)).total;
 }
 
+// Two steps per launch: R = TR + 4 rows plus a copy of the extraction row.
+template <typename T>
+size_t split2_smem_bytes(int tile_rows, int Nth)
+{
+    return split_smem_plan(tile_rows + 4, Nth, (int)sizeof(T)).total + 2 * (size_t)Nth * sizeof(typename V2<T>::t);
+}
+
 int implicit_seg(int Nth) { return Nth <= 128 ? kSegNarrow : (Nth <= 256 ? kSeg : kSegWide); }
 
 int implicit_group(int Nth)
@@ -2071,6 +2129,42 @@ cudaError_t launch_dot(const typename V2<T>::t *x, const typename V2<T>::t *y, c
 }
 
 template <typename T>
+static void (*split2_fn(int Nth))(const StepParams<T>)
+{
+    const int seg = implicit_seg(Nth);
+    return seg == kSegNarrow ? k_split_step2<T, kSegNarrow>
+                             : (seg == kSeg ? k_split_step2<T, kSeg> : k_split_step2<T, kSegWide>);
+}
+
+template <typename T>
+int split2_blocks_per_sm(int Nth, int threads, size_t smem)
+{
+    auto fn = split2_fn<T>(Nth);
+    if (smem_limit_max((const void *)fn) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, threads, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return nb;
+}
+
+template <typename T>
+cudaError_t launch_split_step2(const StepParams<T> &p, int threads, size_t smem, cudaStream_t st)
+{
+    if (p.first || p.imp_only) return cudaErrorInvalidValue;   // two full steps only
+    auto fn = split2_fn<T>(p.Nth);
+    cudaError_t e = smem_limit_max((const void *)fn);
+    if (e != cudaSuccess) return e;
+    int grid = (p.Nr + p.tile_rows - 1) / p.tile_rows;
+    fn<<<grid, threads, smem, st>>>(p);
+    return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_literal_step(const StepParams<T> &p, cudaStream_t st)
 {
     int nm = (p.Nr - 1) * p.Nth, nn = p.Nr * p.Nth;
@@ -2168,6 +2262,12 @@ template int persist_blocks_per_sm<float>(int, int, size_t);
 template int persist_blocks_per_sm<double>(int, int, size_t);
 template cudaError_t launch_split_persist<float>(const StepParams<float> &, int, int, size_t, cudaStream_t);
 template cudaError_t launch_split_persist<double>(const StepParams<double> &, int, int, size_t, cudaStream_t);
+template size_t split2_smem_bytes<float>(int, int);
+template size_t split2_smem_bytes<double>(int, int);
+template int split2_blocks_per_sm<float>(int, int, size_t);
+template int split2_blocks_per_sm<double>(int, int, size_t);
+template cudaError_t launch_split_step2<float>(const StepParams<float> &, int, size_t, cudaStream_t);
+template cudaError_t launch_split_step2<double>(const StepParams<double> &, int, size_t, cudaStream_t);
 template int split_blocks_per_sm<float>(int, int, size_t);
 template int split_blocks_per_sm<double>(int, int, size_t);
 template size_t split_smem_bytes<float>(int, int);

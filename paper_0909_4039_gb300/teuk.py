@@ -42,6 +42,7 @@ EXPORTED = [
     "teuk_batch_workspace_bytes", "teuk_batch_create", "teuk_batch_step", "teuk_batch_tiling",
     "teuk_batch_set_tiling", "teuk_batch_autotune", "teuk_batch_last_error", "teuk_batch_destroy",
     "teuk_apply_step", "teuk_apply_sample", "teuk_adjoint_workspace_bytes", "teuk_adjoint_step", "teuk_dot",
+    "teuk_set_tiling_steps",
 ]
 
 
@@ -110,7 +111,9 @@ def lib(load_only: bool = False):
     L.teuk_set_tiling.argtypes = [vp, ctypes.c_int]
     L.teuk_literal_step_static.argtypes = [vp, vp, vp, i64, vp]
     L.teuk_kernel_config.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
-                                     ctypes.POINTER(ctypes.c_int)]
+                                     ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+    L.teuk_set_tiling_steps.argtypes = [vp, ctypes.c_int, ctypes.c_int]
+    L.teuk_set_tiling_steps.restype = ctypes.c_int
     L.teuk_set_persistent.argtypes = [vp, ctypes.c_int, ctypes.c_int]
     L.teuk_autotune_cold.argtypes = [vp, ctypes.c_int, vp, ctypes.c_size_t, vp, ctypes.POINTER(ctypes.c_int)]
     for name in ("teuk_workspace_bytes", "teuk_init_grid", "teuk_set_source", "teuk_set_weights",
@@ -237,9 +240,14 @@ def teuk_set_tiling(ctx, tile_rows: int):
 
 
 def teuk_kernel_config(ctx) -> dict:
-    pe, nc, gr = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
-    _check(lib().teuk_kernel_config(ctx, ctypes.byref(pe), ctypes.byref(nc), ctypes.byref(gr)), ctx)
-    return {"persistent": bool(pe.value), "consumer_threads": nc.value, "grid": gr.value}
+    pe, nc, gr, ks = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(lib().teuk_kernel_config(ctx, ctypes.byref(pe), ctypes.byref(nc), ctypes.byref(gr), ctypes.byref(ks)), ctx)
+    return {"persistent": bool(pe.value), "consumer_threads": nc.value, "grid": gr.value,
+            "steps_per_launch": ks.value}
+
+
+def teuk_set_tiling_steps(ctx, tile_rows: int, steps_per_launch: int):
+    _check(lib().teuk_set_tiling_steps(ctx, int(tile_rows), int(steps_per_launch)), ctx)
 
 
 def teuk_set_persistent(ctx, tile_rows: int, consumer_threads: int = 480):
@@ -303,8 +311,11 @@ class Stepper:
         out.update(teuk_kernel_config(self.ctx))
         return out
 
-    def set_tiling(self, tile_rows: int):
-        teuk_set_tiling(self.ctx, tile_rows)
+    def set_tiling(self, tile_rows: int, steps_per_launch: int = 1):
+        if steps_per_launch == 1:
+            teuk_set_tiling(self.ctx, tile_rows)
+        else:
+            teuk_set_tiling_steps(self.ctx, tile_rows, steps_per_launch)
 
     def set_persistent(self, tile_rows: int, consumer_threads: int = 480):
         teuk_set_persistent(self.ctx, tile_rows, consumer_threads)

@@ -285,3 +285,41 @@ def test_persistent_kernel_rejected_where_unavailable():
     with pytest.raises(teuk.TeukError):
         st.set_persistent(10, 256)
     st.close()
+
+
+TWO_STEP = [
+    # Nr, Ntheta, tile_rows, steps (odd counts end with a single step; >= 128 replays graphs)
+    (700, 128, 24, 41),
+    (333, 64, 21, 140),
+    (1000, 32, 60, 27),
+    (150, 16, 10, 33),
+    (257, 33, 9, 12),
+]
+
+
+@pytest.mark.parametrize("Nr,Nth,tr,steps", TWO_STEP)
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_two_steps_per_launch_matches_single_steps(Nr, Nth, tr, steps, precision):
+    """The tiled kernel with two time steps per launch (two halo rows, the
+    first step on the widened tile, a sample of the middle step from a copy
+    of the extraction row) gives bitwise the states and waveform of single
+    steps; the oracle agrees within the tolerance."""
+    from oracle import oracle as O
+    w = inputs.Workload("two", s=-2, m=2, a=0.9, Nr=Nr, Ntheta=Nth, rs_min=-60.0, rs_max=240.0, steps=steps,
+                        r0=8.0, amp=0.8 + 0.3j, sig_r=0.9, sig_th=0.25, rs_ext=150.0)
+    u0 = inputs.random_state(w.Nr, w.Ntheta, seed=Nr + 3 * Nth)
+    outs = []
+    for ks in (1, 2):
+        st = gpu_stepper(w, precision, wave_capacity=steps + 2)
+        st.set_tiling(tr, ks)
+        assert st.tiling()["steps_per_launch"] == ks and st.tiling()["tile_rows"] == tr
+        st.set_state(u0, 0)
+        st.step(steps)
+        outs.append((st.get_state(), st.waveform(0, steps + 1), st.current_step))
+        st.close()
+    assert outs[0][2] == outs[1][2] == steps
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+    if steps <= 41:
+        uo, ho = O.run(oracle_problem(w), u0, steps)
+        tol = FP64_TOL if precision == "fp64" else FP32_TOL
+        assert rel_l2(outs[1][0], uo) <= tol and rel_l2(outs[1][1], ho) <= tol
