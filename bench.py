@@ -111,8 +111,9 @@ class ClockSampler:
 
 
 def _profiled_traffic(kernel: str):
-    """DRAM bytes per launch of the step kernel from the committed ncu summary,
-    only while the kernel source is the one that was profiled."""
+    """DRAM bytes per time step of the step kernel from the committed ncu
+    summary (bytes per launch / steps per launch), only while the kernel
+    source is the one that was profiled."""
     import hashlib
     import re
     md = os.path.join(ROOT, "profiles", f"{kernel}_16384x128_fp32.md")
@@ -122,8 +123,9 @@ def _profiled_traffic(kernel: str):
         sha = hashlib.sha1(open(src, "rb").read()).hexdigest()
         m1 = re.search(r"traffic_bytes_per_launch:\s*(\d+)", text)
         m2 = re.search(r"source_sha1:\s*([0-9a-f]{40})", text)
+        m3 = re.search(r"steps_per_launch:\s*(\d+)", text)
         if m1 and m2 and m2.group(1) == sha:
-            return int(m1.group(1))
+            return int(m1.group(1)) // (int(m3.group(1)) if m3 else 1)
     except OSError:
         pass
     return None
@@ -259,7 +261,8 @@ def run_native(args):
         st.set_persistent(args.tile_rows, args.consumers)
         tiling_source = "fixed by --kernel persistent"
     tiling = st.tiling()
-    kernel = "k_split_persist" if tiling.get("persistent") else "k_split_step"
+    kernel = ("k_split_persist" if tiling.get("persistent")
+              else ("k_split_step2" if tiling.get("steps_per_launch", 1) == 2 else "k_split_step"))
     stream = st.stream
     pts = w.Nr * w.Ntheta
 
@@ -360,6 +363,7 @@ def run_native(args):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak,
                      "traffic": _profiled_traffic(kernel) if prec == "fp32" else None,
+                     "per": "time step (achieved and traffic: per launch / steps_per_launch)",
                      "kernel": kernel, "bytes_per_point": bytes_per_pt,
                      "peak_source": f"{peak_src} hbm_gbs (copy, burst)",
                      "median_kernel_us": med_kernel_s * 1e6,

@@ -68,9 +68,24 @@ template <typename C> __device__ __forceinline__ C zero_c2()
     c.y = 0;
     return c;
 }
+// Every sum of two products below is written with one explicit fma.  Left
+// to the compiler, a*b + c*d may fuse either product, and which one it fuses
+// depends on the code around the inlined call; kernels that share these
+// helpers (one or two steps per launch, batched, persistent) then round the
+// same expression differently.  With the fusion fixed they agree bit for bit.
 template <typename C> __device__ __forceinline__ C cmul(C a, C b)
 {
-    return cmk<C>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+    return cmk<C>(fma(a.x, b.x, -(a.y * b.y)), fma(a.x, b.y, a.y * b.x));
+}
+// c + a b
+template <typename C> __device__ __forceinline__ C cfma(C a, C b, C c)
+{
+    return cmk<C>(fma(a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(a.y, b.x, c.y)));
+}
+// c - a b
+template <typename C> __device__ __forceinline__ C cfnma(C a, C b, C c)
+{
+    return cmk<C>(fma(-a.x, b.x, fma(a.y, b.y, c.x)), fma(-a.x, b.y, fma(-a.y, b.x, c.y)));
 }
 template <typename C> __device__ __forceinline__ C cadd(C a, C b) { return cmk<C>(a.x + b.x, a.y + b.y); }
 template <typename C> __device__ __forceinline__ C csub(C a, C b) { return cmk<C>(a.x - b.x, a.y - b.y); }
@@ -81,7 +96,7 @@ template <typename C, typename T> __device__ __forceinline__ C caxpy(T s, C a, C
 }
 template <typename C> __device__ __forceinline__ C cinv(C a)
 {
-    auto d = rcp_fast(a.x * a.x + a.y * a.y);
+    auto d = rcp_fast(fma(a.x, a.x, a.y * a.y));
     return cmk<C>(a.x * d, -a.y * d);
 }
 
@@ -343,7 +358,7 @@ __device__ __forceinline__ void seg_solve(typename V2<T>::t (&w)[S], const typen
     const c2 one = cmk<c2>(T(1), T(0));
     c2 B = zero;
 #pragma unroll
-    for (int k = 0; k < S; ++k) B = csub(w[k], cmul(fm[k], B));
+    for (int k = 0; k < S; ++k) B = cfnma(fm[k], B, w[k]);
     {
         c2 A = P.Af0;
 #pragma unroll
@@ -353,7 +368,7 @@ __device__ __forceinline__ void seg_solve(typename V2<T>::t (&w)[S], const typen
                 c2 Bo = shfl_up_c(B, d, G), Ao = one;
                 if (l + 1 < P.nfw) Ao = shfl_up_c(A, d, G);
                 if (l < P.nf && g >= d) {
-                    B = cadd(cmul(A, Bo), B);
+                    B = cfma(A, Bo, B);
                     if (l + 1 < P.nf) A = cmul(A, Ao);
                 }
             }
@@ -363,12 +378,12 @@ __device__ __forceinline__ void seg_solve(typename V2<T>::t (&w)[S], const typen
     if (g == 0) z = zero;
 #pragma unroll
     for (int k = 0; k < S; ++k) {
-        z = csub(w[k], cmul(fm[k], z));
+        z = cfnma(fm[k], z, w[k]);
         w[k] = cmul(pm[k], z);
     }
     B = zero;
 #pragma unroll
-    for (int k = S - 1; k >= 0; --k) B = csub(w[k], cmul(bm[k], B));
+    for (int k = S - 1; k >= 0; --k) B = cfnma(bm[k], B, w[k]);
     {
         c2 A = P.Ab0;
 #pragma unroll
@@ -378,7 +393,7 @@ __device__ __forceinline__ void seg_solve(typename V2<T>::t (&w)[S], const typen
                 c2 Bo = shfl_down_c(B, d, G), Ao = one;
                 if (l + 1 < P.nbw) Ao = shfl_down_c(A, d, G);
                 if (l < P.nb && g + d < G) {
-                    B = cadd(cmul(A, Bo), B);
+                    B = cfma(A, Bo, B);
                     if (l + 1 < P.nb) A = cmul(A, Ao);
                 }
             }
@@ -388,7 +403,7 @@ __device__ __forceinline__ void seg_solve(typename V2<T>::t (&w)[S], const typen
     if (g == G - 1) x = zero;
 #pragma unroll
     for (int k = S - 1; k >= 0; --k) {
-        x = csub(w[k], cmul(bm[k], x));
+        x = cfnma(bm[k], x, w[k]);
         w[k] = x;
     }
 }
@@ -441,7 +456,7 @@ __device__ void implicit_row_group(const ImpConst<T> &K, typename V2<T>::t *phi,
         for (int k = 0; k < S; ++k) {
             c2 xm = k ? w[k - 1] : xl;
             c2 xp = (k + 1 < S) ? w[(k + 1) < S ? k + 1 : S - 1] : xr;
-            bf[k] = cadd(cmul(C.dg[k], w[k]), caxpy(C.qap[k], xp, cscale<c2>(C.qam[k], xm)));
+            bf[k] = cfma(C.dg[k], w[k], caxpy(C.qap[k], xp, cscale<c2>(C.qam[k], xm)));
         }
     };
 
@@ -458,9 +473,9 @@ __device__ void implicit_row_group(const ImpConst<T> &K, typename V2<T>::t *phi,
 #pragma unroll
         for (int k = 0; k < S; ++k) {
             c2 a1 = cmk<c2>(fma(gh, C.ct[k].x, T(1)), gh * C.ct[k].y);
-            c2 P1 = cmul(csub(y[k], cscale<c2>(gh, bf[k])), C.ia1[k]);
+            c2 P1 = cmul(caxpy(-gh, bf[k], y[k]), C.ia1[k]);
             c2 rphi = caxpy(K.h12g, P1, w[k]);                     // U1_Phi + (1 - 2 gamma) h U1_Pi
-            c2 rpi = csub(y[k], cscale<c2>(K.h1g, cadd(bf[k], cmul(C.ct[k], P1))));
+            c2 rpi = caxpy(-K.h1g, cfma(C.ct[k], P1, bf[k]), y[k]);
             w[k] = caxpy(gh, rpi, cmul(a1, rphi));
             y[k] = rpi;
         }
@@ -471,7 +486,7 @@ __device__ void implicit_row_group(const ImpConst<T> &K, typename V2<T>::t *phi,
         c2 bf[S];
         apply_B(bf);
 #pragma unroll
-        for (int k = 0; k < S; ++k) y[k] = cmul(csub(y[k], cscale<c2>(gh, bf[k])), C.ia1[k]);
+        for (int k = 0; k < S; ++k) y[k] = cmul(caxpy(-gh, bf[k], y[k]), C.ia1[k]);
     }
     if (in_tile) row_store<T, S>(phi, pi, w, y, j0, lenw, vec);
 }
@@ -589,7 +604,7 @@ __device__ __forceinline__ void bK(const T *f, T rs, T S2, T C, T &b, typename V
 {
     const T sg = rs * rs;
     b = f[RF_R] * rs;
-    T kre = fma(b, f[RF_CTR], f[RF_CSR] - f[RF_E1]) + sg * fma(-f[RF_E3], S2, f[RF_E2]);
+    T kre = fma(sg, fma(-f[RF_E3], S2, f[RF_E2]), fma(b, f[RF_CTR], f[RF_CSR] - f[RF_E1]));
     T kim = fma(b, fma(f[RF_CTC], C, f[RF_CTI]), f[RF_CSI]);
     K.x = sg * kre;
     K.y = sg * kim;
@@ -650,8 +665,8 @@ __device__ void lw_segment(const StepParams<T> &p, typename V2<T>::t *sPhi, type
         c2 dg = cscale<c2>(ri, csub(gb, ga));
         c2 Sv = cmul(K, df);
         if (src) Sv = cadd(Sv, patch_val(p, gl, 1, j, ph1));
-        mf = csub(fbar, cscale<c2>(hdt * b, df));
-        mg = cadd(gbar, cscale<c2>(hdt, cadd(cscale<c2>(b, dg), Sv)));
+        mf = caxpy(-(hdt * b), df, fbar);
+        mg = caxpy(hdt, caxpy(b, dg, Sv), gbar);
     };
 
     c2 fb = sPhi[ra * P + j], gb = sPi[ra * P + j];
@@ -683,8 +698,8 @@ __device__ void lw_segment(const StepParams<T> &p, typename V2<T>::t *sPhi, type
             c2 dg = cscale<c2>(ri, csub(mg, mgp));
             c2 Sv = cmul(K, df);
             if (src) Sv = cadd(Sv, patch_val(p, gi, 0, j, ph2));
-            nfv = csub(fb, cscale<c2>(dt * b, df));
-            ngv = cadd(gb, cscale<c2>(dt, cadd(cscale<c2>(b, dg), Sv)));
+            nfv = caxpy(-(dt * b), df, fb);
+            ngv = caxpy(dt, caxpy(b, dg, Sv), gb);
         }
         sPhi[lr * P + j] = nfv;
         sPi[lr * P + j] = ngv;
