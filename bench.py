@@ -255,7 +255,7 @@ def run_native(args):
         tiling_source = ("teuk_autotune_cold (the 4 model-best configurations of each kernel, "
                          "20 L2-flushed steps each)")
     elif args.kernel == "tiled":
-        st.set_tiling(args.tile_rows)
+        st.set_tiling(args.tile_rows, args.steps_per_launch)
         tiling_source = "fixed by --kernel tiled"
     else:
         st.set_persistent(args.tile_rows, args.consumers)
@@ -623,6 +623,8 @@ def main():
                     help="auto: measured choice (cold-L2 autotune); otherwise the given kernel")
     ap.add_argument("--tile-rows", type=int, default=28, help="tile height for --kernel tiled/persistent")
     ap.add_argument("--consumers", type=int, default=480, help="consumer threads for --kernel persistent")
+    ap.add_argument("--steps-per-launch", type=int, choices=[1, 2], default=1,
+                    help="time steps per launch for --kernel tiled")
     ap.add_argument("--time-steps", type=int, default=0,
                     help="adjoint4096: time steps per gradient (default: the workload's 8000)")
     ap.add_argument("--workload", choices=["single", "batch64", "long8", "adjoint4096"], default="single",
