@@ -1006,39 +1006,47 @@ __device__ __forceinline__ void split_tile(const StepParams<T> &p, int tile, int
         }
     };
     const bool ext = !p.imp_only && p.nfix < 0 && p.i_ext >= i0 && p.i_ext < i0 + TR && p.i_ext < Nr;
-    // ---- B: implicit step on the tile rows (all R rows; only the output rows with imp_only)
+    // ---- B and C, once per time step of the launch.  Step k (from 0) runs
+    // the implicit stage on tile rows k .. R-1-k and the Lax-Wendroff stages
+    // on rows k+1 .. R-2-k, so the output rows KS .. KS+TR-1 are exact after
+    // the last step.  One loop body serves every step: the two-step kernel's
+    // code is no larger than the one-step kernel's.
     int ok = 1;   // every bounded wait of this thread succeeded
-    {
-        const int lo = p.imp_only ? KS : 0, hi = p.imp_only ? TR + KS : R;
-        implicit_rows(K, lo, hi, true, ok);
-        // the remaining phases read every row of the tile
-        if (p.bulk && ok)
-            for (int c = 0; c < nch; ++c) ok &= (int)mbar_wait(&s_mbar[c], 0, kWaitLimit);
-    }
-    // all threads agree on the outcome of the bounded waits before acting on it
-    if (!__syncthreads_and(ok)) {
-        // a copy did not complete: report, wait once more, leave the tile alone
-        if (tid == 0) {
-            atomicOr(&p.ctl->flags, FLAG_TIMEOUT);
-            for (int c = 0; c < nch; ++c) mbar_wait(&s_mbar[c], 0, kWaitLimit);
+    const auto sync_all = [] { __syncthreads(); };
+#pragma unroll 1
+    for (int k = 0; k < KS; ++k) {
+        // implicit step: dt/2 for a first step and for the state output, else dt
+        const ImpConst<T> &Ki = k == 0 ? K : p.full;
+        const int lo = p.imp_only ? KS : k, hi = p.imp_only ? TR + KS : R - k;
+        implicit_rows(Ki, lo, hi, k == 0, ok);
+        if (k == 0) {
+            // the remaining phases read every row of the tile
+            if (p.bulk && ok)
+                for (int c = 0; c < nch; ++c) ok &= (int)mbar_wait(&s_mbar[c], 0, kWaitLimit);
+            // all threads agree on the outcome of the bounded waits before acting on it
+            if (!__syncthreads_and(ok)) {
+                // a copy did not complete: report, wait once more, leave the tile alone
+                if (tid == 0) {
+                    atomicOr(&p.ctl->flags, FLAG_TIMEOUT);
+                    for (int c = 0; c < nch; ++c) mbar_wait(&s_mbar[c], 0, kWaitLimit);
+                }
+                return;
+            }
+            if (p.imp_only) break;
+        } else {
+            __syncthreads();
         }
-        return;
-    }
-    if (!p.imp_only) {
-        auto sync_all = [] { __syncthreads(); };
-        // ---- C: Lax-Wendroff (first step: rows 1 .. R-2)
         c2 ph1 = zero, ph2 = zero;
         if (src) {
-            ph1 = from_d2<T>(sph[0]);
-            ph2 = from_d2<T>(sph[1]);
+            ph1 = from_d2<T>(sph[2 * k]);
+            ph2 = from_d2<T>(sph[2 * k + 1]);
         }
-        lw_phase<T>(p, sPhi, sPi, sRt, sTh, 1, R - 2, g0, tid, NT, src, ph1, ph2, sync_all);
+        lw_phase<T>(p, sPhi, sPi, sRt, sTh, k + 1, R - 2 - 2 * k, g0, tid, NT, src, ph1, ph2, sync_all);
         __syncthreads();
-        if constexpr (KS == 2) {
-            // sample of step n+1 from a copy of the extraction row (the row
-            // itself goes on into the second step), then the second step on
-            // rows 1 .. R-2 (implicit) and 2 .. R-3 (Lax-Wendroff)
-            if (ext && tid < 32) {
+        if (k + 1 < KS && ext) {
+            // sample of step n+k+1 from a copy of the extraction row; the row
+            // itself goes on into the next step
+            if (tid < 32) {
                 const int lx = p.i_ext - g0;
                 for (int j = tid; j < N; j += 32) {
                     xPhi[j] = sPhi[lx * P + j];
@@ -1046,16 +1054,7 @@ __device__ __forceinline__ void split_tile(const StepParams<T> &p, int tile, int
                 }
             }
             __syncthreads();
-            if (ext) extract_row(p.i_ext - g0, s_n + 1, true);
-            int ok2 = 1;
-            implicit_rows(p.full, 1, R - 1, false, ok2);
-            __syncthreads();
-            if (src) {
-                ph1 = from_d2<T>(sph[2]);
-                ph2 = from_d2<T>(sph[3]);
-            }
-            lw_phase<T>(p, sPhi, sPi, sRt, sTh, 2, R - 4, g0, tid, NT, src, ph1, ph2, sync_all);
-            __syncthreads();
+            extract_row(p.i_ext - g0, s_n + k + 1, true);
         }
     }
     // ---- D: store the output rows (tile rows KS .. KS+TR-1)
