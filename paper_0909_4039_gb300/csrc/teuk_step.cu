@@ -94,6 +94,47 @@ template <typename C, typename T> __device__ __forceinline__ C caxpy(T s, C a, C
 {
     return cmk<C>(fma(s, a.x, b.x), fma(s, a.y, b.y));
 }
+// FP32 specialisations on packed pairs (add/sub/mul/fma .f32x2 of the
+// sm_100 family): one instruction for both components, each lane rounded
+// exactly as the scalar operation, so results do not change.  The complex
+// multiply keeps scalar fmas: its packed form needs swapped and negated
+// operand pairs, which cost more moves than the packing saves.
+__device__ __forceinline__ unsigned long long pk2(float x, float y)
+{
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(x), "f"(y));
+    return r;
+}
+__device__ __forceinline__ float2 upk2(unsigned long long r)
+{
+    float2 v;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(v.x), "=f"(v.y) : "l"(r));
+    return v;
+}
+template <> __device__ __forceinline__ float2 cadd<float2>(float2 a, float2 b)
+{
+    unsigned long long d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk2(a.x, a.y)), "l"(pk2(b.x, b.y)));
+    return upk2(d);
+}
+template <> __device__ __forceinline__ float2 csub<float2>(float2 a, float2 b)
+{
+    unsigned long long d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk2(a.x, a.y)), "l"(pk2(b.x, b.y)));
+    return upk2(d);
+}
+template <> __device__ __forceinline__ float2 cscale<float2, float>(float s, float2 a)
+{
+    unsigned long long d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk2(s, s)), "l"(pk2(a.x, a.y)));
+    return upk2(d);
+}
+template <> __device__ __forceinline__ float2 caxpy<float2, float>(float s, float2 a, float2 b)
+{
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(pk2(s, s)), "l"(pk2(a.x, a.y)), "l"(pk2(b.x, b.y)));
+    return upk2(d);
+}
 template <typename C> __device__ __forceinline__ C cinv(C a)
 {
     auto d = rcp_fast(fma(a.x, a.x, a.y * a.y));
