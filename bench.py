@@ -390,8 +390,9 @@ def run_native(args):
 
 
 def run_native_batch(args):
-    """Batched instances: one launch per step over every tile of every
-    instance this rank holds."""
+    """Batched instances: one launch over every tile of every instance this
+    rank holds; one timed iteration is one launch of the configured steps
+    per launch."""
     import numpy as np
     import torch
     import torch.distributed as dist
@@ -420,7 +421,7 @@ def run_native_batch(args):
         drs = (w.rs_max - w.rs_min) / (w.Nr - 1)
         st = teuk.Stepper(s=w.s, m=w.m, a=w.a, Nr=w.Nr, Ntheta=w.Ntheta, rstar_min=w.rs_min, rstar_max=w.rs_max,
                           dt=w.cfl * drs, rstar_extract=w.rs_ext, precision=prec, device=dev, stream=stream,
-                          wave_capacity=args.steps + args.warmup + 8)
+                          wave_capacity=2 * (args.steps + args.warmup) + 8)
         st.set_source(w.amp, w.r0, w.sig_r, w.sig_th)
         sts.append(st)
     pts = sum(allw[k].points for k in mine)
@@ -429,6 +430,7 @@ def run_native_batch(args):
     if b is not None:
         b.autotune(5)
         tiling = b.tiling()
+    ks = tiling.get("steps_per_launch", 1)
 
     def barrier():
         torch.cuda.synchronize(dev)
@@ -438,7 +440,7 @@ def run_native_batch(args):
 
     with torch.cuda.stream(stream):
         if b is not None:
-            b.step(args.warmup)
+            b.step(args.warmup * ks)
     barrier()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     with ClockSampler(local) as clk:
@@ -448,7 +450,7 @@ def run_native_batch(args):
             for k in range(args.steps):
                 ev[k][0].record(stream)
                 if b is not None:
-                    b.step(1)
+                    b.step(ks)
                 ev[k][1].record(stream)
         barrier()
         t_wall = time.perf_counter() - t_wall0
@@ -458,9 +460,9 @@ def run_native_batch(args):
         t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
-    ms_per_step = total_ms / args.steps
-    value = pts_all * args.steps / (total_ms * 1e-3) / 1e9
-    avg_s = statistics.fmean(durs) * 1e-3
+    ms_per_step = total_ms / (args.steps * ks)
+    value = pts_all * args.steps * ks / (total_ms * 1e-3) / 1e9
+    avg_s = statistics.fmean(durs) * 1e-3 / ks
     bytes_per_pt = 32 if prec == "fp32" else 64
     peak, peak_src = _peaks()
     achieved = bytes_per_pt * pts / avg_s / 1e9
@@ -469,7 +471,7 @@ def run_native_batch(args):
     # every state and waveform back to the host
     hosts = [torch.zeros((2, st.Nr, st.Ntheta), dtype=torch.complex128, pin_memory=True) for st in sts]
     outs = [torch.empty_like(h, pin_memory=True) for h in hosts]
-    k_e2e = args.steps
+    k_e2e = args.steps * ks
     barrier()
     t0 = time.perf_counter()
     for st, h in zip(sts, hosts):
@@ -502,9 +504,12 @@ def run_native_batch(args):
                    "l2": f"not flushed: the batch's states ({2 * pts_all * bytes_per_pt / 2 / 1e9:.1f} GB) "
                          f"exceed the 129 MB L2",
                    "parallelism": f"instances split over {ws} rank(s) by points", "tiling": tiling,
-                   "tiling_source": "teuk_batch_autotune (coordinate descent over the Ntheta classes, 5 steps)"},
+                   "tiling_source": "teuk_batch_autotune (one and two steps per launch, each a coordinate "
+                                    "descent over the Ntheta classes, 5 launches per trial)",
+                   "iteration": "one timed iteration = one launch = steps_per_launch time steps"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": None, "kernel": "k_split_batch", "bytes_per_point": bytes_per_pt,
+                     "per": "time step (achieved: per launch / steps_per_launch)",
                      "peak_source": f"{peak_src} hbm_gbs (copy, burst)"},
         "e2e": e2e,
         "clocks": clk.summary(),
@@ -549,13 +554,19 @@ def run_native_adjoint(args):
     h = A.waveform(w, prm, N, precision=prec).cpu().numpy()
     target = np.abs(h).max() * inputs.adjoint_target(N + 1, dt, seed=1)
 
-    def grad(wrt_a=True):
+    def grad(wrt_a=True, split=None):
         # forward run keeping sqrt(N) checkpoints, loss gradient on the host,
-        # backward sweep over the checkpoints
+        # backward sweep over the checkpoints; split receives (forward s, sweep s)
+        t0 = time.perf_counter()
         fw = A.forward(w, prm, N, precision=prec)
         try:
             hh = fw.h.cpu().numpy()
-            return A.backward(fw, torch.as_tensor(2.0 * dt * (hh - target)), wrt_a=wrt_a)
+            t1 = time.perf_counter()
+            r = A.backward(fw, torch.as_tensor(2.0 * dt * (hh - target)), wrt_a=wrt_a)
+            torch.cuda.synchronize()
+            if split is not None:
+                split.append((t1 - t0, time.perf_counter() - t1))
+            return r
         finally:
             fw.close()
 
@@ -576,8 +587,10 @@ def run_native_adjoint(args):
     A.waveform(w, prm, N, precision=prec)
     t_fwd = time.perf_counter() - tf0
     tg0 = time.perf_counter()
-    grad(wrt_a=False)
+    split_src, split_all = [], []
+    grad(wrt_a=False, split=split_src)
     t_src = time.perf_counter() - tg0 - t_fwd
+    grad(wrt_a=True, split=split_all)
     if ws > 1:
         tt = torch.tensor([t], device="cuda", dtype=torch.float64)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
@@ -596,8 +609,13 @@ def run_native_adjoint(args):
         "adjoint_cost": {"forward_s": t_fwd, "gradient_s": per,
                          "ratio_all_params": per / t_fwd,
                          "ratio_source_params": (t_src + t_fwd) / t_fwd,
-                         "note": "gradient evaluation (forward waveform + sweep) in forward-run units; "
-                                 "source_params = amplitude and r0 only (no spin term)"},
+                         "sweep_over_forward_all_params": split_all[0][1] / t_fwd,
+                         "sweep_over_forward_source_params": split_src[0][1] / t_fwd,
+                         "checkpointed_forward_s": split_all[0][0],
+                         "note": "ratio_*: gradient evaluation (checkpointed forward run + backward sweep) "
+                                 "in forward-run units; sweep_over_forward_*: the backward sweep alone "
+                                 "(checkpoint recompute, adjoint steps, parameter contractions) over one "
+                                 "plain forward run; source_params = amplitude and r0 only (no spin term)"},
         "e2e": {"value": ws * args.steps / t, "unit": "grad/s", "h2d_bytes_per_step": 16 * (N + 1),
                 "d2h_bytes_per_step": 16 * (N + 1) + 32},
         "clocks": clk.summary(),

@@ -299,9 +299,10 @@ int teuk_dot(teuk_ctx *ctx, const void *d_x, const void *d_y, const void *d_z, v
 
 /* ---------------------------------------------------------------- batches
  * Many independent instances -- each a split-scheme context with its own
- * grid, spin, mode, source and buffers -- advanced together: one launch per
- * step covers every tile of every instance (a flattened tile list of
- * (instance, tile) entries), and long runs replay a captured CUDA graph.
+ * grid, spin, mode, source and buffers -- advanced together: one launch
+ * covers every tile of every instance (a flattened tile list of
+ * (instance, tile) entries) for one or two time steps, and long runs
+ * replay a captured CUDA graph.
  * This is the data-parallel decomposition of the method over independent
  * problems (Sec. 4); each instance computes exactly what teuk_step computes
  * for it alone.  Instances must share the state precision and the theta
@@ -317,14 +318,17 @@ int teuk_batch_workspace_bytes(teuk_ctx *const *ctxs, int count, size_t *bytes);
 
 /* Group contexts into a batch.  d_ws: caller-owned device memory of at
  * least teuk_batch_workspace_bytes, 256-byte aligned, for the lifetime of
- * the batch.  Tile heights start from a shared-memory model (whole implicit
- * passes, two CTAs per SM); teuk_batch_autotune measures them.
+ * the batch.  Steps per launch start at 2 where the kernel offers it
+ * (Ntheta <= 256), else 1; tile heights start from a shared-memory model
+ * (whole implicit passes, two CTAs per SM); teuk_batch_autotune measures
+ * both.
  * TEUK_E_INVAL for mixed precision or segment class, a literal-scheme or
  * repeated context.  Synchronous (uploads the tile list). */
 int teuk_batch_create(teuk_ctx *const *ctxs, int count, void *d_ws, size_t ws_bytes, teuk_batch **out);
 
 /* Advance every instance by nsteps (instances whose state is physical take
- * the half implicit step first, as teuk_step does).  Asynchronous on
+ * the half implicit step first, as teuk_step does; with two steps per
+ * launch an odd remainder takes a one-step launch).  Asynchronous on
  * `stream`; with a non-default stream and nsteps >= 128 chunks of 64 steps
  * replay one captured graph.  Work queued for an instance on another stream
  * (teuk_set_state, teuk_step) must be ordered before this call by the caller
@@ -339,9 +343,18 @@ int teuk_batch_tiling(const teuk_batch *batch, int *tile_rows, int *total_tiles,
  * TEUK_E_INVAL (and the previous tiling kept) if a tile does not fit. */
 int teuk_batch_set_tiling(teuk_batch *batch, const int *tile_rows);
 
-/* Measured tile heights: coordinate descent over the batch's Ntheta
- * classes, each class trying every whole number of implicit passes per tile
- * that fits, timed over trial_steps batched steps (CUDA events on `stream`).
+/* Time steps per launch: 1, or 2 (tiles carry two halo rows a side, both
+ * steps run on them; Ntheta <= 256).  Results are bit for bit those of
+ * single steps.  Setting it keeps the tile heights; TEUK_E_INVAL (and the
+ * previous value kept) if 2 is unavailable or a tile no longer fits. */
+int teuk_batch_steps_per_launch(const teuk_batch *batch, int *steps_per_launch);
+int teuk_batch_set_steps_per_launch(teuk_batch *batch, int steps_per_launch);
+
+/* Measured configuration: for each number of steps per launch the kernel
+ * offers, a coordinate descent over the batch's Ntheta classes, each class
+ * trying every whole number of implicit passes per tile that fits, timed
+ * over trial_steps batched launches (CUDA events on `stream`); the faster
+ * result per time step is kept.
  * The trials overwrite the states: afterwards every instance is zero at
  * step 0 with an empty waveform buffer (sources and weights kept).
  * Synchronous. */

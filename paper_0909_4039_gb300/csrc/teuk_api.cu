@@ -1201,6 +1201,7 @@ struct teuk_batch {
     size_t ws_bytes, par_bytes;      // par_bytes: one parameter table
     size_t off_par[3], off_tiles;    // tables: in = cur, in = cur ^ 1, first step; tile list
     int ntot;
+    int ks;                          // time steps per launch (1, or 2 once every instance is shifted)
     size_t smem;
     cudaGraphExec_t graph;
     cudaStream_t graph_stream;
@@ -1244,18 +1245,25 @@ size_t batch_ws_bytes(teuk_ctx *const *ctxs, int count, size_t *par_bytes, size_
 // Rows of one implicit pass for Ntheta (256 threads / G).
 int batch_rpp(int N) { return 256 / implicit_group(N); }
 
-// Default tile height: the largest whole number of implicit passes whose
-// tile leaves room for two CTAs per SM.
-int batch_default_tr(const teuk_ctx *c)
+// Shared memory of a batch tile of height tr with ks steps per launch.
+size_t batch_tile_smem(int prec, int tr, int N, int ks)
+{
+    if (ks == 2) return prec == TEUK_FP32 ? split2_smem_bytes<float>(tr, N) : split2_smem_bytes<double>(tr, N);
+    return prec == TEUK_FP32 ? split_smem_bytes<float>(tr, N) : split_smem_bytes<double>(tr, N);
+}
+
+// Default tile height: the largest whole number of implicit passes (tile
+// rows plus halos) whose tile leaves room for two CTAs per SM.
+int batch_default_tr(const teuk_ctx *c, int ks)
 {
     const int N = (int)c->d.Ntheta, rpp = batch_rpp(N);
-    const bool f32 = c->d.precision == TEUK_FP32;
     int best = 1;
-    for (int R = rpp; R - 2 <= 254; R += rpp) {
-        size_t sm = f32 ? split_smem_bytes<float>(R - 2, N) : split_smem_bytes<double>(R - 2, N);
-        if (sm > 112 * 1024 && R > rpp) break;
-        if (R - 2 >= 1) best = R - 2;
-        if (R - 2 >= c->d.Nr) break;
+    for (int R = rpp; R - 2 * ks <= 254; R += rpp) {
+        const int tr = R - 2 * ks;
+        if (tr < 1) continue;
+        if (batch_tile_smem(c->d.precision, tr, N, ks) > 112 * 1024 && best > 1) break;
+        best = tr;
+        if (tr >= c->d.Nr) break;
     }
     return best;
 }
@@ -1276,12 +1284,16 @@ int batch_layout(teuk_batch *b)
         nt[i] = (int)((c->d.Nr + b->tr[i] - 1) / b->tr[i]);
         maxt = nt[i] > maxt ? nt[i] : maxt;
         const int N = (int)c->d.Ntheta;
-        size_t sm = b->prec == TEUK_FP32 ? split_smem_bytes<float>(b->tr[i], N) : split_smem_bytes<double>(b->tr[i], N);
+        size_t sm = batch_tile_smem(b->prec, b->tr[i], N, b->ks);
         smem = sm > smem ? sm : smem;
     }
     if (smem > 227 * 1024) return bset_err(b, TEUK_E_INVAL, "a tile of the batch does not fit in shared memory%s");
-    int k = b->prec == TEUK_FP32 ? split_batch_blocks_per_sm<float>(b->seg, smem)
-                                 : split_batch_blocks_per_sm<double>(b->seg, smem);
+    int k = b->prec == TEUK_FP32 ? split_batch_blocks_per_sm<float>(b->seg, smem, b->ks)
+                                 : split_batch_blocks_per_sm<double>(b->seg, smem, b->ks);
+    // the first step of a two-step batch runs the one-step kernel with this shared memory
+    if (k >= 1 && b->ks == 2)
+        k = b->prec == TEUK_FP32 ? split_batch_blocks_per_sm<float>(b->seg, smem, 1)
+                                 : split_batch_blocks_per_sm<double>(b->seg, smem, 1);
     if (k < 1) return bset_err(b, TEUK_E_INVAL, "the batched kernel does not fit on this device with these tiles%s");
     b->htiles.clear();
     for (int t = 0; t < maxt; ++t)
@@ -1322,14 +1334,17 @@ int batch_tables(teuk_batch *b, cudaStream_t st)
     return TEUK_OK;
 }
 
-cudaError_t batch_launch(teuk_batch *b, int table, cudaStream_t st)
+// One launch from parameter table `table` with ks steps (the first-step
+// table always takes one).
+cudaError_t batch_launch(teuk_batch *b, int table, int ks, cudaStream_t st)
 {
     const int2 *tiles = (const int2 *)(b->ws + b->off_tiles);
+    if (table == 2) ks = 1;
     if (b->prec == TEUK_FP32)
         return launch_split_batch<float>((const StepParams<float> *)(b->ws + b->off_par[table]), tiles, b->ntot, b->seg,
-                                         b->smem, st);
+                                         b->smem, ks, st);
     return launch_split_batch<double>((const StepParams<double> *)(b->ws + b->off_par[table]), tiles, b->ntot, b->seg,
-                                      b->smem, st);
+                                      b->smem, ks, st);
 }
 
 int batch_step_impl(teuk_batch *b, int64_t nsteps, cudaStream_t st)
@@ -1342,7 +1357,7 @@ int batch_step_impl(teuk_batch *b, int64_t nsteps, cudaStream_t st)
     for (teuk_ctx *c : b->c) any_first = any_first || !c->shifted;
     if (any_first) {
         // first step from physical states: s_{n+1} = LW C_{dt/2} u_n where needed
-        BCK(batch_launch(b, 2, st), "batched first step");
+        BCK(batch_launch(b, 2, 1, st), "batched first step");
         for (teuk_ctx *c : b->c) {
             c->cur ^= 1;
             c->shifted = 1;
@@ -1360,7 +1375,8 @@ int batch_step_impl(teuk_batch *b, int64_t nsteps, cudaStream_t st)
             cudaGraph_t graph;
             BCK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal), "begin capture");
             cudaError_t le = cudaSuccess;
-            for (int k = 0; k < kGraphChunk && le == cudaSuccess; ++k) le = batch_launch(b, k & 1, st);
+            // kGraphChunk / ks launches: an even count, so the level parity is unchanged
+            for (int k = 0; k < kGraphChunk / b->ks && le == cudaSuccess; ++k) le = batch_launch(b, k & 1, b->ks, st);
             cudaError_t ee = cudaStreamEndCapture(st, &graph);
             if (le != cudaSuccess) return bcuda_err(b, le, "captured batched launch");
             if (ee != cudaSuccess) return bcuda_err(b, ee, "end capture");
@@ -1377,9 +1393,12 @@ int batch_step_impl(teuk_batch *b, int64_t nsteps, cudaStream_t st)
             left -= kGraphChunk;
         }
     }
-    for (int64_t k = 0; k < left; ++k) BCK(batch_launch(b, (int)(k & 1), st), "batched step");
+    // each launch (one or two steps) flips every instance's level once
+    int64_t launches = 0;
+    for (; left >= b->ks; left -= b->ks, ++launches) BCK(batch_launch(b, (int)(launches & 1), b->ks, st), "batched step");
+    for (; left > 0; --left, ++launches) BCK(batch_launch(b, (int)(launches & 1), 1, st), "batched step");
     for (teuk_ctx *c : b->c) {
-        c->cur ^= (int)(left & 1);
+        c->cur ^= (int)(launches & 1);
         c->step += nsteps;
     }
     return TEUK_OK;
@@ -1439,8 +1458,9 @@ int teuk_batch_create(teuk_ctx *const *ctxs, int count, void *d_ws, size_t ws_by
     b->ws_bytes = ws_bytes;
     batch_ws_bytes(ctxs, count, &b->par_bytes, &b->off_tiles);
     for (int k = 0; k < 3; ++k) b->off_par[k] = (size_t)k * b->par_bytes;
+    b->ks = split_batch_available(seg, 2) ? 2 : 1;
     b->tr.resize(count);
-    for (int i = 0; i < count; ++i) b->tr[i] = batch_default_tr(ctxs[i]);
+    for (int i = 0; i < count; ++i) b->tr[i] = batch_default_tr(ctxs[i], b->ks);
     r = batch_layout(b);
     if (r != TEUK_OK) {
         memcpy(g_init_err, b->err, sizeof(g_init_err));
@@ -1502,9 +1522,11 @@ int teuk_batch_autotune(teuk_batch *b, int trial_steps, void *stream)
     if (!b) return TEUK_E_STATE;
     if (trial_steps < 1 || trial_steps > 100000) return bset_err(b, TEUK_E_INVAL, "trial_steps out of range%s");
     cudaStream_t st = (cudaStream_t)stream;
-    // Coordinate descent over the Ntheta classes of the batch: for each
-    // class, every whole number of implicit passes per tile that fits is
-    // timed with the other classes fixed, and the fastest is kept.
+    // For each number of steps per launch the kernel offers, a coordinate
+    // descent over the Ntheta classes of the batch: for each class, every
+    // whole number of implicit passes per tile that fits is timed with the
+    // other classes fixed, and the fastest is kept.  The faster of the
+    // descents' results (time per step) is the configuration.
     std::vector<int> classes;
     for (teuk_ctx *c : b->c) {
         int N = (int)c->d.Ntheta;
@@ -1516,47 +1538,73 @@ int teuk_batch_autotune(teuk_batch *b, int trial_steps, void *stream)
     BCK(cudaEventCreate(&e0), "event");
     BCK(cudaEventCreate(&e1), "event");
     int rc = TEUK_OK;
-    for (int N : classes) {
-        const int rpp = batch_rpp(N);
-        std::vector<int> keep = b->tr;
-        float best = 3.4e38f;
-        int best_tr = -1;
-        for (int R = rpp; R - 2 <= 254 && rc == TEUK_OK; R += rpp) {
-            if (R - 2 < 1) continue;
-            std::vector<int> trial = keep;
-            for (size_t i = 0; i < b->c.size(); ++i)
-                if ((int)b->c[i]->d.Ntheta == N) trial[i] = R - 2;
-            b->tr = trial;
-            if (batch_layout(b) != TEUK_OK) break;   // larger tiles do not fit either
-            for (teuk_ctx *c : b->c) c->shifted = 1;
-            rc = batch_tables(b, st);                 // parameters for these tile heights
+    // ms per step of the current tile list and steps per launch (negative: does not fit)
+    auto trial = [&](float &ms_step) -> int {
+        ms_step = -1.0f;
+        if (batch_layout(b) != TEUK_OK) return TEUK_OK;
+        for (teuk_ctx *c : b->c) c->shifted = 1;
+        int r = batch_tables(b, st);   // parameters for these tile heights
+        if (r != TEUK_OK) return r;
+        cudaError_t e = cudaSuccess;
+        for (int w = 0; w < 2 && e == cudaSuccess; ++w) e = batch_launch(b, w & 1, b->ks, st);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+        for (int w = 0; w < trial_steps && e == cudaSuccess; ++w) e = batch_launch(b, w & 1, b->ks, st);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) return bcuda_err(b, e, "batch autotune trial");
+        ms_step = ms / (float)(trial_steps * b->ks);
+        return TEUK_OK;
+    };
+    float best_all = 3.4e38f;
+    int best_ks = b->ks;
+    std::vector<int> best_tr = b->tr;
+    for (int ks = 1; ks <= 2 && rc == TEUK_OK; ++ks) {
+        if (!split_batch_available(b->seg, ks)) continue;
+        b->ks = ks;
+        for (size_t i = 0; i < b->c.size(); ++i) b->tr[i] = batch_default_tr(b->c[i], ks);
+        for (int N : classes) {
+            const int rpp = batch_rpp(N);
+            std::vector<int> keep = b->tr;
+            float best = 3.4e38f;
+            int best_h = -1;
+            for (int R = rpp; R - 2 * ks <= 254 && rc == TEUK_OK; R += rpp) {
+                if (R - 2 * ks < 1) continue;
+                b->tr = keep;
+                for (size_t i = 0; i < b->c.size(); ++i)
+                    if ((int)b->c[i]->d.Ntheta == N) b->tr[i] = R - 2 * ks;
+                float ms = -1.0f;
+                rc = trial(ms);
+                if (rc != TEUK_OK || ms < 0.0f) break;   // larger tiles do not fit either
+                if (ms < best) {
+                    best = ms;
+                    best_h = R - 2 * ks;
+                }
+            }
+            b->tr = keep;
+            if (best_h > 0)
+                for (size_t i = 0; i < b->c.size(); ++i)
+                    if ((int)b->c[i]->d.Ntheta == N) b->tr[i] = best_h;
             if (rc != TEUK_OK) break;
-            cudaError_t e = cudaSuccess;
-            for (int w = 0; w < 2 && e == cudaSuccess; ++w) e = batch_launch(b, w & 1, st);
-            if (e == cudaSuccess) e = cudaEventRecord(e0, st);
-            for (int w = 0; w < trial_steps && e == cudaSuccess; ++w) e = batch_launch(b, w & 1, st);
-            if (e == cudaSuccess) e = cudaEventRecord(e1, st);
-            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-            float ms = 0.0f;
-            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-            if (e != cudaSuccess) {
-                rc = bcuda_err(b, e, "batch autotune trial");
-                break;
-            }
-            if (ms < best) {
-                best = ms;
-                best_tr = R - 2;
-            }
         }
-        b->tr = keep;
-        if (best_tr > 0)
-            for (size_t i = 0; i < b->c.size(); ++i)
-                if ((int)b->c[i]->d.Ntheta == N) b->tr[i] = best_tr;
         if (rc != TEUK_OK) break;
+        float ms = -1.0f;
+        rc = trial(ms);
+        if (rc == TEUK_OK && ms >= 0.0f && ms < best_all) {
+            best_all = ms;
+            best_ks = ks;
+            best_tr = b->tr;
+        }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    if (rc != TEUK_OK) return rc;
+    b->ks = best_ks;
+    b->tr = best_tr;
+    if (rc != TEUK_OK) {
+        batch_layout(b);
+        return rc;
+    }
     int r = batch_layout(b);
     if (r != TEUK_OK) return r;
     for (teuk_ctx *c : b->c) {
@@ -1568,6 +1616,33 @@ int teuk_batch_autotune(teuk_batch *b, int trial_steps, void *stream)
     }
     BCK(cudaStreamSynchronize(st), "autotune sync");
     return TEUK_OK;
+}
+
+int teuk_batch_steps_per_launch(const teuk_batch *b, int *steps_per_launch)
+{
+    if (!b) return TEUK_E_STATE;
+    if (steps_per_launch) *steps_per_launch = b->ks;
+    return TEUK_OK;
+}
+
+int teuk_batch_set_steps_per_launch(teuk_batch *b, int steps_per_launch)
+{
+    if (!b) return TEUK_E_STATE;
+    if (steps_per_launch != 1 && steps_per_launch != 2)
+        return bset_err(b, TEUK_E_INVAL, "steps_per_launch must be 1 or 2%s");
+    if (!split_batch_available(b->seg, steps_per_launch))
+        return bset_err(b, TEUK_E_INVAL, "two steps per launch need Ntheta <= 256%s");
+    const int old = b->ks;
+    b->ks = steps_per_launch;
+    int r = batch_layout(b);
+    if (r != TEUK_OK) {
+        b->ks = old;
+        char keep[512];
+        memcpy(keep, b->err, sizeof(keep));
+        batch_layout(b);
+        memcpy(b->err, keep, sizeof(keep));
+    }
+    return r;
 }
 
 const char *teuk_batch_last_error(const teuk_batch *b) { return b ? b->err : g_init_err; }

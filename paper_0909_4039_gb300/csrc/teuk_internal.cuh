@@ -227,11 +227,14 @@ cudaError_t launch_split_step2(const StepParams<T> &p, int threads, size_t smem,
 // Batched split step: one CTA of 256 threads per entry of the tile list
 // (instance, tile); params[instance] describes the instance's step.  Every
 // instance must use the theta segment `seg` (implicit_seg of its Ntheta).
+// ks = 2 advances every instance by two steps per launch (no first steps);
+// it exists for segments of up to 8 elements only (split_batch_available).
+bool split_batch_available(int seg, int ks);
 template <typename T>
-int split_batch_blocks_per_sm(int seg, size_t smem);
+int split_batch_blocks_per_sm(int seg, size_t smem, int ks);
 template <typename T>
 cudaError_t launch_split_batch(const StepParams<T> *d_params, const int2 *d_tiles, int ntiles, int seg, size_t smem,
-                               cudaStream_t st);
+                               int ks, cudaStream_t st);
 int implicit_group(int Nth);            // threads per theta row
 int implicit_seg(int Nth);              // theta elements per thread
 constexpr int kSegNarrow = 4;           // theta elements per thread (Ntheta <= 128)

@@ -1148,8 +1148,8 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && S <= 4) ? 2 : 1) k_spl
 // computes the tile.  One launch advances every instance of the batch by one
 // step; the instances may differ in every parameter (grid, spin, mode,
 // source, tile height) as long as they share the state precision and the
-// theta segment S.
-template <typename T, int S>
+// theta segment S.  KS = 2: two time steps per launch, as k_split_step2.
+template <typename T, int S, int KS>
 __global__ void __launch_bounds__(256, (sizeof(T) == 4 && S <= 4) ? 2 : 1)
     k_split_batch(const StepParams<T> *params, const int2 *tiles)
 {
@@ -1159,7 +1159,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && S <= 4) ? 2 : 1)
     if (threadIdx.x < sizeof(StepParams<T>) / 4)
         reinterpret_cast<int *>(&sp)[threadIdx.x] = reinterpret_cast<const int *>(params + e.x)[threadIdx.x];
     __syncthreads();
-    split_tile<T, S, 1>(sp, e.y, (sp.Nr + sp.tile_rows - 1) / sp.tile_rows);
+    split_tile<T, S, KS>(sp, e.y, (sp.Nr + sp.tile_rows - 1) / sp.tile_rows);
 }
 
 __device__ __forceinline__ void mbar_arrive(unsigned long long *m)
@@ -2084,16 +2084,21 @@ cudaError_t launch_split_persist(const StepParams<T> &p, int nc, int grid, size_
 }
 
 template <typename T>
-static void (*batch_fn(int seg))(const StepParams<T> *, const int2 *)
+static void (*batch_fn(int seg, int ks))(const StepParams<T> *, const int2 *)
 {
-    return seg == kSegNarrow ? k_split_batch<T, kSegNarrow>
-                             : (seg == kSeg ? k_split_batch<T, kSeg> : k_split_batch<T, kSegWide>);
+    // two steps per launch for segments of up to 8 elements (Ntheta <= 256)
+    if (ks == 2) return seg == kSegNarrow ? k_split_batch<T, kSegNarrow, 2> : (seg == kSeg ? k_split_batch<T, kSeg, 2> : nullptr);
+    return seg == kSegNarrow ? k_split_batch<T, kSegNarrow, 1>
+                             : (seg == kSeg ? k_split_batch<T, kSeg, 1> : k_split_batch<T, kSegWide, 1>);
 }
 
+bool split_batch_available(int seg, int ks) { return ks == 1 || (ks == 2 && seg != kSegWide); }
+
 template <typename T>
-int split_batch_blocks_per_sm(int seg, size_t smem)
+int split_batch_blocks_per_sm(int seg, size_t smem, int ks)
 {
-    auto fn = batch_fn<T>(seg);
+    auto fn = batch_fn<T>(seg, ks);
+    if (!fn) return 0;
     if (smem_limit_max((const void *)fn) != cudaSuccess) {
         cudaGetLastError();
         return 0;
@@ -2108,9 +2113,10 @@ int split_batch_blocks_per_sm(int seg, size_t smem)
 
 template <typename T>
 cudaError_t launch_split_batch(const StepParams<T> *d_params, const int2 *d_tiles, int ntiles, int seg, size_t smem,
-                               cudaStream_t st)
+                               int ks, cudaStream_t st)
 {
-    auto fn = batch_fn<T>(seg);
+    auto fn = batch_fn<T>(seg, ks);
+    if (!fn) return cudaErrorInvalidValue;
     cudaError_t e = smem_limit_max((const void *)fn);
     if (e != cudaSuccess) return e;
     if (ntiles < 1) return cudaSuccess;
@@ -2302,10 +2308,11 @@ template cudaError_t launch_dot<float>(const float2 *, const float2 *, const flo
                                        cudaStream_t);
 template cudaError_t launch_dot<double>(const double2 *, const double2 *, const double2 *, size_t, double *,
                                         double2 *, cudaStream_t);
-template int split_batch_blocks_per_sm<float>(int, size_t);
-template int split_batch_blocks_per_sm<double>(int, size_t);
-template cudaError_t launch_split_batch<float>(const StepParams<float> *, const int2 *, int, int, size_t, cudaStream_t);
-template cudaError_t launch_split_batch<double>(const StepParams<double> *, const int2 *, int, int, size_t,
+template int split_batch_blocks_per_sm<float>(int, size_t, int);
+template int split_batch_blocks_per_sm<double>(int, size_t, int);
+template cudaError_t launch_split_batch<float>(const StepParams<float> *, const int2 *, int, int, size_t, int,
+                                               cudaStream_t);
+template cudaError_t launch_split_batch<double>(const StepParams<double> *, const int2 *, int, int, size_t, int,
                                                 cudaStream_t);
 template bool persist_available<float>(int, int);
 template bool persist_available<double>(int, int);

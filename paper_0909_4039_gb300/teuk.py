@@ -40,7 +40,8 @@ EXPORTED = [
     "teuk_tiling", "teuk_autotune", "teuk_set_tiling", "teuk_literal_step_static",
     "teuk_kernel_config", "teuk_set_persistent", "teuk_autotune_cold",
     "teuk_batch_workspace_bytes", "teuk_batch_create", "teuk_batch_step", "teuk_batch_tiling",
-    "teuk_batch_set_tiling", "teuk_batch_autotune", "teuk_batch_last_error", "teuk_batch_destroy",
+    "teuk_batch_set_tiling", "teuk_batch_steps_per_launch", "teuk_batch_set_steps_per_launch",
+    "teuk_batch_autotune", "teuk_batch_last_error", "teuk_batch_destroy",
     "teuk_apply_step", "teuk_apply_sample", "teuk_adjoint_workspace_bytes", "teuk_adjoint_step", "teuk_dot",
     "teuk_set_tiling_steps",
 ]
@@ -136,12 +137,15 @@ def lib(load_only: bool = False):
     L.teuk_batch_step.argtypes = [vp, i64, vp]
     L.teuk_batch_tiling.argtypes = [vp, ip, ip, sz]
     L.teuk_batch_set_tiling.argtypes = [vp, ip]
+    L.teuk_batch_steps_per_launch.argtypes = [vp, ip]
+    L.teuk_batch_set_steps_per_launch.argtypes = [vp, ctypes.c_int]
     L.teuk_batch_autotune.argtypes = [vp, ctypes.c_int, vp]
     L.teuk_batch_last_error.argtypes = [vp]
     L.teuk_batch_last_error.restype = ctypes.c_char_p
     L.teuk_batch_destroy.argtypes = [vp]
     for name in ("teuk_batch_workspace_bytes", "teuk_batch_create", "teuk_batch_step", "teuk_batch_tiling",
-                 "teuk_batch_set_tiling", "teuk_batch_autotune", "teuk_batch_destroy"):
+                 "teuk_batch_set_tiling", "teuk_batch_steps_per_launch", "teuk_batch_set_steps_per_launch",
+                 "teuk_batch_autotune", "teuk_batch_destroy"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -430,9 +434,17 @@ class Batch:
         tot = ctypes.c_int()
         sm = ctypes.c_size_t()
         _bcheck(lib().teuk_batch_tiling(self.batch, tr, ctypes.byref(tot), ctypes.byref(sm)), self.batch)
-        return {"tile_rows": list(tr), "total_tiles": tot.value, "smem_bytes": sm.value}
+        ks = ctypes.c_int()
+        _bcheck(lib().teuk_batch_steps_per_launch(self.batch, ctypes.byref(ks)), self.batch)
+        return {"tile_rows": list(tr), "total_tiles": tot.value, "smem_bytes": sm.value,
+                "steps_per_launch": ks.value}
 
-    def set_tiling(self, tile_rows):
+    def set_tiling(self, tile_rows=None, steps_per_launch=None):
+        """Tile height per instance and/or time steps per launch (1 or 2)."""
+        if steps_per_launch is not None:
+            _bcheck(lib().teuk_batch_set_steps_per_launch(self.batch, int(steps_per_launch)), self.batch)
+        if tile_rows is None:
+            return
         n = len(self.steppers)
         if len(tile_rows) != n:
             raise ValueError("one tile height per instance")

@@ -43,12 +43,13 @@ def _batch(steppers):
     return teuk.Batch(steppers)
 
 
+@pytest.mark.parametrize("ks,nsteps", [(1, 130), (2, 130), (2, 41)])
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
-def test_batch_equals_instances_stepped_alone(precision):
-    """130 batched steps (first step, two graph replays of 64, a remainder)
+def test_batch_equals_instances_stepped_alone(precision, ks, nsteps):
+    """Batched steps (first step, graph replays of 64 steps, a remainder;
+    one or two steps per launch, an odd remainder as a one-step launch)
     give every instance the state and waveform it gets alone."""
     ws = _mixed()
-    nsteps = 130
     u0 = [inputs.random_state(w.Nr, w.Ntheta, seed=100 + k) for k, w in enumerate(ws)]
     alone = []
     for w, u in zip(ws, u0):
@@ -61,6 +62,8 @@ def test_batch_equals_instances_stepped_alone(precision):
     for st, u in zip(sts, u0):
         st.set_state(u, 0)
     b = _batch(sts)
+    b.set_tiling(steps_per_launch=ks)
+    assert b.tiling()["steps_per_launch"] == ks
     b.step(nsteps)
     b.synchronize()
     for k, st in enumerate(sts):
@@ -103,15 +106,16 @@ def test_batch_mixed_first_steps_tiling_and_autotune():
     u0 = [inputs.random_state(w.Nr, w.Ntheta, seed=300 + k) for k, w in enumerate(ws)]
     pre = [3 if k % 2 else 0 for k in range(len(ws))]
     results = []
-    for mode in ("default", "manual", "autotune"):
+    for mode in ("default", "manual", "manual-one-step", "autotune"):
         sts = [gpu_stepper(w, "fp32", wave_capacity=64) for w in ws]
         b = _batch(sts)
-        if mode == "manual":
-            b.set_tiling([7 if w.Ntheta >= 64 else 30 for w in ws])
+        assert b.tiling()["steps_per_launch"] == 2
+        if mode.startswith("manual"):
+            b.set_tiling([7 if w.Ntheta >= 64 else 30 for w in ws], 1 if mode.endswith("one-step") else None)
             assert b.tiling()["tile_rows"] == [7 if w.Ntheta >= 64 else 30 for w in ws]
         elif mode == "autotune":
             tr = b.autotune(3)
-            assert all(t >= 1 for t in tr)
+            assert all(t >= 1 for t in tr) and b.tiling()["steps_per_launch"] in (1, 2)
             for st in sts:
                 assert st.current_step == 0 and np.abs(st.get_state()).max() == 0.0
         for st, u, k in zip(sts, u0, pre):
@@ -147,8 +151,20 @@ def test_batch_rejects_incompatible_instances():
         assert b.tiling() == before
     b.set_tiling([31])
     assert b.tiling()["tile_rows"] == [31]
+    for bad in (0, 3):
+        with pytest.raises(teuk.TeukError):
+            b.set_tiling(steps_per_launch=bad)
+        assert b.tiling()["steps_per_launch"] == 2
     b.close()
-    for st in (a, b64, wide, lit):
+    # Ntheta > 256: one step per launch only
+    wider = gpu_stepper(w.with_(Ntheta=300), "fp32", wave_capacity=8)
+    bw = teuk.Batch([wider])
+    assert bw.tiling()["steps_per_launch"] == 1
+    with pytest.raises(teuk.TeukError):
+        bw.set_tiling(steps_per_launch=2)
+    assert bw.tiling()["steps_per_launch"] == 1
+    bw.close()
+    for st in (a, b64, wide, lit, wider):
         st.close()
 
 
