@@ -427,8 +427,13 @@ def run_native_batch(args):
     pts = sum(allw[k].points for k in mine)
     b = teuk.Batch(sts, stream=stream) if sts else None
     tiling = {}
+    tiling_source = ("teuk_batch_autotune (one and two steps per launch, each a coordinate descent over the "
+                     "Ntheta classes, 5 launches per trial)")
     if b is not None:
-        b.autotune(5)
+        if args.no_autotune:
+            tiling_source = "batch defaults (two steps per launch where offered, model tile heights)"
+        else:
+            b.autotune(5)
         tiling = b.tiling()
     ks = tiling.get("steps_per_launch", 1)
 
@@ -504,8 +509,7 @@ def run_native_batch(args):
                    "l2": f"not flushed: the batch's states ({2 * pts_all * bytes_per_pt / 2 / 1e9:.1f} GB) "
                          f"exceed the 129 MB L2",
                    "parallelism": f"instances split over {ws} rank(s) by points", "tiling": tiling,
-                   "tiling_source": "teuk_batch_autotune (one and two steps per launch, each a coordinate "
-                                    "descent over the Ntheta classes, 5 launches per trial)",
+                   "tiling_source": tiling_source,
                    "iteration": "one timed iteration = one launch = steps_per_launch time steps"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": None, "kernel": "k_split_batch", "bytes_per_point": bytes_per_pt,
@@ -643,6 +647,8 @@ def main():
     ap.add_argument("--consumers", type=int, default=480, help="consumer threads for --kernel persistent")
     ap.add_argument("--steps-per-launch", type=int, choices=[1, 2], default=1,
                     help="time steps per launch for --kernel tiled")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="batch64 / long8: keep the batch's default configuration")
     ap.add_argument("--time-steps", type=int, default=0,
                     help="adjoint4096: time steps per gradient (default: the workload's 8000)")
     ap.add_argument("--workload", choices=["single", "batch64", "long8", "adjoint4096"], default="single",
