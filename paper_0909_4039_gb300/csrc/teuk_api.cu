@@ -80,6 +80,8 @@ Layout make_layout(const teuk_grid_desc &d)
     L.thT = f32 ? off : L.th64; if (f32) off = align256(off + ts / 2);
     L.piv = off; off = align256(off + c2 * N * Nr);
     L.pivh = off; off = align256(off + c2 * N * Nr);
+    L.plan = off; off = align256(off + sizeof(int) * Nr);
+    L.planh = off; off = align256(off + sizeof(int) * Nr);
     L.patch = off; off = align256(off + c2 * 2 * N * patch_rows);
     L.patchu = off; off = align256(off + c2 * 2 * N * patch_rows);
     L.w = off; off = align256(off + sizeof(double) * N);
@@ -390,6 +392,7 @@ StepParams<T> make_params(const teuk_ctx *c, int in_level)
         K.h1g = (T)((1.0 - kGamma) * h);
         K.h12g = (T)((1.0 - 2.0 * kGamma) * h);
         K.piv = (const c2 *)(c->coef + (k ? c->L.pivh : c->L.piv));
+        K.plan = (const int *)(c->coef + (k ? c->L.planh : c->L.plan));
     }
     p.dt64 = c->dt;
     p.mOmega = c->mOmega;
@@ -422,6 +425,17 @@ cudaError_t launch_split(const teuk_ctx *c, const StepParams<T> &p, cudaStream_t
 {
     if (c->persist) return launch_split_persist<T>(p, c->nc, c->grid, c->persist_smem, st);
     return launch_split_step<T>(p, c->threads, c->smem, st);
+}
+
+// Scan levels of the implicit solves of every row, for the steps dt and
+// dt/2 (split scheme): computed once from the coefficients and pivots, read
+// by every step kernel.
+cudaError_t compute_plans(teuk_ctx *c, cudaStream_t st)
+{
+    if (c->d.scheme != TEUK_SCHEME_SPLIT) return cudaSuccess;
+    int *pf = (int *)(c->coef + c->L.plan), *ph = (int *)(c->coef + c->L.planh);
+    if (c->d.precision == TEUK_FP32) return launch_scan_plans<float>(make_params<float>(c, 0), pf, ph, st);
+    return launch_scan_plans<double>(make_params<double>(c, 0), pf, ph, st);
 }
 
 cudaError_t launch_one(teuk_ctx *c, int in_level, cudaStream_t st)
@@ -610,6 +624,7 @@ int teuk_init_grid(const teuk_grid_desc *desc, void *d_state, void *d_coef, void
         if ((e = cudaMemsetAsync(c->coef, 0, c->L.total, st)) != cudaSuccess) { r2 = cuda_err(c, e, "zero coef"); break; }
         if ((e = cudaMemsetAsync(c->wave, 0, sizeof(double2) * (size_t)(d.Ntheta + 1) * (size_t)wave_capacity, st)) != cudaSuccess) { r2 = cuda_err(c, e, "zero wave"); break; }
         if ((e = launch_coef_tables(d, drs, dt, c->coef, c->L, st)) != cudaSuccess) { r2 = cuda_err(c, e, "coefficient kernels"); break; }
+        if ((e = compute_plans(c, st)) != cudaSuccess) { r2 = cuda_err(c, e, "scan plans"); break; }
         if ((e = launch_set_ctl(c->coef, c->L, 0, 1, st)) != cudaSuccess) { r2 = cuda_err(c, e, "control block"); break; }
         if ((e = extract_current(c, st)) != cudaSuccess) { r2 = cuda_err(c, e, "extract"); break; }
         if ((e = cudaStreamSynchronize(st)) != cudaSuccess) { r2 = cuda_err(c, e, "init sync"); break; }
@@ -687,6 +702,7 @@ int teuk_set_weights(teuk_ctx *c, const double *w)
         CK(cudaMemcpy(dw, w, sizeof(double) * (size_t)c->d.Ntheta, cudaMemcpyHostToDevice), "weights copy");
     } else {
         CK(launch_coef_tables(c->d, c->drs, c->dt, c->coef, c->L, 0), "default weights");
+        CK(compute_plans(c, 0), "scan plans");
         CK(cudaDeviceSynchronize(), "weights sync");
     }
     return TEUK_OK;

@@ -64,6 +64,7 @@ template <typename T> struct ImpConst {
     typedef typename V2<T>::t c2;
     T gh, gh2, h1g, h12g;    // gamma h, (gamma h)^2, (1-gamma) h, (1-2 gamma) h
     const c2 *piv;           // Thomas pivots of the stage matrix, [Nr][Nth]
+    const int *plan;         // scan levels of each row's solves, [Nr]: forward | backward << 8
 };
 
 // Everything a step kernel needs, passed by value.
@@ -156,7 +157,7 @@ __host__ __device__ inline PersistSmem persist_smem_plan(int R, int N, int tsize
 
 // ---------------------------------------------------------------- host side
 struct Layout {
-    size_t rtab64, rtabT, th64, thT, piv, pivh, patch, patchu, w, ctl, staging, scratch, total;
+    size_t rtab64, rtabT, th64, thT, piv, pivh, plan, planh, patch, patchu, w, ctl, staging, scratch, total;
     size_t staging_elems;    // complex doubles that fit in the staging area
 };
 
@@ -224,6 +225,12 @@ template <typename T>
 int split2_blocks_per_sm(int Nth, int threads, size_t smem);
 template <typename T>
 cudaError_t launch_split_step2(const StepParams<T> &p, int threads, size_t smem, cudaStream_t st);
+// Scan levels of every row's implicit solves for the steps dt (p.full) and
+// dt/2 (p.half), written to plan_full / plan_half ([Nr] ints each).
+template <typename T>
+cudaError_t launch_scan_plans(const StepParams<T> &p, int *plan_full, int *plan_half, cudaStream_t st);
+// Largest tile height of the split kernels (rows of the per-tile plan copy).
+constexpr int kMaxTileRows = 254;
 // Batched split step: one CTA of 256 threads per entry of the tile list
 // (instance, tile); params[instance] describes the instance's step.  Every
 // instance must use the theta segment `seg` (implicit_seg of its Ntheta).

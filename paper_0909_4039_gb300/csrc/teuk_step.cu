@@ -385,16 +385,40 @@ __device__ __forceinline__ ScanPlan<T> scan_plan(const typename V2<T>::t (&fm)[S
     return P;
 }
 
+// The same plan from the stored levels of the row (forward | backward << 8,
+// computed once by scan_plan in k_scan_plans); the levels are a function
+// of the row's coefficients alone, so the stored and the recomputed plans
+// agree.  Every lane of the warp calls this (warp-wide level counts).
+template <typename T, int S>
+__device__ __forceinline__ ScanPlan<T> scan_plan_stored(const typename V2<T>::t (&fm)[S],
+                                                        const typename V2<T>::t (&bm)[S], int plan)
+{
+    typedef typename V2<T>::t c2;
+    ScanPlan<T> P;
+    P.Af0 = cmk<c2>(T(1), T(0));
+    P.Ab0 = P.Af0;
+#pragma unroll
+    for (int k = 0; k < S; ++k) P.Af0 = cmul(cmk<c2>(-fm[k].x, -fm[k].y), P.Af0);
+#pragma unroll
+    for (int k = S - 1; k >= 0; --k) P.Ab0 = cmul(cmk<c2>(-bm[k].x, -bm[k].y), P.Ab0);
+    P.nf = plan & 0xff;
+    P.nb = (plan >> 8) & 0xff;
+    P.nfw = (int)__reduce_max_sync(0xffffffffu, (unsigned)P.nf);
+    P.nbw = (int)__reduce_max_sync(0xffffffffu, (unsigned)P.nb);
+    return P;
+}
+
 // w <- x with forward t_j = w_j - fm_j t_{j-1} (t_{-1} = 0), y_j = pm_j t_j,
 // backward x_j = y_j - bm_j x_{j+1} (x_N = 0), each affine recurrence as a
-// segmented scan over the G lanes of the row.
+// segmented scan over the G lanes of the row.  The scan levels run in a
+// rolled loop over the planned count (usually one): five unrolled levels
+// behind runtime guards cost about 8 % of a step.
 template <typename T, int S>
 __device__ __forceinline__ void seg_solve(typename V2<T>::t (&w)[S], const typename V2<T>::t (&fm)[S],
                                           const typename V2<T>::t (&pm)[S], const typename V2<T>::t (&bm)[S],
                                           const ScanPlan<T> &P, int g, int G)
 {
     typedef typename V2<T>::t c2;
-    constexpr int LOGMAX = 5;
     const c2 zero = cmk<c2>(T(0), T(0));
     const c2 one = cmk<c2>(T(1), T(0));
     c2 B = zero;
@@ -402,16 +426,14 @@ __device__ __forceinline__ void seg_solve(typename V2<T>::t (&w)[S], const typen
     for (int k = 0; k < S; ++k) B = cfnma(fm[k], B, w[k]);
     {
         c2 A = P.Af0;
-#pragma unroll
-        for (int l = 0; l < LOGMAX; ++l) {
-            if (l < P.nfw) {
-                const int d = 1 << l;
-                c2 Bo = shfl_up_c(B, d, G), Ao = one;
-                if (l + 1 < P.nfw) Ao = shfl_up_c(A, d, G);
-                if (l < P.nf && g >= d) {
-                    B = cfma(A, Bo, B);
-                    if (l + 1 < P.nf) A = cmul(A, Ao);
-                }
+#pragma unroll 1
+        for (int l = 0; l < P.nfw; ++l) {
+            const int d = 1 << l;
+            c2 Bo = shfl_up_c(B, d, G), Ao = one;
+            if (l + 1 < P.nfw) Ao = shfl_up_c(A, d, G);
+            if (l < P.nf && g >= d) {
+                B = cfma(A, Bo, B);
+                if (l + 1 < P.nf) A = cmul(A, Ao);
             }
         }
     }
@@ -427,16 +449,14 @@ __device__ __forceinline__ void seg_solve(typename V2<T>::t (&w)[S], const typen
     for (int k = S - 1; k >= 0; --k) B = cfnma(bm[k], B, w[k]);
     {
         c2 A = P.Ab0;
-#pragma unroll
-        for (int l = 0; l < LOGMAX; ++l) {
-            if (l < P.nbw) {
-                const int d = 1 << l;
-                c2 Bo = shfl_down_c(B, d, G), Ao = one;
-                if (l + 1 < P.nbw) Ao = shfl_down_c(A, d, G);
-                if (l < P.nb && g + d < G) {
-                    B = cfma(A, Bo, B);
-                    if (l + 1 < P.nb) A = cmul(A, Ao);
-                }
+#pragma unroll 1
+        for (int l = 0; l < P.nbw; ++l) {
+            const int d = 1 << l;
+            c2 Bo = shfl_down_c(B, d, G), Ao = one;
+            if (l + 1 < P.nbw) Ao = shfl_down_c(A, d, G);
+            if (l < P.nb && g + d < G) {
+                B = cfma(A, Bo, B);
+                if (l + 1 < P.nb) A = cmul(A, Ao);
             }
         }
     }
@@ -470,10 +490,11 @@ __device__ __forceinline__ void row_store(typename V2<T>::t *phi, typename V2<T>
     }
 }
 
+// plan: the row's stored scan levels (K.plan), 0 for a row that is not active.
 template <typename T, int S>
 __device__ void implicit_row_group(const ImpConst<T> &K, typename V2<T>::t *phi, typename V2<T>::t *pi,
                                    const typename V2<T>::t *prow, const T *f, const T *th, int N, bool active,
-                                   bool in_tile, int g, int G, bool vec)
+                                   bool in_tile, int g, int G, bool vec, int plan)
 {
     typedef typename V2<T>::t c2;
     const c2 zero = cmk<c2>(T(0), T(0));
@@ -486,7 +507,7 @@ __device__ void implicit_row_group(const ImpConst<T> &K, typename V2<T>::t *phi,
     RowCoef<T, S> C;
     c2 w[S], y[S];
     row_load<T, S>(K, phi, pi, prow, f, th, N, len, j0, G, vec, C, w, y);
-    const ScanPlan<T> P = scan_plan<T, S>(C.m, C.fk, g, G);
+    const ScanPlan<T> P = scan_plan_stored<T, S>(C.m, C.fk, active ? plan : 0);
 
     // (B + c0rad) U_Phi for the whole segment
     auto apply_B = [&](c2 *bf) {
@@ -902,6 +923,7 @@ __device__ __forceinline__ void split_tile(const StepParams<T> &p, int tile, int
     __shared__ double2 sph[2 * KS];
     __shared__ long long s_n;
     __shared__ __align__(8) unsigned long long s_mbar[kMaxChunks];
+    __shared__ int s_plan[kMaxTileRows + 4];   // stored scan levels of the tile rows
     const int Nr = p.Nr, N = p.Nth, TR = p.tile_rows, R = TR + 2 * KS, P = p.pitch;
     const int tid = threadIdx.x, NT = blockDim.x;
     const int i0 = tile * TR, g0 = i0 - KS;
@@ -1012,6 +1034,12 @@ __device__ __forceinline__ void split_tile(const StepParams<T> &p, int tile, int
         }
     }
     for (int idx = tid; idx < NTF * N; idx += NT) sTh[idx] = p.thtab[idx];
+    // Every implicit step of the launch uses K: with two steps per launch K
+    // is the full step (the launcher refuses first steps and state outputs).
+    for (int lr = tid; lr < R; lr += NT) {
+        const int gi = g0 + lr;
+        s_plan[lr] = (gi >= 0 && gi < Nr) ? K.plan[gi] : 0;
+    }
     __syncthreads();
     const int g = tid % G;
     const bool vec = p.vec != 0;
@@ -1030,7 +1058,7 @@ __device__ __forceinline__ void split_tile(const StepParams<T> &p, int tile, int
             bool active = in_tile && gi >= 1 && gi <= Nr - 2;
             int lrc = in_tile ? lr : lo;
             implicit_row_group<T, S>(Ki, sPhi + lrc * P, sPi + lrc * P, sPiv + lrc * P, sRt + 2 * lrc * NRF, sTh, N,
-                                     active, in_tile, g, G, vec);
+                                     active, in_tile, g, G, vec, s_plan[lrc]);
         }
     };
     // physical sample u = C_{dt/2} s of the extraction row (tile row lx) in
@@ -1041,7 +1069,7 @@ __device__ __forceinline__ void split_tile(const StepParams<T> &p, int tile, int
             bool mine = tid < G;
             bool active = mine && p.i_ext >= 1 && p.i_ext <= Nr - 2;
             implicit_row_group<T, S>(p.half, rf, rg, p.half.piv + (size_t)p.i_ext * N, sRt + 2 * lx * NRF, sTh, N,
-                                     active, mine, tid % G, G, vec);
+                                     active, mine, tid % G, G, vec, p.half.plan[p.i_ext]);
             __syncwarp();
             extract_warp<T>(p, rf, slot);
         }
@@ -1340,7 +1368,7 @@ __global__ void __maxnreg__(PersistRegs<NC>::v) k_split_persist(const StepParams
             bool active = in_tile && gi >= 1 && gi <= Nr - 2;
             int lrc = in_tile ? lr : 0;
             implicit_row_group<T, S>(K, sPhi + lrc * P, sPi + lrc * P, sPiv + lrc * P, sRt + 2 * lrc * NRF, sTh, N,
-                                     active, in_tile, g, G, vec);
+                                     active, in_tile, g, G, vec, active ? K.plan[gi] : 0);
         }
         bar();
         // The extraction row (its r-table entry and, after the Lax-Wendroff
@@ -1366,7 +1394,7 @@ __global__ void __maxnreg__(PersistRegs<NC>::v) k_split_persist(const StepParams
             bool mine = tid < G;
             bool active = mine && p.i_ext >= 1 && p.i_ext <= Nr - 2;
             implicit_row_group<T, S>(p.half, xPhi, xPi, p.half.piv + (size_t)p.i_ext * N, xF, sTh, N, active, mine,
-                                     tid % G, G, vec);
+                                     tid % G, G, vec, p.half.plan[p.i_ext]);
             __syncwarp();
             extract_warp<T>(p, xPhi, s_n + 1);
         }
@@ -1396,6 +1424,36 @@ __device__ double2 sample_warp(const StepParams<T> &p, const typename V2<T>::t *
 
 // h = E u with u = s (physical) or u = C_{dt/2} s on the extraction row; one
 // warp.  The sum is the one the step kernels write to the waveform buffer.
+// Stored scan plans: the levels scan_plan chooses for every row of the
+// grid and both implicit steps (dt and dt/2), from the same coefficient path
+// as implicit_row_group (r table, theta tables and pivots as the step
+// kernels stage them).  One CTA of 256 threads covers 256 / G rows.
+template <typename T, int S>
+__global__ void __launch_bounds__(256) k_scan_plans(const StepParams<T> p, int *plan_full, int *plan_half)
+{
+    typedef typename V2<T>::t c2;
+    const int N = p.Nth, Nr = p.Nr, G = p.group;
+    const int tid = threadIdx.x, g = tid % G;
+    const int gi = (int)blockIdx.x * ((int)blockDim.x / G) + tid / G;
+    const bool in_grid = gi < Nr;
+    const bool active = in_grid && gi >= 1 && gi <= Nr - 2;
+    const int gr = in_grid ? gi : 0;
+    const int j0 = g * S;
+    int len = N - j0;
+    len = len < 0 ? 0 : (len > S ? S : len);
+    if (!active) len = 0;
+    for (int h = 0; h < 2; ++h) {
+        const ImpConst<T> &K = h ? p.half : p.full;
+        const c2 *prow = K.piv + (size_t)gr * N;
+        RowCoef<T, S> C;
+        c2 w[S], y[S];
+        // the state rows are not needed: the pivot row stands in for them
+        row_load<T, S>(K, prow, prow, prow, p.rtab + (size_t)(2 * gr) * NRF, p.thtab, N, len, j0, G, p.vec != 0, C, w, y);
+        const ScanPlan<T> P = scan_plan<T, S>(C.m, C.fk, g, G);
+        if (in_grid && g == 0) (h ? plan_half : plan_full)[gi] = P.nf | (P.nb << 8);
+    }
+}
+
 template <typename T, int S>
 __global__ void __launch_bounds__(32) k_sample(const StepParams<T> p, const typename V2<T>::t *s, int physical,
                                                double2 *h_out)
@@ -1419,7 +1477,7 @@ __global__ void __launch_bounds__(32) k_sample(const StepParams<T> p, const type
         const bool mine = tid < G;
         const bool active = mine && i >= 1 && i <= Nr - 2;
         implicit_row_group<T, S>(p.half, xPhi, xPi, p.half.piv + (size_t)i * N, xF, xTh, N, active, mine, tid % G, G,
-                                 p.vec != 0);
+                                 p.vec != 0, p.half.plan[i]);
         __syncwarp();
     }
     double2 h = sample_warp<T>(p, xPhi);
@@ -2147,6 +2205,17 @@ cudaError_t launch_sample(const StepParams<T> &p, const typename V2<T>::t *s, in
 }
 
 template <typename T>
+cudaError_t launch_scan_plans(const StepParams<T> &p, int *plan_full, int *plan_half, cudaStream_t st)
+{
+    const int seg = implicit_seg(p.Nth);
+    auto fn = seg == kSegNarrow ? k_scan_plans<T, kSegNarrow>
+                                : (seg == kSeg ? k_scan_plans<T, kSeg> : k_scan_plans<T, kSegWide>);
+    const int rows = 256 / p.group;
+    fn<<<(p.Nr + rows - 1) / rows, 256, 0, st>>>(p, plan_full, plan_half);
+    return cudaGetLastError();
+}
+
+template <typename T>
 size_t adjoint_smem_bytes(int tile_rows, int Nth)
 {
     const size_t R = (size_t)tile_rows + 2;
@@ -2294,6 +2363,8 @@ cudaError_t launch_convert_from(int prec, const void *src, double2 *dst, size_t 
 
 template cudaError_t launch_apply_step<float>(const StepParams<float> &, int, size_t, cudaStream_t);
 template cudaError_t launch_apply_step<double>(const StepParams<double> &, int, size_t, cudaStream_t);
+template cudaError_t launch_scan_plans<float>(const StepParams<float> &, int *, int *, cudaStream_t);
+template cudaError_t launch_scan_plans<double>(const StepParams<double> &, int *, int *, cudaStream_t);
 template cudaError_t launch_sample<float>(const StepParams<float> &, const float2 *, int, double2 *, cudaStream_t);
 template cudaError_t launch_sample<double>(const StepParams<double> &, const double2 *, int, double2 *, cudaStream_t);
 template size_t adjoint_smem_bytes<float>(int, int);
