@@ -179,8 +179,9 @@ int teuk_kernel_config(const teuk_ctx *ctx, int *persistent, int *consumer_threa
  * device (tile heights of the tiled kernel with one or two steps per launch,
  * and tile height x consumer count of the persistent kernel) by a
  * wave-quantisation cost model, times the best four of each kind for
- * trial_steps launches each on this grid (CUDA events on `stream`), and keeps
- * the fastest per time step.  The trials overwrite the
+ * trial_steps launches each on this grid (CUDA events on `stream`), in two
+ * interleaved rounds, and keeps the fastest per time step (a candidate's
+ * better round).  The trials overwrite the
  * state: afterwards the field is zero at step 0 and the waveform ring buffer
  * is empty (the source and weights are kept).  Call it right after
  * teuk_init_grid / teuk_set_source.  Synchronous.  *tile_rows_out (may be
@@ -190,7 +191,8 @@ int teuk_autotune(teuk_ctx *ctx, int trial_steps, void *stream, int *tile_rows_o
 /* teuk_autotune for steps that start from a cold L2 (state larger than L2,
  * or a caller that evicts it between steps): before every timed trial step
  * the caller-owned device buffer d_flush (flush_bytes, larger than the L2)
- * is overwritten, outside the timed interval.  Same outcome otherwise. */
+ * is overwritten, outside the timed interval, and a round's score is the
+ * median of the single-launch times per step.  Same outcome otherwise. */
 int teuk_autotune_cold(teuk_ctx *ctx, int trial_steps, void *d_flush, size_t flush_bytes, void *stream,
                        int *tile_rows_out);
 

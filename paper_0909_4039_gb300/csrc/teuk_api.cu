@@ -9,6 +9,7 @@
 #include <string.h>
 
 #include <new>
+#include <algorithm>
 #include <vector>
 
 #include "teuk_internal.cuh"
@@ -314,7 +315,8 @@ int tile_candidates(teuk_ctx *c, TileCand *out, int maxn)
     const int nsm = sm_count();
     const long long Nr = c->d.Nr;
     int n = 0;
-    for (int TR = 2; TR <= 254 && n < maxn; ++TR) {
+    // one-row tiles are the only ones that fit for the widest FP64 rows
+    for (int TR = 1; TR <= kMaxTileRows && n < maxn; ++TR) {
         if (tiled_cand(c, TR, nsm, &out[n])) ++n;
         if (n < maxn && c->d.scheme == TEUK_SCHEME_SPLIT && tiled2_cand(c, TR, nsm, &out[n])) ++n;
         for (int nc : {384, 480})
@@ -927,43 +929,50 @@ static int autotune_impl(teuk_ctx *c, int trial_steps, void *flush, size_t flush
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0), "event");
     CK(cudaEventCreate(&e1), "event");
-    float best = 3.4e38f;
-    int bestk = -1;
+    // Two interleaved rounds over the candidates; a candidate's score is its
+    // better round, each round the median time per step over L2-flushed
+    // single launches (cold) or the mean over back-to-back launches.
+    std::vector<float> score(cand.size(), 3.4e38f), per;
     cudaError_t e = cudaSuccess;
-    for (size_t k = 0; k < cand.size() && e == cudaSuccess; ++k) {
-        if (!apply_cand(c, cand[k])) continue;
-        c->shifted = 1;
-        int lev = c->cur, ku = 0, steps = 0;
-        for (int w = 0; w < 3 && e == cudaSuccess; ++w, lev ^= 1) e = launch_unit(c, lev, st, &ku);
-        float total = 0.0f;
-        if (flush) {
-            for (int w = 0; w < trial_steps && e == cudaSuccess; ++w, lev ^= 1) {
-                float ms = 0.0f;
-                e = cudaMemsetAsync(flush, w & 0xff, flush_bytes, st);
+    for (int round = 0; round < 2 && e == cudaSuccess; ++round)
+        for (size_t k = 0; k < cand.size() && e == cudaSuccess; ++k) {
+            if (!apply_cand(c, cand[k])) continue;
+            c->shifted = 1;
+            int lev = c->cur, ku = 0, steps = 0;
+            for (int w = 0; w < 3 && e == cudaSuccess; ++w, lev ^= 1) e = launch_unit(c, lev, st, &ku);
+            float t = 0.0f;
+            if (flush) {
+                per.clear();
+                for (int w = 0; w < trial_steps && e == cudaSuccess; ++w, lev ^= 1) {
+                    float ms = 0.0f;
+                    e = cudaMemsetAsync(flush, w & 0xff, flush_bytes, st);
+                    if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+                    if (e == cudaSuccess) e = launch_unit(c, lev, st, &ku);
+                    if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+                    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+                    if (e == cudaSuccess && ku > 0) per.push_back(ms / (float)ku);
+                }
+                if (per.empty()) continue;
+                std::nth_element(per.begin(), per.begin() + per.size() / 2, per.end());
+                t = per[per.size() / 2];
+            } else {
                 if (e == cudaSuccess) e = cudaEventRecord(e0, st);
-                if (e == cudaSuccess) e = launch_unit(c, lev, st, &ku);
+                for (int w = 0; w < trial_steps && e == cudaSuccess; ++w, lev ^= 1) {
+                    e = launch_unit(c, lev, st, &ku);
+                    steps += ku;
+                }
                 if (e == cudaSuccess) e = cudaEventRecord(e1, st);
                 if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-                total += ms;
-                steps += ku;
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+                if (steps < 1) continue;
+                t /= (float)steps;   // time per step
             }
-        } else {
-            if (e == cudaSuccess) e = cudaEventRecord(e0, st);
-            for (int w = 0; w < trial_steps && e == cudaSuccess; ++w, lev ^= 1) {
-                e = launch_unit(c, lev, st, &ku);
-                steps += ku;
-            }
-            if (e == cudaSuccess) e = cudaEventRecord(e1, st);
-            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-            if (e == cudaSuccess) e = cudaEventElapsedTime(&total, e0, e1);
+            if (e == cudaSuccess && t < score[k]) score[k] = t;
         }
-        if (steps > 0) total /= (float)steps;   // time per step
-        if (e == cudaSuccess && total < best) {
-            best = total;
-            bestk = (int)k;
-        }
-    }
+    int bestk = -1;
+    for (size_t k = 0; k < cand.size(); ++k)
+        if (score[k] < 3.4e38f && (bestk < 0 || score[k] < score[bestk])) bestk = (int)k;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (e != cudaSuccess) return cuda_err(c, e, "autotune trial");

@@ -43,6 +43,8 @@ SMALL = [
     ("129x1", 129, 1, 0.5, 2, 30),
     ("3x8", 3, 8, 0.9, 2, 5),
     ("70x64", 70, 64, 0.95, 4, 20),
+    # the wide theta class (32 theta points per lane)
+    ("24x300", 24, 300, 0.6, 2, 6),
 ]
 
 
@@ -52,6 +54,22 @@ def test_small_grids_random_data_and_source(name, Nr, Nth, a, m, steps, precisio
     w = inputs.Workload(name, s=-2, m=m, a=a, Nr=Nr, Ntheta=Nth, rs_min=-20.0, rs_max=40.0, steps=steps,
                         r0=6.0, amp=0.7 - 0.4j, sig_r=1.0, sig_th=0.3, rs_ext=30.0)
     uo, ho, ug, hg = _run_both(w, precision, init_seed=Nr * 7 + Nth)
+    assert rel_l2(ug, uo) <= tol, rel_l2(ug, uo)
+    assert rel_l2(hg, ho) <= tol, rel_l2(hg, ho)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", FP64_TOL), ("fp32", 1e-3)])
+def test_widest_theta_rows(precision, tol):
+    """Ntheta = 1024, the largest the library takes.  In FP64 only one-row
+    tiles fit in shared memory (a tile row with its pivots is 48 KB, the
+    theta tables 64 KB), and the launch configuration must find them.  The
+    FP32 bound is looser than 1e-4: at dtheta = pi/1024 and dt = 3.3 the
+    implicit stage matrix has theta entries near 4e4, so the solve's
+    condition number (~1e4) times the FP32 unit roundoff (6e-8) allows
+    errors up to ~6e-4 after one step."""
+    w = inputs.Workload("10x1024", s=-2, m=1, a=0.3, Nr=10, Ntheta=1024, rs_min=-20.0, rs_max=40.0, steps=3,
+                        r0=6.0, amp=0.7 - 0.4j, sig_r=1.0, sig_th=0.3, rs_ext=30.0)
+    uo, ho, ug, hg = _run_both(w, precision, init_seed=11)
     assert rel_l2(ug, uo) <= tol, rel_l2(ug, uo)
     assert rel_l2(hg, ho) <= tol, rel_l2(hg, ho)
 
@@ -294,6 +312,7 @@ TWO_STEP = [
     (1000, 32, 60, 27),
     (150, 16, 10, 33),
     (257, 33, 9, 12),
+    (40, 300, 6, 9),
 ]
 
 
