@@ -143,6 +143,17 @@ int teuk_set_state(teuk_ctx *ctx, const void *src, int64_t step, void *stream);
  * device memory) and its step number to *step (may be NULL).  Synchronous. */
 int teuk_get_state(teuk_ctx *ctx, void *dst, int64_t *step, void *stream);
 
+/* Where the current state lives in the caller's d_state buffer: its byte
+ * offset (one of the two time levels), the level's size in bytes
+ * ([2][Nr][Ntheta] complex values of the state precision, Phi plane then
+ * Pi plane, theta fastest) and whether it holds the shifted split-scheme
+ * state s_n = C_{dt/2}^{-1} u_n (1) or the physical u_n (0).  The caller may
+ * read or overwrite rows of that level between steps, on the context's
+ * stream, e.g. the halo rows of an r* slab of a larger grid (Sec. 4's
+ * decomposition of the grid work); the next teuk_step reads them.  Any
+ * pointer may be NULL. */
+int teuk_state_level(const teuk_ctx *ctx, int64_t *offset_bytes, size_t *level_bytes, int *shifted);
+
 /* Advance nsteps >= 0 time steps on `stream` (asynchronous).  The step
  * counter lives on the device as well, so the launches can be captured in
  * a CUDA graph; long runs replay a cached graph of a fixed chunk of steps.

@@ -774,6 +774,15 @@ int teuk_get_state(teuk_ctx *c, void *dst, int64_t *step, void *stream)
     return TEUK_OK;
 }
 
+int teuk_state_level(const teuk_ctx *c, int64_t *offset_bytes, size_t *level_bytes, int *shifted)
+{
+    if (!c) return TEUK_E_STATE;
+    if (offset_bytes) *offset_bytes = (int64_t)c->cur * (int64_t)c->level_bytes;
+    if (level_bytes) *level_bytes = c->level_bytes;
+    if (shifted) *shifted = (c->d.scheme == TEUK_SCHEME_SPLIT && c->shifted) ? 1 : 0;
+    return TEUK_OK;
+}
+
 int teuk_step(teuk_ctx *c, int64_t nsteps, void *stream)
 {
     if (!c) return TEUK_E_STATE;

@@ -43,7 +43,7 @@ EXPORTED = [
     "teuk_batch_set_tiling", "teuk_batch_steps_per_launch", "teuk_batch_set_steps_per_launch",
     "teuk_batch_autotune", "teuk_batch_last_error", "teuk_batch_destroy",
     "teuk_apply_step", "teuk_apply_sample", "teuk_adjoint_workspace_bytes", "teuk_adjoint_step", "teuk_dot",
-    "teuk_set_tiling_steps",
+    "teuk_set_tiling_steps", "teuk_state_level",
 ]
 
 
@@ -98,6 +98,7 @@ def lib(load_only: bool = False):
     L.teuk_set_state.argtypes = [vp, vp, i64, vp]
     L.teuk_get_state.argtypes = [vp, vp, ctypes.POINTER(i64), vp]
     L.teuk_step.argtypes = [vp, i64, vp]
+    L.teuk_state_level.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_int)]
     L.teuk_extract_waveform.argtypes = [vp, i64, i64, dp, dp, vp]
     L.teuk_current_step.argtypes = [vp]
     L.teuk_current_step.restype = i64
@@ -119,6 +120,7 @@ def lib(load_only: bool = False):
     L.teuk_autotune_cold.argtypes = [vp, ctypes.c_int, vp, ctypes.c_size_t, vp, ctypes.POINTER(ctypes.c_int)]
     for name in ("teuk_workspace_bytes", "teuk_init_grid", "teuk_set_source", "teuk_set_weights",
                  "teuk_set_state", "teuk_get_state", "teuk_step", "teuk_extract_waveform", "teuk_destroy",
+                 "teuk_state_level",
                  "teuk_tiling", "teuk_autotune", "teuk_set_tiling", "teuk_literal_step_static",
                  "teuk_kernel_config", "teuk_set_persistent", "teuk_autotune_cold"):
         getattr(L, name).restype = ctypes.c_int
@@ -204,6 +206,15 @@ def teuk_get_state(ctx, dst_ptr: int, stream: int = 0) -> int:
 
 def teuk_step(ctx, nsteps: int, stream: int = 0):
     _check(lib().teuk_step(ctx, int(nsteps), stream), ctx)
+
+
+def teuk_state_level(ctx):
+    """(byte offset of the current level in d_state, level bytes, shifted)."""
+    off = ctypes.c_int64()
+    nb = ctypes.c_size_t()
+    sh = ctypes.c_int()
+    _check(lib().teuk_state_level(ctx, ctypes.byref(off), ctypes.byref(nb), ctypes.byref(sh)), ctx)
+    return off.value, nb.value, bool(sh.value)
 
 
 def teuk_extract_waveform(ctx, first_step: int, count: int, want_rows: bool = False, Ntheta: int = 0,
@@ -348,6 +359,17 @@ class Stepper:
 
     def step(self, n: int):
         teuk_step(self.ctx, n, self.sh)
+
+    def level_view(self):
+        """The current state level as a [2, Nr, Ntheta] complex tensor view of
+        d_state (complex64 for the FP32 state), and whether it is the shifted
+        split-scheme state.  Rows written through it are read by the next
+        step; order the writes on self.stream."""
+        import torch
+        off, nb, shifted = teuk_state_level(self.ctx)
+        dt = torch.complex64 if self.precision == "fp32" else torch.complex128
+        v = self.d_state[off:off + nb].view(dt).view(2, self.Nr, self.Ntheta)
+        return v, shifted
 
     def waveform(self, first: int, count: int, rows: bool = False):
         return teuk_extract_waveform(self.ctx, first, count, rows, self.Ntheta, self.sh)
