@@ -63,3 +63,32 @@ def test_slab_contexts_see_the_whole_grid_rstar():
     i_ext = int(round((40.0 + 64.0) / 0.5))
     assert sl.geoms[sl.owner].a <= i_ext < sl.geoms[sl.owner].b
     sl.close()
+
+
+def test_state_level_offset_and_shifted_flag():
+    """teuk_state_level: the level flips with every step launch, the state is
+    physical after set_state and shifted after a split step, and rows
+    written through the view are what the next step reads."""
+    from paper_0909_4039_gb300 import teuk
+    kw = _kw("fp64", Nr=65)
+    st = teuk.Stepper(**kw)
+    u0 = inputs.random_state(65, 32, seed=3)
+    import torch
+    st.set_state(u0, 0)
+    st.synchronize()
+    off0, nb, shifted = teuk.teuk_state_level(st.ctx)
+    assert not shifted and nb == 2 * 65 * 32 * 16 and off0 in (0, nb)
+    v, _ = st.level_view()
+    assert np.array_equal(v.cpu().numpy(), u0)          # the physical state, in place
+    st.step(1)
+    off1, _, shifted = teuk.teuk_state_level(st.ctx)
+    assert shifted and off1 != off0
+    # a zeroed level stays zero under the (linear, source-free) step; the
+    # writes are ordered after the step's stream and before the next step
+    st.synchronize()
+    v, _ = st.level_view()
+    v.zero_()
+    torch.cuda.synchronize()
+    st.step(3)
+    assert np.abs(st.get_state()).max() == 0.0
+    st.close()
