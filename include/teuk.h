@@ -49,7 +49,7 @@ extern "C" {
 #define TEUK_E_CUDA 2       /* a CUDA runtime call failed */
 #define TEUK_E_NONFINITE 3  /* a non-finite waveform sample was produced */
 #define TEUK_E_UNSTABLE 4   /* radial Courant number > 1, or literal scheme past its bound */
-#define TEUK_E_TIMEOUT 5    /* reserved for bounded device waits */
+#define TEUK_E_TIMEOUT 5    /* a bounded device wait on a tile copy gave up */
 #define TEUK_E_STATE 6      /* call out of order (e.g. no context) */
 #define TEUK_E_RANGE 7      /* requested waveform steps are not in the ring buffer */
 
@@ -130,13 +130,17 @@ int teuk_set_source(teuk_ctx *ctx, double amp_re, double amp_im, double r0,
 /* Extraction weights w_j (host array of Ntheta doubles).  NULL selects the
  * default: projection on Y = sin(theta/2)^{|m+s|} cos(theta/2)^{|m-s|} in
  * the measure sin theta dtheta, normalised so that sum_j w_j Y_j = 1.
- * Applies to samples taken after the call.  Synchronous. */
+ * Applies to samples taken after the call.  Synchronous: it first waits for
+ * all work on the device (steps in flight on any stream read the weights),
+ * then writes them. */
 int teuk_set_weights(teuk_ctx *ctx, const double *w);
 
 /* Replace the state by src, a [2][Nr][Ntheta] array of complex doubles
  * (re, im interleaved), host or device memory, and set the step counter to
- * `step` (>= 0).  Records the waveform sample of this state.  Asynchronous
- * on `stream` for device src; synchronous for host src. */
+ * `step` (>= 0).  This starts a new run: the error flags that
+ * teuk_extract_waveform reports (TEUK_E_NONFINITE, TEUK_E_TIMEOUT) are
+ * cleared.  Records the waveform sample of this state.  Asynchronous on
+ * `stream` for device src; synchronous for host src. */
 int teuk_set_state(teuk_ctx *ctx, const void *src, int64_t step, void *stream);
 
 /* Copy the current state to dst ([2][Nr][Ntheta] complex doubles, host or
@@ -164,8 +168,10 @@ int teuk_step(teuk_ctx *ctx, int64_t nsteps, void *stream);
  * memory: h_out gets 2*count doubles (re, im), row_out (optional, NULL to
  * skip) gets 2*Ntheta*count doubles.  The steps must still be in the ring
  * buffer (the last wave_capacity recorded steps), else TEUK_E_RANGE.
- * Synchronises `stream` first.  Returns TEUK_E_NONFINITE if a sample taken
- * since init was non-finite. */
+ * Synchronises `stream` first.  Returns TEUK_E_TIMEOUT if a step since the
+ * last teuk_init_grid / teuk_set_state gave up waiting for a tile copy (the
+ * state is then not valid), else TEUK_E_NONFINITE if a sample taken since
+ * then was non-finite. */
 int teuk_extract_waveform(teuk_ctx *ctx, int64_t first_step, int64_t count,
                           double *h_out, double *row_out, void *stream);
 
@@ -226,6 +232,18 @@ int teuk_set_tiling_steps(teuk_ctx *ctx, int tile_rows, int steps_per_launch);
  * otherwise, or if the two tile buffers do not fit in shared memory. */
 int teuk_set_persistent(teuk_ctx *ctx, int tile_rows, int consumer_threads);
 
+/* Bound of the waits of the tiled split-scheme kernels on their state
+ * copies, for testing the failure path without a fault: rounds >= 0 limits
+ * each tile's waits on its state tile to that many mbarrier try_wait rounds
+ * (0: give up at once); rounds < 0 restores the default bound (about four
+ * million rounds, far longer than any copy takes).  A tile whose wait gives
+ * up records TEUK_E_TIMEOUT in the context's control block, then waits for
+ * its own copies with the default bound (so none is in flight when it
+ * exits) and returns without writing its output rows.  teuk_extract_waveform
+ * then returns TEUK_E_TIMEOUT; teuk_set_state clears it and the context
+ * steps normally again.  Drops the context's captured graphs. */
+int teuk_set_wait_limit(teuk_ctx *ctx, int rounds);
+
 /* One literal-scheme step (all of S inside the two Lax-Wendroff stages)
  * that allocates nothing and needs no caller-allocated scratch.  The paper
  * has no counterpart: this entry point exists for callers that cannot
@@ -241,7 +259,9 @@ int teuk_set_persistent(teuk_ctx *ctx, int tile_rows, int consumer_threads);
  *          are read, its state, step counter and waveform are not touched);
  *   d_in   device buffer, [2][Nr][Ntheta] complex values of the context's
  *          state precision (plane 0 Phi, plane 1 Pi); read only;
- *   d_out  device buffer of the same shape, distinct from d_in; written;
+ *   d_out  device buffer of the same shape; written.  It must not overlap
+ *          d_in in any byte (the kernels write d_out while others still
+ *          read d_in): overlapping ranges are refused with TEUK_E_INVAL;
  *   n      step index of d_in (the source phase uses t = n dt).
  * Grids whose midpoints need more than 8 MiB (2 (Nr-1) Ntheta complex
  * values) are rejected with TEUK_E_INVAL before anything is launched.  The
@@ -252,6 +272,17 @@ int teuk_set_persistent(teuk_ctx *ctx, int tile_rows, int consumer_threads);
  * zero (every midpoint is written before it is read).  Asynchronous on
  * `stream`. */
 int teuk_literal_step_static(const teuk_ctx *ctx, const void *d_in, void *d_out, int64_t n, void *stream);
+
+/* FMA throughput of the current device, the ceiling of an ALU-bound step
+ * kernel (the FP64 path is bound by the FP64 pipe: the paper requires double
+ * precision for these evolutions, Sec. 4 and Sec. 5.2).  Runs 8 independent
+ * FMA chains per thread, 256 threads per CTA, 8 CTAs per SM, `iters` rounds
+ * (>= 1), timed with CUDA events on `stream`, and writes the rate in flop/s
+ * (two per FMA) to *flops_per_s.  d_sink: caller-owned device memory of
+ * 8 bytes (written only in an impossible case; it keeps the loop alive).
+ * precision: TEUK_FP64 or TEUK_FP32.  Synchronous.  Errors: TEUK_E_INVAL,
+ * TEUK_E_CUDA. */
+int teuk_fma_rate(int precision, int iters, void *d_sink, void *stream, double *flops_per_s);
 
 /* Current step number (host mirror of the device counter). */
 int64_t teuk_current_step(const teuk_ctx *ctx);

@@ -17,7 +17,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(BUILD_DIR, "libteuk.so")
-SOURCES = ["teuk_api.cu", "teuk_coef.cu", "teuk_step.cu"]
+SOURCES = ["teuk_api.cu", "teuk_coef.cu", "teuk_split_f32.cu", "teuk_split_f64.cu", "teuk_persist.cu",
+           "teuk_adjoint.cu", "teuk_literal.cu", "teuk_measure.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "--expt-relaxed-constexpr"]
 

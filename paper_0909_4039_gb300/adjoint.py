@@ -160,8 +160,13 @@ def forward(w: inputs.Workload, prm: Params, nsteps: int, u0=None, precision: st
     import torch
     op = Operator(w, prm, precision, device=device)
     every = every or max(1, int(round(math.sqrt(max(nsteps, 1)))))
+    caller = torch.cuda.current_stream(op.st.device)
+    # u0 may come from work queued on the caller's stream
+    op.st.stream.wait_stream(caller)
     with torch.cuda.stream(op.st.stream):
         h, ck = run_forward(op, nsteps, u0, every)
+    # and the caller's later work reads h
+    caller.wait_stream(op.st.stream)
     return Forward(op, nsteps, h, ck, every)
 
 
@@ -172,8 +177,16 @@ def backward(fw: Forward, grad_h, wrt_a: bool = True, eps_a: float | None = None
     the adjoint of the initial state (dL/dRe u_0 + i dL/dIm u_0)."""
     import torch
     op = fw.op
+    # grad_h (autograd produces it on the caller's stream) is read by kernels
+    # on the context's stream: order them after the work that wrote it
+    caller = torch.cuda.current_stream(op.st.device)
+    op.st.stream.wait_stream(caller)
+    if torch.is_tensor(grad_h) and grad_h.is_cuda:
+        grad_h.record_stream(op.st.stream)
     with torch.cuda.stream(op.st.stream):
-        return _sweep(fw, grad_h, wrt_a, eps_a)
+        out = _sweep(fw, grad_h, wrt_a, eps_a)
+    caller.wait_stream(op.st.stream)
+    return out
 
 
 def gradients(w: inputs.Workload, prm: Params, nsteps: int, grad_h, u0=None, precision: str = "fp64",
@@ -254,6 +267,7 @@ def waveform(w: inputs.Workload, prm: Params, nsteps: int, u0=None, precision: s
     import torch
     op = Operator(w, prm, precision, device=device)
     try:
+        op.st.stream.wait_stream(torch.cuda.current_stream(op.st.device))
         with torch.cuda.stream(op.st.stream):
             h, _ = run_forward(op, nsteps, u0)
         op.st.synchronize()

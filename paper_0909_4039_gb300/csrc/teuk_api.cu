@@ -5,6 +5,7 @@
 // All arithmetic of the method runs in the kernels of teuk_coef.cu and
 // teuk_step.cu; the host computes only grid constants and bounds.
 #include <math.h>
+#include <stdarg.h>
 #include <stdio.h>
 #include <string.h>
 
@@ -56,6 +57,7 @@ struct teuk_ctx {
     int persist, nc, grid;
     size_t persist_smem;
     int ks;                  // time steps per launch of the tiled kernel (1 or 2)
+    int wait0;               // teuk_set_wait_limit (< 0: default bound)
     size_t smem2;            // shared memory of the two-step kernel
     // graphs, one per starting level
     cudaGraphExec_t graph[2];
@@ -77,6 +79,7 @@ Layout make_layout(const teuk_grid_desc &d)
     size_t off = 0;
     L.rtab64 = off; off = align256(off + rs);
     L.rtabT = f32 ? off : L.rtab64; if (f32) off = align256(off + rs / 2);
+    L.stab = off; off = align256(off + (f32 ? sizeof(float) : sizeof(double)) * (2 * Nr - 1) * NSF);
     L.th64 = off; off = align256(off + ts);
     L.thT = f32 ? off : L.th64; if (f32) off = align256(off + ts / 2);
     L.piv = off; off = align256(off + c2 * N * Nr);
@@ -96,6 +99,14 @@ Layout make_layout(const teuk_grid_desc &d)
     }
     L.scratch = off;
     if (d.scheme == TEUK_SCHEME_LITERAL) off = align256(off + c2 * 2 * (Nr - 1) * N);
+    // FP64 split scheme: materialised coefficients (MatPlanes), three complex
+    // and three real planes [Nr][N], then the Lax-Wendroff planes [2Nr-1][N][4]
+    L.mat = off;
+    L.mat_bytes = 0;
+    if (!f32 && d.scheme == TEUK_SCHEME_SPLIT) {
+        L.mat_bytes = align256(sizeof(double) * Nr * N * 9) + sizeof(double) * 4 * (2 * Nr - 1) * N;
+        off = align256(off + L.mat_bytes);
+    }
     L.total = off;
     return L;
 }
@@ -104,10 +115,13 @@ Layout make_layout(const teuk_grid_desc &d)
 
 namespace {
 
-int set_err(teuk_ctx *c, int code, const char *fmt, const char *a = "", double x = 0.0)
+__attribute__((format(printf, 3, 4))) int set_err(teuk_ctx *c, int code, const char *fmt, ...)
 {
     char *buf = c ? c->err : g_init_err;
-    snprintf(buf, 512, fmt, a, x);
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, 512, fmt, ap);
+    va_end(ap);
     return code;
 }
 
@@ -358,7 +372,7 @@ int choose_tiles(teuk_ctx *c)
     int n = tile_candidates(c, cand.data(), (int)cand.size());
     for (int k = 0; k < n; ++k)
         if (apply_cand(c, cand[k])) return TEUK_OK;
-    return set_err(c, TEUK_E_CUDA, "no tile of the split kernel fits on this device%s");
+    return set_err(c, TEUK_E_CUDA, "no tile of the split kernel fits on this device");
 }
 
 template <typename T>
@@ -383,6 +397,7 @@ StepParams<T> make_params(const teuk_ctx *c, int in_level)
     p.wave_cap = (int)c->cap;
     p.patch_p0 = c->patch_p0;
     p.patch_np = c->patch_np;
+    p.wait0 = c->wait0;
     p.dt = (T)c->dt;
     p.half_dt = (T)(0.5 * c->dt);
     p.drs_inv = (T)(1.0 / c->drs);
@@ -393,12 +408,27 @@ StepParams<T> make_params(const teuk_ctx *c, int in_level)
         K.gh2 = (T)(gh * gh);
         K.h1g = (T)((1.0 - kGamma) * h);
         K.h12g = (T)((1.0 - 2.0 * kGamma) * h);
+        K.h = (T)h;
+        K.g2h1 = (T)(2.0 * gh * (1.0 - kGamma) * h);
         K.piv = (const c2 *)(c->coef + (k ? c->L.pivh : c->L.piv));
         K.plan = (const int *)(c->coef + (k ? c->L.planh : c->L.plan));
     }
     p.dt64 = c->dt;
     p.mOmega = c->mOmega;
     p.rtab = (const T *)(c->coef + c->L.rtabT);
+    p.stab = (const T *)(c->coef + c->L.stab);
+    p.mat_on = c->L.mat_bytes > 0 ? 1 : 0;
+    {
+        const size_t pl = (size_t)d.Nr * (size_t)d.Ntheta;   // elements per plane
+        const char *m = c->coef + c->L.mat;
+        p.mat.fk = (const c2 *)m;
+        p.mat.dg = (const c2 *)(m + 2 * pl * sizeof(T));
+        p.mat.ct = (const c2 *)(m + 4 * pl * sizeof(T));
+        p.mat.sub = (const T *)(m + 6 * pl * sizeof(T));
+        p.mat.qam = (const T *)(m + 7 * pl * sizeof(T));
+        p.mat.qap = (const T *)(m + 8 * pl * sizeof(T));
+        p.mat.lw = (const T *)(m + ((9 * pl * sizeof(T) + 255) & ~(size_t)255));
+    }
     p.thtab = (const T *)(c->coef + c->L.thT);
     p.patch = (const c2 *)(c->coef + c->L.patch);
     p.nfix = -1;
@@ -437,7 +467,11 @@ cudaError_t compute_plans(teuk_ctx *c, cudaStream_t st)
     if (c->d.scheme != TEUK_SCHEME_SPLIT) return cudaSuccess;
     int *pf = (int *)(c->coef + c->L.plan), *ph = (int *)(c->coef + c->L.planh);
     if (c->d.precision == TEUK_FP32) return launch_scan_plans<float>(make_params<float>(c, 0), pf, ph, st);
-    return launch_scan_plans<double>(make_params<double>(c, 0), pf, ph, st);
+    const StepParams<double> p = make_params<double>(c, 0);
+    cudaError_t e = launch_scan_plans<double>(p, pf, ph, st);
+    if (e != cudaSuccess) return e;
+    // the FP64 path's materialised coefficients come from the same tables
+    return launch_mat_coef<double>(p, st);
 }
 
 cudaError_t launch_one(teuk_ctx *c, int in_level, cudaStream_t st)
@@ -555,14 +589,14 @@ int teuk_init_grid(const teuk_grid_desc *desc, void *d_state, void *d_coef, void
                    int64_t wave_capacity, void *stream, teuk_ctx **out)
 {
     teuk_ctx *c = nullptr;
-    if (!out) return set_err(c, TEUK_E_INVAL, "out is NULL%s");
+    if (!out) return set_err(c, TEUK_E_INVAL, "out is NULL");
     *out = nullptr;
     int rc = validate(desc, g_init_err);
     if (rc) return rc;
-    if (!d_state || !d_coef || !d_wave) return set_err(c, TEUK_E_INVAL, "device buffers must not be NULL%s");
+    if (!d_state || !d_coef || !d_wave) return set_err(c, TEUK_E_INVAL, "device buffers must not be NULL");
     if (((uintptr_t)d_state | (uintptr_t)d_coef | (uintptr_t)d_wave) & 255)
-        return set_err(c, TEUK_E_INVAL, "device buffers must be 256-byte aligned%s");
-    if (wave_capacity < 1 || wave_capacity > (1LL << 31)) return set_err(c, TEUK_E_INVAL, "wave_capacity out of range%s");
+        return set_err(c, TEUK_E_INVAL, "device buffers must be 256-byte aligned");
+    if (wave_capacity < 1 || wave_capacity > (1LL << 31)) return set_err(c, TEUK_E_INVAL, "wave_capacity out of range");
 
     teuk_grid_desc d = *desc;
     double drs = (d.rstar_max - d.rstar_min) / (double)(d.Nr - 1);
@@ -573,18 +607,19 @@ int teuk_init_grid(const teuk_grid_desc *desc, void *d_state, void *d_coef, void
     double bmax, qmax, ctmax;
     host_bounds(d, &bmax, &qmax, &ctmax);
     if (bmax * dt / drs > 1.0)
-        return set_err(c, TEUK_E_UNSTABLE, "radial Courant number %s%.4f > 1", "", bmax * dt / drs);
+        return set_err(c, TEUK_E_UNSTABLE, "radial Courant number %.4f > 1", bmax * dt / drs);
     if (d.scheme == TEUK_SCHEME_LITERAL && !d.allow_unstable) {
         double z = fmax(sqrt(qmax * host_atheta_bound(d)) * dt, ctmax * dt);
         if (z > 0.05)
             return set_err(c, TEUK_E_UNSTABLE,
-                           "literal scheme: explicit S has |lambda dt| = %s%.3g > 0.05 (grows each step); "
-                           "use TEUK_SCHEME_SPLIT or set allow_unstable", "", z);
+                           "literal scheme: explicit S has |lambda dt| = %.3g > 0.05 (grows each step); "
+                           "use TEUK_SCHEME_SPLIT or set allow_unstable", z);
     }
 
     c = new (std::nothrow) teuk_ctx();
-    if (!c) return set_err(nullptr, TEUK_E_INVAL, "out of host memory%s");
+    if (!c) return set_err(nullptr, TEUK_E_INVAL, "out of host memory");
     memset(c, 0, sizeof(*c));
+    c->wait0 = -1;   // default bound of the tile-copy waits
     c->d = d;
     c->drs = drs;
     c->dt = dt;
@@ -645,7 +680,7 @@ int teuk_set_source(teuk_ctx *c, double amp_re, double amp_im, double r0, double
 {
     if (!c) return TEUK_E_STATE;
     const teuk_grid_desc &d = c->d;
-    if (!isfinite(amp_re) || !isfinite(amp_im)) return set_err(c, TEUK_E_INVAL, "amplitude must be finite%s");
+    if (!isfinite(amp_re) || !isfinite(amp_im)) return set_err(c, TEUK_E_INVAL, "amplitude must be finite");
     drop_graphs(c);
     const bool off = amp_re == 0.0 && amp_im == 0.0;
     double rp = d.M + sqrt(d.M * d.M - d.a * d.a);
@@ -657,11 +692,11 @@ int teuk_set_source(teuk_ctx *c, double amp_re, double amp_im, double r0, double
         c->amp_re = c->amp_im = 0.0;
         return TEUK_OK;
     }
-    if (!(r0 > rp) || !isfinite(r0)) return set_err(c, TEUK_E_INVAL, "orbit radius must exceed r_+%s");
-    if (!(sigma_rstar > 0.0) || !(sigma_theta > 0.0)) return set_err(c, TEUK_E_INVAL, "source widths must be positive%s");
+    if (!(r0 > rp) || !isfinite(r0)) return set_err(c, TEUK_E_INVAL, "orbit radius must exceed r_+");
+    if (!(sigma_rstar > 0.0) || !(sigma_theta > 0.0)) return set_err(c, TEUK_E_INVAL, "source widths must be positive");
     const bool kepler = isnan(Omega);
     double Om = kepler ? sqrt(d.M) / (pow(r0, 1.5) + d.a * sqrt(d.M)) : Omega;
-    if (!isfinite(Om)) return set_err(c, TEUK_E_INVAL, "Omega must be finite or NaN%s");
+    if (!isfinite(Om)) return set_err(c, TEUK_E_INVAL, "Omega must be finite or NaN");
     double rs0 = host_rstar(d.M, d.a, r0);
     double lo = (rs0 - 9.0 * sigma_rstar - d.rstar_min) / c->drs;
     double hi = (rs0 + 9.0 * sigma_rstar - d.rstar_min) / c->drs;
@@ -671,7 +706,7 @@ int teuk_set_source(teuk_ctx *c, double amp_re, double amp_im, double r0, double
     int np = (int)(p1 - p0 + 1);
     if (p1 < p0) np = 0;
     long long cap_rows = d.Nr < TEUK_MAX_PATCH_ROWS ? d.Nr : TEUK_MAX_PATCH_ROWS;
-    if (np > cap_rows) return set_err(c, TEUK_E_INVAL, "source patch needs more rows than TEUK_MAX_PATCH_ROWS%s");
+    if (np > cap_rows) return set_err(c, TEUK_E_INVAL, "source patch needs more rows than TEUK_MAX_PATCH_ROWS");
     cudaStream_t st = 0;
     if (np > 0) {
         CK(launch_patch(d, c->drs, c->coef, c->L, (int)p0, np, amp_re, amp_im, rs0, sigma_rstar, sigma_theta, st), "source patch");
@@ -698,9 +733,13 @@ int teuk_set_weights(teuk_ctx *c, const double *w)
 {
     if (!c) return TEUK_E_STATE;
     double *dw = (double *)(c->coef + c->L.w);
-    if (w) {
+    if (w)
         for (int64_t j = 0; j < c->d.Ntheta; ++j)
-            if (!isfinite(w[j])) return set_err(c, TEUK_E_INVAL, "weights must be finite%s");
+            if (!isfinite(w[j])) return set_err(c, TEUK_E_INVAL, "weights must be finite");
+    // steps still in flight on any stream read the weights (fused extraction):
+    // let them finish before the weights change
+    CK(cudaDeviceSynchronize(), "weights sync");
+    if (w) {
         CK(cudaMemcpy(dw, w, sizeof(double) * (size_t)c->d.Ntheta, cudaMemcpyHostToDevice), "weights copy");
     } else {
         CK(launch_coef_tables(c->d, c->drs, c->dt, c->coef, c->L, 0), "default weights");
@@ -713,7 +752,7 @@ int teuk_set_weights(teuk_ctx *c, const double *w)
 int teuk_set_state(teuk_ctx *c, const void *src, int64_t step, void *stream)
 {
     if (!c) return TEUK_E_STATE;
-    if (!src || step < 0) return set_err(c, TEUK_E_INVAL, "src must not be NULL and step >= 0%s");
+    if (!src || step < 0) return set_err(c, TEUK_E_INVAL, "src must not be NULL and step >= 0");
     cudaStream_t st = (cudaStream_t)stream;
     size_t n = 2 * (size_t)c->d.Nr * (size_t)c->d.Ntheta;   // complex elements
     char *dst = c->state + (size_t)c->cur * c->level_bytes;
@@ -733,7 +772,7 @@ int teuk_set_state(teuk_ctx *c, const void *src, int64_t step, void *stream)
             CK(launch_convert_to(TEUK_FP32, stg, (float2 *)dst + o, k, st), "state convert");
         }
     }
-    CK(launch_set_ctl(c->coef, c->L, step, 0, st), "control block");
+    CK(launch_set_ctl(c->coef, c->L, step, 1, st), "control block");
     c->step = step;
     c->rec_lo = step;
     c->shifted = 0;
@@ -745,7 +784,7 @@ int teuk_set_state(teuk_ctx *c, const void *src, int64_t step, void *stream)
 int teuk_get_state(teuk_ctx *c, void *dst, int64_t *step, void *stream)
 {
     if (!c) return TEUK_E_STATE;
-    if (!dst) return set_err(c, TEUK_E_INVAL, "dst must not be NULL%s");
+    if (!dst) return set_err(c, TEUK_E_INVAL, "dst must not be NULL");
     cudaStream_t st = (cudaStream_t)stream;
     size_t n = 2 * (size_t)c->d.Nr * (size_t)c->d.Ntheta;
     const char *src = c->state + (size_t)c->cur * c->level_bytes;
@@ -786,7 +825,7 @@ int teuk_state_level(const teuk_ctx *c, int64_t *offset_bytes, size_t *level_byt
 int teuk_step(teuk_ctx *c, int64_t nsteps, void *stream)
 {
     if (!c) return TEUK_E_STATE;
-    if (nsteps < 0) return set_err(c, TEUK_E_INVAL, "nsteps must be >= 0%s");
+    if (nsteps < 0) return set_err(c, TEUK_E_INVAL, "nsteps must be >= 0");
     cudaStream_t st = (cudaStream_t)stream;
     int64_t left = nsteps;
     if (left > 0 && c->d.scheme == TEUK_SCHEME_SPLIT && !c->shifted) {
@@ -851,12 +890,12 @@ int teuk_extract_waveform(teuk_ctx *c, int64_t first, int64_t count, double *h_o
                           void *stream)
 {
     if (!c) return TEUK_E_STATE;
-    if (count < 0 || (count > 0 && !h_out)) return set_err(c, TEUK_E_INVAL, "need count >= 0 and h_out%s");
+    if (count < 0 || (count > 0 && !h_out)) return set_err(c, TEUK_E_INVAL, "need count >= 0 and h_out");
     cudaStream_t st = (cudaStream_t)stream;
     CK(cudaStreamSynchronize(st), "sync");
     int64_t lo = c->rec_lo > c->step - c->cap + 1 ? c->rec_lo : c->step - c->cap + 1;
     if (count > 0 && (first < lo || first + count - 1 > c->step))
-        return set_err(c, TEUK_E_RANGE, "steps not in the ring buffer%s");
+        return set_err(c, TEUK_E_RANGE, "steps not in the ring buffer");
     size_t slot_bytes = sizeof(double2) * (size_t)(c->d.Ntheta + 1);
     int64_t done = 0;
     while (done < count) {
@@ -875,8 +914,8 @@ int teuk_extract_waveform(teuk_ctx *c, int64_t first, int64_t count, double *h_o
     }
     Ctl h;
     CK(cudaMemcpy(&h, c->coef + c->L.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost), "control read");
-    if (h.flags & FLAG_TIMEOUT) return set_err(c, TEUK_E_TIMEOUT, "a bulk copy of a state tile did not complete%s");
-    if (h.flags & FLAG_NONFINITE) return set_err(c, TEUK_E_NONFINITE, "a non-finite waveform sample was produced%s");
+    if (h.flags & FLAG_TIMEOUT) return set_err(c, TEUK_E_TIMEOUT, "a bulk copy of a state tile did not complete");
+    if (h.flags & FLAG_NONFINITE) return set_err(c, TEUK_E_NONFINITE, "a non-finite waveform sample was produced");
     return TEUK_OK;
 }
 
@@ -914,7 +953,7 @@ int teuk_kernel_config(const teuk_ctx *c, int *persistent, int *consumer_threads
 static int autotune_impl(teuk_ctx *c, int trial_steps, void *flush, size_t flush_bytes, cudaStream_t st,
                          int *tile_rows_out)
 {
-    if (trial_steps < 1 || trial_steps > 100000) return set_err(c, TEUK_E_INVAL, "trial_steps out of range%s");
+    if (trial_steps < 1 || trial_steps > 100000) return set_err(c, TEUK_E_INVAL, "trial_steps out of range");
     if (c->d.scheme != TEUK_SCHEME_SPLIT) {
         if (tile_rows_out) *tile_rows_out = c->tile_rows;
         return TEUK_OK;
@@ -933,7 +972,7 @@ static int autotune_impl(teuk_ctx *c, int trial_steps, void *flush, size_t flush
             }
         }
     }
-    if (cand.empty()) return set_err(c, TEUK_E_CUDA, "no tile of the split kernel fits on this device%s");
+    if (cand.empty()) return set_err(c, TEUK_E_CUDA, "no tile of the split kernel fits on this device");
     drop_graphs(c);
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0), "event");
@@ -985,7 +1024,7 @@ static int autotune_impl(teuk_ctx *c, int trial_steps, void *flush, size_t flush
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (e != cudaSuccess) return cuda_err(c, e, "autotune trial");
-    if (bestk < 0) return set_err(c, TEUK_E_CUDA, "no tile of the split kernel fits on this device%s");
+    if (bestk < 0) return set_err(c, TEUK_E_CUDA, "no tile of the split kernel fits on this device");
     apply_cand(c, cand[bestk]);
     int rr = reset_state(c, st);
     if (rr != TEUK_OK) return rr;
@@ -1004,7 +1043,7 @@ int teuk_autotune_cold(teuk_ctx *c, int trial_steps, void *d_flush, size_t flush
                        int *tile_rows_out)
 {
     if (!c) return TEUK_E_STATE;
-    if (!d_flush || flush_bytes == 0) return set_err(c, TEUK_E_INVAL, "need a device flush buffer%s");
+    if (!d_flush || flush_bytes == 0) return set_err(c, TEUK_E_INVAL, "need a device flush buffer");
     return autotune_impl(c, trial_steps, d_flush, flush_bytes, (cudaStream_t)stream, tile_rows_out);
 }
 
@@ -1012,9 +1051,9 @@ int teuk_set_tiling(teuk_ctx *c, int tile_rows)
 {
     if (!c) return TEUK_E_STATE;
     if (c->d.scheme != TEUK_SCHEME_SPLIT) return TEUK_OK;
-    if (tile_rows < 1 || tile_rows > 254) return set_err(c, TEUK_E_INVAL, "tile_rows out of range [1, 254]%s");
+    if (tile_rows < 1 || tile_rows > 254) return set_err(c, TEUK_E_INVAL, "tile_rows out of range [1, 254]");
     TileCand t;
-    if (!tiled_cand(c, tile_rows, sm_count(), &t)) return set_err(c, TEUK_E_INVAL, "tile does not fit in shared memory%s");
+    if (!tiled_cand(c, tile_rows, sm_count(), &t)) return set_err(c, TEUK_E_INVAL, "tile does not fit in shared memory");
     drop_graphs(c);
     apply_cand(c, t);
     return TEUK_OK;
@@ -1024,14 +1063,14 @@ int teuk_set_tiling_steps(teuk_ctx *c, int tile_rows, int steps_per_launch)
 {
     if (!c) return TEUK_E_STATE;
     if (steps_per_launch == 1) return teuk_set_tiling(c, tile_rows);
-    if (steps_per_launch != 2) return set_err(c, TEUK_E_INVAL, "steps_per_launch must be 1 or 2%s");
-    if (c->d.scheme != TEUK_SCHEME_SPLIT) return set_err(c, TEUK_E_INVAL, "two steps per launch need the split scheme%s");
-    if (tile_rows < 1 || tile_rows > 250) return set_err(c, TEUK_E_INVAL, "tile_rows out of range [1, 250]%s");
+    if (steps_per_launch != 2) return set_err(c, TEUK_E_INVAL, "steps_per_launch must be 1 or 2");
+    if (c->d.scheme != TEUK_SCHEME_SPLIT) return set_err(c, TEUK_E_INVAL, "two steps per launch need the split scheme");
+    if (tile_rows < 1 || tile_rows > 250) return set_err(c, TEUK_E_INVAL, "tile_rows out of range [1, 250]");
     TileCand t;
     if (!tiled2_cand(c, tile_rows, sm_count(), &t))
-        return set_err(c, TEUK_E_INVAL, "tile does not fit in shared memory%s");
+        return set_err(c, TEUK_E_INVAL, "tile does not fit in shared memory");
     TileCand tt;
-    if (!tiled_cand(c, tile_rows, sm_count(), &tt)) return set_err(c, TEUK_E_INVAL, "tile does not fit in shared memory%s");
+    if (!tiled_cand(c, tile_rows, sm_count(), &tt)) return set_err(c, TEUK_E_INVAL, "tile does not fit in shared memory");
     drop_graphs(c);
     apply_cand(c, t);
     return TEUK_OK;
@@ -1040,8 +1079,8 @@ int teuk_set_tiling_steps(teuk_ctx *c, int tile_rows, int steps_per_launch)
 int teuk_set_persistent(teuk_ctx *c, int tile_rows, int consumer_threads)
 {
     if (!c) return TEUK_E_STATE;
-    if (c->d.scheme != TEUK_SCHEME_SPLIT) return set_err(c, TEUK_E_INVAL, "the persistent kernel is a split-scheme kernel%s");
-    if (tile_rows < 1 || tile_rows > 254) return set_err(c, TEUK_E_INVAL, "tile_rows out of range [1, 254]%s");
+    if (c->d.scheme != TEUK_SCHEME_SPLIT) return set_err(c, TEUK_E_INVAL, "the persistent kernel is a split-scheme kernel");
+    if (tile_rows < 1 || tile_rows > 254) return set_err(c, TEUK_E_INVAL, "tile_rows out of range [1, 254]");
     TileCand t;
     if (!persist_cand(c, tile_rows, consumer_threads, sm_count(), &t)) {
         const int N = (int)c->d.Ntheta;
@@ -1053,9 +1092,17 @@ int teuk_set_persistent(teuk_ctx *c, int tile_rows, int consumer_threads)
         return set_err(c, TEUK_E_INVAL, "persistent kernel unavailable for this grid: %s", why);
     }
     TileCand tt;
-    if (!tiled_cand(c, tile_rows, sm_count(), &tt)) return set_err(c, TEUK_E_INVAL, "tile does not fit in shared memory%s");
+    if (!tiled_cand(c, tile_rows, sm_count(), &tt)) return set_err(c, TEUK_E_INVAL, "tile does not fit in shared memory");
     drop_graphs(c);
     apply_cand(c, t);
+    return TEUK_OK;
+}
+
+int teuk_set_wait_limit(teuk_ctx *c, int rounds)
+{
+    if (!c) return TEUK_E_STATE;
+    drop_graphs(c);   // captured launches carry the old bound
+    c->wait0 = rounds < 0 ? -1 : rounds;
     return TEUK_OK;
 }
 
@@ -1064,13 +1111,19 @@ int teuk_literal_step_static(const teuk_ctx *c, const void *d_in, void *d_out, i
     teuk_ctx *cm = const_cast<teuk_ctx *>(c);
     if (!c) return TEUK_E_STATE;
     if (c->d.scheme != TEUK_SCHEME_LITERAL)
-        return set_err(cm, TEUK_E_INVAL, "teuk_literal_step_static needs a context of the literal scheme%s");
-    if (!d_in || !d_out || d_in == d_out || n < 0)
-        return set_err(cm, TEUK_E_INVAL, "need distinct non-NULL device buffers and n >= 0%s");
+        return set_err(cm, TEUK_E_INVAL, "teuk_literal_step_static needs a context of the literal scheme");
+    if (!d_in || !d_out || n < 0) return set_err(cm, TEUK_E_INVAL, "need non-NULL device buffers and n >= 0");
     size_t c2 = c->d.precision == TEUK_FP32 ? sizeof(float2) : sizeof(double2);
+    {
+        // the node kernel writes d_out while other threads still read d_in: no byte may be shared
+        const size_t bytes = c2 * 2 * (size_t)c->d.Nr * (size_t)c->d.Ntheta;
+        const uintptr_t a0 = (uintptr_t)d_in, b0 = (uintptr_t)d_out;
+        if (a0 < b0 + bytes && b0 < a0 + bytes)
+            return set_err(cm, TEUK_E_INVAL, "d_in and d_out overlap (each spans %zu bytes)", bytes);
+    }
     size_t need = c2 * 2 * (size_t)(c->d.Nr - 1) * (size_t)c->d.Ntheta;
     if (need > literal_static_scratch_bytes())
-        return set_err(cm, TEUK_E_INVAL, "grid needs %s%.0f bytes of midpoint scratch, above the static limit of 8 MiB", "",
+        return set_err(cm, TEUK_E_INVAL, "grid needs %.0f bytes of midpoint scratch, above the static limit of 8 MiB",
                        (double)need);
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e;
@@ -1128,9 +1181,9 @@ extern "C" {
 int teuk_apply_step(teuk_ctx *c, const void *d_in, void *d_out, int64_t n, int first, void *stream)
 {
     if (!c) return TEUK_E_STATE;
-    if (c->d.scheme != TEUK_SCHEME_SPLIT) return set_err(c, TEUK_E_INVAL, "teuk_apply_step needs the split scheme%s");
+    if (c->d.scheme != TEUK_SCHEME_SPLIT) return set_err(c, TEUK_E_INVAL, "teuk_apply_step needs the split scheme");
     if (!d_in || !d_out || d_in == d_out || n < 0)
-        return set_err(c, TEUK_E_INVAL, "need distinct non-NULL device buffers and n >= 0%s");
+        return set_err(c, TEUK_E_INVAL, "need distinct non-NULL device buffers and n >= 0");
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e;
     if (c->d.precision == TEUK_FP32) {
@@ -1155,9 +1208,9 @@ int teuk_apply_step(teuk_ctx *c, const void *d_in, void *d_out, int64_t n, int f
 int teuk_apply_sample(teuk_ctx *c, const void *d_s, int physical, void *d_h, void *stream)
 {
     if (!c) return TEUK_E_STATE;
-    if (!d_s || !d_h) return set_err(c, TEUK_E_INVAL, "need non-NULL device buffers%s");
+    if (!d_s || !d_h) return set_err(c, TEUK_E_INVAL, "need non-NULL device buffers");
     if (c->d.scheme != TEUK_SCHEME_SPLIT && !physical)
-        return set_err(c, TEUK_E_INVAL, "the literal scheme has no internal state: pass physical = 1%s");
+        return set_err(c, TEUK_E_INVAL, "the literal scheme has no internal state: pass physical = 1");
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e;
     if (c->d.precision == TEUK_FP32)
@@ -1179,9 +1232,9 @@ int teuk_adjoint_step(teuk_ctx *c, const void *d_lam_in, void *d_lam_out, int64_
                       void *d_ws, void *stream)
 {
     if (!c) return TEUK_E_STATE;
-    if (c->d.scheme != TEUK_SCHEME_SPLIT) return set_err(c, TEUK_E_INVAL, "the adjoint needs the split scheme%s");
+    if (c->d.scheme != TEUK_SCHEME_SPLIT) return set_err(c, TEUK_E_INVAL, "the adjoint needs the split scheme");
     if (!d_lam_in || !d_lam_out || d_lam_in == d_lam_out || !d_ws || n < 0)
-        return set_err(c, TEUK_E_INVAL, "need distinct non-NULL device buffers, a workspace and n >= 0%s");
+        return set_err(c, TEUK_E_INVAL, "need distinct non-NULL device buffers, a workspace and n >= 0");
     cudaStream_t st = (cudaStream_t)stream;
     const int tr = adjoint_tile_rows(c);
     double *acc = (double *)d_ws, *part = acc + 8;
@@ -1208,7 +1261,7 @@ int teuk_adjoint_step(teuk_ctx *c, const void *d_lam_in, void *d_lam_out, int64_
 int teuk_dot(teuk_ctx *c, const void *d_x, const void *d_y, const void *d_z, void *d_ws, void *d_out, void *stream)
 {
     if (!c) return TEUK_E_STATE;
-    if (!d_x || !d_y || !d_ws || !d_out) return set_err(c, TEUK_E_INVAL, "need non-NULL device buffers%s");
+    if (!d_x || !d_y || !d_ws || !d_out) return set_err(c, TEUK_E_INVAL, "need non-NULL device buffers");
     cudaStream_t st = (cudaStream_t)stream;
     const size_t n = 2 * (size_t)c->d.Nr * (size_t)c->d.Ntheta;
     double *part = (double *)d_ws + adjoint_ws_doubles(c) - 2 * 256;
@@ -1246,9 +1299,12 @@ struct teuk_batch {
 
 namespace {
 
-int bset_err(teuk_batch *b, int code, const char *fmt, const char *a = "", double x = 0.0)
+__attribute__((format(printf, 3, 4))) int bset_err(teuk_batch *b, int code, const char *fmt, ...)
 {
-    snprintf(b ? b->err : g_init_err, 512, fmt, a, x);
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(b ? b->err : g_init_err, 512, fmt, ap);
+    va_end(ap);
     return code;
 }
 
@@ -1321,14 +1377,14 @@ int batch_layout(teuk_batch *b)
         size_t sm = batch_tile_smem(b->prec, b->tr[i], N, b->ks);
         smem = sm > smem ? sm : smem;
     }
-    if (smem > 227 * 1024) return bset_err(b, TEUK_E_INVAL, "a tile of the batch does not fit in shared memory%s");
+    if (smem > 227 * 1024) return bset_err(b, TEUK_E_INVAL, "a tile of the batch does not fit in shared memory");
     int k = b->prec == TEUK_FP32 ? split_batch_blocks_per_sm<float>(b->seg, smem, b->ks)
                                  : split_batch_blocks_per_sm<double>(b->seg, smem, b->ks);
     // the first step of a two-step batch runs the one-step kernel with this shared memory
     if (k >= 1 && b->ks == 2)
         k = b->prec == TEUK_FP32 ? split_batch_blocks_per_sm<float>(b->seg, smem, 1)
                                  : split_batch_blocks_per_sm<double>(b->seg, smem, 1);
-    if (k < 1) return bset_err(b, TEUK_E_INVAL, "the batched kernel does not fit on this device with these tiles%s");
+    if (k < 1) return bset_err(b, TEUK_E_INVAL, "the batched kernel does not fit on this device with these tiles");
     b->htiles.clear();
     for (int t = 0; t < maxt; ++t)
         for (int i = 0; i < n; ++i)
@@ -1336,7 +1392,7 @@ int batch_layout(teuk_batch *b)
     b->ntot = (int)b->htiles.size();
     b->smem = smem;
     if ((size_t)b->ntot * sizeof(int2) > b->ws_bytes - b->off_tiles)
-        return bset_err(b, TEUK_E_INVAL, "workspace too small for the tile list%s");
+        return bset_err(b, TEUK_E_INVAL, "workspace too small for the tile list");
     // launches in flight on any stream may still read the old list
     BCK(cudaDeviceSynchronize(), "wait before the tile list changes");
     BCK(cudaMemcpy(b->ws + b->off_tiles, b->htiles.data(), sizeof(int2) * b->htiles.size(), cudaMemcpyHostToDevice),
@@ -1517,7 +1573,7 @@ int teuk_batch_create(teuk_ctx *const *ctxs, int count, void *d_ws, size_t ws_by
 int teuk_batch_step(teuk_batch *b, int64_t nsteps, void *stream)
 {
     if (!b) return TEUK_E_STATE;
-    if (nsteps < 0) return bset_err(b, TEUK_E_INVAL, "nsteps must be >= 0%s");
+    if (nsteps < 0) return bset_err(b, TEUK_E_INVAL, "nsteps must be >= 0");
     return batch_step_impl(b, nsteps, (cudaStream_t)stream);
 }
 
@@ -1534,10 +1590,10 @@ int teuk_batch_tiling(const teuk_batch *b, int *tile_rows, int *total_tiles, siz
 int teuk_batch_set_tiling(teuk_batch *b, const int *tile_rows)
 {
     if (!b) return TEUK_E_STATE;
-    if (!tile_rows) return bset_err(b, TEUK_E_INVAL, "tile_rows is NULL%s");
+    if (!tile_rows) return bset_err(b, TEUK_E_INVAL, "tile_rows is NULL");
     std::vector<int> old = b->tr;
     for (size_t i = 0; i < b->tr.size(); ++i) {
-        if (tile_rows[i] < 1 || tile_rows[i] > 254) return bset_err(b, TEUK_E_INVAL, "tile_rows out of range [1, 254]%s");
+        if (tile_rows[i] < 1 || tile_rows[i] > 254) return bset_err(b, TEUK_E_INVAL, "tile_rows out of range [1, 254]");
         b->tr[i] = tile_rows[i];
     }
     int r = batch_layout(b);
@@ -1554,7 +1610,7 @@ int teuk_batch_set_tiling(teuk_batch *b, const int *tile_rows)
 int teuk_batch_autotune(teuk_batch *b, int trial_steps, void *stream)
 {
     if (!b) return TEUK_E_STATE;
-    if (trial_steps < 1 || trial_steps > 100000) return bset_err(b, TEUK_E_INVAL, "trial_steps out of range%s");
+    if (trial_steps < 1 || trial_steps > 100000) return bset_err(b, TEUK_E_INVAL, "trial_steps out of range");
     cudaStream_t st = (cudaStream_t)stream;
     // For each number of steps per launch the kernel offers, a coordinate
     // descent over the Ntheta classes of the batch: for each class, every
@@ -1663,9 +1719,9 @@ int teuk_batch_set_steps_per_launch(teuk_batch *b, int steps_per_launch)
 {
     if (!b) return TEUK_E_STATE;
     if (steps_per_launch != 1 && steps_per_launch != 2)
-        return bset_err(b, TEUK_E_INVAL, "steps_per_launch must be 1 or 2%s");
+        return bset_err(b, TEUK_E_INVAL, "steps_per_launch must be 1 or 2");
     if (!split_batch_available(b->seg, steps_per_launch))
-        return bset_err(b, TEUK_E_INVAL, "two steps per launch need Ntheta <= 256%s");
+        return bset_err(b, TEUK_E_INVAL, "two steps per launch need Ntheta <= 256");
     const int old = b->ks;
     b->ks = steps_per_launch;
     int r = batch_layout(b);

@@ -102,9 +102,11 @@ struct CoefArgs {
     int Nr, Nth;
     double rs_min, drs, dth;
     double gh, gh2;            // gamma h and its square for the pivot table being built
+    double dt;                 // time step (scales the Lax-Wendroff block of the step table)
     int prec;                  // TEUK_FP64 / TEUK_FP32
     double *rtab64;
     void *rtabT;
+    void *stab;
     double *th64;
     void *thT;
     void *piv;
@@ -125,6 +127,30 @@ __global__ void k_rtab(CoefArgs A)
         float *o = (float *)A.rtabT;
         for (int q = 0; q < NRF; ++q) o[(size_t)p * NRF + q] = (float)f[q];
     }
+    // step table (SField): the implicit block as is, the Lax-Wendroff block
+    // times c_p = dt/dr* (node, Eq. 14) or dt/(2 dr*) (half node, Eq. 13)
+    const double cp = ((p & 1) ? 0.5 : 1.0) * A.dt / A.drs;
+    double g[NSF];
+    g[SF_R2] = f[RF_R2];
+    g[SF_AD] = f[RF_AD];
+    g[SF_DELTA] = f[RF_DELTA];
+    g[SF_CTR] = f[RF_CTR];
+    g[SF_CTI] = f[RF_CTI];
+    g[SF_CTC] = f[RF_CTC];
+    g[SF_C0R] = f[RF_C0R];
+    g[SF_C0I] = f[RF_C0I];
+    g[SF_RB] = cp * f[RF_R];
+    g[SF_E2] = cp * f[RF_E2];
+    g[SF_E3] = cp * f[RF_E3];
+    g[SF_RCTR] = cp * f[RF_R] * f[RF_CTR];
+    g[SF_CSE] = cp * (f[RF_CSR] - f[RF_E1]);
+    g[SF_RCTC] = cp * f[RF_R] * f[RF_CTC];
+    g[SF_RCTI] = cp * f[RF_R] * f[RF_CTI];
+    g[SF_CSI] = cp * f[RF_CSI];
+    if (A.prec == TEUK_FP32)
+        for (int q = 0; q < NSF; ++q) ((float *)A.stab)[(size_t)p * NSF + q] = (float)g[q];
+    else
+        for (int q = 0; q < NSF; ++q) ((double *)A.stab)[(size_t)p * NSF + q] = g[q];
 }
 
 // Theta tables and default extraction weights; one CTA, blockDim >= Nth.
@@ -282,6 +308,8 @@ cudaError_t launch_coef_tables(const teuk_grid_desc &d, double drs, double dt, v
     char *base = (char *)coef;
     A.rtab64 = (double *)(base + L.rtab64);
     A.rtabT = base + L.rtabT;
+    A.stab = base + L.stab;
+    A.dt = dt;
     A.th64 = (double *)(base + L.th64);
     A.thT = base + L.thT;
     A.w = (double *)(base + L.w);

@@ -6,6 +6,7 @@
 //            double), plane 0 = Phi, plane 1 = Pi, theta fastest.
 //   coef   : r tables   [2Nr-1][NRF] FP64 and [2Nr-1][NRF] T
 //                        (position p = 2i: node i; p = 2i+1: r*_{i+1/2})
+//            step table [2Nr-1][NSF] T (see SField)
 //            theta tables [NTF][Ntheta] FP64 and T
 //            pivots     two tables [Nr][Ntheta] complex T, for implicit
 //                        steps of length dt and dt/2 (row-major, so the
@@ -40,6 +41,20 @@ enum RField {
     RF_E1, RF_E2, RF_E3, RF_C0R, RF_C0I, RF_RR, RF_X, NRF
 };
 
+// Fields of the step table: one entry of NSF values per r* position (node
+// i at 2i, half node at 2i+1), in the state precision, read by the forward
+// step kernels.  The first block is the implicit stage's (unscaled r-table
+// values); the second is the Lax-Wendroff stages', with c_p = dt/dr* at
+// nodes (Eq. 14) and dt/(2 dr*) at half nodes (Eq. 13) folded in, so that
+// with rs = 1/Sigma, sg = rs^2
+//   c_p b   = rs RB
+//   c_p K   = sg (sg (E2 - E3 sin^2) + rs RCTR + CSE) + i sg (rs (RCTC cos + RCTI) + CSI)
+// (K = b c_t - c_* - b b_* as for RField).
+enum SField {
+    SF_R2 = 0, SF_AD, SF_DELTA, SF_CTR, SF_CTI, SF_CTC, SF_C0R, SF_C0I,
+    SF_RB, SF_E2, SF_E3, SF_RCTR, SF_CSE, SF_RCTC, SF_RCTI, SF_CSI, NSF
+};
+
 // Fields of the theta table.  AM, A0, AP are row j of the angular operator
 // A_th = -(d_thth + cot d_th) + (m + s cos)^2/sin^2 - s, centred differences,
 // parity ghosts folded into A0 at j = 0 and j = Ntheta-1.
@@ -63,8 +78,21 @@ template <> struct V2<double> { typedef double2 t; };
 template <typename T> struct ImpConst {
     typedef typename V2<T>::t c2;
     T gh, gh2, h1g, h12g;    // gamma h, (gamma h)^2, (1-gamma) h, (1-2 gamma) h
+    T h, g2h1;               // h, 2 gamma (1-gamma) h^2
     const c2 *piv;           // Thomas pivots of the stage matrix, [Nr][Nth]
     const int *plan;         // scan levels of each row's solves, [Nr]: forward | backward << 8
+};
+
+// Materialised coefficients of the FP64 path: the implicit step of length
+// dt ([Nr][Nth] per element, as imp_elem forms them) and the Lax-Wendroff
+// stages ([2Nr-1][Nth][4]: c_p b, c_p K, 0 per position and theta).  The FP64
+// pipe is the bound of the FP64 step, so what the step can read instead of
+// recompute it reads.
+template <typename T> struct MatPlanes {
+    typedef typename V2<T>::t c2;
+    const c2 *fk, *dg, *ct;
+    const T *sub, *qam, *qap;
+    const T *lw;
 };
 
 // Everything a step kernel needs, passed by value.
@@ -81,11 +109,15 @@ template <typename T> struct StepParams {
     int i_ext;               // extraction node
     int wave_cap;            // ring-buffer slots
     int patch_p0, patch_np;  // source patch rows [p0, p0+np); np = 0: no source
+    int wait0;               // try_wait rounds of a tile's waits on its state copy (< 0: kWaitLimit)
     T dt, half_dt, drs_inv;  // step, dt/2, 1/dr*
     ImpConst<T> full, half;  // implicit steps of length dt and dt/2
     double dt64;             // dt in FP64 (time and phase)
     double mOmega;           // m * Omega (FP64)
     const T *rtab;           // [2Nr-1][NRF]
+    const T *stab;           // step table [2Nr-1][NSF]
+    MatPlanes<T> mat;        // materialised coefficients (mat_on)
+    int mat_on;              // 1: full steps read them (FP64 state)
     const T *thtab;          // [NTF][Nth]
     const c2 *patch;         // [np][2][Nth]
     const double *w;         // [Nth]
@@ -157,7 +189,9 @@ __host__ __device__ inline PersistSmem persist_smem_plan(int R, int N, int tsize
 
 // ---------------------------------------------------------------- host side
 struct Layout {
-    size_t rtab64, rtabT, th64, thT, piv, pivh, plan, planh, patch, patchu, w, ctl, staging, scratch, total;
+    size_t rtab64, rtabT, stab, th64, thT, piv, pivh, plan, planh, patch, patchu, w, ctl, staging, scratch;
+    size_t mat, mat_bytes;   // materialised coefficients (FP64 split scheme; 0 bytes otherwise)
+    size_t total;
     size_t staging_elems;    // complex doubles that fit in the staging area
 };
 
@@ -229,6 +263,9 @@ cudaError_t launch_split_step2(const StepParams<T> &p, int threads, size_t smem,
 // dt/2 (p.half), written to plan_full / plan_half ([Nr] ints each).
 template <typename T>
 cudaError_t launch_scan_plans(const StepParams<T> &p, int *plan_full, int *plan_half, cudaStream_t st);
+// Materialised coefficients of the FP64 path into p.mat (no-op unless p.mat_on).
+template <typename T>
+cudaError_t launch_mat_coef(const StepParams<T> &p, cudaStream_t st);
 // Largest tile height of the split kernels (rows of the per-tile plan copy).
 constexpr int kMaxTileRows = 254;
 // Batched split step: one CTA of 256 threads per entry of the tile list
@@ -236,17 +273,27 @@ constexpr int kMaxTileRows = 254;
 // instance must use the theta segment `seg` (implicit_seg of its Ntheta).
 // ks = 2 advances every instance by two steps per launch (no first steps);
 // it exists for segments of up to 8 elements only (split_batch_available).
-bool split_batch_available(int seg, int ks);
 template <typename T>
 int split_batch_blocks_per_sm(int seg, size_t smem, int ks);
 template <typename T>
 cudaError_t launch_split_batch(const StepParams<T> *d_params, const int2 *d_tiles, int ntiles, int seg, size_t smem,
                                int ks, cudaStream_t st);
-int implicit_group(int Nth);            // threads per theta row
-int implicit_seg(int Nth);              // theta elements per thread
 constexpr int kSegNarrow = 4;           // theta elements per thread (Ntheta <= 128)
 constexpr int kSeg = 8;                 // theta elements per thread (Ntheta <= 256)
 constexpr int kSegWide = 32;            // theta elements per thread (Ntheta <= 1024)
+// theta elements per thread of the implicit row solves
+inline int implicit_seg(int Nth) { return Nth <= 128 ? kSegNarrow : (Nth <= 256 ? kSeg : kSegWide); }
+// threads per theta row (a power of two, at most a warp)
+inline int implicit_group(int Nth)
+{
+    int seg = implicit_seg(Nth);
+    int need = (Nth + seg - 1) / seg;
+    int G = 1;
+    while (G < need) G <<= 1;
+    return G;
+}
+inline bool split_batch_available(int seg, int ks) { return ks == 1 || (ks == 2 && seg != kSegWide); }
+
 cudaError_t launch_convert_to(int prec, const double2 *src, void *dst, size_t n, cudaStream_t st);
 cudaError_t launch_convert_from(int prec, const void *src, double2 *dst, size_t n, cudaStream_t st);
 

@@ -43,7 +43,7 @@ EXPORTED = [
     "teuk_batch_set_tiling", "teuk_batch_steps_per_launch", "teuk_batch_set_steps_per_launch",
     "teuk_batch_autotune", "teuk_batch_last_error", "teuk_batch_destroy",
     "teuk_apply_step", "teuk_apply_sample", "teuk_adjoint_workspace_bytes", "teuk_adjoint_step", "teuk_dot",
-    "teuk_set_tiling_steps", "teuk_state_level",
+    "teuk_set_tiling_steps", "teuk_state_level", "teuk_set_wait_limit", "teuk_fma_rate",
 ]
 
 
@@ -118,11 +118,14 @@ def lib(load_only: bool = False):
     L.teuk_set_tiling_steps.restype = ctypes.c_int
     L.teuk_set_persistent.argtypes = [vp, ctypes.c_int, ctypes.c_int]
     L.teuk_autotune_cold.argtypes = [vp, ctypes.c_int, vp, ctypes.c_size_t, vp, ctypes.POINTER(ctypes.c_int)]
+    L.teuk_set_wait_limit.argtypes = [vp, ctypes.c_int]
+    L.teuk_fma_rate.argtypes = [ctypes.c_int, ctypes.c_int, vp, vp, dp]
     for name in ("teuk_workspace_bytes", "teuk_init_grid", "teuk_set_source", "teuk_set_weights",
                  "teuk_set_state", "teuk_get_state", "teuk_step", "teuk_extract_waveform", "teuk_destroy",
                  "teuk_state_level",
                  "teuk_tiling", "teuk_autotune", "teuk_set_tiling", "teuk_literal_step_static",
-                 "teuk_kernel_config", "teuk_set_persistent", "teuk_autotune_cold"):
+                 "teuk_kernel_config", "teuk_set_persistent", "teuk_autotune_cold", "teuk_set_wait_limit",
+                 "teuk_fma_rate"):
         getattr(L, name).restype = ctypes.c_int
     L.teuk_apply_step.argtypes = [vp, vp, vp, i64, ctypes.c_int, vp]
     L.teuk_apply_sample.argtypes = [vp, vp, ctypes.c_int, vp, vp]
@@ -252,6 +255,20 @@ def teuk_autotune_cold(ctx, trial_steps: int, d_flush: int, flush_bytes: int, st
 
 def teuk_set_tiling(ctx, tile_rows: int):
     _check(lib().teuk_set_tiling(ctx, int(tile_rows)), ctx)
+
+
+def teuk_set_wait_limit(ctx, rounds: int):
+    """Bound of the tiled kernels' waits on their state copies (test hook;
+    rounds < 0 restores the default)."""
+    _check(lib().teuk_set_wait_limit(ctx, int(rounds)), ctx)
+
+
+def teuk_fma_rate(precision: str, iters: int, d_sink: int, stream: int) -> float:
+    """Measured FMA throughput of the current device in flop/s (two per FMA)."""
+    out = ctypes.c_double()
+    prec = {"fp64": TEUK_FP64, "fp32": TEUK_FP32}[precision]
+    _check(lib().teuk_fma_rate(prec, int(iters), d_sink, stream, ctypes.byref(out)))
+    return out.value
 
 
 def teuk_kernel_config(ctx) -> dict:

@@ -4,6 +4,9 @@ The oracle integrates Eq. 2 (dr*/dr = (r^2+a^2)/Delta) in closed form and
 inverts it by a bracketed Newton iteration in ln(r - r_+).  These checks use
 only facts independent of that code: the Schwarzschild closed form, a finite
 difference of r*(r) against Eq. 2's right-hand side, and the round trip.
+The orbit frequency of the source (Eq. 1's T slot, a circular equatorial
+orbit) is pinned to the circular-geodesic condition of the Kerr metric,
+differentiated by sympy.
 """
 import math
 
@@ -57,9 +60,56 @@ def test_near_horizon_depth():
     assert abs(x / approx - 1.0) < 1e-10
 
 
-def test_kepler_frequency():
-    """Prograde circular equatorial orbit, Omega = M^1/2 / (r0^3/2 + a M^1/2)."""
-    assert abs(O.kepler_omega(1.0, 0.9, 10.0) - 1.0 / (10.0 ** 1.5 + 0.9)) < 1e-15
-    assert abs(O.kepler_omega(1.0, 0.0, 6.0) - 6.0 ** -1.5) < 1e-15
-    # value quoted for the 1024x32 workload (a=0.9, r0=10): 0.0307477/M
-    assert abs(O.kepler_omega(1.0, 0.9, 10.0) - 0.0307477) < 1e-7
+def _kerr_circular_omegas(M, a, r):
+    """Both circular equatorial geodesic frequencies Omega = dphi/dt of the
+    Kerr metric at Boyer-Lindquist radius r, derived here from the metric
+    itself: on a circular orbit u = u^t (1, 0, 0, Omega) the radial geodesic
+    equation reduces to
+        d_r g_tt + 2 Omega d_r g_tphi + Omega^2 d_r g_phiphi = 0
+    at theta = pi/2.  The metric components are those of the Kerr line
+    element in Boyer-Lindquist coordinates (rho^2 = r^2 + a^2 cos^2 theta,
+    Delta = r^2 - 2 M r + a^2); sympy differentiates them."""
+    sp = __import__("sympy")
+    rr, th, MM, aa = sp.symbols("r theta M a", positive=True)
+    rho2 = rr**2 + aa**2 * sp.cos(th)**2
+    g_tt = -(1 - 2 * MM * rr / rho2)
+    g_tp = -2 * MM * aa * rr * sp.sin(th)**2 / rho2
+    g_pp = (rr**2 + aa**2 + 2 * MM * aa**2 * rr * sp.sin(th)**2 / rho2) * sp.sin(th)**2
+    sub = {rr: r, th: sp.pi / 2, MM: M, aa: a}
+    c0, c1, c2 = (float(sp.diff(g, rr).subs(sub).evalf(30)) for g in (g_tt, g_tp, g_pp))
+    W = sp.symbols("W")
+    roots = sp.Poly(c2 * W**2 + 2 * c1 * W + c0, W).nroots(n=30)
+    return sorted(float(x) for x in roots)
+
+
+@pytest.mark.parametrize("a", [0.0, 0.5, 0.9, 0.99, 0.999])
+@pytest.mark.parametrize("r0", [4.0, 6.0, 10.0, 15.0, 20.0])
+def test_kepler_frequency_from_kerr_geodesics(a, r0):
+    """The oracle's orbital frequency (it sets the source phase e^{-i m Omega t})
+    is the prograde circular-orbit frequency of the Kerr metric: of the two
+    roots of the circular-geodesic condition, the one that co-rotates with
+    the hole (Omega > 0 for a >= 0, the larger root).  A dropped a-term, a
+    wrong power of r0 or the retrograde branch fails this."""
+    pytest.importorskip("sympy")
+    lo, hi = _kerr_circular_omegas(1.0, a, r0)
+    assert lo < 0.0 < hi
+    got = O.kepler_omega(1.0, a, r0)
+    assert abs(got - hi) <= 1e-13 * hi, (a, r0, got, hi)
+    if a > 0.0:
+        # the retrograde orbit is distinguishable at this tolerance
+        assert abs(abs(lo) - hi) > 1e-6 * hi
+
+
+def test_kepler_frequency_mass_scaling():
+    """Omega scales as 1/M at fixed r0/M and a/M (the metric has no other
+    length scale)."""
+    for M in (0.5, 2.0, 7.0):
+        assert abs(O.kepler_omega(M, 0.9 * M, 10.0 * M) * M - O.kepler_omega(1.0, 0.9, 10.0)) < 1e-15
+
+
+def test_kepler_frequency_schwarzschild_newtonian_form():
+    """a = 0: Kepler's third law Omega^2 r^3 = M holds exactly for circular
+    Schwarzschild geodesics in Boyer-Lindquist time."""
+    for r0 in (3.5, 6.0, 10.0, 100.0):
+        w = O.kepler_omega(1.0, 0.0, r0)
+        assert abs(w * w * r0**3 - 1.0) < 1e-14
