@@ -682,10 +682,14 @@ int teuk_set_source(teuk_ctx *c, double amp_re, double amp_im, double r0, double
     const teuk_grid_desc &d = c->d;
     if (!isfinite(amp_re) || !isfinite(amp_im)) return set_err(c, TEUK_E_INVAL, "amplitude must be finite");
     drop_graphs(c);
+    // steps still in flight on any stream read the source tables
+    CK(cudaDeviceSynchronize(), "source sync");
     const bool off = amp_re == 0.0 && amp_im == 0.0;
     double rp = d.M + sqrt(d.M * d.M - d.a * d.a);
     const bool orbit_ok = r0 > rp && isfinite(r0) && sigma_rstar > 0.0 && sigma_theta > 0.0;
     if (off && !orbit_ok) {
+        CK(launch_src_fields(d, c->drs, c->coef, c->L, 0, 0, 0.0, 0.0, 0.0, 1.0, 1.0, 0), "source factors");
+        CK(cudaStreamSynchronize(0), "source sync");
         c->patch_np = 0;
         c->unit_np = 0;
         c->mOmega = 0.0;
@@ -708,10 +712,12 @@ int teuk_set_source(teuk_ctx *c, double amp_re, double amp_im, double r0, double
     long long cap_rows = d.Nr < TEUK_MAX_PATCH_ROWS ? d.Nr : TEUK_MAX_PATCH_ROWS;
     if (np > cap_rows) return set_err(c, TEUK_E_INVAL, "source patch needs more rows than TEUK_MAX_PATCH_ROWS");
     cudaStream_t st = 0;
-    if (np > 0) {
+    if (np > 0)
         CK(launch_patch(d, c->drs, c->coef, c->L, (int)p0, np, amp_re, amp_im, rs0, sigma_rstar, sigma_theta, st), "source patch");
-        CK(cudaStreamSynchronize(st), "source sync");
-    }
+    // the factored form the forward step kernels use (zero when the amplitude is)
+    CK(launch_src_fields(d, c->drs, c->coef, c->L, (int)p0, off ? 0 : np, amp_re, amp_im, rs0, sigma_rstar,
+                         sigma_theta, st), "source factors");
+    CK(cudaStreamSynchronize(st), "source sync");
     c->patch_p0 = (int)p0;
     c->patch_np = off ? 0 : np;
     c->unit_p0 = (int)p0;

@@ -147,6 +147,7 @@ __global__ void k_rtab(CoefArgs A)
     g[SF_RCTC] = cp * f[RF_R] * f[RF_CTC];
     g[SF_RCTI] = cp * f[RF_R] * f[RF_CTI];
     g[SF_CSI] = cp * f[RF_CSI];
+    g[SF_SRE] = g[SF_SIM] = g[SF_SR2] = g[SF_SPAD] = 0.0;   // no source until teuk_set_source
     if (A.prec == TEUK_FP32)
         for (int q = 0; q < NSF; ++q) ((float *)A.stab)[(size_t)p * NSF + q] = (float)g[q];
     else
@@ -173,7 +174,7 @@ __global__ void k_theta(CoefArgs A)
         double par = (abs(A.m) % 2 == 0) ? 1.0 : -1.0;   // ghost parity (pole conditions)
         if (j == 0) { a0 += par * am; am = 0.0; }
         if (j == N - 1) { a0 += par * ap; ap = 0.0; }
-        double v[NTF] = {sn * sn, cs, am, a0, ap, 0.0, 0.0, 0.0};
+        double v[NTF] = {sn * sn, cs, am, a0, ap, 0.0, 0.0, 0.0};   // source factors set later
         for (int q = 0; q < NTF; ++q) A.th64[q * N + j] = v[q];
         if (A.prec == TEUK_FP32)
             for (int q = 0; q < NTF; ++q) ((float *)A.thT)[q * N + j] = (float)v[q];
@@ -283,6 +284,61 @@ __global__ void k_patch(PatchArgs A)
     }
 }
 
+struct SrcArgs {
+    int Nr, Nth, p0, np, prec;
+    double rs_min, drs, dth, a;
+    double amp_re, amp_im, rs0, sig_r, sig_th;
+    const double *rtab64;
+    void *stab;
+    double *th64;
+    void *thT;
+};
+
+// Source factors (SField, TField) at step-table position idx (and theta
+// idx for the angular ones), from the FP64 r table; the same Gaussian and
+// prefactor as k_patch, factored.
+__global__ void k_src_fields(SrcArgs A)
+{
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx < A.Nth) {
+        const double th = ((double)idx + 0.5) * A.dth, cs = cos(th), dq = th - 0.5 * kPi;
+        const double G = exp(-dq * dq / (2.0 * A.sig_th * A.sig_th));
+        const double g2 = A.a * A.a * cs * cs * G;
+        A.th64[TF_GTH * A.Nth + idx] = G;
+        A.th64[TF_GA2 * A.Nth + idx] = g2;
+        if (A.prec == TEUK_FP32) {
+            ((float *)A.thT)[TF_GTH * A.Nth + idx] = (float)G;
+            ((float *)A.thT)[TF_GA2 * A.Nth + idx] = (float)g2;
+        }
+    }
+    if (idx >= 2 * A.Nr - 1) return;
+    double sre = 0.0, sim = 0.0, r2 = 0.0;
+    if (A.np > 0 && idx >= 2 * A.p0 && idx < 2 * (A.p0 + A.np)) {
+        const double *f = A.rtab64 + (size_t)idx * NRF;
+        const double r = f[RF_RR], D = f[RF_DELTA];
+        const int gi = idx >> 1;
+        const double rs = (idx & 1) ? A.rs_min + ((double)gi + 0.5) * A.drs : A.rs_min + (double)gi * A.drs;
+        const double dr = rs - A.rs0;
+        const double Gr = exp(-dr * dr / (2.0 * A.sig_r * A.sig_r));
+        const double rad = 4.0 * kPi * D * Gr / (r * r * r);
+        sre = A.amp_re * rad;
+        sim = A.amp_im * rad;
+        r2 = r * r;
+    }
+    const size_t o = (size_t)idx * NSF;
+    if (A.prec == TEUK_FP32) {
+        float *t = (float *)A.stab + o;
+        t[SF_SRE] = (float)sre;
+        t[SF_SIM] = (float)sim;
+        t[SF_SR2] = (float)r2;
+    } else {
+        double *t = (double *)A.stab + o;
+        t[SF_SRE] = sre;
+        t[SF_SIM] = sim;
+        t[SF_SR2] = r2;
+    }
+}
+
 __global__ void k_set_ctl(Ctl *c, long long step, int clear_flags)
 {
     c->step = step;
@@ -354,6 +410,34 @@ cudaError_t launch_patch(const teuk_grid_desc &d, double drs, void *coef, const 
     A.patchu = (char *)coef + L.patchu;
     int total = np * 2 * A.Nth;
     k_patch<<<(total + 255) / 256, 256, 0, st>>>(A);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_src_fields(const teuk_grid_desc &d, double drs, void *coef, const Layout &L, int p0, int np,
+                              double amp_re, double amp_im, double rs0, double sig_r, double sig_th, cudaStream_t st)
+{
+    SrcArgs A;
+    A.Nr = (int)d.Nr;
+    A.Nth = (int)d.Ntheta;
+    A.p0 = p0;
+    A.np = np;
+    A.prec = d.precision;
+    A.rs_min = d.rstar_min;
+    A.drs = drs;
+    A.dth = kPi / (double)d.Ntheta;
+    A.a = d.a;
+    A.amp_re = amp_re;
+    A.amp_im = amp_im;
+    A.rs0 = rs0;
+    A.sig_r = sig_r;
+    A.sig_th = sig_th;
+    char *base = (char *)coef;
+    A.rtab64 = (const double *)(base + L.rtab64);
+    A.stab = base + L.stab;
+    A.th64 = (double *)(base + L.th64);
+    A.thT = base + L.thT;
+    const int n = 2 * A.Nr - 1 > A.Nth ? 2 * A.Nr - 1 : A.Nth;
+    k_src_fields<<<(n + 255) / 256, 256, 0, st>>>(A);
     return cudaGetLastError();
 }
 

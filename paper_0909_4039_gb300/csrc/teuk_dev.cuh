@@ -1006,7 +1006,9 @@ static_assert(RF_R < 12 && RF_R2 < 12 && RF_AD < 12 && RF_CTR < 12 && RF_CTI < 1
 //   Eq. 14:  Phi' = Phi - beta (Phi*_+ - Phi*_-)
 //            Pi'  = Pi + beta (Pi*_+ - Pi*_-) + kap (Phi*_+ - Phi*_-) + dt F.
 // ph1 and ph2 are the source phases e^{-i m Omega t} at t_n and t_n + dt/2
-// times dt/2 and dt.  Tile row lr is global row g0 + lr.
+// times dt/2 and dt; the spatial part of F comes from its factors in the
+// step and theta tables (SField), so the stages read no global memory.
+// Tile row lr is global row g0 + lr.
 // INTERIOR: every node and midpoint of the segment lies strictly inside
 // the grid (1 <= row <= Nr - 2), so the boundary tests are left out; they
 // cost about 8 % of a step when taken in every tile.
@@ -1014,7 +1016,7 @@ static_assert(RF_R < 12 && RF_R2 < 12 && RF_AD < 12 && RF_CTR < 12 && RF_CTI < 1
 // of step-table entry f and theta (sin^2 = S2, cos = C).  The materialised
 // planes of the FP64 path (k_mat_coef) are made by this same function.
 template <typename T>
-__device__ __forceinline__ void lw_coef(const T *f, T S2, T C, T &beta, typename V2<T>::t &kap)
+__device__ __forceinline__ void lw_coef(const T *f, T S2, T C, T &beta, typename V2<T>::t &kap, T *sg_out = nullptr)
 {
     typedef typename V2<T>::t c2;
     constexpr int NA = 16 / (int)sizeof(T);   // one 16-byte load holds R2 and AD
@@ -1027,6 +1029,7 @@ __device__ __forceinline__ void lw_coef(const T *f, T S2, T C, T &beta, typename
     const T kx = fma(sg, fma(-l[SF_E3 - SF_RB], S2, l[SF_E2 - SF_RB]), fma(rs, l[SF_RCTR - SF_RB], l[SF_CSE - SF_RB]));
     const T ky = fma(rs, fma(l[SF_RCTC - SF_RB], C, l[SF_RCTI - SF_RB]), l[SF_CSI - SF_RB]);
     kap = cmk<c2>(sg * kx, sg * ky);
+    if (sg_out) *sg_out = sg;
 }
 
 template <typename T, bool INTERIOR, bool MAT = false>
@@ -1041,17 +1044,37 @@ __device__ void lw_segment(const StepParams<T> &p, typename V2<T>::t *sPhi, type
     const T S2 = sTh[TF_S2 * N + j], C = sTh[TF_C * N + j];
     const c2 zero = cmk<c2>(T(0), T(0));
     const T half = T(0.5);
+    T gth = T(0), ga2 = T(0);
+    if (src) {
+        gth = sTh[TF_GTH * N + j];
+        ga2 = sTh[TF_GA2 * N + j];
+    }
 
-    // beta and kap at tile position e (2 lr: node, 2 k + 1: half node)
-    auto coef = [&](int e, T &beta, c2 &kap) {
+    // beta and kap at tile position e (2 lr: node, 2 k + 1: half node), and
+    // 1/Sigma^2 there when the source needs it
+    auto coef = [&](int e, T &beta, c2 &kap, T &sg, bool need_sg) {
         if constexpr (MAT) {
             T v[4];
             vload<4>(v, p.mat.lw + ((size_t)(2 * g0 + e) * N + j) * 4);
             beta = v[0];
             kap = cmk<c2>(v[1], v[2]);
+            if (need_sg) {
+                const T *f = sSt + e * NSF;
+                const T rs = rsq_(fma(-f[SF_AD], S2, f[SF_R2]));
+                sg = rs * rs;
+            }
         } else {
-            lw_coef<T>(sSt + e * NSF, S2, C, beta, kap);
+            lw_coef<T>(sSt + e * NSF, S2, C, beta, kap, &sg);
         }
+    };
+    // source at tile position e times the scaled phase ph (zero outside the
+    // patch rows): F = SRC sg (SR2 GTH + GA2)
+    auto source = [&](int e, T sg, c2 ph) {
+        const T *f = sSt + e * NSF;
+        T sv[4];
+        vload<4>(sv, f + SF_SRE);
+        const c2 F = cscale<c2>(sg * fma(sv[SF_SR2 - SF_SRE], gth, ga2), cmk<c2>(sv[0], sv[1]));
+        return cmul(F, ph);
     };
 
     // u*_{k+1/2} between tile rows k and k+1 (Eq. 13)
@@ -1062,13 +1085,14 @@ __device__ void lw_segment(const StepParams<T> &p, typename V2<T>::t *sPhi, type
             mg = zero;
             return;
         }
-        T beta;
+        T beta, sg;
         c2 kap;
-        coef(2 * k + 1, beta, kap);
+        const bool s_row = src && gl >= p.patch_p0 && gl < p.patch_p0 + p.patch_np;
+        coef(2 * k + 1, beta, kap, sg, s_row);
         const c2 df = csub(fb, fa);
         mf = caxpy(-beta, df, cscale<c2>(half, cadd(fa, fb)));
         c2 t = caxpy(beta, csub(gb, ga), cscale<c2>(half, cadd(ga, gb)));
-        if (src) t = cadd(t, patch_val(p, gl, 1, j, ph1));
+        if (s_row) t = cadd(t, source(2 * k + 1, sg, ph1));
         mg = cfma(kap, df, t);
     };
 
@@ -1091,13 +1115,14 @@ __device__ void lw_segment(const StepParams<T> &p, typename V2<T>::t *sPhi, type
         c2 nfv = zero, ngv = zero;
         if (INTERIOR || (gi >= 1 && gi <= Nr - 2)) {
             // Eq. 14 at node gi
-            T beta;
+            T beta, sg;
             c2 kap;
-            coef(2 * lr, beta, kap);
+            const bool s_row = src && gi >= p.patch_p0 && gi < p.patch_p0 + p.patch_np;
+            coef(2 * lr, beta, kap, sg, s_row);
             const c2 dmf = csub(mf, mfp);
             nfv = caxpy(-beta, dmf, fb);
             c2 t = caxpy(beta, csub(mg, mgp), gb);
-            if (src) t = cadd(t, patch_val(p, gi, 0, j, ph2));
+            if (s_row) t = cadd(t, source(2 * lr, sg, ph2));
             ngv = cfma(kap, dmf, t);
         }
         sPhi[lr * P + j] = nfv;

@@ -49,16 +49,25 @@ enum RField {
 // with rs = 1/Sigma, sg = rs^2
 //   c_p b   = rs RB
 //   c_p K   = sg (sg (E2 - E3 sin^2) + rs RCTR + CSE) + i sg (rs (RCTC cos + RCTI) + CSI)
-// (K = b c_t - c_* - b b_* as for RField).
+// (K = b c_t - c_* - b b_* as for RField).  The last block holds the
+// radial factors of the source (set by teuk_set_source, zero outside its
+// patch rows): the source term of Eq. 1 after the division that gives
+// Eq. 9 is separable,
+//   F = A 4 pi (r^2 + a^2 cos^2) Delta/(Sigma^2 r^3) G_r(r*) G_th(theta)
+//     = SRC sg (SR2 GTH + GA2),   SRC = A 4 pi Delta G_r / r^3,  SR2 = r^2,
+// with GTH = G_th and GA2 = a^2 cos^2 G_th in the theta table.
 enum SField {
     SF_R2 = 0, SF_AD, SF_DELTA, SF_CTR, SF_CTI, SF_CTC, SF_C0R, SF_C0I,
-    SF_RB, SF_E2, SF_E3, SF_RCTR, SF_CSE, SF_RCTC, SF_RCTI, SF_CSI, NSF
+    SF_RB, SF_E2, SF_E3, SF_RCTR, SF_CSE, SF_RCTC, SF_RCTI, SF_CSI,
+    SF_SRE, SF_SIM, SF_SR2, SF_SPAD, NSF
 };
 
 // Fields of the theta table.  AM, A0, AP are row j of the angular operator
 // A_th = -(d_thth + cot d_th) + (m + s cos)^2/sin^2 - s, centred differences,
 // parity ghosts folded into A0 at j = 0 and j = Ntheta-1.
-enum TField { TF_S2 = 0, TF_C, TF_AM, TF_A0, TF_AP, TF_PAD0, TF_PAD1, TF_PAD2, NTF };
+// GTH, GA2: the angular factors of the source (see SField), set by
+// teuk_set_source.
+enum TField { TF_S2 = 0, TF_C, TF_AM, TF_A0, TF_AP, TF_GTH, TF_GA2, TF_PAD2, NTF };
 
 // Error flags in Ctl::flags.
 enum : unsigned { FLAG_NONFINITE = 1u, FLAG_TIMEOUT = 2u };
@@ -141,11 +150,11 @@ template <typename T> struct StepParams {
 constexpr double kGamma = 0.29289321881345247559915563789515;
 constexpr double kPi = 3.14159265358979323846264338327950;
 
-// Shared-memory carve-up of the split kernel for R = tile_rows + 2 rows of
-// N theta points; every section starts on a 16-byte boundary.  piv holds
-// the tile rows' Thomas pivots; rt holds the r-table entries of positions
-// 2(i0-1) .. 2(i0+TR) (nodes and half nodes interleaved, as in the global
-// table).
+// Shared-memory carve-up of the split kernel for R = tile_rows + 2 KS rows
+// of N theta points; every section starts on a 16-byte boundary.  piv holds
+// the tile rows' Thomas pivots; rt holds the step-table entries (SField) of
+// the tile's positions, nodes and half nodes interleaved as in the global
+// table.
 struct SplitSmem {
     unsigned phi, pi, piv, rt, th, total;
 };
@@ -158,15 +167,15 @@ __host__ __device__ inline SplitSmem split_smem_plan(int R, int N, int tsize)
     s.pi = smem_align16(plane);
     s.piv = smem_align16(s.pi + plane);
     s.rt = smem_align16(s.piv + plane);
-    s.th = smem_align16(s.rt + (unsigned)(2 * R - 1) * NRF * (unsigned)tsize);
+    s.th = smem_align16(s.rt + (unsigned)(2 * R - 1) * NSF * (unsigned)tsize);
     s.total = smem_align16(s.th + (unsigned)NTF * (unsigned)N * (unsigned)tsize);
     return s;
 }
 
 // Shared-memory carve-up of the persistent split kernel: theta tables, a
-// copy of the extraction row (state and r-table entry) and two tile
+// copy of the extraction row (state and step-table entry) and two tile
 // buffers, each with the two state planes [R][N], the pivots [R][N] and the
-// interleaved r-table entries [2R-1][NRF].
+// interleaved step-table entries [2R-1][NSF].
 struct PersistSmem {
     unsigned th, xphi, xpi, xf, buf, bpi, bpiv, brt, bsize, total;
 };
@@ -178,11 +187,11 @@ __host__ __device__ inline PersistSmem persist_smem_plan(int R, int N, int tsize
     s.xphi = smem_align16((unsigned)NTF * (unsigned)N * (unsigned)tsize);
     s.xpi = smem_align16(s.xphi + (unsigned)N * c2);
     s.xf = smem_align16(s.xpi + (unsigned)N * c2);
-    s.buf = smem_align16(s.xf + NRF * (unsigned)tsize);
+    s.buf = smem_align16(s.xf + NSF * (unsigned)tsize);
     s.bpi = smem_align16(plane);
     s.bpiv = smem_align16(s.bpi + plane);
     s.brt = smem_align16(s.bpiv + plane);
-    s.bsize = smem_align16(s.brt + (unsigned)(2 * R - 1) * NRF * (unsigned)tsize);
+    s.bsize = smem_align16(s.brt + (unsigned)(2 * R - 1) * NSF * (unsigned)tsize);
     s.total = s.buf + 2u * s.bsize;
     return s;
 }
@@ -205,6 +214,10 @@ cudaError_t launch_patch(const teuk_grid_desc &d, double drs, void *coef, const 
                          double sig_r, double sig_th, cudaStream_t st);
 cudaError_t launch_set_ctl(void *coef, const Layout &L, long long step, int clear_flags,
                            cudaStream_t st);
+// Source factors in the step and theta tables (SField, TField): positions
+// 2 p0 .. 2 (p0 + np) - 1 get the radial factor, every other position zero.
+cudaError_t launch_src_fields(const teuk_grid_desc &d, double drs, void *coef, const Layout &L, int p0, int np,
+                              double amp_re, double amp_im, double rs0, double sig_r, double sig_th, cudaStream_t st);
 
 // Adjoint and operator entry points (teuk_step.cu).
 template <typename T>
