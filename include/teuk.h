@@ -183,8 +183,11 @@ int teuk_tiling(const teuk_ctx *ctx, int *tile_rows, int *threads, size_t *smem_
 /* Which split-scheme kernel steps the grid.  *persistent = 1: the
  * persistent kernel (one CTA per SM walks the tiles; a producer warp moves
  * them by TMA into two shared-memory buffers while *consumer_threads threads
- * compute, so tile loads and stores overlap the arithmetic); 0: the tiled
- * kernel (one CTA per tile).  *grid is the number of CTAs per launch.
+ * compute, so tile loads and stores overlap the arithmetic); 2: the
+ * pipelined kernel (two steps per launch; about two CTAs per SM walk the
+ * tiles, each double-buffering them, so the copies of a CTA's next tile
+ * land while the current one computes); 0: the tiled kernel (one CTA per
+ * tile).  *grid is the number of CTAs per launch.
  * *steps_per_launch is 2 when the tiled kernel advances two time steps per
  * launch (temporal blocking: two halo rows on either side, one state read
  * and write per two steps), else 1.  Any pointer may be NULL.  For the
@@ -225,6 +228,16 @@ int teuk_set_tiling(teuk_ctx *ctx, int tile_rows);
  * result does not depend on the choice.  TEUK_E_INVAL if the tile does not
  * fit or steps_per_launch is not 1 or 2. */
 int teuk_set_tiling_steps(teuk_ctx *ctx, int tile_rows, int steps_per_launch);
+
+/* Select the pipelined split-scheme kernel (two time steps per launch,
+ * persistent CTAs of `threads` threads, 256 or 512, double-buffered tiles;
+ * see teuk_kernel_config) with the given tile height.  The first step of a
+ * run and an odd last step take the one-step tiled kernel at the same
+ * height.  The result does not depend on the choice.  TEUK_E_INVAL if the
+ * rows are not 16-byte multiples (Ntheta odd in FP32), two tile buffers do
+ * not fit in shared memory, or the CTA does not fit an SM (512 threads:
+ * Ntheta <= 256 and the FP32 state only in practice). */
+int teuk_set_pipelined(teuk_ctx *ctx, int tile_rows, int threads);
 
 /* Select the persistent split-scheme kernel with the given tile height and
  * consumer_threads in {384, 480}.  It exists for the FP32 state with

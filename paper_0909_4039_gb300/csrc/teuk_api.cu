@@ -55,6 +55,7 @@ struct teuk_ctx {
     int tile_rows, threads;
     size_t smem;
     int persist, nc, grid;
+    int pipe;                // the pipelined two-step kernel (grid persistent CTAs)
     size_t persist_smem;
     int ks;                  // time steps per launch of the tiled kernel (1 or 2)
     int wait0;               // teuk_set_wait_limit (< 0: default bound)
@@ -228,6 +229,7 @@ struct TileCand {
     int R;                   // tile_rows + 2
     int persist, nc, grid;
     int ks;                  // time steps per launch (tiled kernel)
+    int pipe;                // 1: the pipelined two-step kernel (grid persistent CTAs)
     size_t smem;
 };
 
@@ -261,6 +263,7 @@ static bool tiled_cand(const teuk_ctx *c, int TR, int nsm, TileCand *out)
     out->nc = 0;
     out->grid = (int)tiles;
     out->ks = 1;
+    out->pipe = 0;
     out->smem = sm;
     return true;
 }
@@ -289,6 +292,39 @@ static bool tiled2_cand(const teuk_ctx *c, int TR, int nsm, TileCand *out)
     out->nc = 0;
     out->grid = (int)tiles;
     out->ks = 2;
+    out->pipe = 0;
+    out->smem = sm;
+    return true;
+}
+
+// A pipelined two-step candidate of height TR with `threads` per CTA: grid =
+// resident CTAs (or fewer tiles), each walking ceil(tiles / grid) tiles of
+// the same per-tile work as tiled2_cand with the loads of all but its first
+// tile overlapped.
+static bool pipe_cand(const teuk_ctx *c, int TR, int threads, int nsm, TileCand *out)
+{
+    const int N = (int)c->d.Ntheta;
+    const bool f32 = c->d.precision == TEUK_FP32;
+    if (((size_t)N * (f32 ? sizeof(float2) : sizeof(double2))) % 16 != 0) return false;   // rows move by TMA
+    size_t sm = f32 ? pipe_smem_bytes<float>(TR, N) : pipe_smem_bytes<double>(TR, N);
+    if (sm > 227 * 1024) return false;
+    int k = f32 ? pipe_blocks_per_sm<float>(N, threads, sm) : pipe_blocks_per_sm<double>(N, threads, sm);
+    if (k < 1) return false;
+    const long long Nr = c->d.Nr;
+    long long tiles = (Nr + TR - 1) / TR;
+    long long grid = tiles < (long long)k * nsm ? tiles : (long long)k * nsm;
+    long long per = (tiles + grid - 1) / grid;
+    int rpp = threads / implicit_group(N);
+    auto rpad = [&](int r) { return ((r + rpp - 1) / rpp) * rpp; };
+    double rows = (0.6 * (rpad(TR + 4) + rpad(TR + 2)) + 0.4 * (2.0 * TR + 6.0)) * 256.0 / threads + 1.0;
+    const int warps = k * threads / 32;
+    out->cost = 0.5 * (double)per * k * rows * (warps < 16 ? 1.2 : 1.0) + 2.0;
+    out->R = TR + 2;
+    out->persist = 0;
+    out->nc = threads;
+    out->grid = (int)grid;
+    out->ks = 2;
+    out->pipe = 1;
     out->smem = sm;
     return true;
 }
@@ -319,6 +355,7 @@ static bool persist_cand(const teuk_ctx *c, int TR, int nc, int nsm, TileCand *o
     out->nc = nc;
     out->grid = (int)grid;
     out->ks = 1;
+    out->pipe = 0;
     out->smem = sm;
     return true;
 }
@@ -333,6 +370,8 @@ int tile_candidates(teuk_ctx *c, TileCand *out, int maxn)
     for (int TR = 1; TR <= kMaxTileRows && n < maxn; ++TR) {
         if (tiled_cand(c, TR, nsm, &out[n])) ++n;
         if (n < maxn && c->d.scheme == TEUK_SCHEME_SPLIT && tiled2_cand(c, TR, nsm, &out[n])) ++n;
+        for (int th : {256, 512})
+            if (n < maxn && c->d.scheme == TEUK_SCHEME_SPLIT && pipe_cand(c, TR, th, nsm, &out[n])) ++n;
         for (int nc : {384, 480})
             if (n < maxn && persist_cand(c, TR, nc, nsm, &out[n])) ++n;
         if (TR >= Nr) break;
@@ -358,8 +397,9 @@ static bool apply_cand(teuk_ctx *c, const TileCand &k)
     c->threads = 256;
     c->smem = t.smem;
     c->persist = k.persist;
-    c->nc = k.persist ? k.nc : 0;
-    c->grid = k.persist ? k.grid : 0;
+    c->pipe = k.pipe;
+    c->nc = (k.persist || k.pipe) ? k.nc : 0;
+    c->grid = (k.persist || k.pipe) ? k.grid : 0;
     c->persist_smem = k.persist ? k.smem : 0;
     c->ks = k.persist ? 1 : k.ks;
     c->smem2 = (!k.persist && k.ks == 2) ? k.smem : 0;
@@ -493,10 +533,12 @@ cudaError_t launch_unit(teuk_ctx *c, int in_level, cudaStream_t st, int *steps)
         *steps = 2;
         if (c->d.precision == TEUK_FP32) {
             StepParams<float> p = make_params<float>(c, in_level);
-            return launch_split_step2<float>(p, c->threads, c->smem2, st);
+            return c->pipe ? launch_split_pipe<float>(p, c->nc, c->grid, c->smem2, st)
+                           : launch_split_step2<float>(p, c->threads, c->smem2, st);
         }
         StepParams<double> p = make_params<double>(c, in_level);
-        return launch_split_step2<double>(p, c->threads, c->smem2, st);
+        return c->pipe ? launch_split_pipe<double>(p, c->nc, c->grid, c->smem2, st)
+                       : launch_split_step2<double>(p, c->threads, c->smem2, st);
     }
     *steps = 1;
     return launch_one(c, in_level, st);
@@ -946,9 +988,9 @@ int teuk_tiling(const teuk_ctx *c, int *tile_rows, int *threads, size_t *smem_by
 int teuk_kernel_config(const teuk_ctx *c, int *persistent, int *consumer_threads, int *grid, int *steps_per_launch)
 {
     if (!c) return TEUK_E_STATE;
-    if (persistent) *persistent = c->persist;
-    if (consumer_threads) *consumer_threads = c->persist ? c->nc : c->threads;
-    if (grid) *grid = c->persist ? c->grid : (int)((c->d.Nr + c->tile_rows - 1) / c->tile_rows);
+    if (persistent) *persistent = c->persist ? 1 : (c->pipe ? 2 : 0);
+    if (consumer_threads) *consumer_threads = (c->persist || c->pipe) ? c->nc : c->threads;
+    if (grid) *grid = (c->persist || c->pipe) ? c->grid : (int)((c->d.Nr + c->tile_rows - 1) / c->tile_rows);
     if (steps_per_launch) *steps_per_launch = c->d.scheme == TEUK_SCHEME_SPLIT ? c->ks : 1;
     return TEUK_OK;
 }
@@ -968,10 +1010,10 @@ static int autotune_impl(teuk_ctx *c, int trial_steps, void *flush, size_t flush
     int n = tile_candidates(c, all.data(), (int)all.size());
     // the best few of each kernel by the model
     std::vector<TileCand> cand;
-    for (int kind = 0; kind < 3; ++kind) {   // tiled, tiled two steps per launch, persistent
+    for (int kind = 0; kind < 4; ++kind) {   // tiled, tiled two steps per launch, persistent, pipelined
         int taken = 0;
         for (int k = 0; k < n && taken < 4; ++k) {
-            const int kk = all[k].persist ? 2 : (all[k].ks == 2 ? 1 : 0);
+            const int kk = all[k].pipe ? 3 : (all[k].persist ? 2 : (all[k].ks == 2 ? 1 : 0));
             if (kk == kind) {
                 cand.push_back(all[k]);
                 ++taken;
@@ -1075,6 +1117,23 @@ int teuk_set_tiling_steps(teuk_ctx *c, int tile_rows, int steps_per_launch)
     TileCand t;
     if (!tiled2_cand(c, tile_rows, sm_count(), &t))
         return set_err(c, TEUK_E_INVAL, "tile does not fit in shared memory");
+    TileCand tt;
+    if (!tiled_cand(c, tile_rows, sm_count(), &tt)) return set_err(c, TEUK_E_INVAL, "tile does not fit in shared memory");
+    drop_graphs(c);
+    apply_cand(c, t);
+    return TEUK_OK;
+}
+
+int teuk_set_pipelined(teuk_ctx *c, int tile_rows, int threads)
+{
+    if (!c) return TEUK_E_STATE;
+    if (c->d.scheme != TEUK_SCHEME_SPLIT) return set_err(c, TEUK_E_INVAL, "the pipelined kernel is a split-scheme kernel");
+    if (tile_rows < 1 || tile_rows > 250) return set_err(c, TEUK_E_INVAL, "tile_rows out of range [1, 250]");
+    if (threads != 256 && threads != 512) return set_err(c, TEUK_E_INVAL, "threads must be 256 or 512");
+    TileCand t;
+    if (!pipe_cand(c, tile_rows, threads, sm_count(), &t))
+        return set_err(c, TEUK_E_INVAL, "pipelined kernel unavailable: rows must be 16-byte multiples and two tile "
+                                        "buffers must fit in shared memory");
     TileCand tt;
     if (!tiled_cand(c, tile_rows, sm_count(), &tt)) return set_err(c, TEUK_E_INVAL, "tile does not fit in shared memory");
     drop_graphs(c);

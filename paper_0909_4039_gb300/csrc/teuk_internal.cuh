@@ -196,6 +196,32 @@ __host__ __device__ inline PersistSmem persist_smem_plan(int R, int N, int tsize
     return s;
 }
 
+// Shared-memory carve-up of the pipelined split kernel (two steps per
+// launch, persistent CTAs): theta tables, a copy of the extraction row, then
+// two tile buffers of R = tile_rows + 4 rows, each with the state planes
+// and pivots [R][N], the step-table entries of the tile's positions
+// [2R][NSF] and the scan plans of its rows (R + 8 ints, the copy starts on
+// a 16-byte boundary of the global plan array).
+struct PipeSmem {
+    unsigned th, xphi, xpi, buf, pi, piv, st, plan, bsize, total;
+};
+__host__ __device__ inline PipeSmem pipe_smem_plan(int R, int N, int tsize)
+{
+    PipeSmem s;
+    const unsigned c2 = 2u * (unsigned)tsize, plane = (unsigned)R * (unsigned)N * c2;
+    s.th = 0;
+    s.xphi = smem_align16((unsigned)NTF * (unsigned)N * (unsigned)tsize);
+    s.xpi = smem_align16(s.xphi + (unsigned)N * c2);
+    s.buf = smem_align16(s.xpi + (unsigned)N * c2);
+    s.pi = smem_align16(plane);
+    s.piv = smem_align16(s.pi + plane);
+    s.st = smem_align16(s.piv + plane);
+    s.plan = smem_align16(s.st + 2u * (unsigned)R * NSF * (unsigned)tsize);
+    s.bsize = smem_align16(s.plan + ((unsigned)R + 8u) * 4u);
+    s.total = s.buf + 2u * s.bsize;
+    return s;
+}
+
 // ---------------------------------------------------------------- host side
 struct Layout {
     size_t rtab64, rtabT, stab, th64, thT, piv, pivh, plan, planh, patch, patchu, w, ctl, staging, scratch;
@@ -276,6 +302,16 @@ cudaError_t launch_split_step2(const StepParams<T> &p, int threads, size_t smem,
 // dt/2 (p.half), written to plan_full / plan_half ([Nr] ints each).
 template <typename T>
 cudaError_t launch_scan_plans(const StepParams<T> &p, int *plan_full, int *plan_half, cudaStream_t st);
+// Pipelined split kernel: two time steps per launch, `grid` persistent CTAs
+// of `threads` (256, or 512 for Ntheta <= 256) walk the tiles, each
+// double-buffering them in shared memory (the next tile's copies land while
+// the current one computes).  Full steps only, bulk-copyable rows (p.bulk).
+template <typename T>
+size_t pipe_smem_bytes(int tile_rows, int Nth);
+template <typename T>
+int pipe_blocks_per_sm(int Nth, int threads, size_t smem);
+template <typename T>
+cudaError_t launch_split_pipe(const StepParams<T> &p, int threads, int grid, size_t smem, cudaStream_t st);
 // Materialised coefficients of the FP64 path into p.mat (no-op unless p.mat_on).
 template <typename T>
 cudaError_t launch_mat_coef(const StepParams<T> &p, cudaStream_t st);

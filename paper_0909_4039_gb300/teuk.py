@@ -44,6 +44,7 @@ EXPORTED = [
     "teuk_batch_autotune", "teuk_batch_last_error", "teuk_batch_destroy",
     "teuk_apply_step", "teuk_apply_sample", "teuk_adjoint_workspace_bytes", "teuk_adjoint_step", "teuk_dot",
     "teuk_set_tiling_steps", "teuk_state_level", "teuk_set_wait_limit", "teuk_fma_rate",
+    "teuk_set_pipelined",
 ]
 
 
@@ -119,13 +120,14 @@ def lib(load_only: bool = False):
     L.teuk_set_persistent.argtypes = [vp, ctypes.c_int, ctypes.c_int]
     L.teuk_autotune_cold.argtypes = [vp, ctypes.c_int, vp, ctypes.c_size_t, vp, ctypes.POINTER(ctypes.c_int)]
     L.teuk_set_wait_limit.argtypes = [vp, ctypes.c_int]
+    L.teuk_set_pipelined.argtypes = [vp, ctypes.c_int, ctypes.c_int]
     L.teuk_fma_rate.argtypes = [ctypes.c_int, ctypes.c_int, vp, vp, dp]
     for name in ("teuk_workspace_bytes", "teuk_init_grid", "teuk_set_source", "teuk_set_weights",
                  "teuk_set_state", "teuk_get_state", "teuk_step", "teuk_extract_waveform", "teuk_destroy",
                  "teuk_state_level",
                  "teuk_tiling", "teuk_autotune", "teuk_set_tiling", "teuk_literal_step_static",
                  "teuk_kernel_config", "teuk_set_persistent", "teuk_autotune_cold", "teuk_set_wait_limit",
-                 "teuk_fma_rate"):
+                 "teuk_fma_rate", "teuk_set_pipelined"):
         getattr(L, name).restype = ctypes.c_int
     L.teuk_apply_step.argtypes = [vp, vp, vp, i64, ctypes.c_int, vp]
     L.teuk_apply_sample.argtypes = [vp, vp, ctypes.c_int, vp, vp]
@@ -257,6 +259,10 @@ def teuk_set_tiling(ctx, tile_rows: int):
     _check(lib().teuk_set_tiling(ctx, int(tile_rows)), ctx)
 
 
+def teuk_set_pipelined(ctx, tile_rows: int, threads: int = 256):
+    _check(lib().teuk_set_pipelined(ctx, int(tile_rows), int(threads)), ctx)
+
+
 def teuk_set_wait_limit(ctx, rounds: int):
     """Bound of the tiled kernels' waits on their state copies (test hook;
     rounds < 0 restores the default)."""
@@ -274,8 +280,8 @@ def teuk_fma_rate(precision: str, iters: int, d_sink: int, stream: int) -> float
 def teuk_kernel_config(ctx) -> dict:
     pe, nc, gr, ks = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
     _check(lib().teuk_kernel_config(ctx, ctypes.byref(pe), ctypes.byref(nc), ctypes.byref(gr), ctypes.byref(ks)), ctx)
-    return {"persistent": bool(pe.value), "consumer_threads": nc.value, "grid": gr.value,
-            "steps_per_launch": ks.value}
+    return {"persistent": pe.value == 1, "pipelined": pe.value == 2, "consumer_threads": nc.value,
+            "grid": gr.value, "steps_per_launch": ks.value}
 
 
 def teuk_set_tiling_steps(ctx, tile_rows: int, steps_per_launch: int):
@@ -351,6 +357,9 @@ class Stepper:
 
     def set_persistent(self, tile_rows: int, consumer_threads: int = 480):
         teuk_set_persistent(self.ctx, tile_rows, consumer_threads)
+
+    def set_pipelined(self, tile_rows: int, threads: int = 256):
+        teuk_set_pipelined(self.ctx, tile_rows, threads)
 
     def set_source(self, amp=1.0, r0=10.0, sigma_rstar=0.1, sigma_theta=0.1, Omega=float("nan")):
         teuk_set_source(self.ctx, amp, r0, sigma_rstar, sigma_theta, Omega)

@@ -354,7 +354,8 @@ def test_kernel_variants_agree_bitwise_over_long_runs(precision):
     w = inputs.Workload("long", s=-2, m=2, a=0.7, Nr=457, Ntheta=128, rs_min=-60.0, rs_max=240.0, steps=1001,
                         r0=12.0, amp=0.8 - 0.8j, sig_r=0.9, sig_th=0.25, rs_ext=150.0)
     u0 = inputs.random_state(w.Nr, w.Ntheta, seed=104)
-    configs = [("tiled", 30, 1), ("tiled", 7, 2), ("tiled", 26, 2), ("tiled", 12, 1)]
+    configs = [("tiled", 30, 1), ("tiled", 7, 2), ("tiled", 26, 2), ("tiled", 12, 1), ("pipelined", 12, 256),
+               ("pipelined", 2, 256)]
     if precision == "fp32":
         configs.append(("persistent", 8, 480))
     outs = []
@@ -362,6 +363,8 @@ def test_kernel_variants_agree_bitwise_over_long_runs(precision):
         st = gpu_stepper(w, precision, wave_capacity=w.steps + 1)
         if kind == "tiled":
             st.set_tiling(tr, x)
+        elif kind == "pipelined":
+            st.set_pipelined(tr, x)
         else:
             st.set_persistent(tr, x)
         st.set_state(u0, 0)
@@ -371,3 +374,61 @@ def test_kernel_variants_agree_bitwise_over_long_runs(precision):
     for (kind, tr, x), (u, h) in zip(configs[1:], outs[1:]):
         assert np.array_equal(u, outs[0][0]), (kind, tr, x, rel_l2(u, outs[0][0]))
         assert np.array_equal(h, outs[0][1]), (kind, tr, x, rel_l2(h, outs[0][1]))
+
+
+PIPE = [
+    # Nr, Ntheta, tile_rows, threads, steps: more tiles than resident CTAs (each
+    # CTA walks several tiles through both buffers), ragged last tiles, the
+    # source and the extraction node inside tiles, odd step counts, graph
+    # replays (>= 128)
+    (2000, 128, 3, 256, 41),
+    (3001, 64, 5, 256, 130),
+    (1234, 32, 2, 256, 27),
+    (457, 128, 12, 256, 33),
+    (620, 16, 1, 256, 19),
+    (1500, 128, 2, 512, 41),
+    (2222, 64, 7, 512, 29),
+]
+
+
+@pytest.mark.parametrize("Nr,Nth,tr,threads,steps", PIPE)
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_pipelined_kernel_matches_tiled_and_oracle(Nr, Nth, tr, threads, steps, precision):
+    """The pipelined two-step kernel (persistent CTAs, double-buffered tiles)
+    gives bitwise the states and waveform of the tiled kernel; the oracle
+    agrees within the tolerance."""
+    from oracle import oracle as O
+    w = inputs.Workload("pipe", s=-2, m=2, a=0.9, Nr=Nr, Ntheta=Nth, rs_min=-60.0, rs_max=240.0, steps=steps,
+                        r0=8.0, amp=0.8 + 0.3j, sig_r=0.9, sig_th=0.25, rs_ext=150.0)
+    u0 = inputs.random_state(w.Nr, w.Ntheta, seed=Nr + 5 * Nth)
+    outs = []
+    for kind in ("tiled", "pipelined"):
+        st = gpu_stepper(w, precision, wave_capacity=steps + 2)
+        if kind == "tiled":
+            st.set_tiling(tr, 1)
+        else:
+            st.set_pipelined(tr, threads)
+            cfg = st.tiling()
+            assert cfg["pipelined"] and cfg["steps_per_launch"] == 2 and cfg["tile_rows"] == tr
+            assert cfg["grid"] <= (Nr + tr - 1) // tr
+        st.set_state(u0, 0)
+        st.step(steps)
+        outs.append((st.get_state(), st.waveform(0, steps + 1), st.current_step))
+        st.close()
+    assert outs[0][2] == outs[1][2] == steps
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+    if steps <= 41:
+        uo, ho = O.run(oracle_problem(w), u0, steps)
+        tol = FP64_TOL if precision == "fp64" else FP32_TOL
+        assert rel_l2(outs[1][0], uo) <= tol and rel_l2(outs[1][1], ho) <= tol
+
+
+def test_pipelined_kernel_rejected_where_unavailable():
+    """Odd Ntheta in FP32 (rows not 16-byte multiples) has no pipelined kernel."""
+    from paper_0909_4039_gb300 import teuk
+    w = inputs.Workload("pipe-odd", s=-2, m=2, a=0.5, Nr=100, Ntheta=33, rs_min=-20.0, rs_max=40.0, steps=0,
+                        amp=0.0)
+    st = gpu_stepper(w, "fp32", with_source=False, wave_capacity=4)
+    with pytest.raises(teuk.TeukError):
+        st.set_pipelined(4)
+    st.close()
