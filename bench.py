@@ -742,11 +742,12 @@ def run_native_adjoint(args):
     h = A.waveform(w, prm, N, precision=prec).cpu().numpy()
     target = np.abs(h).max() * inputs.adjoint_target(N + 1, dt, seed=1)
 
-    def grad(wrt_a=True, split=None):
-        # forward run keeping sqrt(N) checkpoints, loss gradient on the host,
-        # backward sweep over the checkpoints; split receives (forward s, sweep s)
+    def grad(wrt_a=True, split=None, every=None):
+        # forward run keeping sqrt(N) checkpoints (every=1: every state), loss
+        # gradient on the host, backward sweep over the checkpoints; split
+        # receives (forward s, sweep s)
         t0 = time.perf_counter()
-        fw = A.forward(w, prm, N, precision=prec)
+        fw = A.forward(w, prm, N, precision=prec, every=every)
         try:
             hh = fw.h.cpu().numpy()
             t1 = time.perf_counter()
@@ -779,6 +780,18 @@ def run_native_adjoint(args):
     grad(wrt_a=False, split=split_src)
     t_src = time.perf_counter() - tg0 - t_fwd
     grad(wrt_a=True, split=split_all)
+    # every state kept (no recompute), where the device holds N states
+    store_all = None
+    state_bytes = 2 * w.Nr * w.Ntheta * (16 if prec == "fp64" else 8)
+    free, _ = torch.cuda.mem_get_info()
+    if (N + 2) * state_bytes < 0.8 * free:
+        split_sa = []
+        ts0 = time.perf_counter()
+        grad(wrt_a=True, split=split_sa, every=1)
+        t_sa = time.perf_counter() - ts0
+        store_all = {"gradient_s": t_sa, "ratio_all_params": t_sa / t_fwd,
+                     "sweep_over_forward": split_sa[0][1] / t_fwd, "states_bytes": (N + 1) * state_bytes,
+                     "note": "every state kept during the forward run (N states in HBM), no recompute"}
     if ws > 1:
         tt = torch.tensor([t], device="cuda", dtype=torch.float64)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
@@ -800,10 +813,12 @@ def run_native_adjoint(args):
                          "sweep_over_forward_all_params": split_all[0][1] / t_fwd,
                          "sweep_over_forward_source_params": split_src[0][1] / t_fwd,
                          "checkpointed_forward_s": split_all[0][0],
+                         "store_all": store_all,
                          "note": "ratio_*: gradient evaluation (checkpointed forward run + backward sweep) "
                                  "in forward-run units; sweep_over_forward_*: the backward sweep alone "
-                                 "(checkpoint recompute, adjoint steps, parameter contractions) over one "
-                                 "plain forward run; source_params = amplitude and r0 only (no spin term)"},
+                                 "(checkpoint recompute, adjoint steps with the spin term contracted in "
+                                 "them) over one plain forward run; source_params = amplitude and r0 "
+                                 "only (no spin term)"},
         "e2e": {"value": ws * args.steps / t, "unit": "grad/s", "h2d_bytes_per_step": 16 * (N + 1),
                 "d2h_bytes_per_step": 16 * (N + 1) + 32},
         "clocks": clk.summary(),

@@ -331,9 +331,10 @@ int teuk_apply_step(teuk_ctx *ctx, const void *d_in, void *d_out, int64_t n, int
  * physical, else E C_{dt/2} d_s; the same FP64 sum the steps write. */
 int teuk_apply_sample(teuk_ctx *ctx, const void *d_s, int physical, void *d_h, void *stream);
 
-/* Device workspace of teuk_adjoint_step and teuk_dot, in *bytes.  Its first
- * four doubles accumulate the source derivatives (see teuk_adjoint_step);
- * zero them before a backward sweep. */
+/* Device workspace of teuk_adjoint_step, teuk_adjoint_step_spin and
+ * teuk_dot, in *bytes.  Its first eight doubles accumulate the parameter
+ * derivatives (see teuk_adjoint_step and teuk_adjoint_step_spin); zero them
+ * before a backward sweep. */
 int teuk_adjoint_workspace_bytes(const teuk_ctx *ctx, size_t *bytes);
 
 /* One step of the backward (adjoint) sweep:
@@ -347,6 +348,21 @@ int teuk_adjoint_workspace_bytes(const teuk_ctx *ctx, size_t *bytes);
  * frequency; sum over the backward sweep, in a fixed order). */
 int teuk_adjoint_step(teuk_ctx *ctx, const void *d_lam_in, void *d_lam_out, int64_t n, int first,
                       const void *d_gseed, void *d_ws, void *stream);
+
+/* teuk_adjoint_step together with the step's part of the spin derivative:
+ * the same lam_n and source accumulators, plus
+ *   acc[4] += Re <lam_{n+1}, dM_n/da s_n> + Re <g_n, d(E C_{dt/2})/da s_n>
+ * (the second term for n >= 1 with d_gseed), so that after a backward sweep
+ * dL/da = acc[4].  d_s holds s_n, the state the step took (u_0 if first),
+ * in the same layout; it is read only.  The spin a enters every coefficient
+ * of Eq. 1 after Eqs. 2-4 (through r(r*; a), Delta and Sigma^2 of Eq. 7),
+ * the source prefactor, the orbit's r0*(a) and Kepler frequency.  The
+ * contraction uses exact derivatives of the FP64 coefficient tables
+ * (forward-mode, r(r*; a) by implicit differentiation of Eq. 2) with the
+ * forward stage values the kernel recomputes from s_n: no extra step
+ * applications.  Zero acc[4] (with acc[0..3]) before a sweep. */
+int teuk_adjoint_step_spin(teuk_ctx *ctx, const void *d_lam_in, void *d_lam_out, const void *d_s, int64_t n,
+                           int first, const void *d_gseed, void *d_ws, void *stream);
 
 /* d_out (one complex double, device) = sum conj(x) (y - z) over both
  * planes (z may be NULL: sum conj(x) y), in FP64 and a fixed order; the

@@ -9,15 +9,19 @@ is differentiated in reverse mode: with g_n = dL/dRe h_n + i dL/dIm h_n,
 The transposed steps are the library's hand-written adjoint kernels
 (teuk_adjoint_step).  The source amplitude A and the orbit radius r0 enter
 only the source term, whose derivatives the adjoint kernel contracts on the
-source patch.  The spin a enters every coefficient (through r(r*; a), the
-pivots, the source prefactor, r0* and the Kepler frequency); its term
-<lam_{n+1}, dM_n/da s_n> is the central difference (M_n(a+e) - M_n(a-e)) s_n / 2e
-of two forward steps from the same state, contracted with lam_{n+1}
-(truncation error O(e^2)).
+source patch.  The spin a enters every coefficient (through r(r*; a),
+Delta and Sigma^2, the source prefactor, r0* and the Kepler frequency); its
+terms <lam_{n+1}, dM_n/da s_n> and <g_n, d(E C_{dt/2})/da s_n> are contracted
+inside the adjoint step from exact derivatives of the coefficient tables and
+the forward stage values of s_n (teuk_adjoint_step_spin).  For checking,
+spin="fd" takes them instead as central differences of two forward steps
+at a +- e.
 
 The backward sweep needs s_n at every step: states are kept every
 k ~ sqrt(N) steps during the forward run and each segment is recomputed from
 its checkpoint before it is swept (sqrt(N) checkpointing with recompute).
+With every = 1 every state is kept and nothing is recomputed (the memory of
+N states, which the HBM of one GPU holds for the named adjoint workload).
 
 Everything runs in the library's kernels on device buffers; PyTorch holds
 the buffers and carries the gradients.
@@ -67,6 +71,7 @@ class Operator:
         L = teuk.lib()
         self._step, self._sample = L.teuk_apply_step, L.teuk_apply_sample
         self._adj, self._dot = L.teuk_adjoint_step, L.teuk_dot
+        self._adjs = L.teuk_adjoint_step_spin
         self._ctx, self._ws = self.st.ctx, self.ws.data_ptr()
 
     def empty(self):
@@ -91,6 +96,12 @@ class Operator:
         LAUNCHES[0] += 2     # the adjoint step and the reduction of its partial sums
         self._ok(self._adj(self._ctx, lam_in.data_ptr(), lam_out.data_ptr(), int(n), int(first), gseed_ptr,
                            self._ws, self.sh))
+
+    def adjoint_spin(self, lam_in, lam_out, s, n: int, first: bool, gseed_ptr):
+        """adjoint() plus the step's spin-derivative term (acc[4]); s = s_n."""
+        LAUNCHES[0] += 2
+        self._ok(self._adjs(self._ctx, lam_in.data_ptr(), lam_out.data_ptr(), s.data_ptr(), int(n), int(first),
+                            gseed_ptr, self._ws, self.sh))
 
     def dot(self, x, y, out_ptr: int, z=None):
         """out = <x, y - z> (z None: <x, y>)."""
@@ -118,16 +129,16 @@ def _ptr(t, k: int) -> int:
 
 
 def run_forward(op: Operator, nsteps: int, u0=None, every: int | None = None):
-    """Waveform h_0..h_N (complex128, device) and the checkpoints: {0: u_0}
-    and {n: s_n} for every n divisible by `every`.  Call on the operator's
-    stream."""
+    """Waveform h_0..h_N (complex128, device), the checkpoints {0: u_0} and
+    {n: s_n} for every n divisible by `every`, and the last state s_N (u_0
+    when N = 0).  Call on the operator's stream."""
     torch = op.torch
     h = torch.zeros(nsteps + 1, dtype=torch.complex128, device=op.st.device)
     u = op.zeros() if u0 is None else torch.as_tensor(u0).to(device=op.st.device, dtype=op.ctype).reshape(op.shape)
     ck = {0: u.clone()}
     op.sample(u, True, _ptr(h, 0))
     if nsteps == 0:
-        return h, ck
+        return h, ck, u
     s, t = op.empty(), op.empty()
     op.step(u, s, 0, True)
     for n in range(1, nsteps + 1):
@@ -137,21 +148,22 @@ def run_forward(op: Operator, nsteps: int, u0=None, every: int | None = None):
         if n < nsteps:
             op.step(s, t, n, False)
             s, t = t, s
-    return h, ck
+    return h, ck, s
 
 
 class Forward:
     """A forward run kept for a backward sweep: the operator, the waveform
     and the checkpoints (sqrt(N) states)."""
 
-    def __init__(self, op, nsteps, h, ck, every):
-        self.op, self.nsteps, self.h, self.ck, self.every = op, nsteps, h, ck, every
+    def __init__(self, op, nsteps, h, ck, every, last=None):
+        self.op, self.nsteps, self.h, self.ck, self.every, self.last = op, nsteps, h, ck, every, last
 
     def close(self):
         if self.op is not None:
             self.op.close()
             self.op = None
         self.ck = None
+        self.last = None
 
 
 def forward(w: inputs.Workload, prm: Params, nsteps: int, u0=None, precision: str = "fp64",
@@ -164,17 +176,19 @@ def forward(w: inputs.Workload, prm: Params, nsteps: int, u0=None, precision: st
     # u0 may come from work queued on the caller's stream
     op.st.stream.wait_stream(caller)
     with torch.cuda.stream(op.st.stream):
-        h, ck = run_forward(op, nsteps, u0, every)
+        h, ck, last = run_forward(op, nsteps, u0, every)
     # and the caller's later work reads h
     caller.wait_stream(op.st.stream)
-    return Forward(op, nsteps, h, ck, every)
+    return Forward(op, nsteps, h, ck, every, last)
 
 
-def backward(fw: Forward, grad_h, wrt_a: bool = True, eps_a: float | None = None) -> dict:
+def backward(fw: Forward, grad_h, wrt_a: bool = True, eps_a: float | None = None, spin: str = "analytic") -> dict:
     """Reverse-mode derivatives of a loss whose gradient with respect to the
     waveform h_0..h_N of the forward run is grad_h (complex, dL/dRe h +
     i dL/dIm h): dL/dRe A, dL/dIm A, dL/dr0, dL/da (None unless wrt_a) and
-    the adjoint of the initial state (dL/dRe u_0 + i dL/dIm u_0)."""
+    the adjoint of the initial state (dL/dRe u_0 + i dL/dIm u_0).
+    spin = "analytic" contracts the spin term inside the adjoint steps;
+    "fd" takes it as central differences of forward steps at a +- eps_a."""
     import torch
     op = fw.op
     # grad_h (autograd produces it on the caller's stream) is read by kernels
@@ -184,32 +198,38 @@ def backward(fw: Forward, grad_h, wrt_a: bool = True, eps_a: float | None = None
     if torch.is_tensor(grad_h) and grad_h.is_cuda:
         grad_h.record_stream(op.st.stream)
     with torch.cuda.stream(op.st.stream):
-        out = _sweep(fw, grad_h, wrt_a, eps_a)
+        out = _sweep(fw, grad_h, wrt_a, eps_a, spin)
     caller.wait_stream(op.st.stream)
     return out
 
 
 def gradients(w: inputs.Workload, prm: Params, nsteps: int, grad_h, u0=None, precision: str = "fp64",
-              every: int | None = None, wrt_a: bool = True, eps_a: float | None = None, device=None):
+              every: int | None = None, wrt_a: bool = True, eps_a: float | None = None, device=None,
+              spin: str = "analytic"):
     """forward() followed by backward(); returns backward's dictionary plus
     the waveform under "h"."""
     fw = forward(w, prm, nsteps, u0, precision, every, device)
     try:
-        out = backward(fw, grad_h, wrt_a, eps_a)
+        out = backward(fw, grad_h, wrt_a, eps_a, spin)
         out["h"] = fw.h
         return out
     finally:
         fw.close()
 
 
-def _sweep(fw: Forward, grad_h, wrt_a, eps_a):
+def _sweep(fw: Forward, grad_h, wrt_a, eps_a, spin="analytic"):
     import torch
     op, nsteps, ck = fw.op, fw.nsteps, fw.ck
     w, prm, precision = op.w, op.prm, op.precision
     g = torch.as_tensor(grad_h).to(device=op.st.device, dtype=torch.complex128).contiguous()
     if g.numel() != nsteps + 1:
         raise ValueError("grad_h needs one entry per sample h_0..h_N")
-    if wrt_a:
+    if spin not in ("analytic", "fd"):
+        raise ValueError("spin must be 'analytic' or 'fd'")
+    analytic = wrt_a and spin == "analytic"
+    if analytic and fw.last is None:
+        raise ValueError("the forward run kept no last state")
+    if wrt_a and not analytic:
         eps = eps_a if eps_a is not None else (1e-4 if precision == "fp64" else 1e-3)
         dev = op.st.device
         opp = Operator(w, Params(prm.amp, prm.r0, prm.a + eps), precision, device=dev, stream=op.st.stream)
@@ -220,34 +240,45 @@ def _sweep(fw: Forward, grad_h, wrt_a, eps_a):
     op.ws.zero_()
     lam, lam2 = op.zeros(), op.empty()
     # lam_N from the last sample alone (lam_{N+1} = 0)
-    op.adjoint(lam, lam2, nsteps, nsteps == 0, _ptr(g, nsteps))
+    if analytic:
+        op.adjoint_spin(lam, lam2, fw.last, nsteps, nsteps == 0, _ptr(g, nsteps))
+    else:
+        op.adjoint(lam, lam2, nsteps, nsteps == 0, _ptr(g, nsteps))
     lam, lam2 = lam2, lam
     bounds = sorted(k for k in ck) + [nsteps]
     for a, b in reversed(list(zip(bounds[:-1], bounds[1:]))):
-        # states s_a .. s_b of this segment (s_0 is the physical u_0)
+        # states s_a .. s_b of this segment (s_0 is the physical u_0); the
+        # adjoint steps n = b-1 .. a read s_n, so with the contracted spin
+        # terms s_b is not needed (a checkpoint every step recomputes nothing)
         states = [ck[a]]
-        for n in range(a, b):
+        last = b - 1 if analytic else b
+        for n in range(a, last):
             nxt = op.empty()
             op.step(states[-1], nxt, n, n == 0)
             states.append(nxt)
-        if wrt_a:
+        if wrt_a and not analytic:
             # a-derivative of the samples h_n, n in (a, b]
             for n in range(max(a + 1, 1), b + 1):
                 opp.sample(states[n - a], False, _ptr(samp, 2 * n))
                 opm.sample(states[n - a], False, _ptr(samp, 2 * n + 1))
         for n in range(b - 1, a - 1, -1):
             sn = states[n - a]
-            if wrt_a:
-                # <lam_{n+1}, (M_n(a + e) - M_n(a - e)) s_n>
-                opp.step(sn, tp, n, n == 0)
-                opm.step(sn, tm, n, n == 0)
-                op.dot(lam, tp, _ptr(dots, n), z=tm)
-            op.adjoint(lam, lam2, n, n == 0, _ptr(g, n))
+            if analytic:
+                op.adjoint_spin(lam, lam2, sn, n, n == 0, _ptr(g, n))
+            else:
+                if wrt_a:
+                    # <lam_{n+1}, (M_n(a + e) - M_n(a - e)) s_n>
+                    opp.step(sn, tp, n, n == 0)
+                    opm.step(sn, tm, n, n == 0)
+                    op.dot(lam, tp, _ptr(dots, n), z=tm)
+                op.adjoint(lam, lam2, n, n == 0, _ptr(g, n))
             lam, lam2 = lam2, lam
         del states
-    acc = op.ws[:4].cpu().numpy()
+    acc = op.ws[:8].cpu().numpy()
     out = {"dA_re": float(acc[0]), "dA_im": float(-acc[1]), "dr0": float(acc[2]), "du0": lam.clone()}
-    if wrt_a:
+    if analytic:
+        out["da"] = float(acc[4])
+    elif wrt_a:
         d = dots.cpu().numpy()
         sp = samp.cpu().numpy()
         gn = g.cpu().numpy()
@@ -269,7 +300,7 @@ def waveform(w: inputs.Workload, prm: Params, nsteps: int, u0=None, precision: s
     try:
         op.st.stream.wait_stream(torch.cuda.current_stream(op.st.device))
         with torch.cuda.stream(op.st.stream):
-            h, _ = run_forward(op, nsteps, u0)
+            h, _, _ = run_forward(op, nsteps, u0)
         op.st.synchronize()
         return h
     finally:

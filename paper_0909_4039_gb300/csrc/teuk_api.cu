@@ -48,6 +48,7 @@ struct teuk_ctx {
     int patch_p0, patch_np, unit_p0, unit_np;
     double mOmega;
     double amp_re, amp_im, rs0, sig_r, drs0_dr0, m_dOmega;
+    double m_dOmega_da;     // m dOmega/da (Kepler frequency; 0 for a given Omega)
     // launch configuration: tiled kernel (tile_rows, threads, smem) or the
     // persistent kernel (persist = 1: nc consumer threads, grid CTAs,
     // persist_smem); the tiled kernel at the same tile height also serves
@@ -81,6 +82,7 @@ Layout make_layout(const teuk_grid_desc &d)
     L.rtab64 = off; off = align256(off + rs);
     L.rtabT = f32 ? off : L.rtab64; if (f32) off = align256(off + rs / 2);
     L.stab = off; off = align256(off + (f32 ? sizeof(float) : sizeof(double)) * (2 * Nr - 1) * NSF);
+    L.dstab = off; off = align256(off + (f32 ? sizeof(float) : sizeof(double)) * (2 * Nr - 1) * NSF);
     L.th64 = off; off = align256(off + ts);
     L.thT = f32 ? off : L.th64; if (f32) off = align256(off + ts / 2);
     L.piv = off; off = align256(off + c2 * N * Nr);
@@ -457,6 +459,8 @@ StepParams<T> make_params(const teuk_ctx *c, int in_level)
     p.mOmega = c->mOmega;
     p.rtab = (const T *)(c->coef + c->L.rtabT);
     p.stab = (const T *)(c->coef + c->L.stab);
+    p.dstab = (const T *)(c->coef + c->L.dstab);
+    p.m_dOmega_da = c->m_dOmega_da;
     p.mat_on = c->L.mat_bytes > 0 ? 1 : 0;
     {
         const size_t pl = (size_t)d.Nr * (size_t)d.Ntheta;   // elements per plane
@@ -730,7 +734,7 @@ int teuk_set_source(teuk_ctx *c, double amp_re, double amp_im, double r0, double
     double rp = d.M + sqrt(d.M * d.M - d.a * d.a);
     const bool orbit_ok = r0 > rp && isfinite(r0) && sigma_rstar > 0.0 && sigma_theta > 0.0;
     if (off && !orbit_ok) {
-        CK(launch_src_fields(d, c->drs, c->coef, c->L, 0, 0, 0.0, 0.0, 0.0, 1.0, 1.0, 0), "source factors");
+        CK(launch_src_fields(d, c->drs, c->coef, c->L, 0, 0, 0.0, 0.0, 0.0, 1.0, 1.0, 0.0, 0), "source factors");
         CK(cudaStreamSynchronize(0), "source sync");
         c->patch_np = 0;
         c->unit_np = 0;
@@ -757,8 +761,10 @@ int teuk_set_source(teuk_ctx *c, double amp_re, double amp_im, double r0, double
     if (np > 0)
         CK(launch_patch(d, c->drs, c->coef, c->L, (int)p0, np, amp_re, amp_im, rs0, sigma_rstar, sigma_theta, st), "source patch");
     // the factored form the forward step kernels use (zero when the amplitude is)
+    // r0* moves with the spin: d r0*/d a at fixed r0 (Eq. 2)
+    const double drs0_da = host_drstar_da(d.M, d.a, r0 - rp);
     CK(launch_src_fields(d, c->drs, c->coef, c->L, (int)p0, off ? 0 : np, amp_re, amp_im, rs0, sigma_rstar,
-                         sigma_theta, st), "source factors");
+                         sigma_theta, drs0_da, st), "source factors");
     CK(cudaStreamSynchronize(st), "source sync");
     c->patch_p0 = (int)p0;
     c->patch_np = off ? 0 : np;
@@ -774,6 +780,8 @@ int teuk_set_source(teuk_ctx *c, double amp_re, double amp_im, double r0, double
     const double Delta0 = r0 * r0 - 2.0 * d.M * r0 + d.a * d.a;
     c->drs0_dr0 = (r0 * r0 + d.a * d.a) / Delta0;
     c->m_dOmega = kepler ? (double)d.m * (-1.5 * sqrt(r0) * Om * Om / sqrt(d.M)) : 0.0;
+    // and dOmega/da = -M / (r0^(3/2) + a M^(1/2))^2 = -Omega^2 for the Kepler frequency
+    c->m_dOmega_da = kepler ? (double)d.m * (-Om * Om) : 0.0;
     return TEUK_OK;
 }
 
@@ -1232,11 +1240,28 @@ int adjoint_tile_rows(const teuk_ctx *c)
     return best;
 }
 
+// Tile height of the adjoint step with the spin derivative: twice the
+// shared memory per row (eight state planes), at most about 200 KB per tile.
+int adjoint_spin_tile_rows(const teuk_ctx *c)
+{
+    const int N = (int)c->d.Ntheta;
+    const bool f32 = c->d.precision == TEUK_FP32;
+    const long long want = (c->d.Nr + 2LL * sm_count() - 1) / (2LL * sm_count());
+    int best = 1;
+    for (int tr = 1; tr <= 30; ++tr) {
+        size_t sm = f32 ? adjoint_spin_smem_bytes<float>(tr, N) : adjoint_spin_smem_bytes<double>(tr, N);
+        if (sm <= 200 * 1024) best = tr;
+    }
+    if (want >= 4 && want < best) best = (int)want;
+    return best;
+}
+
 size_t adjoint_ws_doubles(const teuk_ctx *c)
 {
-    const int tr = adjoint_tile_rows(c);
-    const int grid = (int)((c->d.Nr + tr - 1) / tr);
-    return 8 + 4 * (size_t)grid + 2 * 256;   // accumulators, per-CTA parts, dot parts
+    const int tr = adjoint_tile_rows(c), trs = adjoint_spin_tile_rows(c);
+    const int grid = (int)((c->d.Nr + tr - 1) / tr), grids = (int)((c->d.Nr + trs - 1) / trs);
+    const int gmax = grid > grids ? grid : grids;
+    return 8 + 6 * (size_t)gmax + 2 * 256;   // accumulators, per-CTA parts, dot parts
 }
 
 }  // namespace
@@ -1320,6 +1345,36 @@ int teuk_adjoint_step(teuk_ctx *c, const void *d_lam_in, void *d_lam_out, int64_
         e = launch_adjoint_step<double>(p, tr, (const double2 *)d_gseed, part, acc, st);
     }
     if (e != cudaSuccess) return cuda_err(c, e, "adjoint step");
+    return TEUK_OK;
+}
+
+int teuk_adjoint_step_spin(teuk_ctx *c, const void *d_lam_in, void *d_lam_out, const void *d_s, int64_t n, int first,
+                           const void *d_gseed, void *d_ws, void *stream)
+{
+    if (!c) return TEUK_E_STATE;
+    if (c->d.scheme != TEUK_SCHEME_SPLIT) return set_err(c, TEUK_E_INVAL, "the adjoint needs the split scheme");
+    if (!d_lam_in || !d_lam_out || !d_s || d_lam_in == d_lam_out || d_s == d_lam_out || !d_ws || n < 0)
+        return set_err(c, TEUK_E_INVAL, "need distinct non-NULL device buffers, a workspace and n >= 0");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int tr = adjoint_spin_tile_rows(c);
+    double *acc = (double *)d_ws, *part = acc + 8;
+    cudaError_t e;
+    if (c->d.precision == TEUK_FP32) {
+        StepParams<float> p = make_params<float>(c, 0);
+        p.uin = (const float2 *)d_lam_in;
+        p.uout = (float2 *)d_lam_out;
+        p.first = first ? 1 : 0;
+        p.nfix = n;
+        e = launch_adjoint_spin<float>(p, tr, (const float2 *)d_s, (const double2 *)d_gseed, part, acc, st);
+    } else {
+        StepParams<double> p = make_params<double>(c, 0);
+        p.uin = (const double2 *)d_lam_in;
+        p.uout = (double2 *)d_lam_out;
+        p.first = first ? 1 : 0;
+        p.nfix = n;
+        e = launch_adjoint_spin<double>(p, tr, (const double2 *)d_s, (const double2 *)d_gseed, part, acc, st);
+    }
+    if (e != cudaSuccess) return cuda_err(c, e, "adjoint step (spin)");
     return TEUK_OK;
 }
 

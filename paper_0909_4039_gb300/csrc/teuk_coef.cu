@@ -71,29 +71,101 @@ __device__ double x_of_rstar(const Kerr &k, double rs)
     return exp(u);
 }
 
-// All r-only factors at one radial position (see RField).
-__device__ void rfields(const Kerr &k, int s, int m, double x, double *f)
+// Forward-mode dual number v + d eps (eps^2 = 0): d carries the derivative
+// with respect to the spin a through every operation.
+struct Dual {
+    double v, d;
+};
+__host__ __device__ inline Dual dual(double v, double d = 0.0) { return Dual{v, d}; }
+__host__ __device__ inline Dual operator+(Dual a, Dual b) { return Dual{a.v + b.v, a.d + b.d}; }
+__host__ __device__ inline Dual operator-(Dual a, Dual b) { return Dual{a.v - b.v, a.d - b.d}; }
+__host__ __device__ inline Dual operator*(Dual a, Dual b) { return Dual{a.v * b.v, a.v * b.d + a.d * b.v}; }
+__host__ __device__ inline Dual operator/(Dual a, Dual b)
 {
-    const double M = k.M, a = k.a;
-    double r = k.rp + x;
-    double D = x * (x + (k.rp - k.rm));            // Delta without cancellation
-    double R = r * r + a * a;
+    const double q = a.v / b.v;
+    return Dual{q, (a.d - q * b.d) / b.v};
+}
+__host__ __device__ inline Dual operator*(double s, Dual a) { return Dual{s * a.v, s * a.d}; }
+
+__host__ __device__ inline double dual_or(double M, double) { return M; }
+__host__ __device__ inline Dual dual_or(double M, Dual) { return dual(M); }
+
+// All r-only factors at one radial position (see RField), for N = double,
+// or N = Dual with r, x, Delta and a carrying their spin derivatives.
+template <typename N>
+__device__ void rfields_t(double M, N a, int s, int m, N r, N x, N D, N *f)
+{
+    const double sd = (double)s, md = (double)m;
+    const N R = r * r + a * a;
     f[RF_R] = R;
     f[RF_R2] = R * R;
     f[RF_AD] = a * a * D;
     f[RF_DELTA] = D;
-    f[RF_CTR] = 2.0 * s * (r * D - M * (r * r - a * a));
-    f[RF_CTI] = 4.0 * M * a * m * r;
-    f[RF_CTC] = 2.0 * s * a * D;
-    f[RF_CSR] = 6.0 * R * D / r + 2.0 * r * D + 2.0 * s * R * (r - M);
-    f[RF_CSI] = 2.0 * a * m * R;
-    f[RF_E1] = 2.0 * r * D;
-    f[RF_E2] = 2.0 * r * D * R * R;
-    f[RF_E3] = a * a * D * R * (r - M);
-    f[RF_C0R] = 6.0 * D * D / (r * r) + 6.0 * (1.0 + s) * D * (r - M) / r;
-    f[RF_C0I] = 6.0 * a * m * D / r + 4.0 * s * m * a * (r - M);
+    f[RF_CTR] = (2.0 * sd) * (r * D - M * (r * r - a * a));
+    f[RF_CTI] = (4.0 * M * md) * (a * r);
+    f[RF_CTC] = (2.0 * sd) * (a * D);
+    f[RF_CSR] = 6.0 * (R * D / r) + 2.0 * (r * D) + (2.0 * sd) * (R * (r - dual_or(M, r)));
+    f[RF_CSI] = (2.0 * md) * (a * R);
+    f[RF_E1] = 2.0 * (r * D);
+    f[RF_E2] = 2.0 * (r * D * R * R);
+    f[RF_E3] = a * a * D * R * (r - dual_or(M, r));
+    f[RF_C0R] = 6.0 * (D * D / (r * r)) + (6.0 * (1.0 + sd)) * (D * (r - dual_or(M, r)) / r);
+    f[RF_C0I] = (6.0 * md) * (a * D / r) + (4.0 * sd * md) * (a * (r - dual_or(M, r)));
     f[RF_RR] = r;
     f[RF_X] = x;
+}
+
+__device__ void rfields(const Kerr &k, int s, int m, double x, double *f)
+{
+    const double r = k.rp + x;
+    const double D = x * (x + (k.rp - k.rm));      // Delta without cancellation
+    rfields_t<double>(k.M, k.a, s, m, r, x, D, f);
+}
+
+// d r*/d a at fixed r (Eq. 2 with its constant; x = r - r_+, d = r_+ - M):
+//   (M^2 a / d^3) ln(x/(x + 2d)) + (M a / d^2) (r_+/x + r_-/(x + 2d)),
+// so that at fixed r* the radius moves by dr/da = -(d r*/d a) Delta/(r^2 + a^2).
+__host__ __device__ inline double drstar_da(const Kerr &k, double x)
+{
+    const double d = k.rp - k.M, a = k.a, M = k.M;
+    if (a == 0.0) return 0.0;
+    return (M * M * a / (d * d * d)) * log(x / (x + 2.0 * d)) + (M * a / (d * d)) * (k.rp / x + k.rm / (x + 2.0 * d));
+}
+
+// The r-table fields at fixed r* as duals in a: r(r*; a), x = r - r_+(a),
+// Delta = x (x + r_+ - r_-) and a itself carry their derivatives.
+__device__ void rfields_dual(const Kerr &k, int s, int m, double x, Dual *f)
+{
+    const double r = k.rp + x, d = k.rp - k.M, a = k.a;
+    const double Dl = x * (x + 2.0 * d);
+    const double dr = -drstar_da(k, x) * Dl / (r * r + a * a);
+    const double drp = d > 0.0 ? -a / d : 0.0;   // d r_+ / d a
+    const Dual rd = dual(r, dr), xd = dual(x, dr - drp), twod = dual(2.0 * d, d > 0.0 ? -2.0 * a / d : 0.0);
+    rfields_t<Dual>(k.M, dual(a, 1.0), s, m, rd, xd, xd * (xd + twod), f);
+}
+
+// Step-table fields (SField) from the r-table fields f; the source block
+// is zero (teuk_set_source fills it).
+template <typename N>
+__device__ void stab_fields(const N *f, double cp, N *g)
+{
+    g[SF_R2] = f[RF_R2];
+    g[SF_AD] = f[RF_AD];
+    g[SF_DELTA] = f[RF_DELTA];
+    g[SF_CTR] = f[RF_CTR];
+    g[SF_CTI] = f[RF_CTI];
+    g[SF_CTC] = f[RF_CTC];
+    g[SF_C0R] = f[RF_C0R];
+    g[SF_C0I] = f[RF_C0I];
+    g[SF_RB] = cp * f[RF_R];
+    g[SF_E2] = cp * f[RF_E2];
+    g[SF_E3] = cp * f[RF_E3];
+    g[SF_RCTR] = cp * (f[RF_R] * f[RF_CTR]);
+    g[SF_CSE] = cp * (f[RF_CSR] - f[RF_E1]);
+    g[SF_RCTC] = cp * (f[RF_R] * f[RF_CTC]);
+    g[SF_RCTI] = cp * (f[RF_R] * f[RF_CTI]);
+    g[SF_CSI] = cp * f[RF_CSI];
+    g[SF_SRE] = g[SF_SIM] = g[SF_SR2] = g[SF_SPAD] = 0.0 * f[RF_R];
 }
 
 struct CoefArgs {
@@ -106,7 +178,7 @@ struct CoefArgs {
     int prec;                  // TEUK_FP64 / TEUK_FP32
     double *rtab64;
     void *rtabT;
-    void *stab;
+    void *stab, *dstab;
     double *th64;
     void *thT;
     void *piv;
@@ -131,27 +203,19 @@ __global__ void k_rtab(CoefArgs A)
     // times c_p = dt/dr* (node, Eq. 14) or dt/(2 dr*) (half node, Eq. 13)
     const double cp = ((p & 1) ? 0.5 : 1.0) * A.dt / A.drs;
     double g[NSF];
-    g[SF_R2] = f[RF_R2];
-    g[SF_AD] = f[RF_AD];
-    g[SF_DELTA] = f[RF_DELTA];
-    g[SF_CTR] = f[RF_CTR];
-    g[SF_CTI] = f[RF_CTI];
-    g[SF_CTC] = f[RF_CTC];
-    g[SF_C0R] = f[RF_C0R];
-    g[SF_C0I] = f[RF_C0I];
-    g[SF_RB] = cp * f[RF_R];
-    g[SF_E2] = cp * f[RF_E2];
-    g[SF_E3] = cp * f[RF_E3];
-    g[SF_RCTR] = cp * f[RF_R] * f[RF_CTR];
-    g[SF_CSE] = cp * (f[RF_CSR] - f[RF_E1]);
-    g[SF_RCTC] = cp * f[RF_R] * f[RF_CTC];
-    g[SF_RCTI] = cp * f[RF_R] * f[RF_CTI];
-    g[SF_CSI] = cp * f[RF_CSI];
-    g[SF_SRE] = g[SF_SIM] = g[SF_SR2] = g[SF_SPAD] = 0.0;   // no source until teuk_set_source
-    if (A.prec == TEUK_FP32)
+    stab_fields<double>(f, cp, g);
+    // and its derivative with respect to a at fixed r* (the same formulas on
+    // dual numbers; the source block is set by teuk_set_source)
+    Dual fd[NRF], gd[NSF];
+    rfields_dual(A.k, A.s, A.m, x, fd);
+    stab_fields<Dual>(fd, cp, gd);
+    if (A.prec == TEUK_FP32) {
         for (int q = 0; q < NSF; ++q) ((float *)A.stab)[(size_t)p * NSF + q] = (float)g[q];
-    else
+        for (int q = 0; q < NSF; ++q) ((float *)A.dstab)[(size_t)p * NSF + q] = (float)gd[q].d;
+    } else {
         for (int q = 0; q < NSF; ++q) ((double *)A.stab)[(size_t)p * NSF + q] = g[q];
+        for (int q = 0; q < NSF; ++q) ((double *)A.dstab)[(size_t)p * NSF + q] = gd[q].d;
+    }
 }
 
 // Theta tables and default extraction weights; one CTA, blockDim >= Nth.
@@ -285,11 +349,13 @@ __global__ void k_patch(PatchArgs A)
 }
 
 struct SrcArgs {
+    Kerr k;
+    int s, m;
     int Nr, Nth, p0, np, prec;
     double rs_min, drs, dth, a;
-    double amp_re, amp_im, rs0, sig_r, sig_th;
+    double amp_re, amp_im, rs0, sig_r, sig_th, drs0_da;
     const double *rtab64;
-    void *stab;
+    void *stab, *dstab;
     double *th64;
     void *thT;
 };
@@ -304,15 +370,18 @@ __global__ void k_src_fields(SrcArgs A)
         const double th = ((double)idx + 0.5) * A.dth, cs = cos(th), dq = th - 0.5 * kPi;
         const double G = exp(-dq * dq / (2.0 * A.sig_th * A.sig_th));
         const double g2 = A.a * A.a * cs * cs * G;
+        const double dg2 = 2.0 * A.a * cs * cs * G;   // d GA2 / d a
         A.th64[TF_GTH * A.Nth + idx] = G;
         A.th64[TF_GA2 * A.Nth + idx] = g2;
+        A.th64[TF_DGA2 * A.Nth + idx] = dg2;
         if (A.prec == TEUK_FP32) {
             ((float *)A.thT)[TF_GTH * A.Nth + idx] = (float)G;
             ((float *)A.thT)[TF_GA2 * A.Nth + idx] = (float)g2;
+            ((float *)A.thT)[TF_DGA2 * A.Nth + idx] = (float)dg2;
         }
     }
     if (idx >= 2 * A.Nr - 1) return;
-    double sre = 0.0, sim = 0.0, r2 = 0.0;
+    double sre = 0.0, sim = 0.0, r2 = 0.0, dsre = 0.0, dsim = 0.0, dr2 = 0.0;
     if (A.np > 0 && idx >= 2 * A.p0 && idx < 2 * (A.p0 + A.np)) {
         const double *f = A.rtab64 + (size_t)idx * NRF;
         const double r = f[RF_RR], D = f[RF_DELTA];
@@ -324,18 +393,34 @@ __global__ void k_src_fields(SrcArgs A)
         sre = A.amp_re * rad;
         sim = A.amp_im * rad;
         r2 = r * r;
+        // spin derivatives at fixed r*: Delta and r through r(r*; a), the
+        // Gaussian through its centre r0*(a)
+        Dual fd[NRF];
+        rfields_dual(A.k, A.s, A.m, f[RF_X], fd);
+        const Dual rd = fd[RF_RR], Dd = fd[RF_DELTA];
+        const Dual Gd = dual(Gr, Gr * dr * A.drs0_da / (A.sig_r * A.sig_r));
+        const Dual radd = (4.0 * kPi) * (Dd * Gd / (rd * rd * rd));
+        dsre = A.amp_re * radd.d;
+        dsim = A.amp_im * radd.d;
+        dr2 = (rd * rd).d;
     }
     const size_t o = (size_t)idx * NSF;
     if (A.prec == TEUK_FP32) {
-        float *t = (float *)A.stab + o;
+        float *t = (float *)A.stab + o, *u = (float *)A.dstab + o;
         t[SF_SRE] = (float)sre;
         t[SF_SIM] = (float)sim;
         t[SF_SR2] = (float)r2;
+        u[SF_SRE] = (float)dsre;
+        u[SF_SIM] = (float)dsim;
+        u[SF_SR2] = (float)dr2;
     } else {
-        double *t = (double *)A.stab + o;
+        double *t = (double *)A.stab + o, *u = (double *)A.dstab + o;
         t[SF_SRE] = sre;
         t[SF_SIM] = sim;
         t[SF_SR2] = r2;
+        u[SF_SRE] = dsre;
+        u[SF_SIM] = dsim;
+        u[SF_SR2] = dr2;
     }
 }
 
@@ -365,6 +450,7 @@ cudaError_t launch_coef_tables(const teuk_grid_desc &d, double drs, double dt, v
     A.rtab64 = (double *)(base + L.rtab64);
     A.rtabT = base + L.rtabT;
     A.stab = base + L.stab;
+    A.dstab = base + L.dstab;
     A.dt = dt;
     A.th64 = (double *)(base + L.th64);
     A.thT = base + L.thT;
@@ -413,10 +499,17 @@ cudaError_t launch_patch(const teuk_grid_desc &d, double drs, void *coef, const 
     return cudaGetLastError();
 }
 
+double host_drstar_da(double M, double a, double x) { return drstar_da(make_kerr(M, a), x); }
+
 cudaError_t launch_src_fields(const teuk_grid_desc &d, double drs, void *coef, const Layout &L, int p0, int np,
-                              double amp_re, double amp_im, double rs0, double sig_r, double sig_th, cudaStream_t st)
+                              double amp_re, double amp_im, double rs0, double sig_r, double sig_th,
+                              double drs0_da, cudaStream_t st)
 {
     SrcArgs A;
+    A.k = make_kerr(d.M, d.a);
+    A.s = d.s;
+    A.m = d.m;
+    A.drs0_da = drs0_da;
     A.Nr = (int)d.Nr;
     A.Nth = (int)d.Ntheta;
     A.p0 = p0;
@@ -434,6 +527,7 @@ cudaError_t launch_src_fields(const teuk_grid_desc &d, double drs, void *coef, c
     char *base = (char *)coef;
     A.rtab64 = (const double *)(base + L.rtab64);
     A.stab = base + L.stab;
+    A.dstab = base + L.dstab;
     A.th64 = (double *)(base + L.th64);
     A.thT = base + L.thT;
     const int n = 2 * A.Nr - 1 > A.Nth ? 2 * A.Nr - 1 : A.Nth;

@@ -819,7 +819,7 @@ template <typename T, int S, bool MAT = false>
 __device__ void implicit_row_fwd(const ImpConst<T> &K, typename V2<T>::t *phi, typename V2<T>::t *pi,
                                  const typename V2<T>::t *prow, const T *f, const T *th, int N, bool active,
                                  bool in_tile, int g, int G, bool vec, int plan, const MatPlanes<T> *mat = nullptr,
-                                 int gi = 0)
+                                 int gi = 0, typename V2<T>::t *u1phi = nullptr, typename V2<T>::t *u1pi = nullptr)
 {
     typedef typename V2<T>::t c2;
     const int j0 = g * S;
@@ -844,6 +844,13 @@ __device__ void implicit_row_fwd(const ImpConst<T> &K, typename V2<T>::t *phi, t
         }
     }
     seg_solve_lu<T, S>(y, C, P, g, G);             // U1_Pi
+    if (u1phi && in_tile) {
+        // the first stage value U1 (U1_Phi = u_Phi + gh U1_Pi), for the adjoint's spin term
+        c2 t[S];
+#pragma unroll
+        for (int k = 0; k < S; ++k) t[k] = caxpy(K.gh, y[k], w[k]);
+        row_store<T, S>(u1phi, u1pi, t, y, j0, lenw, vec);
+    }
     {
         c2 Y[S];
         apply_W<T, S>(C, y, Y, g, G);

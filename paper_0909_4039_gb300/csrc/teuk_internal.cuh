@@ -6,7 +6,8 @@
 //            double), plane 0 = Phi, plane 1 = Pi, theta fastest.
 //   coef   : r tables   [2Nr-1][NRF] FP64 and [2Nr-1][NRF] T
 //                        (position p = 2i: node i; p = 2i+1: r*_{i+1/2})
-//            step table [2Nr-1][NSF] T (see SField)
+//            step table [2Nr-1][NSF] T (see SField) and its spin
+//                        derivative d/da at fixed r* (split scheme)
 //            theta tables [NTF][Ntheta] FP64 and T
 //            pivots     two tables [Nr][Ntheta] complex T, for implicit
 //                        steps of length dt and dt/2 (row-major, so the
@@ -67,7 +68,8 @@ enum SField {
 // parity ghosts folded into A0 at j = 0 and j = Ntheta-1.
 // GTH, GA2: the angular factors of the source (see SField), set by
 // teuk_set_source.
-enum TField { TF_S2 = 0, TF_C, TF_AM, TF_A0, TF_AP, TF_GTH, TF_GA2, TF_PAD2, NTF };
+// DGA2 = d GA2 / d a (the spin derivative of the adjoint).
+enum TField { TF_S2 = 0, TF_C, TF_AM, TF_A0, TF_AP, TF_GTH, TF_GA2, TF_DGA2, NTF };
 
 // Error flags in Ctl::flags.
 enum : unsigned { FLAG_NONFINITE = 1u, FLAG_TIMEOUT = 2u };
@@ -125,6 +127,7 @@ template <typename T> struct StepParams {
     double mOmega;           // m * Omega (FP64)
     const T *rtab;           // [2Nr-1][NRF]
     const T *stab;           // step table [2Nr-1][NSF]
+    const T *dstab;          // its derivative with respect to the spin a at fixed r* and theta
     MatPlanes<T> mat;        // materialised coefficients (mat_on)
     int mat_on;              // 1: full steps read them (FP64 state)
     const T *thtab;          // [NTF][Nth]
@@ -144,6 +147,7 @@ template <typename T> struct StepParams {
     const c2 *patchu;
     int unit_p0, unit_np;    // rows of the unit-amplitude patch (np = 0: none)
     double amp_re, amp_im, rs_min64, drs64, rs0, inv_sig_r2, drs0_dr0, m_dOmega;
+    double m_dOmega_da;      // m dOmega/da of the orbit (spin derivative of the source phase)
 };
 
 // SDIRK2 constant gamma = 1 - 1/sqrt(2) (Alexander 1977).
@@ -224,7 +228,7 @@ __host__ __device__ inline PipeSmem pipe_smem_plan(int R, int N, int tsize)
 
 // ---------------------------------------------------------------- host side
 struct Layout {
-    size_t rtab64, rtabT, stab, th64, thT, piv, pivh, plan, planh, patch, patchu, w, ctl, staging, scratch;
+    size_t rtab64, rtabT, stab, dstab, th64, thT, piv, pivh, plan, planh, patch, patchu, w, ctl, staging, scratch;
     size_t mat, mat_bytes;   // materialised coefficients (FP64 split scheme; 0 bytes otherwise)
     size_t total;
     size_t staging_elems;    // complex doubles that fit in the staging area
@@ -243,7 +247,10 @@ cudaError_t launch_set_ctl(void *coef, const Layout &L, long long step, int clea
 // Source factors in the step and theta tables (SField, TField): positions
 // 2 p0 .. 2 (p0 + np) - 1 get the radial factor, every other position zero.
 cudaError_t launch_src_fields(const teuk_grid_desc &d, double drs, void *coef, const Layout &L, int p0, int np,
-                              double amp_re, double amp_im, double rs0, double sig_r, double sig_th, cudaStream_t st);
+                              double amp_re, double amp_im, double rs0, double sig_r, double sig_th,
+                              double drs0_da, cudaStream_t st);
+// d r*/d a at fixed Boyer-Lindquist r (Eq. 2 with the usual constant), x = r - r_+.
+double host_drstar_da(double M, double a, double x);
 
 // Adjoint and operator entry points (teuk_step.cu).
 template <typename T>
@@ -256,6 +263,14 @@ cudaError_t launch_adjoint_step(const StepParams<T> &p, int tile_rows, const dou
                                 double *acc, cudaStream_t st);
 template <typename T>
 size_t adjoint_smem_bytes(int tile_rows, int Nth);
+// The adjoint step with the spin derivative (k_adjoint_spin): sin = s_n,
+// per-CTA parts of six sums, acc[0 .. 5] += their totals (acc[4]: the spin
+// term).
+template <typename T>
+size_t adjoint_spin_smem_bytes(int tile_rows, int Nth);
+template <typename T>
+cudaError_t launch_adjoint_spin(const StepParams<T> &p, int tile_rows, const typename V2<T>::t *sin,
+                                const double2 *gseed, double *part, double *acc, cudaStream_t st);
 template <typename T>
 int adjoint_grid(int Nr, int tile_rows);
 template <typename T>

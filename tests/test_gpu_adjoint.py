@@ -207,3 +207,102 @@ def test_adjoint_workload_4096x64_full_size():
     print(f"\nadjoint 4096x64x8000: grad {got}, central differences {fd}, "
           f"forward {t_fwd:.2f} s, gradient sweep {t_adj:.2f} s ({t_adj / t_fwd:.2f} forward runs)")
     assert np.all(np.abs(got - fd) <= 1e-5 * np.abs(fd) + 1e-10 * np.abs(fd).max()), (got, fd)
+
+
+@pytest.mark.parametrize("first,m,Nth", [(False, 2, 16), (True, 2, 16), (False, 3, 33), (False, 1, 64)])
+def test_one_step_spin_term_against_step_differences(first, m, Nth):
+    """The spin term of one adjoint step, Re <lam, dM_n/da s> (+ the sample's
+    Re <g, d(E C_{dt/2})/da s>), contracted inside teuk_adjoint_step_spin from
+    the coefficient derivatives, against central differences of the step
+    and sample operators at a +- e (independent forward evaluations), with
+    the source on; FP64.  Also: the step's lam_n and source accumulators
+    equal those of teuk_adjoint_step."""
+    import torch
+    from paper_0909_4039_gb300 import adjoint as A
+    w = _w(110, Nth, a=0.6, m=m, sig_r=0.8)
+    prm = A.Params(0.8 - 0.5j, 6.0, 0.6)
+    n = 0 if first else 17
+    eps = 1e-5
+    op = A.Operator(w, prm, "fp64")
+    opp = A.Operator(w, A.Params(prm.amp, prm.r0, prm.a + eps), "fp64", stream=op.st.stream)
+    opm = A.Operator(w, A.Params(prm.amp, prm.r0, prm.a - eps), "fp64", stream=op.st.stream)
+    with torch.cuda.stream(op.st.stream):
+        s = _rand(op.shape, 21, op.st.device, op.ctype, zero_boundary=True)
+        lam = _rand(op.shape, 22, op.st.device, op.ctype)
+        g = torch.tensor([1.1 - 0.6j], dtype=torch.complex128, device=op.st.device)
+        tp, tm = op.empty(), op.empty()
+        opp.step(s, tp, n, first)
+        opm.step(s, tm, n, first)
+        fd = (_cdot(op, lam, tp) - _cdot(op, lam, tm)).real / (2 * eps)
+        if not first:
+            hp = torch.zeros(1, dtype=torch.complex128, device=op.st.device)
+            hm = torch.zeros(1, dtype=torch.complex128, device=op.st.device)
+            opp.sample(s, False, hp.data_ptr())
+            opm.sample(s, False, hm.data_ptr())
+            op.st.synchronize()
+            fd += (np.conj(g.item()) * (hp.item() - hm.item())).real / (2 * eps)
+        op.ws.zero_()
+        out_s = op.empty()
+        op.adjoint_spin(lam, out_s, s, n, first, g.data_ptr())
+        acc_s = op.ws[:8].clone()
+        op.ws.zero_()
+        out_r = op.empty()
+        op.adjoint(lam, out_r, n, first, g.data_ptr())
+        acc_r = op.ws[:8].clone()
+        op.st.synchronize()
+    got = float(acc_s[4].item())
+    assert abs(got - fd) <= 1e-7 * abs(fd) + 1e-12, (got, fd)
+    assert rel_l2(out_s.cpu().numpy(), out_r.cpu().numpy()) <= 1e-13
+    assert np.allclose(acc_s[:4].cpu().numpy(), acc_r[:4].cpu().numpy(), rtol=1e-12, atol=1e-300)
+    for o in (op, opp, opm):
+        o.close()
+
+
+def test_analytic_spin_gradient_matches_step_differences_sweep():
+    """The whole sweep: dL/da from the contracted spin terms against the
+    sweep that takes them as central differences of forward steps (FP64)."""
+    import torch
+    from paper_0909_4039_gb300 import adjoint as A
+    w = _w(160, 16, a=0.55, m=2, sig_r=0.8)
+    N = 120
+    dt = 0.5 * (w.rs_max - w.rs_min) / (w.Nr - 1)
+    prm = A.Params(0.6 + 0.2j, 7.5, 0.55)
+    target = 1e-3 * inputs.adjoint_target(N + 1, dt, seed=9)
+    h = A.waveform(w, prm, N).cpu().numpy()
+    gh = torch.as_tensor(2.0 * dt * (h - target))
+    ra = A.gradients(w, prm, N, gh, every=11)
+    rf = A.gradients(w, prm, N, gh, every=11, spin="fd", eps_a=1e-5)
+    assert abs(ra["da"] - rf["da"]) <= 1e-7 * abs(rf["da"]), (ra["da"], rf["da"])
+    for k in ("dA_re", "dA_im", "dr0"):
+        assert abs(ra[k] - rf[k]) <= 1e-11 * abs(rf[k]) + 1e-300, (k, ra[k], rf[k])
+
+
+def test_adjoint_workload_grid_against_oracle_window():
+    """The adjoint workload's grid (4096 x 64, a = 0.7, orbit r0 = 10, the
+    sqrt(N) checkpointed sweep) over a window of 1000 steps: the gradient
+    with respect to (Re A, Im A, r0, a) against central differences of the
+    FP64 oracle's loss (independent code), each parameter shifted by 1e-6
+    relative (1e-3 for A, where the loss is quadratic).  The waveform is
+    taken at r* = 60M, which the signal reaches within the window (at 500M,
+    1000 steps from zero data give a zero waveform and zero gradients)."""
+    import torch
+    from oracle import oracle as O
+    from paper_0909_4039_gb300 import adjoint as A
+    w = inputs.ADJOINT_4096x64.with_(rs_ext=60.0)
+    N = 1000
+    dt = 0.5 * (w.rs_max - w.rs_min) / (w.Nr - 1)
+    prm = A.Params(complex(w.amp), w.r0, w.a)
+    h = A.waveform(w, prm, N).cpu().numpy()
+    target = (np.abs(h).max() + 1e-30) * inputs.adjoint_target(N + 1, dt, seed=1)
+    r = A.gradients(w, prm, N, torch.as_tensor(2.0 * dt * (h - target)))
+    got = np.array([r["dA_re"], r["dA_im"], r["dr0"], r["da"]])
+
+    def oracle_loss(q):
+        wq = w.with_(a=q.a, r0=q.r0, amp=q.amp)
+        _, ho = O.run(oracle_problem(wq), None, N)
+        return _loss(ho, target, dt)
+
+    fd = _fd_gradients(oracle_loss, prm)
+    print(f"\nadjoint 4096x64, 1000 steps: GPU {got}, oracle differences {fd}")
+    assert np.all(np.abs(fd) > 0.0)
+    assert np.all(np.abs(got - fd) <= 1e-6 * np.abs(fd) + 1e-12 * np.abs(fd).max()), (got, fd)
