@@ -315,6 +315,25 @@ def fp64_leg(w, dev, launches: int, warmup: int, flush):
         st.close()
 
 
+# What the parity tests hold and where the stated tolerances (FP64 1e-12,
+# FP32 1e-4, relative L2 against the oracle) are met or missed; the numbers
+# are those the GPU tests measure.  The FP32 state at this workload's full
+# length is measured live in the line's "accuracy" key.
+TOLERANCE_OUTCOME = {
+    "fp32_state": "meets 1e-4 over windows (40 steps of 16384x128, 150 of 1024x32); misses it at full "
+                  "length: ~0.3 at 1000 steps of 1024x32, ~2.6 at 20000 steps of 16384x128",
+    "fp64_state": "meets 1e-12 over windows (250 steps of 1024x32); misses it at 2000 steps of 1024x32 "
+                  "(7.5e-8), within 10x of the disagreement of two FP64 oracle builds that differ only in "
+                  "FMA contraction (5e-8)",
+    "waveform": "1024x32, extraction at r* = 500, 1600 steps (200 steps of signal): FP64 meets 1e-12 "
+                "(6e-14), FP32 meets 1e-4 (4e-6); FP32 misses 1e-4 from step ~1700 (4e-3 at 2000)",
+    "reason": "s = -2 ingoing waves grow like r^-4 (Phi = psi/r^3), so rounding at large r is amplified "
+              "~1e8 on the way to the light ring, and the slowly growing modes of the walled problem "
+              "(0.004-0.02/M) amplify it further; the floor is the method's conditioning, not an "
+              "implementation error",
+}
+
+
 def accuracy_leg(w, dev, nsteps: int):
     """The FP32-state path against the FP64 path (which the parity tests hold
     to the oracle) after nsteps from the workload's zero initial data with
@@ -535,7 +554,8 @@ def run_native(args):
                    "l2": "flushed between timed iterations (256 MB write, outside the events); one "
                          "iteration = one launch = steps_per_launch time steps",
                    "parallelism": f"replicas x{ws}", "tiling": tiling,
-                   "tiling_source": tiling_source},
+                   "tiling_source": tiling_source,
+                   "tolerance": TOLERANCE_OUTCOME},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak,
                      "traffic": _profiled_traffic(kernel) if prec == "fp32" else None,
@@ -742,12 +762,12 @@ def run_native_adjoint(args):
     h = A.waveform(w, prm, N, precision=prec).cpu().numpy()
     target = np.abs(h).max() * inputs.adjoint_target(N + 1, dt, seed=1)
 
-    def grad(wrt_a=True, split=None, every=None):
-        # forward run keeping sqrt(N) checkpoints (every=1: every state), loss
-        # gradient on the host, backward sweep over the checkpoints; split
-        # receives (forward s, sweep s)
+    def grad(wrt_a=True, split=None, every=None, tape=False):
+        # forward run keeping sqrt(N) checkpoints (every=1: every state;
+        # tape: every step's stage values), loss gradient on the host,
+        # backward sweep; split receives (forward s, sweep s)
         t0 = time.perf_counter()
-        fw = A.forward(w, prm, N, precision=prec, every=every)
+        fw = A.forward(w, prm, N, precision=prec, every=every, tape=tape)
         try:
             hh = fw.h.cpu().numpy()
             t1 = time.perf_counter()
@@ -780,8 +800,9 @@ def run_native_adjoint(args):
     grad(wrt_a=False, split=split_src)
     t_src = time.perf_counter() - tg0 - t_fwd
     grad(wrt_a=True, split=split_all)
-    # every state kept (no recompute), where the device holds N states
-    store_all = None
+    # every state kept (no segment recompute), and every step's tape (no
+    # recompute at all), where the device holds them
+    store_all, taped = None, None
     state_bytes = 2 * w.Nr * w.Ntheta * (16 if prec == "fp64" else 8)
     free, _ = torch.cuda.mem_get_info()
     if (N + 2) * state_bytes < 0.8 * free:
@@ -791,7 +812,24 @@ def run_native_adjoint(args):
         t_sa = time.perf_counter() - ts0
         store_all = {"gradient_s": t_sa, "ratio_all_params": t_sa / t_fwd,
                      "sweep_over_forward": split_sa[0][1] / t_fwd, "states_bytes": (N + 1) * state_bytes,
-                     "note": "every state kept during the forward run (N states in HBM), no recompute"}
+                     "note": "every state kept during the forward run (N states in HBM), no segment recompute"}
+    tape_bytes = A.Operator(w, prm, prec).tape_bytes
+    torch.cuda.empty_cache()
+    free, _ = torch.cuda.mem_get_info()
+    if N * tape_bytes < 0.8 * free:
+        split_tp = []
+        grad(wrt_a=True, tape=True)          # warm-up of the tape allocation
+        torch.cuda.synchronize()
+        tt0 = time.perf_counter()
+        rt = grad(wrt_a=True, split=split_tp, tape=True)
+        t_tp = time.perf_counter() - tt0
+        taped = {"gradient_s": t_tp, "ratio_all_params": t_tp / t_fwd,
+                 "forward_with_tape_over_forward": split_tp[0][0] / t_fwd,
+                 "sweep_over_forward": split_tp[0][1] / t_fwd, "tape_bytes": N * tape_bytes,
+                 "gradient": [rt["dA_re"], rt["dA_im"], rt["dr0"], rt["da"]],
+                 "note": "every step records its stage values during the forward run "
+                         "(teuk_apply_step_tape, two states per step in HBM); the sweep recomputes nothing"}
+    torch.cuda.empty_cache()
     if ws > 1:
         tt = torch.tensor([t], device="cuda", dtype=torch.float64)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
@@ -814,6 +852,7 @@ def run_native_adjoint(args):
                          "sweep_over_forward_source_params": split_src[0][1] / t_fwd,
                          "checkpointed_forward_s": split_all[0][0],
                          "store_all": store_all,
+                         "taped": taped,
                          "note": "ratio_*: gradient evaluation (checkpointed forward run + backward sweep) "
                                  "in forward-run units; sweep_over_forward_*: the backward sweep alone "
                                  "(checkpoint recompute, adjoint steps with the spin term contracted in "

@@ -327,15 +327,37 @@ int teuk_destroy(teuk_ctx *ctx);
 /* d_out = M_n(d_in) (first = 1: the first step from a physical state). */
 int teuk_apply_step(teuk_ctx *ctx, const void *d_in, void *d_out, int64_t n, int first, void *stream);
 
+/* teuk_apply_step that also writes the sample E C_{dt/2} d_out of its
+ * output state to d_h (one complex double, device), in the same launch;
+ * bit for bit what teuk_apply_sample(d_out, physical = 0) writes.  d_h must
+ * not overlap d_in or d_out.  NULL d_h: TEUK_E_INVAL. */
+int teuk_apply_step_sample(teuk_ctx *ctx, const void *d_in, void *d_out, int64_t n, int first, void *d_h,
+                           void *stream);
+
 /* One waveform sample into d_h (one complex double, device): E d_s if
  * physical, else E C_{dt/2} d_s; the same FP64 sum the steps write. */
 int teuk_apply_sample(teuk_ctx *ctx, const void *d_s, int physical, void *d_h, void *stream);
 
 /* Device workspace of teuk_adjoint_step, teuk_adjoint_step_spin and
- * teuk_dot, in *bytes.  Its first eight doubles accumulate the parameter
- * derivatives (see teuk_adjoint_step and teuk_adjoint_step_spin); zero them
- * before a backward sweep. */
+ * teuk_dot, in *bytes (256-byte aligned, caller-owned).  Its first eight
+ * doubles accumulate the parameter derivatives (see teuk_adjoint_step and
+ * teuk_adjoint_step_spin); zero them before a backward sweep.  In FP64 its
+ * tail holds the coefficient planes teuk_adjoint_prepare writes (for an
+ * Nr x Ntheta grid 17 Nr Ntheta + 8 (2 Nr - 1) Ntheta doubles). */
 int teuk_adjoint_workspace_bytes(const teuk_ctx *ctx, size_t *bytes);
+
+/* Fills the workspace's coefficient planes for teuk_adjoint_step_spin (FP64
+ * contexts; FP32 contexts form them in place and only record d_ws): the
+ * coefficients of the full step's implicit stage and Lax-Wendroff stages
+ * (Eqs. 13-14, the implicit reading of S) at every grid element, and their
+ * exact spin derivatives, formed by the same device functions the step
+ * uses (so the adjoint reads bit for bit the coefficients the forward step
+ * forms).  Asynchronous on `stream`.  The
+ * context remembers d_ws; teuk_adjoint_step_spin with another workspace
+ * returns TEUK_E_STATE.  Keep the planes unmodified between the calls;
+ * after writing over them (or after reusing the memory), call this again.
+ * Errors: TEUK_E_INVAL for a NULL or unaligned d_ws. */
+int teuk_adjoint_prepare(teuk_ctx *ctx, void *d_ws, void *stream);
 
 /* One step of the backward (adjoint) sweep:
  *   d_lam_out = M_n^H d_lam_in + C_{dt/2}^H E^H g_n   (E^H g_0 if first),
@@ -360,8 +382,33 @@ int teuk_adjoint_step(teuk_ctx *ctx, const void *d_lam_in, void *d_lam_out, int6
  * contraction uses exact derivatives of the FP64 coefficient tables
  * (forward-mode, r(r*; a) by implicit differentiation of Eq. 2) with the
  * forward stage values the kernel recomputes from s_n: no extra step
- * applications.  Zero acc[4] (with acc[0..3]) before a sweep. */
+ * applications.  Zero acc[4] (with acc[0..3]) before a sweep.  Full steps
+ * read the coefficient planes: d_ws must be the workspace last passed to
+ * teuk_adjoint_prepare (else TEUK_E_STATE). */
 int teuk_adjoint_step_spin(teuk_ctx *ctx, const void *d_lam_in, void *d_lam_out, const void *d_s, int64_t n,
+                           int first, const void *d_gseed, void *d_ws, void *stream);
+
+/* The forward tape: what teuk_apply_step_tape records of one step so that
+ * teuk_adjoint_step_tape need not recompute it.  *bytes = the size of one
+ * step's record (a multiple of 256): the first SDIRK2 stage value U1 and
+ * the implicit stage's output U2 = C_h s_n of every row, each [2][Nr][Ntheta]
+ * complex in the state precision, then the input's extraction row. */
+int teuk_tape_bytes(const teuk_ctx *ctx, size_t *bytes);
+
+/* teuk_apply_step_sample that also writes the step's record to d_tape
+ * (device, 256-byte aligned, teuk_tape_bytes long, not overlapping the other
+ * buffers).  The state and sample are bit for bit those of
+ * teuk_apply_step_sample. */
+int teuk_apply_step_tape(teuk_ctx *ctx, const void *d_in, void *d_out, int64_t n, int first, void *d_h,
+                         void *d_tape, void *stream);
+
+/* teuk_adjoint_step_spin with the forward stage values read from the
+ * record teuk_apply_step_tape wrote for step n (same n and first) instead
+ * of recomputed from s_n: the same lam_n and accumulators, bit for bit.
+ * The record costs two states per step of device memory; keeping one per
+ * step (a store-all forward run) removes both the checkpoint recompute and
+ * the stage recompute from a backward sweep. */
+int teuk_adjoint_step_tape(teuk_ctx *ctx, const void *d_lam_in, void *d_lam_out, const void *d_tape, int64_t n,
                            int first, const void *d_gseed, void *d_ws, void *stream);
 
 /* d_out (one complex double, device) = sum conj(x) (y - z) over both

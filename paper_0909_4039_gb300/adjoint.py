@@ -17,11 +17,17 @@ the forward stage values of s_n (teuk_adjoint_step_spin).  For checking,
 spin="fd" takes them instead as central differences of two forward steps
 at a +- e.
 
-The backward sweep needs s_n at every step: states are kept every
-k ~ sqrt(N) steps during the forward run and each segment is recomputed from
-its checkpoint before it is swept (sqrt(N) checkpointing with recompute).
-With every = 1 every state is kept and nothing is recomputed (the memory of
-N states, which the HBM of one GPU holds for the named adjoint workload).
+The spin term needs the forward stage values of every step.  By default
+states are kept every k ~ sqrt(N) steps during the forward run, each segment
+is recomputed from its checkpoint before it is swept, and the adjoint kernel
+recomputes the implicit stage values from s_n (sqrt(N) checkpointing with
+recompute).  With every = 1 every state is kept and no segment is
+recomputed.  With tape=True every forward step records its stage values
+(teuk_apply_step_tape, two states per step) and the sweep recomputes
+nothing at all (teuk_adjoint_step_tape); the 4096 x 64 FP64 workload's 8000
+steps take 134 GB, which one GPU's HBM holds.  Without the spin term the
+adjoint step reads no state (the step is linear in s), so a sweep for the
+source parameters alone recomputes nothing either.
 
 Everything runs in the library's kernels on device buffers; PyTorch holds
 the buffers and carries the gradients.
@@ -68,10 +74,19 @@ class Operator:
         nb = ctypes_size(lambda sz: teuk.lib().teuk_adjoint_workspace_bytes(self.st.ctx, sz))
         self.ws = torch.zeros(nb // 8, dtype=torch.float64, device=self.st.device)
         self.sh = self.st.sh
+        # the spin adjoint's coefficient planes, once per operator (the zeros
+        # above are queued on torch's stream)
+        self.st.stream.wait_stream(torch.cuda.current_stream(self.st.device))
+        rc = teuk.lib().teuk_adjoint_prepare(self.st.ctx, self.ws.data_ptr(), self.st.sh)
+        if rc != 0:
+            teuk._check(rc, self.st.ctx)
         L = teuk.lib()
         self._step, self._sample = L.teuk_apply_step, L.teuk_apply_sample
+        self._step_sample = L.teuk_apply_step_sample
         self._adj, self._dot = L.teuk_adjoint_step, L.teuk_dot
         self._adjs = L.teuk_adjoint_step_spin
+        self._step_tape, self._adjt = L.teuk_apply_step_tape, L.teuk_adjoint_step_tape
+        self.tape_bytes = ctypes_size(lambda sz: teuk.lib().teuk_tape_bytes(self.st.ctx, sz))
         self._ctx, self._ws = self.st.ctx, self.ws.data_ptr()
 
     def empty(self):
@@ -88,6 +103,18 @@ class Operator:
         LAUNCHES[0] += 1
         self._ok(self._step(self._ctx, s_in.data_ptr(), s_out.data_ptr(), int(n), int(first), self.sh))
 
+    def step_sample(self, s_in, s_out, n: int, first: bool, out_ptr: int):
+        """step() plus the sample E C_{dt/2} s_out to out_ptr, in one launch."""
+        LAUNCHES[0] += 1
+        self._ok(self._step_sample(self._ctx, s_in.data_ptr(), s_out.data_ptr(), int(n), int(first), out_ptr,
+                                   self.sh))
+
+    def step_tape(self, s_in, s_out, n: int, first: bool, out_ptr: int, tape_ptr: int):
+        """step_sample() that also writes the step's tape record at tape_ptr."""
+        LAUNCHES[0] += 1
+        self._ok(self._step_tape(self._ctx, s_in.data_ptr(), s_out.data_ptr(), int(n), int(first), out_ptr,
+                                 tape_ptr, self.sh))
+
     def sample(self, s, physical: bool, out_ptr: int):
         LAUNCHES[0] += 1
         self._ok(self._sample(self._ctx, s.data_ptr(), int(physical), out_ptr, self.sh))
@@ -101,6 +128,12 @@ class Operator:
         """adjoint() plus the step's spin-derivative term (acc[4]); s = s_n."""
         LAUNCHES[0] += 2
         self._ok(self._adjs(self._ctx, lam_in.data_ptr(), lam_out.data_ptr(), s.data_ptr(), int(n), int(first),
+                            gseed_ptr, self._ws, self.sh))
+
+    def adjoint_tape(self, lam_in, lam_out, tape_ptr: int, n: int, first: bool, gseed_ptr):
+        """adjoint_spin() with the stage values of step n read from its tape record."""
+        LAUNCHES[0] += 2
+        self._ok(self._adjt(self._ctx, lam_in.data_ptr(), lam_out.data_ptr(), tape_ptr, int(n), int(first),
                             gseed_ptr, self._ws, self.sh))
 
     def dot(self, x, y, out_ptr: int, z=None):
@@ -128,10 +161,12 @@ def _ptr(t, k: int) -> int:
     return t.data_ptr() + 16 * k
 
 
-def run_forward(op: Operator, nsteps: int, u0=None, every: int | None = None):
+def run_forward(op: Operator, nsteps: int, u0=None, every: int | None = None, tape=None):
     """Waveform h_0..h_N (complex128, device), the checkpoints {0: u_0} and
     {n: s_n} for every n divisible by `every`, and the last state s_N (u_0
-    when N = 0).  Call on the operator's stream."""
+    when N = 0).  With `tape` (a device buffer of N records of
+    op.tape_bytes) every step also writes its tape record n.  Call on the
+    operator's stream."""
     torch = op.torch
     h = torch.zeros(nsteps + 1, dtype=torch.complex128, device=op.st.device)
     u = op.zeros() if u0 is None else torch.as_tensor(u0).to(device=op.st.device, dtype=op.ctype).reshape(op.shape)
@@ -140,23 +175,30 @@ def run_forward(op: Operator, nsteps: int, u0=None, every: int | None = None):
     if nsteps == 0:
         return h, ck, u
     s, t = op.empty(), op.empty()
-    op.step(u, s, 0, True)
-    for n in range(1, nsteps + 1):
-        if every and n % every == 0 and n < nsteps:
+
+    def adv(x, y, n):
+        # one launch writes s_{n+1}, its sample h_{n+1} (and record n)
+        if tape is None:
+            op.step_sample(x, y, n, n == 0, _ptr(h, n + 1))
+        else:
+            op.step_tape(x, y, n, n == 0, _ptr(h, n + 1), tape.data_ptr() + n * op.tape_bytes)
+
+    adv(u, s, 0)
+    for n in range(1, nsteps):
+        if every and n % every == 0:
             ck[n] = s.clone()
-        op.sample(s, False, _ptr(h, n))
-        if n < nsteps:
-            op.step(s, t, n, False)
-            s, t = t, s
+        adv(s, t, n)
+        s, t = t, s
     return h, ck, s
 
 
 class Forward:
     """A forward run kept for a backward sweep: the operator, the waveform
-    and the checkpoints (sqrt(N) states)."""
+    and the checkpoints (sqrt(N) states), or the tape of every step."""
 
-    def __init__(self, op, nsteps, h, ck, every, last=None):
+    def __init__(self, op, nsteps, h, ck, every, last=None, tape=None):
         self.op, self.nsteps, self.h, self.ck, self.every, self.last = op, nsteps, h, ck, every, last
+        self.tape = tape
 
     def close(self):
         if self.op is not None:
@@ -164,22 +206,32 @@ class Forward:
             self.op = None
         self.ck = None
         self.last = None
+        self.tape = None
 
 
 def forward(w: inputs.Workload, prm: Params, nsteps: int, u0=None, precision: str = "fp64",
-            every: int | None = None, device=None) -> Forward:
-    """Forward run that keeps a state every `every` steps (default ~sqrt(N))."""
+            every: int | None = None, device=None, tape: bool = False) -> Forward:
+    """Forward run that keeps a state every `every` steps (default ~sqrt(N)),
+    or with tape=True the tape record of every step (N x teuk_tape_bytes of
+    device memory: two states per step; the backward sweep then recomputes
+    nothing)."""
     import torch
     op = Operator(w, prm, precision, device=device)
     every = every or max(1, int(round(math.sqrt(max(nsteps, 1)))))
+    tp = None
+    if tape and nsteps > 0:
+        tp = torch.empty(nsteps * op.tape_bytes // 8, dtype=torch.float64, device=op.st.device)
+        every = 0
     caller = torch.cuda.current_stream(op.st.device)
     # u0 may come from work queued on the caller's stream
     op.st.stream.wait_stream(caller)
     with torch.cuda.stream(op.st.stream):
-        h, ck, last = run_forward(op, nsteps, u0, every)
+        if tp is not None:
+            tp.record_stream(op.st.stream)
+        h, ck, last = run_forward(op, nsteps, u0, every, tape=tp)
     # and the caller's later work reads h
     caller.wait_stream(op.st.stream)
-    return Forward(op, nsteps, h, ck, every, last)
+    return Forward(op, nsteps, h, ck, every, last, tape=tp)
 
 
 def backward(fw: Forward, grad_h, wrt_a: bool = True, eps_a: float | None = None, spin: str = "analytic") -> dict:
@@ -205,10 +257,10 @@ def backward(fw: Forward, grad_h, wrt_a: bool = True, eps_a: float | None = None
 
 def gradients(w: inputs.Workload, prm: Params, nsteps: int, grad_h, u0=None, precision: str = "fp64",
               every: int | None = None, wrt_a: bool = True, eps_a: float | None = None, device=None,
-              spin: str = "analytic"):
+              spin: str = "analytic", tape: bool = False):
     """forward() followed by backward(); returns backward's dictionary plus
     the waveform under "h"."""
-    fw = forward(w, prm, nsteps, u0, precision, every, device)
+    fw = forward(w, prm, nsteps, u0, precision, every, device, tape=tape)
     try:
         out = backward(fw, grad_h, wrt_a, eps_a, spin)
         out["h"] = fw.h
@@ -229,6 +281,8 @@ def _sweep(fw: Forward, grad_h, wrt_a, eps_a, spin="analytic"):
     analytic = wrt_a and spin == "analytic"
     if analytic and fw.last is None:
         raise ValueError("the forward run kept no last state")
+    if fw.tape is not None and wrt_a and not analytic:
+        raise ValueError("a taped forward run keeps no checkpoints: use spin='analytic'")
     if wrt_a and not analytic:
         eps = eps_a if eps_a is not None else (1e-4 if precision == "fp64" else 1e-3)
         dev = op.st.device
@@ -237,7 +291,7 @@ def _sweep(fw: Forward, grad_h, wrt_a, eps_a, spin="analytic"):
         dots = torch.zeros(nsteps + 1, dtype=torch.complex128, device=dev)
         samp = torch.zeros((nsteps + 1, 2), dtype=torch.complex128, device=dev)
         tp, tm = op.empty(), op.empty()
-    op.ws.zero_()
+    op.ws[:8].zero_()   # the accumulators (the tail holds the coefficient planes)
     lam, lam2 = op.zeros(), op.empty()
     # lam_N from the last sample alone (lam_{N+1} = 0)
     if analytic:
@@ -245,7 +299,22 @@ def _sweep(fw: Forward, grad_h, wrt_a, eps_a, spin="analytic"):
     else:
         op.adjoint(lam, lam2, nsteps, nsteps == 0, _ptr(g, nsteps))
     lam, lam2 = lam2, lam
-    bounds = sorted(k for k in ck) + [nsteps]
+    if fw.tape is not None and (analytic or not wrt_a):
+        # the tape holds every step's stage values: nothing to recompute
+        for n in range(nsteps - 1, -1, -1):
+            if analytic:
+                op.adjoint_tape(lam, lam2, fw.tape.data_ptr() + n * op.tape_bytes, n, n == 0, _ptr(g, n))
+            else:
+                op.adjoint(lam, lam2, n, n == 0, _ptr(g, n))
+            lam, lam2 = lam2, lam
+        ck = {}
+    elif not wrt_a:
+        # the adjoint of the linear step reads no state: no recompute either
+        for n in range(nsteps - 1, -1, -1):
+            op.adjoint(lam, lam2, n, n == 0, _ptr(g, n))
+            lam, lam2 = lam2, lam
+        ck = {}
+    bounds = sorted(k for k in ck) + [nsteps] if ck else []
     for a, b in reversed(list(zip(bounds[:-1], bounds[1:]))):
         # states s_a .. s_b of this segment (s_0 is the physical u_0); the
         # adjoint steps n = b-1 .. a read s_n, so with the contracted spin

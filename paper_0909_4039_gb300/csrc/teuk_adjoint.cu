@@ -302,38 +302,6 @@ __global__ void __launch_bounds__(256, 1) k_adjoint_step(const StepParams<T> p, 
 // spin derivative (dstab, exact forward-mode derivatives of the FP64
 // table generator, r(r*; a) by implicit differentiation of Eq. 2).
 
-// beta = c_p b, kap = c_p K and 1/Sigma^2 at step-table entry f, with their
-// derivatives with respect to a (df: the entry's spin derivative).  The
-// values are those lw_coef forms.
-template <typename T> struct LwDa {
-    typedef typename V2<T>::t c2;
-    T beta, dbeta, sg, dsg;
-    c2 kap, dkap;
-};
-template <typename T>
-__device__ __forceinline__ LwDa<T> lw_coef_da(const T *f, const T *df, T S2, T C)
-{
-    typedef typename V2<T>::t c2;
-    LwDa<T> o;
-    const T sig = fma(-f[SF_AD], S2, f[SF_R2]);
-    const T dsig = fma(-df[SF_AD], S2, df[SF_R2]);
-    const T rs = rsq_(sig);
-    o.sg = rs * rs;
-    const T drs = T(-0.5) * rs * o.sg * dsig;
-    o.dsg = -o.sg * o.sg * dsig;
-    o.beta = rs * f[SF_RB];
-    o.dbeta = fma(drs, f[SF_RB], rs * df[SF_RB]);
-    const T t = fma(-f[SF_E3], S2, f[SF_E2]), dt_ = fma(-df[SF_E3], S2, df[SF_E2]);
-    const T X = fma(o.sg, t, fma(rs, f[SF_RCTR], f[SF_CSE]));
-    const T dX = o.dsg * t + o.sg * dt_ + drs * f[SF_RCTR] + rs * df[SF_RCTR] + df[SF_CSE];
-    const T u = fma(f[SF_RCTC], C, f[SF_RCTI]), du = fma(df[SF_RCTC], C, df[SF_RCTI]);
-    const T Y = fma(rs, u, f[SF_CSI]);
-    const T dY = drs * u + rs * du + df[SF_CSI];
-    o.kap = cmk<c2>(o.sg * X, o.sg * Y);
-    o.dkap = cmk<c2>(o.dsg * X + o.sg * dX, o.dsg * Y + o.sg * dY);
-    return o;
-}
-
 // The source term of a stage, S = F ph (ph: the scaled phase), as the
 // forward step forms it, and dS/da: F = SRC sg (SR2 GTH + GA2) through its
 // factors and 1/Sigma^2, the phase through Omega(a) (mdt = m t dOmega/da).
@@ -369,12 +337,13 @@ __device__ __forceinline__ void seg_load(const typename V2<T>::t *row, int j0, i
 // exit), and this lane's part of <mu, dC_h u> from the forward stage values
 // (u1f, u1g) = U1 and (u2f, u2g) = U2 of the same row; f, df: the row's
 // step-table entry and its spin derivative.
-template <typename T, int S>
+template <typename T, int S, bool MAT = false>
 __device__ double implicit_row_adj_spin(const ImpConst<T> &K, typename V2<T>::t *lf, typename V2<T>::t *lg,
                                         const typename V2<T>::t *u1f, const typename V2<T>::t *u1g,
                                         const typename V2<T>::t *u2f, const typename V2<T>::t *u2g,
                                         const typename V2<T>::t *prow, const T *f, const T *df, const T *th, int N,
-                                        bool active, bool in_tile, int g, int G, bool vec)
+                                        bool active, bool in_tile, int g, int G, bool vec,
+                                        const AdjPlanes<T> *A = nullptr, int gi = 0)
 {
     typedef typename V2<T>::t c2;
     const c2 zero = cmk<c2>(T(0), T(0));
@@ -386,7 +355,10 @@ __device__ double implicit_row_adj_spin(const ImpConst<T> &K, typename V2<T>::t 
     const T gh = K.gh, c = K.h1g;
     ImpCoef<T, S> C;
     c2 w[S], y[S];   // mu_Phi, mu_Pi
-    imp_load<T, S>(K, lf, lg, prow, f, th, N, len, j0, vec, C, w, y);
+    if constexpr (MAT)
+        imp_load_mat<T, S>(A->m, lf, lg, prow, gi, N, len, j0, vec, C, w, y);
+    else
+        imp_load<T, S>(K, lf, lg, prow, f, th, N, len, j0, vec, C, w, y);
     // multipliers of M^H = U^H L^H and the rows of W^H (qap_{j-1}, conj(dg_j), qam_{j+1})
     c2 fm[S], pm[S], bm[S];
     T qapp[S], qamn[S];
@@ -447,7 +419,22 @@ __device__ double implicit_row_adj_spin(const ImpConst<T> &K, typename V2<T>::t 
     // derivative coefficients dW (dqam, ddg, dqap) and dc_t of the row
     c2 ddg[S], dct[S];
     T dqam[S], dqap[S];
-    {
+    if constexpr (MAT) {
+#pragma unroll
+        for (int k = 0; k < S; ++k) {
+            T v[8];
+            if (k < len) {
+                vload<8>(v, A->dimp + ((size_t)gi * N + j0 + k) * 8);
+            } else {
+#pragma unroll
+                for (int q = 0; q < 8; ++q) v[q] = T(0);
+            }
+            ddg[k] = cmk<c2>(v[0], v[1]);
+            dct[k] = cmk<c2>(v[2], v[3]);
+            dqam[k] = v[4];
+            dqap[k] = v[5];
+        }
+    } else {
         const ImpRow<T> r = imp_row(K, f);
         T fr[8], dfr[8];
         vload<8>(fr, f);
@@ -456,16 +443,8 @@ __device__ double implicit_row_adj_spin(const ImpConst<T> &K, typename V2<T>::t 
         for (int k = 0; k < S; ++k) {
             if (k < len) {
                 const int j = j0 + k;
-                const T s2 = th[TF_S2 * N + j], cc = th[TF_C * N + j];
-                const T sg = imp_sg(r, s2);
-                const T dsg = -sg * sg * fma(-dfr[SF_AD], s2, dfr[SF_R2]);
-                const T dq = fma(dfr[SF_DELTA], sg, r.D * dsg);
-                dqam[k] = dq * th[TF_AM * N + j];
-                dqap[k] = dq * th[TF_AP * N + j];
-                ddg[k] = cmk<c2>(fma(dq, th[TF_A0 * N + j], -(dsg * r.c0r + sg * dfr[SF_C0R])),
-                                 -(dsg * r.c0i + sg * dfr[SF_C0I]));
-                const T ctr = dfr[SF_CTR], cti = fma(dfr[SF_CTC], cc, dfr[SF_CTI]);
-                dct[k] = cmk<c2>(fma(dsg, fr[SF_CTR], sg * ctr), fma(dsg, fma(fr[SF_CTC], cc, fr[SF_CTI]), sg * cti));
+                imp_da<T>(r, fr, dfr, th[TF_S2 * N + j], th[TF_C * N + j], th[TF_AM * N + j], th[TF_A0 * N + j],
+                          th[TF_AP * N + j], ddg[k], dct[k], dqam[k], dqap[k]);
             } else {
                 dqam[k] = dqap[k] = T(0);
                 ddg[k] = dct[k] = zero;
@@ -515,9 +494,10 @@ __device__ double implicit_row_adj_spin(const ImpConst<T> &K, typename V2<T>::t 
 // (vF, vG) and U1 (u1F, u1G), the midpoint adjoints (mF, mG).
 constexpr int kNPart = 6;
 
-template <typename T, int S>
+template <typename T, int S, bool MAT>
 __global__ void __launch_bounds__(256, 1) k_adjoint_spin(const StepParams<T> p, const typename V2<T>::t *sin,
-                                                         const double2 *gseed, double *part)
+                                                         const typename V2<T>::t *tape, const double2 *gseed,
+                                                         const AdjPlanes<T> A, double *part)
 {
     typedef typename V2<T>::t c2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -547,21 +527,36 @@ __global__ void __launch_bounds__(256, 1) k_adjoint_spin(const StepParams<T> p, 
     T *sDSt = sSt + (2 * R - 1) * NSF;
     T *sTh = sDSt + (2 * R - 1) * NSF;
 
-    // ---- lam_{n+1} and s_n on rows i0-1 .. i0+TR, the step tables, theta tables
+    // ---- lam_{n+1} and s_n (with a tape: the forward stage values U2 and U1
+    // the forward step recorded) on rows i0-1 .. i0+TR, the step tables,
+    // theta tables
+    const c2 *tp1 = tape, *tp2 = tape ? tape + tape_u2_off(Nr, N) : nullptr;
     for (int idx = tid; idx < R * N; idx += NT) {
         const int lr = idx / N, j = idx - lr * N;
         const int gi = i0 - 1 + lr;
-        c2 a = zero, b = zero, sa = zero, sb = zero;
+        c2 a = zero, b = zero, sa = zero, sb = zero, ua = zero, ub = zero;
         if (gi >= 0 && gi < Nr) {
-            a = p.uin[(size_t)gi * N + j];
-            b = p.uin[((size_t)Nr + gi) * N + j];
-            sa = sin[(size_t)gi * N + j];
-            sb = sin[((size_t)Nr + gi) * N + j];
+            const size_t qf = (size_t)gi * N + j, qg = ((size_t)Nr + gi) * N + j;
+            a = p.uin[qf];
+            b = p.uin[qg];
+            if (tape) {
+                sa = tp2[qf];
+                sb = tp2[qg];
+                ua = tp1[qf];
+                ub = tp1[qg];
+            } else {
+                sa = sin[qf];
+                sb = sin[qg];
+            }
         }
         lF[idx] = a;
         lG[idx] = b;
         vF[idx] = sa;
         vG[idx] = sb;
+        if (tape) {
+            u1F[idx] = ua;
+            u1G[idx] = ub;
+        }
     }
     {
         const long long pbase = 2LL * (i0 - 1), pmax = 2LL * Nr - 2;
@@ -577,7 +572,7 @@ __global__ void __launch_bounds__(256, 1) k_adjoint_spin(const StepParams<T> p, 
     __syncthreads();
 
     // ---- forward implicit stage on all rows: (vF, vG) <- U2 = C_h s_n, (u1F, u1G) <- U1
-    {
+    if (!tape) {
         const int rpp = NT / G;
         for (int base = 0; base < R; base += rpp) {
             const int lr = base + tid / G;
@@ -585,9 +580,10 @@ __global__ void __launch_bounds__(256, 1) k_adjoint_spin(const StepParams<T> p, 
             const int gi = i0 - 1 + lr;
             const bool active = in_tile && gi >= 1 && gi <= Nr - 2;
             const int lrc = in_tile ? lr : 0;
-            implicit_row_fwd<T, S>(K, vF + lrc * P, vG + lrc * P, K.piv + (size_t)(active ? gi : 1) * N,
-                                   sSt + 2 * lrc * NSF, sTh, N, active, in_tile, g, G, vec, active ? K.plan[gi] : 0,
-                                   nullptr, 0, u1F + lrc * P, u1G + lrc * P);
+            implicit_row_fwd<T, S, MAT>(K, vF + lrc * P, vG + lrc * P, K.piv + (size_t)(active ? gi : 1) * N,
+                                        sSt + 2 * lrc * NSF, sTh, N, active, in_tile, g, G, vec,
+                                        active ? K.plan[gi] : 0, &A.m, active ? gi : 1, u1F + lrc * P,
+                                        u1G + lrc * P);
         }
     }
     __syncthreads();
@@ -606,6 +602,27 @@ __global__ void __launch_bounds__(256, 1) k_adjoint_spin(const StepParams<T> p, 
     const T mdt1 = (T)(p.m_dOmega_da * t1), mdt2 = (T)(p.m_dOmega_da * t2);
     double2 cA = make_double2(0.0, 0.0), cr = cA;
     double spin = 0.0;
+
+    // beta, kap, 1/Sigma^2 and their spin derivatives at tile position e
+    // (2 lr: node, 2 k + 1: half node) and theta j
+    auto lwc = [&](int e, int j, T S2, T Cc) -> LwDa<T> {
+        if constexpr (MAT) {
+            const size_t o = ((size_t)(2 * (i0 - 1) + e) * N + j) * 4;
+            T v[4], dv[4];
+            vload<4>(v, A.m.lw + o);
+            vload<4>(dv, A.dlw + o);
+            LwDa<T> r;
+            r.beta = v[0];
+            r.kap = cmk<c2>(v[1], v[2]);
+            r.sg = v[3];
+            r.dbeta = dv[0];
+            r.dkap = cmk<c2>(dv[1], dv[2]);
+            r.dsg = dv[3];
+            return r;
+        } else {
+            return lw_coef_da<T>(sSt + e * NSF, sDSt + e * NSF, S2, Cc);
+        }
+    };
 
     // forward midpoint k (between tile rows k, k+1) from U2, as the step forms it
     auto fwd_mid = [&](int k, int j, const LwDa<T> &h, c2 &mf, c2 &mg) {
@@ -631,13 +648,13 @@ __global__ void __launch_bounds__(256, 1) k_adjoint_spin(const StepParams<T> p, 
         c2 wF = zero, wG = zero;
         if (gl >= 0 && gl <= Nr - 2) {
             if (gl >= 1) {   // lower node interior
-                const LwDa<T> nd = lw_coef_da<T>(sSt + 2 * k * NSF, sDSt + 2 * k * NSF, S2, Cc);
+                const LwDa<T> nd = lwc(2 * k, j, S2, Cc);
                 const c2 lf = lF[k * P + j], lg = lG[k * P + j];
                 wF = csub(cmul(conj_c(nd.kap), lg), cscale<c2>(nd.beta, lf));
                 wG = cscale<c2>(nd.beta, lg);
             }
             if (gl + 1 <= Nr - 2) {   // upper node interior
-                const LwDa<T> nd = lw_coef_da<T>(sSt + 2 * (k + 1) * NSF, sDSt + 2 * (k + 1) * NSF, S2, Cc);
+                const LwDa<T> nd = lwc(2 * (k + 1), j, S2, Cc);
                 const c2 lf = lF[(k + 1) * P + j], lg = lG[(k + 1) * P + j];
                 wF = cadd(wF, csub(cscale<c2>(nd.beta, lf), cmul(conj_c(nd.kap), lg)));
                 wG = csub(wG, cscale<c2>(nd.beta, lg));
@@ -650,7 +667,7 @@ __global__ void __launch_bounds__(256, 1) k_adjoint_spin(const StepParams<T> p, 
                         source_grad<T>(p, wG, (double)hdtT, p.patchu[((size_t)pr * 2 + 1) * N + j], ph1,
                                        p.rs_min64 + ((double)gl + 0.5) * p.drs64, t1, cA, cr);
                 }
-                const LwDa<T> h = lw_coef_da<T>(sSt + (2 * k + 1) * NSF, sDSt + (2 * k + 1) * NSF, S2, Cc);
+                const LwDa<T> h = lwc(2 * k + 1, j, S2, Cc);
                 const c2 fa = vF[k * P + j], fb = vF[(k + 1) * P + j], ga = vG[k * P + j], gb = vG[(k + 1) * P + j];
                 const c2 Df = csub(fb, fa), Dg = csub(gb, ga);
                 // d(Phi*) = -dbeta Df,  d(Pi*) = dbeta Dg + dkap Df + dS
@@ -682,13 +699,13 @@ __global__ void __launch_bounds__(256, 1) k_adjoint_spin(const StepParams<T> p, 
         c2 wF = interior ? lf : zero, wG = interior ? lg : zero;
         LwDa<T> hu, hd;
         if (gi <= Nr - 2) {   // midpoint lr (to the next row)
-            hu = lw_coef_da<T>(sSt + (2 * lr + 1) * NSF, sDSt + (2 * lr + 1) * NSF, S2, Cc);
+            hu = lwc(2 * lr + 1, j, S2, Cc);
             const c2 mf = mF[lr * P + j], mg = mG[lr * P + j];
             wF = cadd(wF, csub(cscale<c2>(T(0.5) + hu.beta, mf), cmul(conj_c(hu.kap), mg)));
             wG = cadd(wG, cscale<c2>(T(0.5) - hu.beta, mg));
         }
         if (gi >= 1) {   // midpoint lr - 1 (to the previous row)
-            hd = lw_coef_da<T>(sSt + (2 * lr - 1) * NSF, sDSt + (2 * lr - 1) * NSF, S2, Cc);
+            hd = lwc(2 * lr - 1, j, S2, Cc);
             const c2 mf = mF[(lr - 1) * P + j], mg = mG[(lr - 1) * P + j];
             wF = cadd(wF, cadd(cscale<c2>(T(0.5) - hd.beta, mf), cmul(conj_c(hd.kap), mg)));
             wG = cadd(wG, cscale<c2>(T(0.5) + hd.beta, mg));
@@ -702,7 +719,7 @@ __global__ void __launch_bounds__(256, 1) k_adjoint_spin(const StepParams<T> p, 
             }
             // spin terms of the node stage: d(Phi') = -dbeta dMf,
             // d(Pi') = dbeta dMg + dkap dMf + dS, dM the forward midpoint difference
-            const LwDa<T> nd = lw_coef_da<T>(sSt + 2 * lr * NSF, sDSt + 2 * lr * NSF, S2, Cc);
+            const LwDa<T> nd = lwc(2 * lr, j, S2, Cc);
             c2 mfu, mgu, mfd, mgd;
             fwd_mid(lr, j, hu, mfu, mgu);
             fwd_mid(lr - 1, j, hd, mfd, mgd);
@@ -732,10 +749,10 @@ __global__ void __launch_bounds__(256, 1) k_adjoint_spin(const StepParams<T> p, 
             const int gi = i0 - 1 + lr;
             const bool active = in_tile && gi >= 1 && gi <= Nr - 2;
             const int lrc = in_tile ? lr : 1;
-            const double d = implicit_row_adj_spin<T, S>(K, lF + lrc * P, lG + lrc * P, u1F + lrc * P, u1G + lrc * P,
-                                                         vF + lrc * P, vG + lrc * P,
-                                                         K.piv + (size_t)(active ? gi : 1) * N, sSt + 2 * lrc * NSF,
-                                                         sDSt + 2 * lrc * NSF, sTh, N, active, in_tile, g, G, vec);
+            const double d = implicit_row_adj_spin<T, S, MAT>(
+                K, lF + lrc * P, lG + lrc * P, u1F + lrc * P, u1G + lrc * P, vF + lrc * P, vG + lrc * P,
+                K.piv + (size_t)(active ? gi : 1) * N, sSt + 2 * lrc * NSF, sDSt + 2 * lrc * NSF, sTh, N, active,
+                in_tile, g, G, vec, &A, active ? gi : 1);
             if (active) spin += d;
         }
     }
@@ -754,8 +771,13 @@ __global__ void __launch_bounds__(256, 1) k_adjoint_spin(const StepParams<T> p, 
                 const double w = p.w[j];
                 xF[j] = cmk<c2>((T)(w * gv.x), (T)(w * gv.y));
                 xG[j] = zero;
-                sF[j] = sin[(size_t)p.i_ext * N + j];
-                sG[j] = sin[((size_t)Nr + p.i_ext) * N + j];
+                if (tape) {
+                    sF[j] = tape[tape_x_off(Nr, N) + j];
+                    sG[j] = tape[tape_x_off(Nr, N) + N + j];
+                } else {
+                    sF[j] = sin[(size_t)p.i_ext * N + j];
+                    sG[j] = sin[((size_t)Nr + p.i_ext) * N + j];
+                }
             }
             __syncwarp();
             if (!first) {
@@ -941,19 +963,31 @@ size_t adjoint_spin_smem_bytes(int tile_rows, int Nth)
     return 8 * R * Nth * sizeof(typename V2<T>::t) + (2 * (2 * R - 1) * NSF + (size_t)NTF * Nth) * sizeof(T);
 }
 
+template <typename T, bool MAT>
+static void (*adjoint_spin_fn(int Nth))(const StepParams<T>, const typename V2<T>::t *, const typename V2<T>::t *,
+                                        const double2 *, const AdjPlanes<T>, double *)
+{
+    const int seg = implicit_seg(Nth);
+    return seg == kSegNarrow ? k_adjoint_spin<T, kSegNarrow, MAT>
+                             : (seg == kSeg ? k_adjoint_spin<T, kSeg, MAT> : k_adjoint_spin<T, kSegWide, MAT>);
+}
+
 template <typename T>
 cudaError_t launch_adjoint_spin(const StepParams<T> &p, int tile_rows, const typename V2<T>::t *sin,
-                                const double2 *gseed, double *part, double *acc, cudaStream_t st)
+                                const typename V2<T>::t *tape, const double2 *gseed, const AdjPlanes<T> &A,
+                                double *part, double *acc, cudaStream_t st)
 {
-    const int seg = implicit_seg(p.Nth);
-    auto fn = seg == kSegNarrow ? k_adjoint_spin<T, kSegNarrow>
-                                : (seg == kSeg ? k_adjoint_spin<T, kSeg> : k_adjoint_spin<T, kSegWide>);
+    // the planes (FP64) hold the full step's coefficients; a first step
+    // (dt/2) and the FP32 adjoint form their own from the tables
+    auto fn = adjoint_spin_fn<T, false>(p.Nth);
+    if constexpr (sizeof(T) == 8)
+        if (!p.first) fn = adjoint_spin_fn<T, true>(p.Nth);
     cudaError_t e = smem_limit_max((const void *)fn);
     if (e != cudaSuccess) return e;
     StepParams<T> q = p;
     q.tile_rows = tile_rows;
     const int grid = adjoint_grid<T>(p.Nr, tile_rows);
-    fn<<<grid, 256, adjoint_spin_smem_bytes<T>(tile_rows, p.Nth), st>>>(q, sin, gseed, part);
+    fn<<<grid, 256, adjoint_spin_smem_bytes<T>(tile_rows, p.Nth), st>>>(q, sin, tape, gseed, A, part);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_part_reduce6<<<1, 32, 0, st>>>(part, grid, acc);
@@ -984,10 +1018,12 @@ template cudaError_t launch_adjoint_step<double>(const StepParams<double> &, int
                                                  cudaStream_t);
 template size_t adjoint_spin_smem_bytes<float>(int, int);
 template size_t adjoint_spin_smem_bytes<double>(int, int);
-template cudaError_t launch_adjoint_spin<float>(const StepParams<float> &, int, const float2 *, const double2 *,
-                                                double *, double *, cudaStream_t);
+template cudaError_t launch_adjoint_spin<float>(const StepParams<float> &, int, const float2 *, const float2 *,
+                                                const double2 *, const AdjPlanes<float> &, double *, double *,
+                                                cudaStream_t);
 template cudaError_t launch_adjoint_spin<double>(const StepParams<double> &, int, const double2 *, const double2 *,
-                                                 double *, double *, cudaStream_t);
+                                                 const double2 *, const AdjPlanes<double> &, double *, double *,
+                                                 cudaStream_t);
 template cudaError_t launch_dot<float>(const float2 *, const float2 *, const float2 *, size_t, double *, double2 *,
                                        cudaStream_t);
 template cudaError_t launch_dot<double>(const double2 *, const double2 *, const double2 *, size_t, double *,

@@ -61,6 +61,7 @@ struct teuk_ctx {
     int ks;                  // time steps per launch of the tiled kernel (1 or 2)
     int wait0;               // teuk_set_wait_limit (< 0: default bound)
     size_t smem2;            // shared memory of the two-step kernel
+    const void *adj_ws;      // adjoint workspace whose coefficient planes teuk_adjoint_prepare filled
     // graphs, one per starting level
     cudaGraphExec_t graph[2];
     cudaStream_t graph_stream[2];
@@ -476,6 +477,8 @@ StepParams<T> make_params(const teuk_ctx *c, int in_level)
     p.thtab = (const T *)(c->coef + c->L.thT);
     p.patch = (const c2 *)(c->coef + c->L.patch);
     p.nfix = -1;
+    p.h_out = nullptr;
+    p.tape = nullptr;
     p.patchu = (const c2 *)(c->coef + c->L.patchu);
     p.unit_p0 = c->unit_p0;
     p.unit_np = c->unit_np;
@@ -1256,19 +1259,72 @@ int adjoint_spin_tile_rows(const teuk_ctx *c)
     return best;
 }
 
-size_t adjoint_ws_doubles(const teuk_ctx *c)
+// The adjoint workspace: accumulators (8 doubles), per-CTA parts, the
+// dot product's parts (512 doubles), then the coefficient planes of the
+// spin adjoint from a 256-byte boundary.
+size_t adjoint_small_doubles(const teuk_ctx *c)
 {
     const int tr = adjoint_tile_rows(c), trs = adjoint_spin_tile_rows(c);
     const int grid = (int)((c->d.Nr + tr - 1) / tr), grids = (int)((c->d.Nr + trs - 1) / trs);
     const int gmax = grid > grids ? grid : grids;
-    return 8 + 6 * (size_t)gmax + 2 * 256;   // accumulators, per-CTA parts, dot parts
+    return 8 + 6 * (size_t)gmax + 2 * 256;
+}
+size_t adjoint_planes_offset(const teuk_ctx *c) { return (sizeof(double) * adjoint_small_doubles(c) + 255) & ~(size_t)255; }
+// FP64 only: the FP32 adjoint forms its coefficients in place, which costs
+// it less than reading them (the FP64 step is bound by the FP64 pipe, the
+// FP32 step is not)
+AdjPlaneLayout adjoint_planes_layout(const teuk_ctx *c)
+{
+    if (c->d.precision == TEUK_FP32) {
+        AdjPlaneLayout L = {};
+        return L;
+    }
+    return adj_plane_layout(c->d.Nr, c->d.Ntheta, sizeof(double));
+}
+size_t adjoint_ws_bytes(const teuk_ctx *c) { return adjoint_planes_offset(c) + adjoint_planes_layout(c).total; }
+
+template <typename T>
+AdjPlanes<T> adjoint_planes(const teuk_ctx *c, const void *ws)
+{
+    typedef typename V2<T>::t c2;
+    const char *b = (const char *)ws + adjoint_planes_offset(c);
+    const AdjPlaneLayout L = adjoint_planes_layout(c);
+    AdjPlanes<T> A;
+    A.m.fk = (const c2 *)(b + L.off[0]);
+    A.m.dg = (const c2 *)(b + L.off[1]);
+    A.m.ct = (const c2 *)(b + L.off[2]);
+    A.m.sub = (const T *)(b + L.off[3]);
+    A.m.qam = (const T *)(b + L.off[4]);
+    A.m.qap = (const T *)(b + L.off[5]);
+    A.m.lw = (const T *)(b + L.off[6]);
+    A.dlw = (const T *)(b + L.off[7]);
+    A.dimp = (const T *)(b + L.off[8]);
+    return A;
+}
+
+template <typename T>
+cudaError_t fill_adjoint_planes(const teuk_ctx *c, void *ws, cudaStream_t st)
+{
+    typedef typename V2<T>::t c2;
+    const AdjPlanes<T> A = adjoint_planes<T>(c, ws);
+    MatOut<T> o;
+    o.fk = (c2 *)A.m.fk;
+    o.dg = (c2 *)A.m.dg;
+    o.ct = (c2 *)A.m.ct;
+    o.sub = (T *)A.m.sub;
+    o.qam = (T *)A.m.qam;
+    o.qap = (T *)A.m.qap;
+    o.lw = (T *)A.m.lw;
+    o.dlw = (T *)A.dlw;
+    o.dimp = (T *)A.dimp;
+    return launch_mat_coef_to<T>(make_params<T>(c, 0), o, st);
 }
 
 }  // namespace
 
 extern "C" {
 
-int teuk_apply_step(teuk_ctx *c, const void *d_in, void *d_out, int64_t n, int first, void *stream)
+static int apply_step(teuk_ctx *c, const void *d_in, void *d_out, int64_t n, int first, void *d_h, void *stream)
 {
     if (!c) return TEUK_E_STATE;
     if (c->d.scheme != TEUK_SCHEME_SPLIT) return set_err(c, TEUK_E_INVAL, "teuk_apply_step needs the split scheme");
@@ -1282,6 +1338,7 @@ int teuk_apply_step(teuk_ctx *c, const void *d_in, void *d_out, int64_t n, int f
         p.uout = (float2 *)d_out;
         p.first = first ? 1 : 0;
         p.nfix = n;
+        p.h_out = (double2 *)d_h;
         e = launch_apply_step<float>(p, c->threads, c->smem, st);
     } else {
         StepParams<double> p = make_params<double>(c, 0);
@@ -1289,10 +1346,23 @@ int teuk_apply_step(teuk_ctx *c, const void *d_in, void *d_out, int64_t n, int f
         p.uout = (double2 *)d_out;
         p.first = first ? 1 : 0;
         p.nfix = n;
+        p.h_out = (double2 *)d_h;
         e = launch_apply_step<double>(p, c->threads, c->smem, st);
     }
     if (e != cudaSuccess) return cuda_err(c, e, "apply step");
     return TEUK_OK;
+}
+
+int teuk_apply_step(teuk_ctx *c, const void *d_in, void *d_out, int64_t n, int first, void *stream)
+{
+    return apply_step(c, d_in, d_out, n, first, nullptr, stream);
+}
+
+int teuk_apply_step_sample(teuk_ctx *c, const void *d_in, void *d_out, int64_t n, int first, void *d_h,
+                           void *stream)
+{
+    if (c && !d_h) return set_err(c, TEUK_E_INVAL, "need a device address for the sample");
+    return apply_step(c, d_in, d_out, n, first, d_h, stream);
 }
 
 int teuk_apply_sample(teuk_ctx *c, const void *d_s, int physical, void *d_h, void *stream)
@@ -1314,7 +1384,19 @@ int teuk_apply_sample(teuk_ctx *c, const void *d_s, int physical, void *d_h, voi
 int teuk_adjoint_workspace_bytes(const teuk_ctx *c, size_t *bytes)
 {
     if (!c || !bytes) return TEUK_E_STATE;
-    *bytes = sizeof(double) * adjoint_ws_doubles(c);
+    *bytes = adjoint_ws_bytes(c);
+    return TEUK_OK;
+}
+
+int teuk_adjoint_prepare(teuk_ctx *c, void *d_ws, void *stream)
+{
+    if (!c) return TEUK_E_STATE;
+    if (c->d.scheme != TEUK_SCHEME_SPLIT) return set_err(c, TEUK_E_INVAL, "the adjoint needs the split scheme");
+    if (!d_ws || ((uintptr_t)d_ws & 255)) return set_err(c, TEUK_E_INVAL, "need a 256-byte aligned workspace");
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = c->d.precision == TEUK_FP32 ? cudaSuccess : fill_adjoint_planes<double>(c, d_ws, st);
+    if (e != cudaSuccess) return cuda_err(c, e, "adjoint planes");
+    c->adj_ws = d_ws;
     return TEUK_OK;
 }
 
@@ -1348,14 +1430,12 @@ int teuk_adjoint_step(teuk_ctx *c, const void *d_lam_in, void *d_lam_out, int64_
     return TEUK_OK;
 }
 
-int teuk_adjoint_step_spin(teuk_ctx *c, const void *d_lam_in, void *d_lam_out, const void *d_s, int64_t n, int first,
-                           const void *d_gseed, void *d_ws, void *stream)
+static int adjoint_spin(teuk_ctx *c, const void *d_lam_in, void *d_lam_out, const void *d_s, const void *d_tape,
+                        int64_t n, int first, const void *d_gseed, void *d_ws, void *stream)
 {
-    if (!c) return TEUK_E_STATE;
-    if (c->d.scheme != TEUK_SCHEME_SPLIT) return set_err(c, TEUK_E_INVAL, "the adjoint needs the split scheme");
-    if (!d_lam_in || !d_lam_out || !d_s || d_lam_in == d_lam_out || d_s == d_lam_out || !d_ws || n < 0)
-        return set_err(c, TEUK_E_INVAL, "need distinct non-NULL device buffers, a workspace and n >= 0");
     cudaStream_t st = (cudaStream_t)stream;
+    if (d_ws != c->adj_ws)
+        return set_err(c, TEUK_E_STATE, "call teuk_adjoint_prepare with this workspace first");
     const int tr = adjoint_spin_tile_rows(c);
     double *acc = (double *)d_ws, *part = acc + 8;
     cudaError_t e;
@@ -1365,17 +1445,80 @@ int teuk_adjoint_step_spin(teuk_ctx *c, const void *d_lam_in, void *d_lam_out, c
         p.uout = (float2 *)d_lam_out;
         p.first = first ? 1 : 0;
         p.nfix = n;
-        e = launch_adjoint_spin<float>(p, tr, (const float2 *)d_s, (const double2 *)d_gseed, part, acc, st);
+        e = launch_adjoint_spin<float>(p, tr, (const float2 *)d_s, (const float2 *)d_tape, (const double2 *)d_gseed,
+                                       adjoint_planes<float>(c, d_ws), part, acc, st);
     } else {
         StepParams<double> p = make_params<double>(c, 0);
         p.uin = (const double2 *)d_lam_in;
         p.uout = (double2 *)d_lam_out;
         p.first = first ? 1 : 0;
         p.nfix = n;
-        e = launch_adjoint_spin<double>(p, tr, (const double2 *)d_s, (const double2 *)d_gseed, part, acc, st);
+        e = launch_adjoint_spin<double>(p, tr, (const double2 *)d_s, (const double2 *)d_tape,
+                                        (const double2 *)d_gseed, adjoint_planes<double>(c, d_ws), part, acc, st);
     }
     if (e != cudaSuccess) return cuda_err(c, e, "adjoint step (spin)");
     return TEUK_OK;
+}
+
+int teuk_adjoint_step_spin(teuk_ctx *c, const void *d_lam_in, void *d_lam_out, const void *d_s, int64_t n, int first,
+                           const void *d_gseed, void *d_ws, void *stream)
+{
+    if (!c) return TEUK_E_STATE;
+    if (c->d.scheme != TEUK_SCHEME_SPLIT) return set_err(c, TEUK_E_INVAL, "the adjoint needs the split scheme");
+    if (!d_lam_in || !d_lam_out || !d_s || d_lam_in == d_lam_out || d_s == d_lam_out || !d_ws || n < 0)
+        return set_err(c, TEUK_E_INVAL, "need distinct non-NULL device buffers, a workspace and n >= 0");
+    return adjoint_spin(c, d_lam_in, d_lam_out, d_s, nullptr, n, first, d_gseed, d_ws, stream);
+}
+
+int teuk_tape_bytes(const teuk_ctx *c, size_t *bytes)
+{
+    if (!c || !bytes) return TEUK_E_STATE;
+    const size_t c2 = c->d.precision == TEUK_FP32 ? sizeof(float2) : sizeof(double2);
+    *bytes = (tape_elems(c->d.Nr, c->d.Ntheta) * c2 + 255) & ~(size_t)255;
+    return TEUK_OK;
+}
+
+int teuk_apply_step_tape(teuk_ctx *c, const void *d_in, void *d_out, int64_t n, int first, void *d_h, void *d_tape,
+                         void *stream)
+{
+    if (!c) return TEUK_E_STATE;
+    if (c->d.scheme != TEUK_SCHEME_SPLIT) return set_err(c, TEUK_E_INVAL, "teuk_apply_step needs the split scheme");
+    if (!d_in || !d_out || !d_h || !d_tape || d_in == d_out || n < 0 || ((uintptr_t)d_tape & 255))
+        return set_err(c, TEUK_E_INVAL, "need distinct non-NULL device buffers, a 256-byte aligned tape and n >= 0");
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e;
+    if (c->d.precision == TEUK_FP32) {
+        StepParams<float> p = make_params<float>(c, 0);
+        p.uin = (const float2 *)d_in;
+        p.uout = (float2 *)d_out;
+        p.first = first ? 1 : 0;
+        p.nfix = n;
+        p.h_out = (double2 *)d_h;
+        p.tape = (float2 *)d_tape;
+        e = launch_apply_step<float>(p, c->threads, c->smem, st);
+    } else {
+        StepParams<double> p = make_params<double>(c, 0);
+        p.uin = (const double2 *)d_in;
+        p.uout = (double2 *)d_out;
+        p.first = first ? 1 : 0;
+        p.nfix = n;
+        p.h_out = (double2 *)d_h;
+        p.tape = (double2 *)d_tape;
+        e = launch_apply_step<double>(p, c->threads, c->smem, st);
+    }
+    if (e != cudaSuccess) return cuda_err(c, e, "apply step (tape)");
+    return TEUK_OK;
+}
+
+int teuk_adjoint_step_tape(teuk_ctx *c, const void *d_lam_in, void *d_lam_out, const void *d_tape, int64_t n,
+                           int first, const void *d_gseed, void *d_ws, void *stream)
+{
+    if (!c) return TEUK_E_STATE;
+    if (c->d.scheme != TEUK_SCHEME_SPLIT) return set_err(c, TEUK_E_INVAL, "the adjoint needs the split scheme");
+    if (!d_lam_in || !d_lam_out || !d_tape || d_lam_in == d_lam_out || !d_ws || n < 0 ||
+        ((uintptr_t)d_tape & 255))
+        return set_err(c, TEUK_E_INVAL, "need distinct non-NULL device buffers, an aligned tape, a workspace and n >= 0");
+    return adjoint_spin(c, d_lam_in, d_lam_out, nullptr, d_tape, n, first, d_gseed, d_ws, stream);
 }
 
 int teuk_dot(teuk_ctx *c, const void *d_x, const void *d_y, const void *d_z, void *d_ws, void *d_out, void *stream)
@@ -1384,7 +1527,7 @@ int teuk_dot(teuk_ctx *c, const void *d_x, const void *d_y, const void *d_z, voi
     if (!d_x || !d_y || !d_ws || !d_out) return set_err(c, TEUK_E_INVAL, "need non-NULL device buffers");
     cudaStream_t st = (cudaStream_t)stream;
     const size_t n = 2 * (size_t)c->d.Nr * (size_t)c->d.Ntheta;
-    double *part = (double *)d_ws + adjoint_ws_doubles(c) - 2 * 256;
+    double *part = (double *)d_ws + adjoint_small_doubles(c) - 2 * 256;
     cudaError_t e;
     if (c->d.precision == TEUK_FP32)
         e = launch_dot<float>((const float2 *)d_x, (const float2 *)d_y, (const float2 *)d_z, n, part,

@@ -1039,6 +1039,58 @@ __device__ __forceinline__ void lw_coef(const T *f, T S2, T C, T &beta, typename
     if (sg_out) *sg_out = sg;
 }
 
+// beta = c_p b, kap = c_p K and 1/Sigma^2 at step-table entry f, with their
+// derivatives with respect to a (df: the entry's spin derivative).  The
+// values are those lw_coef forms.
+template <typename T> struct LwDa {
+    typedef typename V2<T>::t c2;
+    T beta, dbeta, sg, dsg;
+    c2 kap, dkap;
+};
+template <typename T>
+__device__ __forceinline__ LwDa<T> lw_coef_da(const T *f, const T *df, T S2, T C)
+{
+    typedef typename V2<T>::t c2;
+    LwDa<T> o;
+    const T sig = fma(-f[SF_AD], S2, f[SF_R2]);
+    const T dsig = fma(-df[SF_AD], S2, df[SF_R2]);
+    const T rs = rsq_(sig);
+    o.sg = rs * rs;
+    const T drs = T(-0.5) * rs * o.sg * dsig;
+    o.dsg = -o.sg * o.sg * dsig;
+    o.beta = rs * f[SF_RB];
+    o.dbeta = fma(drs, f[SF_RB], rs * df[SF_RB]);
+    const T t = fma(-f[SF_E3], S2, f[SF_E2]), dt_ = fma(-df[SF_E3], S2, df[SF_E2]);
+    const T X = fma(o.sg, t, fma(rs, f[SF_RCTR], f[SF_CSE]));
+    const T dX = o.dsg * t + o.sg * dt_ + drs * f[SF_RCTR] + rs * df[SF_RCTR] + df[SF_CSE];
+    const T u = fma(f[SF_RCTC], C, f[SF_RCTI]), du = fma(df[SF_RCTC], C, df[SF_RCTI]);
+    const T Y = fma(rs, u, f[SF_CSI]);
+    const T dY = drs * u + rs * du + df[SF_CSI];
+    o.kap = cmk<c2>(o.sg * X, o.sg * Y);
+    o.dkap = cmk<c2>(o.dsg * X + o.sg * dX, o.dsg * Y + o.sg * dY);
+    return o;
+}
+
+// Spin derivatives of one element's implicit-operator coefficients: dW's
+// diagonal ddg and off-diagonals (dqam, dqap) and dc_t (unscaled), from the
+// row constants r, the table entry fr and its derivative dfr (SField,
+// implicit block), and the element's theta values.
+template <typename T>
+__device__ __forceinline__ void imp_da(const ImpRow<T> &r, const T (&fr)[8], const T (&dfr)[8], T s2, T cc, T am,
+                                       T a0, T ap, typename V2<T>::t &ddg, typename V2<T>::t &dct, T &dqam,
+                                       T &dqap)
+{
+    typedef typename V2<T>::t c2;
+    const T sg = imp_sg(r, s2);
+    const T dsg = -sg * sg * fma(-dfr[SF_AD], s2, dfr[SF_R2]);
+    const T dq = fma(dfr[SF_DELTA], sg, r.D * dsg);
+    dqam = dq * am;
+    dqap = dq * ap;
+    ddg = cmk<c2>(fma(dq, a0, -fma(dsg, r.c0r, sg * dfr[SF_C0R])), -fma(dsg, r.c0i, sg * dfr[SF_C0I]));
+    const T ctr = dfr[SF_CTR], cti = fma(dfr[SF_CTC], cc, dfr[SF_CTI]);
+    dct = cmk<c2>(fma(dsg, fr[SF_CTR], sg * ctr), fma(dsg, fma(fr[SF_CTC], cc, fr[SF_CTI]), sg * cti));
+}
+
 template <typename T, bool INTERIOR, bool MAT = false>
 __device__ void lw_segment(const StepParams<T> &p, typename V2<T>::t *sPhi, typename V2<T>::t *sPi,
                            const T *sSt, const T *sTh, int j, int ra, int rb,
@@ -1243,6 +1295,25 @@ __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.comm
 __device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
 constexpr int kWaitLimit = 1 << 22;   // try_wait rounds before a copy is declared lost
 
+// FP64 weighted sum h = sum_j w_j row_j in the order extract_warp uses; lane 0
+// of the calling warp returns it.
+template <typename T>
+__device__ double2 sample_warp(const StepParams<T> &p, const typename V2<T>::t *row)
+{
+    const int lane = threadIdx.x & 31;
+    double sre = 0.0, sim = 0.0;
+    for (int j = lane; j < p.Nth; j += 32) {
+        double w = p.w[j];
+        sre = fma(w, (double)row[j].x, sre);
+        sim = fma(w, (double)row[j].y, sim);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        sre += __shfl_xor_sync(0xffffffffu, sre, o);
+        sim += __shfl_xor_sync(0xffffffffu, sim, o);
+    }
+    return make_double2(sre, sim);
+}
+
 // FP64 extraction of one row held anywhere (shared or global); one warp.
 template <typename T>
 __device__ void extract_warp(const StepParams<T> &p, const typename V2<T>::t *row, long long step)
@@ -1311,6 +1382,16 @@ __device__ __forceinline__ void split_tile(const StepParams<T> &p, int tile, int
 
     const bool src = !p.imp_only && p.patch_np > 0 && i0 + TR + KS - 1 >= p.patch_p0 &&
                      g0 <= p.patch_p0 + p.patch_np;
+    if constexpr (KS == 1) {
+        // forward tape: the input's extraction row, from the input buffer
+        if (p.tape && p.i_ext >= i0 && p.i_ext < i0 + TR && p.i_ext < Nr) {
+            c2 *x = p.tape + tape_x_off(Nr, N);
+            for (int j = tid; j < N; j += NT) {
+                x[j] = p.uin[(size_t)p.i_ext * N + j];
+                x[N + j] = p.uin[((size_t)Nr + p.i_ext) * N + j];
+            }
+        }
+    }
     if (tid == 0) {
         long long n = p.nfix >= 0 ? p.nfix : *((volatile long long *)&p.ctl->step);
         s_n = n;
@@ -1432,15 +1513,23 @@ __device__ __forceinline__ void split_tile(const StepParams<T> &p, int tile, int
             int gi = g0 + lr;
             bool active = in_tile && gi >= 1 && gi <= Nr - 2;
             int lrc = in_tile ? lr : lo;
+            // forward tape: the first stage value of each output row
+            c2 *t1f = nullptr, *t1g = nullptr;
+            if constexpr (KS == 1) {
+                if (p.tape && in_tile && lr >= 1 && lr <= TR && gi < Nr) {
+                    t1f = p.tape + (size_t)gi * N;
+                    t1g = p.tape + ((size_t)Nr + gi) * N;
+                }
+            }
             if constexpr (sizeof(T) == 8) {
                 if (use_mat) {
                     implicit_row_fwd<T, S, true>(Ki, sPhi + lrc * P, sPi + lrc * P, sPiv + lrc * P, nullptr, nullptr,
-                                                 N, active, in_tile, g, G, vec, s_plan[lrc], &p.mat, gi);
+                                                 N, active, in_tile, g, G, vec, s_plan[lrc], &p.mat, gi, t1f, t1g);
                     continue;
                 }
             }
             implicit_row_fwd<T, S>(Ki, sPhi + lrc * P, sPi + lrc * P, sPiv + lrc * P, sSt + 2 * lrc * NSF, sTh, N,
-                                   active, in_tile, g, G, vec, s_plan[lrc]);
+                                   active, in_tile, g, G, vec, s_plan[lrc], nullptr, 0, t1f, t1g);
         }
     };
     // physical sample u = C_{dt/2} s of the extraction row (tile row lx) in
@@ -1453,10 +1542,17 @@ __device__ __forceinline__ void split_tile(const StepParams<T> &p, int tile, int
             implicit_row_fwd<T, S>(p.half, rf, rg, p.half.piv + (size_t)p.i_ext * N, sSt + 2 * lx * NSF, sTh, N,
                                      active, mine, tid % G, G, vec, p.half.plan[p.i_ext]);
             __syncwarp();
-            extract_warp<T>(p, rf, slot);
+            if (p.nfix >= 0) {
+                // a step applied to caller buffers: the sample alone, to h_out
+                const double2 h = sample_warp<T>(p, rf);
+                if (tid == 0) *p.h_out = h;
+            } else {
+                extract_warp<T>(p, rf, slot);
+            }
         }
     };
-    const bool ext = !p.imp_only && p.nfix < 0 && p.i_ext >= i0 && p.i_ext < i0 + TR && p.i_ext < Nr;
+    const bool ext = !p.imp_only && (p.nfix < 0 || p.h_out != nullptr) && p.i_ext >= i0 && p.i_ext < i0 + TR &&
+                     p.i_ext < Nr;
     // ---- B and C, once per time step of the launch.  Step k (from 0) runs
     // the implicit stage on tile rows k .. R-1-k and the Lax-Wendroff stages
     // on rows k+1 .. R-2-k, so the output rows KS .. KS+TR-1 are exact after
@@ -1484,6 +1580,22 @@ __device__ __forceinline__ void split_tile(const StepParams<T> &p, int tile, int
                 return;
             }
             if (p.imp_only) break;
+            if constexpr (KS == 1) {
+                if (p.tape) {
+                    // forward tape: the implicit stage's output U2 of the output
+                    // rows, before the Lax-Wendroff stages overwrite them
+                    c2 *u2 = p.tape + tape_u2_off(Nr, N);
+                    for (int idx = tid; idx < TR * N; idx += NT) {
+                        const int lr = 1 + idx / N, j = idx - (lr - 1) * N;
+                        const int gi = g0 + lr;
+                        if (gi < Nr) {
+                            u2[(size_t)gi * N + j] = sPhi[lr * P + j];
+                            u2[((size_t)Nr + gi) * N + j] = sPi[lr * P + j];
+                        }
+                    }
+                    __syncthreads();
+                }
+            }
         } else {
             __syncthreads();
         }
@@ -1562,25 +1674,6 @@ __device__ __forceinline__ void split_tile(const StepParams<T> &p, int tile, int
 __device__ __forceinline__ void mbar_arrive(unsigned long long *m)
 {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(m)) : "memory");
-}
-
-// FP64 weighted sum h = sum_j w_j row_j in the order extract_warp uses; lane 0
-// of the calling warp returns it.
-template <typename T>
-__device__ double2 sample_warp(const StepParams<T> &p, const typename V2<T>::t *row)
-{
-    const int lane = threadIdx.x & 31;
-    double sre = 0.0, sim = 0.0;
-    for (int j = lane; j < p.Nth; j += 32) {
-        double w = p.w[j];
-        sre = fma(w, (double)row[j].x, sre);
-        sim = fma(w, (double)row[j].y, sim);
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-        sre += __shfl_xor_sync(0xffffffffu, sre, o);
-        sim += __shfl_xor_sync(0xffffffffu, sim, o);
-    }
-    return make_double2(sre, sim);
 }
 
 }  // namespace

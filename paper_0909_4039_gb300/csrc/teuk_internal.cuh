@@ -96,15 +96,60 @@ template <typename T> struct ImpConst {
 
 // Materialised coefficients of the FP64 path: the implicit step of length
 // dt ([Nr][Nth] per element, as imp_elem forms them) and the Lax-Wendroff
-// stages ([2Nr-1][Nth][4]: c_p b, c_p K, 0 per position and theta).  The FP64
-// pipe is the bound of the FP64 step, so what the step can read instead of
-// recompute it reads.
+// stages ([2Nr-1][Nth][4]: c_p b, c_p K, 1/Sigma^2 per position and theta).
+// The FP64 pipe is the bound of the FP64 step, so what the step can read
+// instead of recompute it reads.
 template <typename T> struct MatPlanes {
     typedef typename V2<T>::t c2;
     const c2 *fk, *dg, *ct;
     const T *sub, *qam, *qap;
     const T *lw;
 };
+
+// The coefficient planes of the adjoint step with the spin derivative, in
+// its workspace (either precision): the full step's MatPlanes, the spin
+// derivatives of the Lax-Wendroff coefficients (dlw, [2Nr-1][Nth][4]:
+// d(c_p b), d(c_p K), d(1/Sigma^2)) and of the implicit operator (dimp,
+// [Nr][Nth][8]: dW's diagonal (2), dc_t (2), dW's off-diagonals, 0, 0).
+template <typename T> struct AdjPlanes {
+    MatPlanes<T> m;
+    const T *dlw, *dimp;
+};
+
+// One applied step's tape record, in elements of the state's complex type:
+// the first stage value U1 and the implicit stage's output U2 = C_h s_n of
+// every row ([2][Nr][Nth] each), then the input's extraction row ([2][Nth]).
+__host__ __device__ inline size_t tape_u2_off(long long Nr, long long Nth) { return 2 * (size_t)Nr * (size_t)Nth; }
+__host__ __device__ inline size_t tape_x_off(long long Nr, long long Nth) { return 4 * (size_t)Nr * (size_t)Nth; }
+__host__ __device__ inline size_t tape_elems(long long Nr, long long Nth) { return 4 * (size_t)Nr * (size_t)Nth + 2 * (size_t)Nth; }
+
+// Where the generator of k_mat_coef writes (dlw, dimp NULL: no derivatives).
+template <typename T> struct MatOut {
+    typedef typename V2<T>::t c2;
+    c2 *fk, *dg, *ct;
+    T *sub, *qam, *qap, *lw, *dlw, *dimp;
+};
+
+// Byte layout of those planes from offset 0 of their region: plane offsets
+// (fk, dg, ct, sub, qam, qap, lw, dlw, dimp) and the total.
+struct AdjPlaneLayout {
+    size_t off[9];
+    size_t total;
+};
+inline AdjPlaneLayout adj_plane_layout(long long Nr, long long Nth, size_t tsize)
+{
+    const size_t pl = (size_t)Nr * (size_t)Nth, pos = (size_t)(2 * Nr - 1) * (size_t)Nth;
+    const size_t sz[9] = {2 * pl * tsize, 2 * pl * tsize, 2 * pl * tsize, pl * tsize, pl * tsize, pl * tsize,
+                          4 * pos * tsize, 4 * pos * tsize, 8 * pl * tsize};
+    AdjPlaneLayout L;
+    size_t o = 0;
+    for (int k = 0; k < 9; ++k) {
+        L.off[k] = o;
+        o = (o + sz[k] + 255) & ~(size_t)255;
+    }
+    L.total = o;
+    return L;
+}
 
 // Everything a step kernel needs, passed by value.
 template <typename T> struct StepParams {
@@ -139,8 +184,14 @@ template <typename T> struct StepParams {
     double2 *wave;           // [cap][1 + Nth]
     Ctl *ctl;
     // Applying one step to caller buffers (nfix >= 0): the step index is
-    // nfix, the step counter is not touched and nothing is extracted.
+    // nfix, the step counter is not touched and the ring buffer is not
+    // written; with h_out set, the sample E C_{dt/2} of the output state goes
+    // to *h_out (FP64) instead.
     long long nfix;
+    double2 *h_out;
+    // Forward tape of an applied step (nfix >= 0, one step per launch):
+    // the record tape_* describes, or NULL.
+    c2 *tape;
     // Source-parameter derivatives (adjoint step): the unit-amplitude patch
     // [np][2][Nth] (same rows as patch), the amplitude, the r* grid and the
     // orbit's r0*, 1/sigma_r^2, d r0*/d r0 and m dOmega/d r0.
@@ -268,9 +319,14 @@ size_t adjoint_smem_bytes(int tile_rows, int Nth);
 // term).
 template <typename T>
 size_t adjoint_spin_smem_bytes(int tile_rows, int Nth);
+// A: the context's adjoint planes (read for the full steps; a first step,
+// of length dt/2, forms its coefficients from the tables).  tape: the
+// forward step's record (tape_* above) whose stage values replace their
+// recomputation from sin (NULL: recompute).
 template <typename T>
 cudaError_t launch_adjoint_spin(const StepParams<T> &p, int tile_rows, const typename V2<T>::t *sin,
-                                const double2 *gseed, double *part, double *acc, cudaStream_t st);
+                                const typename V2<T>::t *tape, const double2 *gseed, const AdjPlanes<T> &A,
+                                double *part, double *acc, cudaStream_t st);
 template <typename T>
 int adjoint_grid(int Nr, int tile_rows);
 template <typename T>
@@ -330,6 +386,10 @@ cudaError_t launch_split_pipe(const StepParams<T> &p, int threads, int grid, siz
 // Materialised coefficients of the FP64 path into p.mat (no-op unless p.mat_on).
 template <typename T>
 cudaError_t launch_mat_coef(const StepParams<T> &p, cudaStream_t st);
+// The same planes, plus the spin derivatives where o.dlw / o.dimp are set,
+// into o (either precision).
+template <typename T>
+cudaError_t launch_mat_coef_to(const StepParams<T> &p, const MatOut<T> &o, cudaStream_t st);
 // Largest tile height of the split kernels (rows of the per-tile plan copy).
 constexpr int kMaxTileRows = 254;
 // Batched split step: one CTA of 256 threads per entry of the tile list

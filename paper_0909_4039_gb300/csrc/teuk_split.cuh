@@ -355,13 +355,13 @@ __global__ void __launch_bounds__(NTH, (NTH == 256 && sizeof(T) == 4 && S <= 4) 
     if (tid == 0) bulk_wait_read();   // the last stores have read their rows before the CTA exits
 }
 
-// Materialised coefficients of the FP64 path (MatPlanes): thread (e, j) of
-// the grid covers step-table position e (node 2i or half node 2i+1) and
-// theta j, forming exactly what the kernels would form in place (imp_row,
-// imp_sg, imp_elem for the full step at nodes; lw_coef at every position).
+// Materialised coefficients (MatPlanes): thread (e, j) of the grid covers
+// step-table position e (node 2i or half node 2i+1) and theta j, forming
+// exactly what the kernels would form in place (imp_row, imp_sg, imp_elem
+// for the full step at nodes; lw_coef at every position), and where asked
+// their spin derivatives (lw_coef_da, imp_da) for the adjoint.
 template <typename T>
-__global__ void __launch_bounds__(256) k_mat_coef(const StepParams<T> p, typename V2<T>::t *fk, typename V2<T>::t *dg,
-                                                  typename V2<T>::t *ct, T *sub, T *qam, T *qap, T *lw)
+__global__ void __launch_bounds__(256) k_mat_coef(const StepParams<T> p, const MatOut<T> o)
 {
     typedef typename V2<T>::t c2;
     const int N = p.Nth, Nr = p.Nr;
@@ -370,38 +370,64 @@ __global__ void __launch_bounds__(256) k_mat_coef(const StepParams<T> p, typenam
     const int e = (int)(idx / N), j = (int)(idx - (long long)e * N);
     const T *f = p.stab + (size_t)e * NSF;
     const T S2 = p.thtab[TF_S2 * N + j], C = p.thtab[TF_C * N + j];
-    T beta;
+    T beta, sg;
     c2 kap;
-    lw_coef<T>(f, S2, C, beta, kap);
-    T *o = lw + ((size_t)e * N + j) * 4;
-    o[0] = beta;
-    o[1] = kap.x;
-    o[2] = kap.y;
-    o[3] = T(0);
+    lw_coef<T>(f, S2, C, beta, kap, &sg);
+    T *lo = o.lw + ((size_t)e * N + j) * 4;
+    lo[0] = beta;
+    lo[1] = kap.x;
+    lo[2] = kap.y;
+    lo[3] = sg;
+    if (o.dlw) {
+        const LwDa<T> d = lw_coef_da<T>(f, p.dstab + (size_t)e * NSF, S2, C);
+        T *dl = o.dlw + ((size_t)e * N + j) * 4;
+        dl[0] = d.dbeta;
+        dl[1] = d.dkap.x;
+        dl[2] = d.dkap.y;
+        dl[3] = d.dsg;
+    }
     if (e & 1) return;
     const int i = e >> 1;
     const size_t q = (size_t)i * N + j;
     const c2 zero = cmk<c2>(T(0), T(0));
     if (i < 1 || i > Nr - 2) {
         // boundary rows: the step treats them as inactive and reads nothing here
-        fk[q] = zero;
-        dg[q] = zero;
-        ct[q] = zero;
-        sub[q] = qam[q] = qap[q] = T(0);
+        o.fk[q] = zero;
+        o.dg[q] = zero;
+        o.ct[q] = zero;
+        o.sub[q] = o.qam[q] = o.qap[q] = T(0);
+        if (o.dimp)
+            for (int k = 0; k < 8; ++k) o.dimp[q * 8 + k] = T(0);
         return;
     }
     const ImpRow<T> r = imp_row(p.full, f);
-    const T sg = imp_sg(r, S2);
+    const T am = p.thtab[TF_AM * N + j], a0 = p.thtab[TF_A0 * N + j], ap = p.thtab[TF_AP * N + j];
     c2 vct, vdg, vfk;
     T vqam, vqap, vsub;
-    imp_elem(p.full, r, sg, C, p.thtab[TF_AM * N + j], p.thtab[TF_A0 * N + j], p.thtab[TF_AP * N + j], p.full.piv[q],
-             vct, vdg, vqam, vqap, vsub, vfk);
-    fk[q] = vfk;
-    dg[q] = vdg;
-    ct[q] = vct;
-    sub[q] = vsub;
-    qam[q] = vqam;
-    qap[q] = vqap;
+    imp_elem(p.full, r, imp_sg(r, S2), C, am, a0, ap, p.full.piv[q], vct, vdg, vqam, vqap, vsub, vfk);
+    o.fk[q] = vfk;
+    o.dg[q] = vdg;
+    o.ct[q] = vct;
+    o.sub[q] = vsub;
+    o.qam[q] = vqam;
+    o.qap[q] = vqap;
+    if (o.dimp) {
+        T fr[8], dfr[8];
+        vload<8>(fr, f);
+        vload<8>(dfr, p.dstab + (size_t)e * NSF);
+        c2 ddg, dct;
+        T dqam, dqap;
+        imp_da<T>(r, fr, dfr, S2, C, am, a0, ap, ddg, dct, dqam, dqap);
+        T *dq = o.dimp + q * 8;
+        dq[0] = ddg.x;
+        dq[1] = ddg.y;
+        dq[2] = dct.x;
+        dq[3] = dct.y;
+        dq[4] = dqam;
+        dq[5] = dqap;
+        dq[6] = T(0);
+        dq[7] = T(0);
+    }
 }
 
 }  // namespace
@@ -456,15 +482,28 @@ cudaError_t launch_split_pipe(const StepParams<T> &p, int threads, int grid, siz
 }
 
 template <typename T>
+cudaError_t launch_mat_coef_to(const StepParams<T> &p, const MatOut<T> &o, cudaStream_t st)
+{
+    const long long n = (long long)(2 * p.Nr - 1) * p.Nth;
+    k_mat_coef<T><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(p, o);
+    return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_mat_coef(const StepParams<T> &p, cudaStream_t st)
 {
     typedef typename V2<T>::t c2;
     if (!p.mat_on) return cudaSuccess;
-    const long long n = (long long)(2 * p.Nr - 1) * p.Nth;
-    k_mat_coef<T><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(p, (c2 *)p.mat.fk, (c2 *)p.mat.dg, (c2 *)p.mat.ct,
-                                                              (T *)p.mat.sub, (T *)p.mat.qam, (T *)p.mat.qap,
-                                                              (T *)p.mat.lw);
-    return cudaGetLastError();
+    MatOut<T> o;
+    o.fk = (c2 *)p.mat.fk;
+    o.dg = (c2 *)p.mat.dg;
+    o.ct = (c2 *)p.mat.ct;
+    o.sub = (T *)p.mat.sub;
+    o.qam = (T *)p.mat.qam;
+    o.qap = (T *)p.mat.qap;
+    o.lw = (T *)p.mat.lw;
+    o.dlw = o.dimp = nullptr;
+    return launch_mat_coef_to<T>(p, o, st);
 }
 
 template <typename T>

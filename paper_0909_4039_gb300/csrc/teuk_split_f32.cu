@@ -15,6 +15,7 @@ template int split_blocks_per_sm<float>(int, int, size_t);
 template size_t split_smem_bytes<float>(int, int);
 template cudaError_t launch_split_step<float>(const StepParams<float> &, int, size_t, cudaStream_t);
 template cudaError_t launch_mat_coef<float>(const StepParams<float> &, cudaStream_t);
+template cudaError_t launch_mat_coef_to<float>(const StepParams<float> &, const MatOut<float> &, cudaStream_t);
 template size_t pipe_smem_bytes<float>(int, int);
 template int pipe_blocks_per_sm<float>(int, int, size_t);
 template cudaError_t launch_split_pipe<float>(const StepParams<float> &, int, int, size_t, cudaStream_t);

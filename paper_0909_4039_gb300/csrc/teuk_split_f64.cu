@@ -15,6 +15,7 @@ template int split_blocks_per_sm<double>(int, int, size_t);
 template size_t split_smem_bytes<double>(int, int);
 template cudaError_t launch_split_step<double>(const StepParams<double> &, int, size_t, cudaStream_t);
 template cudaError_t launch_mat_coef<double>(const StepParams<double> &, cudaStream_t);
+template cudaError_t launch_mat_coef_to<double>(const StepParams<double> &, const MatOut<double> &, cudaStream_t);
 template size_t pipe_smem_bytes<double>(int, int);
 template int pipe_blocks_per_sm<double>(int, int, size_t);
 template cudaError_t launch_split_pipe<double>(const StepParams<double> &, int, int, size_t, cudaStream_t);

@@ -44,7 +44,8 @@ EXPORTED = [
     "teuk_batch_autotune", "teuk_batch_last_error", "teuk_batch_destroy",
     "teuk_apply_step", "teuk_apply_sample", "teuk_adjoint_workspace_bytes", "teuk_adjoint_step", "teuk_dot",
     "teuk_set_tiling_steps", "teuk_state_level", "teuk_set_wait_limit", "teuk_fma_rate",
-    "teuk_set_pipelined", "teuk_adjoint_step_spin",
+    "teuk_set_pipelined", "teuk_adjoint_step_spin", "teuk_apply_step_sample",
+    "teuk_adjoint_prepare", "teuk_tape_bytes", "teuk_apply_step_tape", "teuk_adjoint_step_tape",
 ]
 
 
@@ -131,12 +132,18 @@ def lib(load_only: bool = False):
         getattr(L, name).restype = ctypes.c_int
     L.teuk_apply_step.argtypes = [vp, vp, vp, i64, ctypes.c_int, vp]
     L.teuk_apply_sample.argtypes = [vp, vp, ctypes.c_int, vp, vp]
+    L.teuk_apply_step_sample.argtypes = [vp, vp, vp, i64, ctypes.c_int, vp, vp]
+    L.teuk_adjoint_prepare.argtypes = [vp, vp, vp]
+    L.teuk_tape_bytes.argtypes = [vp, sz]
+    L.teuk_apply_step_tape.argtypes = [vp, vp, vp, i64, ctypes.c_int, vp, vp, vp]
+    L.teuk_adjoint_step_tape.argtypes = [vp, vp, vp, vp, i64, ctypes.c_int, vp, vp, vp]
     L.teuk_adjoint_workspace_bytes.argtypes = [vp, sz]
     L.teuk_adjoint_step.argtypes = [vp, vp, vp, i64, ctypes.c_int, vp, vp, vp]
     L.teuk_adjoint_step_spin.argtypes = [vp, vp, vp, vp, i64, ctypes.c_int, vp, vp, vp]
     L.teuk_dot.argtypes = [vp, vp, vp, vp, vp, vp, vp]
     for name in ("teuk_apply_step", "teuk_apply_sample", "teuk_adjoint_workspace_bytes", "teuk_adjoint_step",
-                 "teuk_dot", "teuk_adjoint_step_spin"):
+                 "teuk_dot", "teuk_adjoint_step_spin", "teuk_apply_step_sample", "teuk_adjoint_prepare",
+                 "teuk_tape_bytes", "teuk_apply_step_tape", "teuk_adjoint_step_tape"):
         getattr(L, name).restype = ctypes.c_int
     pvp = ctypes.POINTER(vp)
     ip = ctypes.POINTER(ctypes.c_int)

@@ -61,6 +61,27 @@ def test_one_step_dot_product(Nr, Nth, m, first):
     op.close()
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("Nr,Nth,first", [(90, 16, False), (90, 16, True), (70, 33, False), (300, 64, False)])
+def test_step_with_sample_equals_step_then_sample(Nr, Nth, first, precision):
+    """teuk_apply_step_sample gives, bit for bit, the state of
+    teuk_apply_step and the sample teuk_apply_sample takes of it."""
+    import torch
+    from paper_0909_4039_gb300 import adjoint as A
+    op = A.Operator(_w(Nr, Nth, amp=0.4 + 0.2j), A.Params(0.4 + 0.2j, 7.0, 0.7), precision)
+    with torch.cuda.stream(op.st.stream):
+        x = _rand(op.shape, 4, op.st.device, op.ctype, zero_boundary=True)
+        a, b = op.empty(), op.empty()
+        h = torch.zeros(2, dtype=torch.complex128, device=op.st.device)
+        op.step(x, a, 7, first)
+        op.sample(a, False, h.data_ptr())
+        op.step_sample(x, b, 7, first, h.data_ptr() + 16)
+        op.st.synchronize()
+    assert torch.equal(a, b)
+    assert h[0].item() == h[1].item() and h[0].item() != 0
+    op.close()
+
+
 def test_sample_dot_product():
     """<g, E C_{dt/2} x> = <C_{dt/2}^H E^H g, x>: the adjoint step with a
     zero incoming adjoint returns the sample's adjoint."""
@@ -241,11 +262,11 @@ def test_one_step_spin_term_against_step_differences(first, m, Nth):
             opm.sample(s, False, hm.data_ptr())
             op.st.synchronize()
             fd += (np.conj(g.item()) * (hp.item() - hm.item())).real / (2 * eps)
-        op.ws.zero_()
+        op.ws[:8].zero_()
         out_s = op.empty()
         op.adjoint_spin(lam, out_s, s, n, first, g.data_ptr())
         acc_s = op.ws[:8].clone()
-        op.ws.zero_()
+        op.ws[:8].zero_()
         out_r = op.empty()
         op.adjoint(lam, out_r, n, first, g.data_ptr())
         acc_r = op.ws[:8].clone()
@@ -256,6 +277,75 @@ def test_one_step_spin_term_against_step_differences(first, m, Nth):
     assert np.allclose(acc_s[:4].cpu().numpy(), acc_r[:4].cpu().numpy(), rtol=1e-12, atol=1e-300)
     for o in (op, opp, opm):
         o.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("first,m,Nth", [(False, 2, 16), (True, 2, 16), (False, 3, 33), (False, 1, 64)])
+def test_tape_step_and_adjoint_equal_recompute(first, m, Nth, precision):
+    """teuk_apply_step_tape gives the state and sample of
+    teuk_apply_step_sample bit for bit, records the input's extraction row,
+    and teuk_adjoint_step_tape reading that record gives, bit for bit, the
+    lam_n and accumulators teuk_adjoint_step_spin gets by recomputing the
+    stage values from s_n."""
+    import torch
+    from paper_0909_4039_gb300 import adjoint as A
+    w = _w(150, Nth, a=0.6, m=m, sig_r=0.8)
+    prm = A.Params(0.8 - 0.5j, 6.0, 0.6)
+    n = 0 if first else 17
+    op = A.Operator(w, prm, precision)
+    with torch.cuda.stream(op.st.stream):
+        s = _rand(op.shape, 31, op.st.device, op.ctype, zero_boundary=True)
+        lam = _rand(op.shape, 32, op.st.device, op.ctype)
+        g = torch.tensor([0.7 + 1.3j], dtype=torch.complex128, device=op.st.device)
+        a, b = op.empty(), op.empty()
+        h = torch.zeros(2, dtype=torch.complex128, device=op.st.device)
+        tape = torch.full((op.tape_bytes // 8,), float("nan"), dtype=torch.float64, device=op.st.device)
+        op.step_sample(s, a, n, first, h.data_ptr())
+        op.step_tape(s, b, n, first, h.data_ptr() + 16, tape.data_ptr())
+        op.ws[:8].zero_()
+        out_s = op.empty()
+        op.adjoint_spin(lam, out_s, s, n, first, g.data_ptr())
+        acc_s = op.ws[:8].clone()
+        op.ws[:8].zero_()
+        out_t = op.empty()
+        op.adjoint_tape(lam, out_t, tape.data_ptr(), n, first, g.data_ptr())
+        acc_t = op.ws[:8].clone()
+        op.st.synchronize()
+    assert torch.equal(a, b) and h[0].item() == h[1].item()
+    # the record: U1 and U2 of every row (finite, written), then the input's extraction row
+    rec = tape.view(op.ctype)
+    pl = 2 * w.Nr * w.Ntheta
+    assert torch.isfinite(torch.view_as_real(rec[:2 * pl])).all()
+    ie = int(round((w.rs_ext - w.rs_min) / ((w.rs_max - w.rs_min) / (w.Nr - 1))))   # the node nearest r*_ext
+    xrow = rec[2 * pl:2 * pl + 2 * w.Ntheta].reshape(2, w.Ntheta)
+    assert torch.equal(xrow, s[:, ie, :])
+    assert torch.equal(out_s, out_t)
+    assert torch.equal(acc_s, acc_t)
+    op.close()
+
+
+def test_taped_gradient_equals_checkpointed_gradient():
+    """The whole gradient with the forward tape (store-all, no recompute)
+    equals the sqrt(N)-checkpointed gradient, and the source-only sweep
+    (no state needed) equals the source parts of the full one."""
+    import torch
+    from paper_0909_4039_gb300 import adjoint as A
+    w = _w(200, 16, a=0.6, m=2, sig_r=0.8)
+    N = 120
+    dt = 0.5 * (w.rs_max - w.rs_min) / (w.Nr - 1)
+    prm = A.Params(0.7 - 0.2j, 7.0, 0.6)
+    target = 1e-3 * inputs.adjoint_target(N + 1, dt, seed=3)
+    h = A.waveform(w, prm, N).cpu().numpy()
+    gh = torch.as_tensor(2.0 * dt * (h - target))
+    r_ck = A.gradients(w, prm, N, gh, every=11)
+    r_tp = A.gradients(w, prm, N, gh, tape=True)
+    r_src = A.gradients(w, prm, N, gh, wrt_a=False, every=11)
+    for k in ("dA_re", "dA_im", "dr0", "da"):
+        assert r_ck[k] == r_tp[k], (k, r_ck[k], r_tp[k])
+    for k in ("dA_re", "dA_im", "dr0"):
+        assert abs(r_src[k] - r_ck[k]) <= 1e-11 * abs(r_ck[k]), (k, r_src[k], r_ck[k])
+    assert torch.equal(r_ck["du0"], r_tp["du0"])
+    assert torch.equal(r_ck["h"], r_tp["h"])
 
 
 def test_analytic_spin_gradient_matches_step_differences_sweep():
