@@ -523,7 +523,9 @@ __global__ void __launch_bounds__(256, 1) k_adjoint_spin(const StepParams<T> p, 
     c2 *vG = vF + plane;
     c2 *u1F = vG + plane;
     c2 *u1G = u1F + plane;
-    T *sSt = (T *)(u1G + plane);
+    c2 *fmF = u1G + plane;   // forward midpoints (Lax-Wendroff stage 1 of U2)
+    c2 *fmG = fmF + plane;
+    T *sSt = (T *)(fmG + plane);
     T *sDSt = sSt + (2 * R - 1) * NSF;
     T *sTh = sDSt + (2 * R - 1) * NSF;
 
@@ -624,22 +626,6 @@ __global__ void __launch_bounds__(256, 1) k_adjoint_spin(const StepParams<T> p, 
         }
     };
 
-    // forward midpoint k (between tile rows k, k+1) from U2, as the step forms it
-    auto fwd_mid = [&](int k, int j, const LwDa<T> &h, c2 &mf, c2 &mg) {
-        const c2 fa = vF[k * P + j], fb = vF[(k + 1) * P + j], ga = vG[k * P + j], gb = vG[(k + 1) * P + j];
-        const c2 df = csub(fb, fa);
-        mf = caxpy(-h.beta, df, cscale<c2>(T(0.5), cadd(fa, fb)));
-        c2 t = caxpy(h.beta, csub(gb, ga), cscale<c2>(T(0.5), cadd(ga, gb)));
-        const int gl = i0 - 1 + k;
-        if (src && gl >= p.patch_p0 && gl < p.patch_p0 + p.patch_np) {
-            c2 Sv, dS;
-            src_da<T>(sSt + (2 * k + 1) * NSF, sDSt + (2 * k + 1) * NSF, h.sg, h.dsg, sTh[TF_GTH * N + j],
-                      sTh[TF_GA2 * N + j], sTh[TF_DGA2 * N + j], sph1, mdt1, Sv, dS);
-            t = cadd(t, Sv);
-        }
-        mg = cfma(h.kap, df, t);
-    };
-
     // ---- adjoints of the midpoints k = 0 .. R-2, and their spin terms
     for (int idx = tid; idx < (R - 1) * N; idx += NT) {
         const int k = idx / N, j = idx - k * N;
@@ -659,7 +645,18 @@ __global__ void __launch_bounds__(256, 1) k_adjoint_spin(const StepParams<T> p, 
                 wF = cadd(wF, csub(cscale<c2>(nd.beta, lf), cmul(conj_c(nd.kap), lg)));
                 wG = csub(wG, cscale<c2>(nd.beta, lg));
             }
-            // sources and spin terms of this midpoint (owned by the tile of its lower node)
+            // the forward midpoint from U2, as the step forms it (stored for
+            // the node stage's spin terms), and this midpoint's spin term
+            // (owned by the tile of its lower node)
+            const LwDa<T> h = lwc(2 * k + 1, j, S2, Cc);
+            const c2 fa = vF[k * P + j], fb = vF[(k + 1) * P + j], ga = vG[k * P + j], gb = vG[(k + 1) * P + j];
+            const c2 Df = csub(fb, fa), Dg = csub(gb, ga);
+            c2 Sv = zero, dS = zero;
+            if (src && gl >= p.patch_p0 && gl < p.patch_p0 + p.patch_np)
+                src_da<T>(sSt + (2 * k + 1) * NSF, sDSt + (2 * k + 1) * NSF, h.sg, h.dsg, sTh[TF_GTH * N + j],
+                          sTh[TF_GA2 * N + j], sTh[TF_DGA2 * N + j], sph1, mdt1, Sv, dS);
+            fmF[idx] = caxpy(-h.beta, Df, cscale<c2>(T(0.5), cadd(fa, fb)));
+            fmG[idx] = cfma(h.kap, Df, cadd(caxpy(h.beta, Dg, cscale<c2>(T(0.5), cadd(ga, gb))), Sv));
             if (k >= 1 && k <= TR) {
                 if (srcu) {
                     const int pr = gl - p.unit_p0;
@@ -667,18 +664,9 @@ __global__ void __launch_bounds__(256, 1) k_adjoint_spin(const StepParams<T> p, 
                         source_grad<T>(p, wG, (double)hdtT, p.patchu[((size_t)pr * 2 + 1) * N + j], ph1,
                                        p.rs_min64 + ((double)gl + 0.5) * p.drs64, t1, cA, cr);
                 }
-                const LwDa<T> h = lwc(2 * k + 1, j, S2, Cc);
-                const c2 fa = vF[k * P + j], fb = vF[(k + 1) * P + j], ga = vG[k * P + j], gb = vG[(k + 1) * P + j];
-                const c2 Df = csub(fb, fa), Dg = csub(gb, ga);
                 // d(Phi*) = -dbeta Df,  d(Pi*) = dbeta Dg + dkap Df + dS
                 const c2 dmf = cscale<c2>(-h.dbeta, Df);
-                c2 dmg = cfma(h.dkap, Df, cscale<c2>(h.dbeta, Dg));
-                if (src && gl >= p.patch_p0 && gl < p.patch_p0 + p.patch_np) {
-                    c2 Sv, dS;
-                    src_da<T>(sSt + (2 * k + 1) * NSF, sDSt + (2 * k + 1) * NSF, h.sg, h.dsg, sTh[TF_GTH * N + j],
-                              sTh[TF_GA2 * N + j], sTh[TF_DGA2 * N + j], sph1, mdt1, Sv, dS);
-                    dmg = cadd(dmg, dS);
-                }
+                const c2 dmg = cadd(cfma(h.dkap, Df, cscale<c2>(h.dbeta, Dg)), dS);
                 spin += (double)wF.x * (double)dmf.x + (double)wF.y * (double)dmf.y + (double)wG.x * (double)dmg.x +
                         (double)wG.y * (double)dmg.y;
             }
@@ -720,10 +708,8 @@ __global__ void __launch_bounds__(256, 1) k_adjoint_spin(const StepParams<T> p, 
             // spin terms of the node stage: d(Phi') = -dbeta dMf,
             // d(Pi') = dbeta dMg + dkap dMf + dS, dM the forward midpoint difference
             const LwDa<T> nd = lwc(2 * lr, j, S2, Cc);
-            c2 mfu, mgu, mfd, mgd;
-            fwd_mid(lr, j, hu, mfu, mgu);
-            fwd_mid(lr - 1, j, hd, mfd, mgd);
-            const c2 dMf = csub(mfu, mfd), dMg = csub(mgu, mgd);
+            const c2 dMf = csub(fmF[lr * P + j], fmF[(lr - 1) * P + j]);
+            const c2 dMg = csub(fmG[lr * P + j], fmG[(lr - 1) * P + j]);
             const c2 dnf = cscale<c2>(-nd.dbeta, dMf);
             c2 dng = cfma(nd.dkap, dMf, cscale<c2>(nd.dbeta, dMg));
             if (src && gi >= p.patch_p0 && gi < p.patch_p0 + p.patch_np) {
@@ -960,7 +946,7 @@ template <typename T>
 size_t adjoint_spin_smem_bytes(int tile_rows, int Nth)
 {
     const size_t R = (size_t)tile_rows + 2;
-    return 8 * R * Nth * sizeof(typename V2<T>::t) + (2 * (2 * R - 1) * NSF + (size_t)NTF * Nth) * sizeof(T);
+    return 10 * R * Nth * sizeof(typename V2<T>::t) + (2 * (2 * R - 1) * NSF + (size_t)NTF * Nth) * sizeof(T);
 }
 
 template <typename T, bool MAT>
