@@ -1606,15 +1606,19 @@ size_t batch_tile_smem(int prec, int tr, int N, int ks)
 }
 
 // Default tile height: the largest whole number of implicit passes (tile
-// rows plus halos) whose tile leaves room for two CTAs per SM.
+// rows plus halos) whose tile leaves room for as many CTAs per SM as the
+// kernel's registers allow: two for FP32 rows of up to 128 theta points,
+// one otherwise (wider segments and FP64 take over 128 registers a thread).
 int batch_default_tr(const teuk_ctx *c, int ks)
 {
     const int N = (int)c->d.Ntheta, rpp = batch_rpp(N);
+    const size_t budget =
+        (c->d.precision == TEUK_FP32 && implicit_seg(N) <= kSegNarrow) ? 112 * 1024 : 220 * 1024;
     int best = 1;
     for (int R = rpp; R - 2 * ks <= 254; R += rpp) {
         const int tr = R - 2 * ks;
         if (tr < 1) continue;
-        if (batch_tile_smem(c->d.precision, tr, N, ks) > 112 * 1024 && best > 1) break;
+        if (batch_tile_smem(c->d.precision, tr, N, ks) > budget && best > 1) break;
         best = tr;
         if (tr >= c->d.Nr) break;
     }
