@@ -550,6 +550,10 @@ def run_native(args):
     finite = bool(np.isfinite(out_np).all() and np.isfinite(h).all())
 
     clocks = clk.summary()
+    if prec == "fp64":
+        # the FP64 step is bound by the FP64 pipe: its roofline is the ALU one
+        sink = torch.zeros(1, dtype=torch.float64, device=dev)
+        fp64_peak = teuk.teuk_fma_rate("fp64", 2048, sink.data_ptr(), torch.cuda.current_stream(dev).cuda_stream) / 1e12
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -561,7 +565,12 @@ def run_native(args):
                    "parallelism": f"replicas x{ws}", "tiling": tiling,
                    "tiling_source": tiling_source,
                    "tolerance": TOLERANCE_OUTCOME},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+        "roofline": {"bound": "alu", "achieved": FLOPS_PER_POINT * pts / avg_kernel_s / 1e12, "peak": fp64_peak,
+                     "unit": "TFLOP/s", "frac": FLOPS_PER_POINT * pts / avg_kernel_s / 1e12 / fp64_peak,
+                     "traffic": None, "per": "time step", "kernel": kernel, "flops_per_point": FLOPS_PER_POINT,
+                     "peak_source": "teuk_fma_rate FP64 in this run (independent FMA chains on all SMs)"}
+        if prec == "fp64" else
+        {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak,
                      "traffic": _profiled_traffic(kernel) if prec == "fp32" else None,
                      "per": "time step (achieved and traffic: per launch / steps_per_launch)",

@@ -6,6 +6,19 @@
 namespace teuk {
 namespace {
 
+// Tile of CTA b among nt: the tile holding the extraction row goes first.
+// Its CTA also runs the sample's adjoint on that row (FP64 solves of one row
+// by one warp), which then overlaps the other tiles instead of trailing the
+// last wave (FP64 adjoint step with the spin term on 4096 x 64: the SMs were
+// busy 70 % of the launch before).
+__device__ __forceinline__ int tile_of_block(int b, int nt, int i_ext, int tile_rows)
+{
+    int e = i_ext / tile_rows;
+    e = e < nt ? e : nt - 1;
+    b += e;
+    return b < nt ? b : b - nt;
+}
+
 // h = E u with u = s (physical) or u = C_{dt/2} s on the extraction row; one
 // warp.  The sum is the one the step kernels write to the waveform buffer.
 template <typename T, int S>
@@ -68,7 +81,8 @@ __device__ __forceinline__ void source_grad(const StepParams<T> &p, typename V2<
 // midpoint adjoint (mF, mG) from its two nodes, then every node from its two
 // midpoints.  The CTA's contributions to the source derivatives
 // (sum over steps of <lam_{n+1}, dF_n/dp> for p = Re A, Im A, r0) go to
-// part[4 blockIdx.x + (0..3)] = (Re cA, Im cA, Re cr, Im cr).
+// part[4 tile + (0..3)] = (Re cA, Im cA, Re cr, Im cr); the extraction
+// row's tile runs first (see tile_of_block).
 template <typename T, int S>
 __global__ void __launch_bounds__(256, 1) k_adjoint_step(const StepParams<T> p, const double2 *gseed, double *part)
 {
@@ -77,7 +91,8 @@ __global__ void __launch_bounds__(256, 1) k_adjoint_step(const StepParams<T> p, 
     __shared__ double s_red[8][4];
     const int Nr = p.Nr, N = p.Nth, TR = p.tile_rows, R = TR + 2, P = N;
     const int tid = threadIdx.x, NT = blockDim.x;
-    const int i0 = blockIdx.x * TR;
+    const int tile = tile_of_block((int)blockIdx.x, (int)gridDim.x, p.i_ext, TR);
+    const int i0 = tile * TR;
     const int G = p.group;
     const bool first = p.first != 0;
     const ImpConst<T> &K = first ? p.half : p.full;
@@ -281,7 +296,7 @@ __global__ void __launch_bounds__(256, 1) k_adjoint_step(const StepParams<T> p, 
     if (tid < 4) {
         double acc = 0.0;
         for (int w = 0; w < NT / 32; ++w) acc += s_red[w][tid];
-        part[4 * blockIdx.x + tid] = acc;
+        part[4 * tile + tid] = acc;
     }
 }
 
@@ -504,7 +519,8 @@ __global__ void __launch_bounds__(256, 1) k_adjoint_spin(const StepParams<T> p, 
     __shared__ double s_red[8][kNPart];
     const int Nr = p.Nr, N = p.Nth, TR = p.tile_rows, R = TR + 2, P = N;
     const int tid = threadIdx.x, NT = blockDim.x;
-    const int i0 = blockIdx.x * TR;
+    const int tile = tile_of_block((int)blockIdx.x, (int)gridDim.x, p.i_ext, TR);
+    const int i0 = tile * TR;
     const int G = p.group;
     const bool first = p.first != 0;
     const ImpConst<T> &K = first ? p.half : p.full;
@@ -809,7 +825,7 @@ __global__ void __launch_bounds__(256, 1) k_adjoint_spin(const StepParams<T> p, 
     if (tid < kNPart) {
         double acc = 0.0;
         for (int w = 0; w < NT / 32; ++w) acc += s_red[w][tid];
-        part[kNPart * blockIdx.x + tid] = acc;
+        part[kNPart * tile + tid] = acc;
     }
 }
 
