@@ -165,6 +165,15 @@ template <int S, typename V> __device__ __forceinline__ void vstore(V *dst, cons
     for (int i = 0; i < S / per; ++i) q[i] = pack16(r + i * per);
 }
 
+// a / b for a >= 0, b > 0: a shift when b is a power of two (theta counts
+// and lane groups usually are), else an unsigned division, which is
+// shorter than the signed one.
+__device__ __forceinline__ int udiv(int a, int b)
+{
+    if ((b & (b - 1)) == 0) return a >> (__ffs(b) - 1);
+    return (int)((unsigned)a / (unsigned)b);
+}
+
 // Local coefficients of the implicit part at node row (table f) and theta j.
 template <typename T> struct Loc {
     typedef typename V2<T>::t c2;
@@ -816,12 +825,13 @@ __device__ __forceinline__ void apply_W(const ImpCoef<T, S> &C, const typename V
 // stored scan levels (0 for a row that is not active).  Same map as
 // implicit_row_group.
 template <typename T, int S, bool MAT = false>
-__device__ void implicit_row_fwd(const ImpConst<T> &K, typename V2<T>::t *phi, typename V2<T>::t *pi,
+__device__ void implicit_row_fwd(const ImpConst<T> &K0, typename V2<T>::t *phi, typename V2<T>::t *pi,
                                  const typename V2<T>::t *prow, const T *f, const T *th, int N, bool active,
                                  bool in_tile, int g, int G, bool vec, int plan, const MatPlanes<T> *mat = nullptr,
                                  int gi = 0, typename V2<T>::t *u1phi = nullptr, typename V2<T>::t *u1pi = nullptr)
 {
     typedef typename V2<T>::t c2;
+    const ImpConst<T> K = K0;   // the step's constants, read once from the parameters
     const int j0 = g * S;
     int len = N - j0;
     len = len < 0 ? 0 : (len > S ? S : len);
@@ -1091,7 +1101,7 @@ __device__ __forceinline__ void imp_da(const ImpRow<T> &r, const T (&fr)[8], con
     dct = cmk<c2>(fma(dsg, fr[SF_CTR], sg * ctr), fma(dsg, fma(fr[SF_CTC], cc, fr[SF_CTI]), sg * cti));
 }
 
-template <typename T, bool INTERIOR, bool MAT = false>
+template <typename T, bool INTERIOR, bool MAT = false, bool SRC = true>
 __device__ void lw_segment(const StepParams<T> &p, typename V2<T>::t *sPhi, typename V2<T>::t *sPi,
                            const T *sSt, const T *sTh, int j, int ra, int rb,
                            typename V2<T>::t pf, typename V2<T>::t pg, typename V2<T>::t nf,
@@ -1104,7 +1114,7 @@ __device__ void lw_segment(const StepParams<T> &p, typename V2<T>::t *sPhi, type
     const c2 zero = cmk<c2>(T(0), T(0));
     const T half = T(0.5);
     T gth = T(0), ga2 = T(0);
-    if (src) {
+    if (SRC && src) {
         gth = sTh[TF_GTH * N + j];
         ga2 = sTh[TF_GA2 * N + j];
     }
@@ -1146,7 +1156,7 @@ __device__ void lw_segment(const StepParams<T> &p, typename V2<T>::t *sPhi, type
         }
         T beta, sg;
         c2 kap;
-        const bool s_row = src && gl >= p.patch_p0 && gl < p.patch_p0 + p.patch_np;
+        const bool s_row = SRC && src && gl >= p.patch_p0 && gl < p.patch_p0 + p.patch_np;
         coef(2 * k + 1, beta, kap, sg, s_row);
         const c2 df = csub(fb, fa);
         mf = caxpy(-beta, df, cscale<c2>(half, cadd(fa, fb)));
@@ -1176,7 +1186,7 @@ __device__ void lw_segment(const StepParams<T> &p, typename V2<T>::t *sPhi, type
             // Eq. 14 at node gi
             T beta, sg;
             c2 kap;
-            const bool s_row = src && gi >= p.patch_p0 && gi < p.patch_p0 + p.patch_np;
+            const bool s_row = SRC && src && gi >= p.patch_p0 && gi < p.patch_p0 + p.patch_np;
             coef(2 * lr, beta, kap, sg, s_row);
             const c2 dmf = csub(mf, mfp);
             nfv = caxpy(-beta, dmf, fb);
@@ -1215,7 +1225,7 @@ template <typename T> __device__ __forceinline__ typename V2<T>::t from_d2(doubl
 // NC / N row segments; the rows on either side of a segment are read before
 // bar() (a barrier over the NC threads), as the neighbouring segments
 // overwrite them.
-template <typename T, bool INTERIOR, bool MAT = false, typename Bar>
+template <typename T, bool INTERIOR, bool MAT = false, typename Bar, bool SRC = true>
 __device__ __forceinline__ void lw_phase(const StepParams<T> &p, typename V2<T>::t *sPhi, typename V2<T>::t *sPi,
                                          const T *sSt, const T *sTh, int r0, int nr, int g0, int ctid, int NC,
                                          bool src, typename V2<T>::t ph1, typename V2<T>::t ph2, Bar bar)
@@ -1224,9 +1234,9 @@ __device__ __forceinline__ void lw_phase(const StepParams<T> &p, typename V2<T>:
     const int N = p.Nth, P = p.pitch;
     const c2 zero = cmk<c2>(T(0), T(0));
     if (N <= NC) {
-        const int nseg = NC / N;
-        const int sl = (nr + nseg - 1) / nseg;
-        const int j = ctid % N, sgm = ctid / N;
+        const int nseg = udiv(NC, N);
+        const int sl = udiv(nr + nseg - 1, nseg);
+        const int sgm = udiv(ctid, N), j = ctid - sgm * N;
         int ra = r0 + sgm * sl, rb = r0 + (sgm + 1) * sl;
         if (rb > r0 + nr) rb = r0 + nr;
         const bool work = sgm < nseg && ra < rb;
@@ -1238,13 +1248,13 @@ __device__ __forceinline__ void lw_phase(const StepParams<T> &p, typename V2<T>:
             ng = sPi[rb * P + j];
         }
         bar();
-        if (work) lw_segment<T, INTERIOR, MAT>(p, sPhi, sPi, sSt, sTh, j, ra, rb, pf, pg, nf, ng, g0, ph1, ph2, src);
+        if (work) lw_segment<T, INTERIOR, MAT, SRC>(p, sPhi, sPi, sSt, sTh, j, ra, rb, pf, pg, nf, ng, g0, ph1, ph2, src);
     } else {
         // each thread owns whole columns: rows r0-1 and r0+nr are read before any write
         for (int j = ctid; j < N; j += NC) {
             c2 pf = sPhi[(r0 - 1) * P + j], pg = sPi[(r0 - 1) * P + j];
             c2 nf = sPhi[(r0 + nr) * P + j], ng = sPi[(r0 + nr) * P + j];
-            lw_segment<T, INTERIOR, MAT>(p, sPhi, sPi, sSt, sTh, j, r0, r0 + nr, pf, pg, nf, ng, g0, ph1, ph2, src);
+            lw_segment<T, INTERIOR, MAT, SRC>(p, sPhi, sPi, sSt, sTh, j, r0, r0 + nr, pf, pg, nf, ng, g0, ph1, ph2, src);
         }
     }
 }
@@ -1377,8 +1387,11 @@ __device__ __forceinline__ void split_tile(const StepParams<T> &p, int tile, int
     T *sTh = (T *)(smem_raw + plan.th);
     c2 *xPhi = (c2 *)(smem_raw + plan.total);   // KS = 2: copy of the extraction row
     c2 *xPi = xPhi + N;
-    // implicit step of this launch: dt/2 for the first step and for the state output
-    const ImpConst<T> &K = (p.first || p.imp_only) ? p.half : p.full;
+    // implicit step of this launch: dt/2 for the first step and for the state
+    // output (one step per launch only; with two steps per launch it is the
+    // full step, chosen at compile time so that its constants are read at
+    // fixed parameter offsets)
+    const ImpConst<T> &K = (KS == 1 && (p.first || p.imp_only)) ? p.half : p.full;
 
     const bool src = !p.imp_only && p.patch_np > 0 && i0 + TR + KS - 1 >= p.patch_p0 &&
                      g0 <= p.patch_p0 + p.patch_np;
@@ -1418,18 +1431,19 @@ __device__ __forceinline__ void split_tile(const StepParams<T> &p, int tile, int
     // ---- A: tile rows g0 .. g0+R-1 (state and pivots), r and theta tables
     const c2 zero = cmk<c2>(T(0), T(0));
     // (row, column) walk of the tile without integer division in the loop
-    const int t_lr = tid / N, t_j = tid - t_lr * N;
-    const int d_lr = NT / N, d_j = NT - d_lr * N;
+    const int t_lr = udiv(tid, N), t_j = tid - t_lr * N;
+    const int d_lr = udiv(NT, N), d_j = NT - d_lr * N;
     // rows of the tile that exist on the grid: [ga, gb] globally, from tile row la
     const int ga = g0 < 0 ? 0 : g0;
     const int gb = g0 + R - 1 > Nr - 1 ? Nr - 1 : g0 + R - 1;
     const int la = ga - g0, nrows = gb - ga + 1;
     // The state tile arrives in chunks of whole implicit passes, one mbarrier
     // each, so that the first pass can start while later rows are in flight.
-    const int rpp = NT / G;   // theta rows per implicit pass
-    int cr = rpp;             // rows per chunk
-    while ((R + cr - 1) / cr > kMaxChunks) cr += rpp;
-    const int nch = (R + cr - 1) / cr;
+    const int lgG = __ffs(G) - 1;   // G is a power of two
+    const int rpp = NT >> lgG;      // theta rows per implicit pass
+    int cr = rpp;                   // rows per chunk
+    while (udiv(R + cr - 1, cr) > kMaxChunks) cr += rpp;
+    const int nch = udiv(R + cr - 1, cr);
     if (p.bulk) {
         if (tid == 0) {
             for (int c = 0; c < nch; ++c) mbar_init(&s_mbar[c], 1);
@@ -1493,7 +1507,7 @@ __device__ __forceinline__ void split_tile(const StepParams<T> &p, int tile, int
         s_plan[lr] = (gi >= 0 && gi < Nr) ? K.plan[gi] : 0;
     }
     __syncthreads();
-    const int g = tid % G;
+    const int g = tid & (G - 1), tq = tid >> lgG;   // lane in the row group, row of the pass
     const bool vec = p.vec != 0;
     // bound of the waits on this tile's state copy (the drain after a failed
     // wait always uses kWaitLimit, so no copy is in flight when the CTA exits)
@@ -1506,9 +1520,9 @@ __device__ __forceinline__ void split_tile(const StepParams<T> &p, int tile, int
                 // the chunks that hold this pass's rows
                 int last = base + rpp - 1;
                 if (last > hi - 1) last = hi - 1;
-                for (int c = base / cr; c <= last / cr; ++c) ok &= (int)mbar_wait(&s_mbar[c], 0, wait_lim);
+                for (int c = udiv(base, cr); c <= udiv(last, cr); ++c) ok &= (int)mbar_wait(&s_mbar[c], 0, wait_lim);
             }
-            int lr = base + tid / G;
+            int lr = base + tq;
             bool in_tile = lr < hi;
             int gi = g0 + lr;
             bool active = in_tile && gi >= 1 && gi <= Nr - 2;
@@ -1540,7 +1554,7 @@ __device__ __forceinline__ void split_tile(const StepParams<T> &p, int tile, int
             bool mine = tid < G;
             bool active = mine && p.i_ext >= 1 && p.i_ext <= Nr - 2;
             implicit_row_fwd<T, S>(p.half, rf, rg, p.half.piv + (size_t)p.i_ext * N, sSt + 2 * lx * NSF, sTh, N,
-                                     active, mine, tid % G, G, vec, p.half.plan[p.i_ext]);
+                                     active, mine, tid & (G - 1), G, vec, p.half.plan[p.i_ext]);
             __syncwarp();
             if (p.nfix >= 0) {
                 // a step applied to caller buffers: the sample alone, to h_out
@@ -1563,7 +1577,7 @@ __device__ __forceinline__ void split_tile(const StepParams<T> &p, int tile, int
 #pragma unroll 1
     for (int k = 0; k < KS; ++k) {
         // implicit step: dt/2 for a first step and for the state output, else dt
-        const ImpConst<T> &Ki = k == 0 ? K : p.full;
+        const ImpConst<T> &Ki = (KS == 1 && k == 0) ? K : p.full;
         const int lo = p.imp_only ? KS : k, hi = p.imp_only ? TR + KS : R - k;
         implicit_rows(Ki, lo, hi, k == 0, ok, p.mat_on && !(k == 0 && (p.first || p.imp_only)));
         if (k == 0) {
@@ -1619,7 +1633,11 @@ __device__ __forceinline__ void split_tile(const StepParams<T> &p, int tile, int
             }
         }
         if (!lw_done) {
-            if (interior)
+            // most tiles hold no source row: they take a form without the source tests
+            if (interior && !src)
+                lw_phase<T, true, false, decltype(sync_all), false>(p, sPhi, sPi, sSt, sTh, k + 1, R - 2 - 2 * k, g0,
+                                                                    tid, NT, false, ph1, ph2, sync_all);
+            else if (interior)
                 lw_phase<T, true>(p, sPhi, sPi, sSt, sTh, k + 1, R - 2 - 2 * k, g0, tid, NT, src, ph1, ph2, sync_all);
             else
                 lw_phase<T, false>(p, sPhi, sPi, sSt, sTh, k + 1, R - 2 - 2 * k, g0, tid, NT, src, ph1, ph2, sync_all);
