@@ -1382,7 +1382,6 @@ __device__ __forceinline__ void split_tile(const StepParams<T> &p, int tile, int
     const SplitSmem plan = split_smem_plan(R, N, (int)sizeof(T));
     c2 *sPhi = (c2 *)(smem_raw + plan.phi);
     c2 *sPi = (c2 *)(smem_raw + plan.pi);
-    c2 *sPiv = (c2 *)(smem_raw + plan.piv);
     T *sSt = (T *)(smem_raw + plan.rt);   // step-table entries (SField) of the tile's positions
     T *sTh = (T *)(smem_raw + plan.th);
     c2 *xPhi = (c2 *)(smem_raw + plan.total);   // KS = 2: copy of the extraction row
@@ -1428,7 +1427,9 @@ __device__ __forceinline__ void split_tile(const StepParams<T> &p, int tile, int
                 sph[2 * k + 1] = make_double2(p.dt64 * e2.x, p.dt64 * e2.y);
             }
     }
-    // ---- A: tile rows g0 .. g0+R-1 (state and pivots), r and theta tables
+    // ---- A: tile rows g0 .. g0+R-1 (state), r and theta tables; the row
+    // solves read their pivots from global memory (L2), which leaves room for
+    // taller tiles
     const c2 zero = cmk<c2>(T(0), T(0));
     // (row, column) walk of the tile without integer division in the loop
     const int t_lr = udiv(tid, N), t_j = tid - t_lr * N;
@@ -1453,12 +1454,11 @@ __device__ __forceinline__ void split_tile(const StepParams<T> &p, int tile, int
                 if (r0 < la) r0 = la;
                 if (r1 > la + nrows) r1 = la + nrows;
                 unsigned bytes = r1 > r0 ? (unsigned)(r1 - r0) * (unsigned)N * (unsigned)sizeof(c2) : 0u;
-                mbar_expect_tx(&s_mbar[c], 3 * bytes);   // with no bytes this is a plain arrival
+                mbar_expect_tx(&s_mbar[c], 2 * bytes);   // with no bytes this is a plain arrival
                 if (bytes) {
                     const size_t gr = (size_t)(ga + r0 - la);
                     bulk_g2s(sPhi + r0 * P, p.uin + gr * N, bytes, &s_mbar[c]);
                     bulk_g2s(sPi + r0 * P, p.uin + ((size_t)Nr + gr) * N, bytes, &s_mbar[c]);
-                    bulk_g2s(sPiv + r0 * P, K.piv + gr * N, bytes, &s_mbar[c]);
                 }
             }
         }
@@ -1475,15 +1475,13 @@ __device__ __forceinline__ void split_tile(const StepParams<T> &p, int tile, int
     } else {
         for (int lr = t_lr, j = t_j; lr < R;) {
             int gi = g0 + lr;
-            c2 fv = zero, gv = zero, ev = zero;
+            c2 fv = zero, gv = zero;
             if (gi >= 0 && gi < Nr) {
                 fv = p.uin[(size_t)gi * N + j];
                 gv = p.uin[((size_t)Nr + gi) * N + j];
-                ev = K.piv[(size_t)gi * N + j];
             }
             sPhi[lr * P + j] = fv;
             sPi[lr * P + j] = gv;
-            sPiv[lr * P + j] = ev;
             lr += d_lr;
             j += d_j;
             if (j >= N) { j -= N; ++lr; }
@@ -1537,12 +1535,12 @@ __device__ __forceinline__ void split_tile(const StepParams<T> &p, int tile, int
             }
             if constexpr (sizeof(T) == 8) {
                 if (use_mat) {
-                    implicit_row_fwd<T, S, true>(Ki, sPhi + lrc * P, sPi + lrc * P, sPiv + lrc * P, nullptr, nullptr,
+                    implicit_row_fwd<T, S, true>(Ki, sPhi + lrc * P, sPi + lrc * P, Ki.piv + (size_t)(active ? gi : 1) * N, nullptr, nullptr,
                                                  N, active, in_tile, g, G, vec, s_plan[lrc], &p.mat, gi, t1f, t1g);
                     continue;
                 }
             }
-            implicit_row_fwd<T, S>(Ki, sPhi + lrc * P, sPi + lrc * P, sPiv + lrc * P, sSt + 2 * lrc * NSF, sTh, N,
+            implicit_row_fwd<T, S>(Ki, sPhi + lrc * P, sPi + lrc * P, Ki.piv + (size_t)(active ? gi : 1) * N, sSt + 2 * lrc * NSF, sTh, N,
                                    active, in_tile, g, G, vec, s_plan[lrc], nullptr, 0, t1f, t1g);
         }
     };

@@ -221,7 +221,7 @@ __host__ __device__ inline SplitSmem split_smem_plan(int R, int N, int tsize)
     s.phi = 0;
     s.pi = smem_align16(plane);
     s.piv = smem_align16(s.pi + plane);
-    s.rt = smem_align16(s.piv + plane);
+    s.rt = s.piv;   // no pivot plane: the row solves read the pivots from global memory (L2)
     s.th = smem_align16(s.rt + (unsigned)(2 * R - 1) * NSF * (unsigned)tsize);
     s.total = smem_align16(s.th + (unsigned)NTF * (unsigned)N * (unsigned)tsize);
     return s;
