@@ -755,7 +755,11 @@ __device__ __forceinline__ void seg_solve_lu(typename V2<T>::t (&w)[S], const Im
     c2 B = zero;
 #pragma unroll
     for (int k = 0; k < S; ++k) B = cmul(C.e[k], caxpy(-C.sub[k], B, w[k]));
-    {
+    if (P.nfw == 1) {
+        // the common case: one level (the loop below, without its overhead)
+        const c2 Bo = shfl_up_c(B, 1, G);
+        if (P.nf >= 1 && g >= 1) B = cfma(P.Af0, Bo, B);
+    } else {
         c2 A = P.Af0;
 #pragma unroll 1
         for (int l = 0; l < P.nfw; ++l) {
@@ -768,8 +772,8 @@ __device__ __forceinline__ void seg_solve_lu(typename V2<T>::t (&w)[S], const Im
             }
         }
     }
+    // lane 0's incoming value meets sub = 0 (first row of the operator)
     c2 z = shfl_up_c(B, 1, G);
-    if (g == 0) z = zero;
 #pragma unroll
     for (int k = 0; k < S; ++k) {
         z = cmul(C.e[k], caxpy(-C.sub[k], z, w[k]));
@@ -778,7 +782,10 @@ __device__ __forceinline__ void seg_solve_lu(typename V2<T>::t (&w)[S], const Im
     B = zero;
 #pragma unroll
     for (int k = S - 1; k >= 0; --k) B = cfnma(C.fk[k], B, w[k]);
-    {
+    if (P.nbw == 1) {
+        const c2 Bo = shfl_down_c(B, 1, G);
+        if (P.nb >= 1 && g + 1 < G) B = cfma(P.Ab0, Bo, B);
+    } else {
         c2 A = P.Ab0;
 #pragma unroll 1
         for (int l = 0; l < P.nbw; ++l) {
@@ -791,8 +798,8 @@ __device__ __forceinline__ void seg_solve_lu(typename V2<T>::t (&w)[S], const Im
             }
         }
     }
+    // the last lane's incoming value meets fk = 0 (last row, or padding)
     c2 x = shfl_down_c(B, 1, G);
-    if (g == G - 1) x = zero;
 #pragma unroll
     for (int k = S - 1; k >= 0; --k) {
         x = cfnma(C.fk[k], x, w[k]);
@@ -801,16 +808,16 @@ __device__ __forceinline__ void seg_solve_lu(typename V2<T>::t (&w)[S], const Im
 }
 
 // out = W x for the lane's segment; x_{j0-1} and x_{j0+S} come from the
-// neighbouring lanes (zero past the row's ends).
+// neighbouring lanes.  Past the row's ends the shuffles return the lane's
+// own (finite) values, which meet zero off-diagonals: the angular operator's
+// first row has no sub-diagonal and its last no super-diagonal (the pole
+// ghosts are folded into the diagonal), and padding elements are zero.
 template <typename T, int S>
 __device__ __forceinline__ void apply_W(const ImpCoef<T, S> &C, const typename V2<T>::t (&x)[S],
                                         typename V2<T>::t (&out)[S], int g, int G)
 {
     typedef typename V2<T>::t c2;
-    const c2 zero = cmk<c2>(T(0), T(0));
-    c2 xl = shfl_up_c(x[S - 1], 1, G), xr = shfl_down_c(x[0], 1, G);
-    if (g == 0) xl = zero;
-    if (g == G - 1) xr = zero;
+    const c2 xl = shfl_up_c(x[S - 1], 1, G), xr = shfl_down_c(x[0], 1, G);
 #pragma unroll
     for (int k = 0; k < S; ++k) {
         const c2 xm = k ? x[k - 1] : xl;
@@ -1168,6 +1175,9 @@ __device__ void lw_segment(const StepParams<T> &p, typename V2<T>::t *sPhi, type
     c2 fb = sPhi[ra * P + j], gb = sPi[ra * P + j];
     c2 mfp, mgp;
     midpoint(ra - 1, pf, pg, fb, gb, mfp, mgp);
+    // two rows per trip: the window's values change registers instead of
+    // being copied at the end of every row
+#pragma unroll 2
     for (int lr = ra; lr < rb; ++lr) {
         int gi = g0 + lr;
         if (!INTERIOR && gi >= Nr) break;
@@ -1286,6 +1296,12 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned by
 {
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
                  ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(m)) : "memory");
+}
+// Brings global bytes [src, src + bytes) into L2 without waiting (16-byte
+// aligned, a multiple of 16 bytes).
+__device__ __forceinline__ void prefetch_l2(const void *src, unsigned bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
 }
 __device__ __forceinline__ bool mbar_wait(unsigned long long *m, unsigned parity, int limit)
 {
@@ -1459,6 +1475,8 @@ __device__ __forceinline__ void split_tile(const StepParams<T> &p, int tile, int
                     const size_t gr = (size_t)(ga + r0 - la);
                     bulk_g2s(sPhi + r0 * P, p.uin + gr * N, bytes, &s_mbar[c]);
                     bulk_g2s(sPi + r0 * P, p.uin + ((size_t)Nr + gr) * N, bytes, &s_mbar[c]);
+                    // the chunk's pivot rows, which the row solves read from global memory
+                    prefetch_l2(K.piv + gr * N, bytes);
                 }
             }
         }
