@@ -270,7 +270,7 @@ __host__ __device__ inline PipeSmem pipe_smem_plan(int R, int N, int tsize)
     s.buf = smem_align16(s.xpi + (unsigned)N * c2);
     s.pi = smem_align16(plane);
     s.piv = smem_align16(s.pi + plane);
-    s.st = smem_align16(s.piv + plane);
+    s.st = s.piv;   // no pivot plane: the row solves read the pivots from global memory (L2)
     s.plan = smem_align16(s.st + 2u * (unsigned)R * NSF * (unsigned)tsize);
     s.bsize = smem_align16(s.plan + ((unsigned)R + 8u) * 4u);
     s.total = s.buf + 2u * s.bsize;

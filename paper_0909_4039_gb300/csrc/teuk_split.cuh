@@ -101,7 +101,8 @@ __global__ void __launch_bounds__(256) k_scan_plans(const StepParams<T> p, int *
 // gridDim.x persistent CTAs (about two per SM) walk the tiles t = blockIdx.x,
 // blockIdx.x + gridDim.x, ...  Each CTA holds two tile buffers in shared
 // memory: while tile k computes in one, the bulk copies of tile k+1 (state
-// rows, pivots, step-table entries, scan plans) land in the other, so the
+// rows, step-table entries, scan plans; its pivot rows are prefetched into
+// L2, where the row solves read them) land in the other, so the
 // loads of every tile but the first overlap the arithmetic.  The per-tile
 // work is that of split_tile with KS = 2 (same device functions, same
 // results bit for bit); the extraction row is sampled from a copy, so the
@@ -160,7 +161,7 @@ __global__ void __launch_bounds__(NTH, (NTH == 256 && sizeof(T) == 4 && S <= 4) 
     auto issue = [&](int t, int b) {
         const Geo q = geo(t);
         unsigned char *B = buf(b);
-        c2 *bPhi = (c2 *)B, *bPi = (c2 *)(B + L.pi), *bPiv = (c2 *)(B + L.piv);
+        c2 *bPhi = (c2 *)B, *bPi = (c2 *)(B + L.pi);
         T *bSt = (T *)(B + L.st);
         int *bPl = (int *)(B + L.plan);
         const int e0 = 2 * q.ga, e1 = 2 * q.gb + 1 > 2 * Nr - 2 ? 2 * Nr - 2 : 2 * q.gb + 1;
@@ -172,12 +173,12 @@ __global__ void __launch_bounds__(NTH, (NTH == 256 && sizeof(T) == 4 && S <= 4) 
             if (r0 < q.la) r0 = q.la;
             if (r1 > q.la + q.nrows) r1 = q.la + q.nrows;
             const unsigned bytes = r1 > r0 ? (unsigned)(r1 - r0) * (unsigned)N * (unsigned)sizeof(c2) : 0u;
-            mbar_expect_tx(&s_full[b][c], 3 * bytes + (c == 0 ? st_bytes + pl_bytes : 0u));
+            mbar_expect_tx(&s_full[b][c], 2 * bytes + (c == 0 ? st_bytes + pl_bytes : 0u));
             if (bytes) {
                 const size_t gr = (size_t)(q.ga + r0 - q.la);
                 bulk_g2s(bPhi + r0 * P, p.uin + gr * N, bytes, &s_full[b][c]);
                 bulk_g2s(bPi + r0 * P, p.uin + ((size_t)Nr + gr) * N, bytes, &s_full[b][c]);
-                bulk_g2s(bPiv + r0 * P, K.piv + gr * N, bytes, &s_full[b][c]);
+                prefetch_l2(K.piv + gr * N, bytes);
             }
             if (c == 0) {
                 bulk_g2s(bSt + (e0 - 2 * q.g0) * NSF, p.stab + (size_t)e0 * NSF, st_bytes, &s_full[b][0]);
@@ -216,7 +217,7 @@ __global__ void __launch_bounds__(NTH, (NTH == 256 && sizeof(T) == 4 && S <= 4) 
         const unsigned par = (unsigned)((k >> 1) & 1);
         const Geo q = geo(t);
         unsigned char *B = buf(b);
-        c2 *sPhi = (c2 *)B, *sPi = (c2 *)(B + L.pi), *sPiv = (c2 *)(B + L.piv);
+        c2 *sPhi = (c2 *)B, *sPi = (c2 *)(B + L.pi);
         T *sSt = (T *)(B + L.st);
         const int *sPl = (const int *)(B + L.plan);
         const int tn = t + (int)gridDim.x;
@@ -250,12 +251,12 @@ __global__ void __launch_bounds__(NTH, (NTH == 256 && sizeof(T) == 4 && S <= 4) 
                 const int plan = active ? sPl[gi - q.a0] : 0;
                 if constexpr (sizeof(T) == 8) {
                     if (p.mat_on) {
-                        implicit_row_fwd<T, S, true>(K, sPhi + lrc * P, sPi + lrc * P, sPiv + lrc * P, nullptr, nullptr,
+                        implicit_row_fwd<T, S, true>(K, sPhi + lrc * P, sPi + lrc * P, K.piv + (size_t)(active ? gi : 1) * N, nullptr, nullptr,
                                                      N, active, in_tile, g, G, vec, plan, &p.mat, gi);
                         continue;
                     }
                 }
-                implicit_row_fwd<T, S>(K, sPhi + lrc * P, sPi + lrc * P, sPiv + lrc * P, sSt + 2 * lrc * NSF, sTh, N,
+                implicit_row_fwd<T, S>(K, sPhi + lrc * P, sPi + lrc * P, K.piv + (size_t)(active ? gi : 1) * N, sSt + 2 * lrc * NSF, sTh, N,
                                        active, in_tile, g, G, vec, plan);
             }
         };
