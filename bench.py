@@ -321,7 +321,7 @@ def fp64_leg(w, dev, launches: int, warmup: int, flush):
 # length is measured live in the line's "accuracy" key.
 TOLERANCE_OUTCOME = {
     "fp32_state": "meets 1e-4 over windows (40 steps of 16384x128, 150 of 1024x32); misses it at full "
-                  "length: ~0.3 at 1000 steps of 1024x32, ~2.6 at 20000 steps of 16384x128",
+                  "length: ~0.3 at 1000 steps of 1024x32, ~2 at 20000 steps of 16384x128 (the accuracy key)",
     "fp64_state": "meets 1e-12 over windows (250 steps of 1024x32); misses it at 2000 steps of 1024x32 "
                   "(7.5e-8), within 10x of the disagreement of two FP64 oracle builds that differ only in "
                   "FMA contraction (5e-8)",
