@@ -421,3 +421,34 @@ def test_fp32_gradient_of_the_adjoint_workload():
     print(f"\nFP32 gradient relative errors (Re A, Im A, r0, a): {err}")
     assert np.all(err < 2e-3), err
     assert err[3] < 1e-3, err
+
+
+def test_adjoint_entry_points_reject_bad_calls():
+    """Error paths of the spin adjoint and the taped step: another workspace
+    than the prepared one, a missing sample address, an unaligned tape."""
+    import ctypes
+    import torch
+    from paper_0909_4039_gb300 import adjoint as A
+    from paper_0909_4039_gb300 import teuk
+    L = teuk.lib()
+    op = A.Operator(_w(60, 16), A.Params(0.3, 7.0, 0.5), "fp64")
+    with torch.cuda.stream(op.st.stream):
+        s, t, lam, lam2 = op.zeros(), op.zeros(), op.zeros(), op.zeros()
+        other = torch.zeros_like(op.ws)
+        rc = L.teuk_adjoint_step_spin(op.st.ctx, lam.data_ptr(), lam2.data_ptr(), s.data_ptr(), 3, 0, None,
+                                      other.data_ptr(), op.sh)
+        assert rc == 6   # TEUK_E_STATE: the workspace was not prepared
+        rc = L.teuk_apply_step_sample(op.st.ctx, s.data_ptr(), t.data_ptr(), 3, 0, None, op.sh)
+        assert rc == 1   # TEUK_E_INVAL: no sample address
+        tape = torch.zeros(op.tape_bytes // 8 + 64, dtype=torch.float64, device=op.st.device)
+        h = torch.zeros(1, dtype=torch.complex128, device=op.st.device)
+        rc = L.teuk_apply_step_tape(op.st.ctx, s.data_ptr(), t.data_ptr(), 3, 0, h.data_ptr(),
+                                    tape.data_ptr() + 8, op.sh)
+        assert rc == 1   # TEUK_E_INVAL: unaligned tape
+        size = ctypes.c_size_t()
+        assert L.teuk_tape_bytes(op.st.ctx, ctypes.byref(size)) == 0 and size.value % 256 == 0
+        assert size.value >= 16 * (4 * 60 * 16 + 2 * 16)
+        # the prepared workspace works
+        op.adjoint_spin(lam, lam2, s, 3, False, None)
+        op.st.synchronize()
+    op.close()
