@@ -90,6 +90,11 @@ Layout make_layout(const teuk_grid_desc &d)
     L.pivh = off; off = align256(off + c2 * N * Nr);
     L.plan = off; off = align256(off + sizeof(int) * Nr);
     L.planh = off; off = align256(off + sizeof(int) * Nr);
+    {
+        const size_t lanes = (size_t)implicit_group((int)N);
+        L.seg = off; off = align256(off + c2 * 2 * lanes * Nr);
+        L.segh = off; off = align256(off + c2 * 2 * lanes * Nr);
+    }
     L.patch = off; off = align256(off + c2 * 2 * N * patch_rows);
     L.patchu = off; off = align256(off + c2 * 2 * N * patch_rows);
     L.w = off; off = align256(off + sizeof(double) * N);
@@ -455,6 +460,7 @@ StepParams<T> make_params(const teuk_ctx *c, int in_level)
         K.g2h1 = (T)(2.0 * gh * (1.0 - kGamma) * h);
         K.piv = (const c2 *)(c->coef + (k ? c->L.pivh : c->L.piv));
         K.plan = (const int *)(c->coef + (k ? c->L.planh : c->L.plan));
+        K.seg = (const c2 *)(c->coef + (k ? c->L.segh : c->L.seg));
     }
     p.dt64 = c->dt;
     p.mOmega = c->mOmega;
@@ -513,9 +519,11 @@ cudaError_t compute_plans(teuk_ctx *c, cudaStream_t st)
 {
     if (c->d.scheme != TEUK_SCHEME_SPLIT) return cudaSuccess;
     int *pf = (int *)(c->coef + c->L.plan), *ph = (int *)(c->coef + c->L.planh);
-    if (c->d.precision == TEUK_FP32) return launch_scan_plans<float>(make_params<float>(c, 0), pf, ph, st);
+    char *sf = c->coef + c->L.seg, *sh = c->coef + c->L.segh;
+    if (c->d.precision == TEUK_FP32)
+        return launch_scan_plans<float>(make_params<float>(c, 0), pf, ph, (float2 *)sf, (float2 *)sh, st);
     const StepParams<double> p = make_params<double>(c, 0);
-    cudaError_t e = launch_scan_plans<double>(p, pf, ph, st);
+    cudaError_t e = launch_scan_plans<double>(p, pf, ph, (double2 *)sf, (double2 *)sh, st);
     if (e != cudaSuccess) return e;
     // the FP64 path's materialised coefficients come from the same tables
     return launch_mat_coef<double>(p, st);

@@ -719,8 +719,29 @@ __device__ __forceinline__ void imp_load_mat(const MatPlanes<T> &M, const typena
 // Scan plan of the LU solve from the row's stored levels: the segment maps'
 // multiplicative parts are prod(-e_j sub_j) forward and prod(-fk_j)
 // backward (formed only when a level uses them).
+// The lane segment's products prod(-e_j sub_j) (Af0) and prod(-fk_j) (Ab0),
+// factor by factor: separate products of the sub-diagonals and of the
+// pivots can overflow and underflow on stiff rows.  k_scan_plans stores
+// them per row and lane with this same function.
 template <typename T, int S>
-__device__ __forceinline__ ScanPlan<T> scan_plan_lu(const ImpCoef<T, S> &C, int plan)
+__device__ __forceinline__ ScanPlan<T> scan_plan_products(const ImpCoef<T, S> &C)
+{
+    typedef typename V2<T>::t c2;
+    ScanPlan<T> P;
+    P.Af0 = cmk<c2>(T(1), T(0));
+    P.Ab0 = P.Af0;
+#pragma unroll
+    for (int k = 0; k < S; ++k) P.Af0 = cmul(cscale<c2>(-C.sub[k], C.e[k]), P.Af0);
+#pragma unroll
+    for (int k = S - 1; k >= 0; --k) P.Ab0 = cmul(cmk<c2>(-C.fk[k].x, -C.fk[k].y), P.Ab0);
+    return P;
+}
+
+// seg: the row's stored segment products ([G][2] per row, see ImpConst) or
+// NULL (formed here).
+template <typename T, int S>
+__device__ __forceinline__ ScanPlan<T> scan_plan_lu(const ImpCoef<T, S> &C, int plan,
+                                                    const typename V2<T>::t *seg = nullptr)
 {
     typedef typename V2<T>::t c2;
     ScanPlan<T> P;
@@ -730,9 +751,12 @@ __device__ __forceinline__ ScanPlan<T> scan_plan_lu(const ImpCoef<T, S> &C, int 
     P.nb = (plan >> 8) & 0xff;
     P.nfw = (int)__reduce_max_sync(0xffffffffu, (unsigned)P.nf);
     P.nbw = (int)__reduce_max_sync(0xffffffffu, (unsigned)P.nb);
+    if (seg) {
+        if (P.nfw > 0) P.Af0 = seg[0];
+        if (P.nbw > 0) P.Ab0 = seg[1];
+        return P;
+    }
     if (P.nfw > 0) {
-        // factor by factor: separate products of the sub-diagonals and of
-        // the pivots can overflow and underflow on stiff rows
 #pragma unroll
         for (int k = 0; k < S; ++k) P.Af0 = cmul(cscale<c2>(-C.sub[k], C.e[k]), P.Af0);
     }
@@ -835,7 +859,8 @@ template <typename T, int S, bool MAT = false>
 __device__ void implicit_row_fwd(const ImpConst<T> &K0, typename V2<T>::t *phi, typename V2<T>::t *pi,
                                  const typename V2<T>::t *prow, const T *f, const T *th, int N, bool active,
                                  bool in_tile, int g, int G, bool vec, int plan, const MatPlanes<T> *mat = nullptr,
-                                 int gi = 0, typename V2<T>::t *u1phi = nullptr, typename V2<T>::t *u1pi = nullptr)
+                                 int gi = 0, typename V2<T>::t *u1phi = nullptr, typename V2<T>::t *u1pi = nullptr,
+                                 const typename V2<T>::t *seg = nullptr)
 {
     typedef typename V2<T>::t c2;
     const ImpConst<T> K = K0;   // the step's constants, read once from the parameters
@@ -850,7 +875,7 @@ __device__ void implicit_row_fwd(const ImpConst<T> &K0, typename V2<T>::t *phi, 
         imp_load_mat<T, S>(*mat, phi, pi, prow, gi, N, len, j0, vec, C, w, y);
     else
         imp_load<T, S>(K, phi, pi, prow, f, th, N, len, j0, vec, C, w, y);
-    const ScanPlan<T> P = scan_plan_lu<T, S>(C, active ? plan : 0);
+    const ScanPlan<T> P = scan_plan_lu<T, S>(C, active ? plan : 0, seg);
     {
         c2 Wu[S];
         apply_W<T, S>(C, w, Wu, g, G);
@@ -1551,15 +1576,18 @@ __device__ __forceinline__ void split_tile(const StepParams<T> &p, int tile, int
                     t1g = p.tape + ((size_t)Nr + gi) * N;
                 }
             }
+            // FP64: the stored segment products spare FP64 arithmetic, the
+            // bound of that path; FP32 forms them (cheaper than the loads)
+            const c2 *segr = sizeof(T) == 8 ? Ki.seg + ((size_t)(active ? gi : 1) * G + g) * 2 : nullptr;
             if constexpr (sizeof(T) == 8) {
                 if (use_mat) {
                     implicit_row_fwd<T, S, true>(Ki, sPhi + lrc * P, sPi + lrc * P, Ki.piv + (size_t)(active ? gi : 1) * N, nullptr, nullptr,
-                                                 N, active, in_tile, g, G, vec, s_plan[lrc], &p.mat, gi, t1f, t1g);
+                                                 N, active, in_tile, g, G, vec, s_plan[lrc], &p.mat, gi, t1f, t1g, segr);
                     continue;
                 }
             }
             implicit_row_fwd<T, S>(Ki, sPhi + lrc * P, sPi + lrc * P, Ki.piv + (size_t)(active ? gi : 1) * N, sSt + 2 * lrc * NSF, sTh, N,
-                                   active, in_tile, g, G, vec, s_plan[lrc], nullptr, 0, t1f, t1g);
+                                   active, in_tile, g, G, vec, s_plan[lrc], nullptr, 0, t1f, t1g, segr);
         }
     };
     // physical sample u = C_{dt/2} s of the extraction row (tile row lx) in

@@ -92,6 +92,10 @@ template <typename T> struct ImpConst {
     T h, g2h1;               // h, 2 gamma (1-gamma) h^2
     const c2 *piv;           // Thomas pivots of the stage matrix, [Nr][Nth]
     const int *plan;         // scan levels of each row's solves, [Nr]: forward | backward << 8
+    // each lane segment's products of the solve's multipliers, [Nr][G][2]:
+    // prod(-e_j sub_j) (forward) and prod(-fk_j) (backward), as
+    // scan_plan_lu forms them; read when the row's scan uses a level
+    const c2 *seg;
 };
 
 // Materialised coefficients of the FP64 path: the implicit step of length
@@ -279,7 +283,8 @@ __host__ __device__ inline PipeSmem pipe_smem_plan(int R, int N, int tsize)
 
 // ---------------------------------------------------------------- host side
 struct Layout {
-    size_t rtab64, rtabT, stab, dstab, th64, thT, piv, pivh, plan, planh, patch, patchu, w, ctl, staging, scratch;
+    size_t rtab64, rtabT, stab, dstab, th64, thT, piv, pivh, plan, planh, seg, segh, patch, patchu, w, ctl, staging,
+        scratch;
     size_t mat, mat_bytes;   // materialised coefficients (FP64 split scheme; 0 bytes otherwise)
     size_t total;
     size_t staging_elems;    // complex doubles that fit in the staging area
@@ -372,7 +377,8 @@ cudaError_t launch_split_step2(const StepParams<T> &p, int threads, size_t smem,
 // Scan levels of every row's implicit solves for the steps dt (p.full) and
 // dt/2 (p.half), written to plan_full / plan_half ([Nr] ints each).
 template <typename T>
-cudaError_t launch_scan_plans(const StepParams<T> &p, int *plan_full, int *plan_half, cudaStream_t st);
+cudaError_t launch_scan_plans(const StepParams<T> &p, int *plan_full, int *plan_half, typename V2<T>::t *seg_full,
+                              typename V2<T>::t *seg_half, cudaStream_t st);
 // Pipelined split kernel: two time steps per launch, `grid` persistent CTAs
 // of `threads` (256, or 512 for Ntheta <= 256) walk the tiles, each
 // double-buffering them in shared memory (the next tile's copies land while

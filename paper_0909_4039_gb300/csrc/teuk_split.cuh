@@ -69,7 +69,8 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && S <= 4) ? 2 : 1)
 // same coefficient path (step table, theta tables and pivots as the step
 // kernels read them).  One CTA of 256 threads covers 256 / G rows.
 template <typename T, int S>
-__global__ void __launch_bounds__(256) k_scan_plans(const StepParams<T> p, int *plan_full, int *plan_half)
+__global__ void __launch_bounds__(256) k_scan_plans(const StepParams<T> p, int *plan_full, int *plan_half,
+                                                    typename V2<T>::t *seg_full, typename V2<T>::t *seg_half)
 {
     typedef typename V2<T>::t c2;
     const int N = p.Nth, Nr = p.Nr, G = p.group;
@@ -93,6 +94,13 @@ __global__ void __launch_bounds__(256) k_scan_plans(const StepParams<T> p, int *
         for (int k = 0; k < S; ++k) fm[k] = cscale<c2>(C.sub[k], C.e[k]);
         const ScanPlan<T> P = scan_plan<T, S>(fm, C.fk, g, G);
         if (in_grid && g == 0) (h ? plan_half : plan_full)[gi] = P.nf | (P.nb << 8);
+        // the lane segment's multiplier products, formed as scan_plan_lu forms them
+        const ScanPlan<T> Q = scan_plan_products<T, S>(C);
+        if (in_grid) {
+            c2 *o = (h ? seg_half : seg_full) + ((size_t)gi * G + g) * 2;
+            o[0] = Q.Af0;
+            o[1] = Q.Ab0;
+        }
     }
 }
 
@@ -597,13 +605,14 @@ cudaError_t launch_apply_step(const StepParams<T> &p, int threads, size_t smem, 
 }
 
 template <typename T>
-cudaError_t launch_scan_plans(const StepParams<T> &p, int *plan_full, int *plan_half, cudaStream_t st)
+cudaError_t launch_scan_plans(const StepParams<T> &p, int *plan_full, int *plan_half, typename V2<T>::t *seg_full,
+                              typename V2<T>::t *seg_half, cudaStream_t st)
 {
     const int seg = implicit_seg(p.Nth);
     auto fn = seg == kSegNarrow ? k_scan_plans<T, kSegNarrow>
                                 : (seg == kSeg ? k_scan_plans<T, kSeg> : k_scan_plans<T, kSegWide>);
     const int rows = 256 / p.group;
-    fn<<<(p.Nr + rows - 1) / rows, 256, 0, st>>>(p, plan_full, plan_half);
+    fn<<<(p.Nr + rows - 1) / rows, 256, 0, st>>>(p, plan_full, plan_half, seg_full, seg_half);
     return cudaGetLastError();
 }
 

@@ -4,7 +4,8 @@
 namespace teuk {
 
 template cudaError_t launch_apply_step<float>(const StepParams<float> &, int, size_t, cudaStream_t);
-template cudaError_t launch_scan_plans<float>(const StepParams<float> &, int *, int *, cudaStream_t);
+template cudaError_t launch_scan_plans<float>(const StepParams<float> &, int *, int *, float2 *, float2 *,
+                                               cudaStream_t);
 template int split_batch_blocks_per_sm<float>(int, size_t, int);
 template cudaError_t launch_split_batch<float>(const StepParams<float> *, const int2 *, int, int, size_t, int,
                                                cudaStream_t);

@@ -4,7 +4,8 @@
 namespace teuk {
 
 template cudaError_t launch_apply_step<double>(const StepParams<double> &, int, size_t, cudaStream_t);
-template cudaError_t launch_scan_plans<double>(const StepParams<double> &, int *, int *, cudaStream_t);
+template cudaError_t launch_scan_plans<double>(const StepParams<double> &, int *, int *, double2 *, double2 *,
+                                               cudaStream_t);
 template int split_batch_blocks_per_sm<double>(int, size_t, int);
 template cudaError_t launch_split_batch<double>(const StepParams<double> *, const int2 *, int, int, size_t, int,
                                                 cudaStream_t);
