@@ -367,7 +367,10 @@ int teuk_adjoint_prepare(teuk_ctx *ctx, void *d_ws, void *stream);
  * derivatives are added to the workspace accumulators acc[0..3]:
  *   dL/dRe A = acc[0],  dL/dIm A = -acc[1],  dL/dr0 = acc[2]
  * (A the source amplitude, r0 the orbit radius through r0* and the Kepler
- * frequency; sum over the backward sweep, in a fixed order). */
+ * frequency; sum over the backward sweep, in a fixed order).  In FP64, full
+ * steps (first = 0) with the workspace last passed to teuk_adjoint_prepare
+ * read its coefficient planes (the same results up to rounding; the FP64
+ * pipe bounds this step); otherwise the coefficients are formed in place. */
 int teuk_adjoint_step(teuk_ctx *ctx, const void *d_lam_in, void *d_lam_out, int64_t n, int first,
                       const void *d_gseed, void *d_ws, void *stream);
 

@@ -352,7 +352,7 @@ __device__ __forceinline__ void seg_load(const typename V2<T>::t *row, int j0, i
 // exit), and this lane's part of <mu, dC_h u> from the forward stage values
 // (u1f, u1g) = U1 and (u2f, u2g) = U2 of the same row; f, df: the row's
 // step-table entry and its spin derivative.
-template <typename T, int S, bool MAT = false>
+template <typename T, int S, bool MAT = false, bool SPIN = true>
 __device__ double implicit_row_adj_spin(const ImpConst<T> &K, typename V2<T>::t *lf, typename V2<T>::t *lg,
                                         const typename V2<T>::t *u1f, const typename V2<T>::t *u1g,
                                         const typename V2<T>::t *u2f, const typename V2<T>::t *u2g,
@@ -430,6 +430,10 @@ __device__ double implicit_row_adj_spin(const ImpConst<T> &K, typename V2<T>::t 
     for (int k = 0; k < S; ++k) {
         w[k] = cadd(n2f[k], caxpy(-gh, Y[k], xf[k]));
         y[k] = cadd(n2p[k], n1p[k]);
+    }
+    if constexpr (!SPIN) {
+        if (in_tile) row_store<T, S>(lf, lg, w, y, j0, lenw, vec);
+        return 0.0;
     }
     // derivative coefficients dW (dqam, ddg, dqap) and dc_t of the row
     c2 ddg[S], dct[S];
@@ -509,7 +513,7 @@ __device__ double implicit_row_adj_spin(const ImpConst<T> &K, typename V2<T>::t 
 // (vF, vG) and U1 (u1F, u1G), the midpoint adjoints (mF, mG).
 constexpr int kNPart = 6;
 
-template <typename T, int S, bool MAT>
+template <typename T, int S, bool MAT, bool SPIN>
 __global__ void __launch_bounds__(256, 1) k_adjoint_spin(const StepParams<T> p, const typename V2<T>::t *sin,
                                                          const typename V2<T>::t *tape, const double2 *gseed,
                                                          const AdjPlanes<T> A, double *part)
@@ -557,7 +561,8 @@ __global__ void __launch_bounds__(256, 1) k_adjoint_spin(const StepParams<T> p, 
             const size_t qf = (size_t)gi * N + j, qg = ((size_t)Nr + gi) * N + j;
             a = p.uin[qf];
             b = p.uin[qg];
-            if (tape) {
+            if (!SPIN) {
+            } else if (tape) {
                 sa = tp2[qf];
                 sb = tp2[qg];
                 ua = tp1[qf];
@@ -590,7 +595,7 @@ __global__ void __launch_bounds__(256, 1) k_adjoint_spin(const StepParams<T> p, 
     __syncthreads();
 
     // ---- forward implicit stage on all rows: (vF, vG) <- U2 = C_h s_n, (u1F, u1G) <- U1
-    if (!tape) {
+    if (SPIN && !tape) {
         const int rpp = NT / G;
         for (int base = 0; base < R; base += rpp) {
             const int lr = base + tid / G;
@@ -661,30 +666,32 @@ __global__ void __launch_bounds__(256, 1) k_adjoint_spin(const StepParams<T> p, 
                 wF = cadd(wF, csub(cscale<c2>(nd.beta, lf), cmul(conj_c(nd.kap), lg)));
                 wG = csub(wG, cscale<c2>(nd.beta, lg));
             }
-            // the forward midpoint from U2, as the step forms it (stored for
-            // the node stage's spin terms), and this midpoint's spin term
-            // (owned by the tile of its lower node)
-            const LwDa<T> h = lwc(2 * k + 1, j, S2, Cc);
-            const c2 fa = vF[k * P + j], fb = vF[(k + 1) * P + j], ga = vG[k * P + j], gb = vG[(k + 1) * P + j];
-            const c2 Df = csub(fb, fa), Dg = csub(gb, ga);
-            c2 Sv = zero, dS = zero;
-            if (src && gl >= p.patch_p0 && gl < p.patch_p0 + p.patch_np)
-                src_da<T>(sSt + (2 * k + 1) * NSF, sDSt + (2 * k + 1) * NSF, h.sg, h.dsg, sTh[TF_GTH * N + j],
-                          sTh[TF_GA2 * N + j], sTh[TF_DGA2 * N + j], sph1, mdt1, Sv, dS);
-            fmF[idx] = caxpy(-h.beta, Df, cscale<c2>(T(0.5), cadd(fa, fb)));
-            fmG[idx] = cfma(h.kap, Df, cadd(caxpy(h.beta, Dg, cscale<c2>(T(0.5), cadd(ga, gb))), Sv));
-            if (k >= 1 && k <= TR) {
-                if (srcu) {
-                    const int pr = gl - p.unit_p0;
-                    if (pr >= 0 && pr < p.unit_np)
-                        source_grad<T>(p, wG, (double)hdtT, p.patchu[((size_t)pr * 2 + 1) * N + j], ph1,
-                                       p.rs_min64 + ((double)gl + 0.5) * p.drs64, t1, cA, cr);
+            // the source derivatives of this midpoint (owned by the tile of its lower node)
+            if (srcu && k >= 1 && k <= TR) {
+                const int pr = gl - p.unit_p0;
+                if (pr >= 0 && pr < p.unit_np)
+                    source_grad<T>(p, wG, (double)hdtT, p.patchu[((size_t)pr * 2 + 1) * N + j], ph1,
+                                   p.rs_min64 + ((double)gl + 0.5) * p.drs64, t1, cA, cr);
+            }
+            if constexpr (SPIN) {
+                // the forward midpoint from U2, as the step forms it (stored for
+                // the node stage's spin terms), and this midpoint's spin term
+                const LwDa<T> h = lwc(2 * k + 1, j, S2, Cc);
+                const c2 fa = vF[k * P + j], fb = vF[(k + 1) * P + j], ga = vG[k * P + j], gb = vG[(k + 1) * P + j];
+                const c2 Df = csub(fb, fa), Dg = csub(gb, ga);
+                c2 Sv = zero, dS = zero;
+                if (src && gl >= p.patch_p0 && gl < p.patch_p0 + p.patch_np)
+                    src_da<T>(sSt + (2 * k + 1) * NSF, sDSt + (2 * k + 1) * NSF, h.sg, h.dsg, sTh[TF_GTH * N + j],
+                              sTh[TF_GA2 * N + j], sTh[TF_DGA2 * N + j], sph1, mdt1, Sv, dS);
+                fmF[idx] = caxpy(-h.beta, Df, cscale<c2>(T(0.5), cadd(fa, fb)));
+                fmG[idx] = cfma(h.kap, Df, cadd(caxpy(h.beta, Dg, cscale<c2>(T(0.5), cadd(ga, gb))), Sv));
+                if (k >= 1 && k <= TR) {
+                    // d(Phi*) = -dbeta Df,  d(Pi*) = dbeta Dg + dkap Df + dS
+                    const c2 dmf = cscale<c2>(-h.dbeta, Df);
+                    const c2 dmg = cadd(cfma(h.dkap, Df, cscale<c2>(h.dbeta, Dg)), dS);
+                    spin += (double)wF.x * (double)dmf.x + (double)wF.y * (double)dmf.y +
+                            (double)wG.x * (double)dmg.x + (double)wG.y * (double)dmg.y;
                 }
-                // d(Phi*) = -dbeta Df,  d(Pi*) = dbeta Dg + dkap Df + dS
-                const c2 dmf = cscale<c2>(-h.dbeta, Df);
-                const c2 dmg = cadd(cfma(h.dkap, Df, cscale<c2>(h.dbeta, Dg)), dS);
-                spin += (double)wF.x * (double)dmf.x + (double)wF.y * (double)dmf.y + (double)wG.x * (double)dmg.x +
-                        (double)wG.y * (double)dmg.y;
             }
         }
         mF[idx] = wF;
@@ -721,6 +728,7 @@ __global__ void __launch_bounds__(256, 1) k_adjoint_spin(const StepParams<T> p, 
                     source_grad<T>(p, lg, (double)dtT, p.patchu[((size_t)pr * 2) * N + j], ph2,
                                    p.rs_min64 + (double)gi * p.drs64, t2, cA, cr);
             }
+            if constexpr (SPIN) {
             // spin terms of the node stage: d(Phi') = -dbeta dMf,
             // d(Pi') = dbeta dMg + dkap dMf + dS, dM the forward midpoint difference
             const LwDa<T> nd = lwc(2 * lr, j, S2, Cc);
@@ -736,6 +744,7 @@ __global__ void __launch_bounds__(256, 1) k_adjoint_spin(const StepParams<T> p, 
             }
             spin += (double)lf.x * (double)dnf.x + (double)lf.y * (double)dnf.y + (double)lg.x * (double)dng.x +
                     (double)lg.y * (double)dng.y;
+            }
         }
         lF[lr * P + j] = wF;
         lG[lr * P + j] = wG;
@@ -751,7 +760,7 @@ __global__ void __launch_bounds__(256, 1) k_adjoint_spin(const StepParams<T> p, 
             const int gi = i0 - 1 + lr;
             const bool active = in_tile && gi >= 1 && gi <= Nr - 2;
             const int lrc = in_tile ? lr : 1;
-            const double d = implicit_row_adj_spin<T, S, MAT>(
+            const double d = implicit_row_adj_spin<T, S, MAT, SPIN>(
                 K, lF + lrc * P, lG + lrc * P, u1F + lrc * P, u1G + lrc * P, vF + lrc * P, vG + lrc * P,
                 K.piv + (size_t)(active ? gi : 1) * N, sSt + 2 * lrc * NSF, sDSt + 2 * lrc * NSF, sTh, N, active,
                 in_tile, g, G, vec, &A, active ? gi : 1);
@@ -773,7 +782,8 @@ __global__ void __launch_bounds__(256, 1) k_adjoint_spin(const StepParams<T> p, 
                 const double w = p.w[j];
                 xF[j] = cmk<c2>((T)(w * gv.x), (T)(w * gv.y));
                 xG[j] = zero;
-                if (tape) {
+                if (!SPIN) {
+                } else if (tape) {
                     sF[j] = tape[tape_x_off(Nr, N) + j];
                     sG[j] = tape[tape_x_off(Nr, N) + N + j];
                 } else {
@@ -786,11 +796,12 @@ __global__ void __launch_bounds__(256, 1) k_adjoint_spin(const StepParams<T> p, 
                 const bool mine = tid < G;
                 const bool active = mine && p.i_ext >= 1 && p.i_ext <= Nr - 2;
                 // forward C_{dt/2} on the row of s_n: (sF, sG) <- U2, (aF, aG) <- U1
-                implicit_row_fwd<T, S>(p.half, sF, sG, p.half.piv + (size_t)p.i_ext * N, sSt + 2 * lx * NSF, sTh, N,
-                                       active, mine, tid % G, G, vec, active ? p.half.plan[p.i_ext] : 0, nullptr, 0,
-                                       aF, aG);
+                if constexpr (SPIN)
+                    implicit_row_fwd<T, S>(p.half, sF, sG, p.half.piv + (size_t)p.i_ext * N, sSt + 2 * lx * NSF, sTh,
+                                           N, active, mine, tid % G, G, vec, active ? p.half.plan[p.i_ext] : 0,
+                                           nullptr, 0, aF, aG);
                 __syncwarp();
-                const double d = implicit_row_adj_spin<T, S>(p.half, xF, xG, aF, aG, sF, sG,
+                const double d = implicit_row_adj_spin<T, S, false, SPIN>(p.half, xF, xG, aF, aG, sF, sG,
                                                              p.half.piv + (size_t)p.i_ext * N, sSt + 2 * lx * NSF,
                                                              sDSt + 2 * lx * NSF, sTh, N, active, mine, tid % G, G,
                                                              vec);
@@ -965,13 +976,13 @@ size_t adjoint_spin_smem_bytes(int tile_rows, int Nth)
     return 10 * R * Nth * sizeof(typename V2<T>::t) + (2 * (2 * R - 1) * NSF + (size_t)NTF * Nth) * sizeof(T);
 }
 
-template <typename T, bool MAT>
+template <typename T, bool MAT, bool SPIN = true>
 static void (*adjoint_spin_fn(int Nth))(const StepParams<T>, const typename V2<T>::t *, const typename V2<T>::t *,
                                         const double2 *, const AdjPlanes<T>, double *)
 {
     const int seg = implicit_seg(Nth);
-    return seg == kSegNarrow ? k_adjoint_spin<T, kSegNarrow, MAT>
-                             : (seg == kSeg ? k_adjoint_spin<T, kSeg, MAT> : k_adjoint_spin<T, kSegWide, MAT>);
+    return seg == kSegNarrow ? k_adjoint_spin<T, kSegNarrow, MAT, SPIN>
+                             : (seg == kSeg ? k_adjoint_spin<T, kSeg, MAT, SPIN> : k_adjoint_spin<T, kSegWide, MAT, SPIN>);
 }
 
 template <typename T>
@@ -994,6 +1005,28 @@ cudaError_t launch_adjoint_spin(const StepParams<T> &p, int tile_rows, const typ
     if (e != cudaSuccess) return e;
     k_part_reduce6<<<1, 32, 0, st>>>(part, grid, acc);
     return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_adjoint_planes(const StepParams<T> &p, int tile_rows, const double2 *gseed, const AdjPlanes<T> &A,
+                                  double *part, double *acc, cudaStream_t st)
+{
+    if constexpr (sizeof(T) != 8) {
+        return cudaErrorInvalidValue;
+    } else {
+        if (p.first) return cudaErrorInvalidValue;
+        auto fn = adjoint_spin_fn<T, true, false>(p.Nth);
+        cudaError_t e = smem_limit_max((const void *)fn);
+        if (e != cudaSuccess) return e;
+        StepParams<T> q = p;
+        q.tile_rows = tile_rows;
+        const int grid = adjoint_grid<T>(p.Nr, tile_rows);
+        fn<<<grid, 256, adjoint_spin_smem_bytes<T>(tile_rows, p.Nth), st>>>(q, nullptr, nullptr, gseed, A, part);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        k_part_reduce6<<<1, 32, 0, st>>>(part, grid, acc);
+        return cudaGetLastError();
+    }
 }
 
 template <typename T>
@@ -1026,6 +1059,8 @@ template cudaError_t launch_adjoint_spin<float>(const StepParams<float> &, int, 
 template cudaError_t launch_adjoint_spin<double>(const StepParams<double> &, int, const double2 *, const double2 *,
                                                  const double2 *, const AdjPlanes<double> &, double *, double *,
                                                  cudaStream_t);
+template cudaError_t launch_adjoint_planes<double>(const StepParams<double> &, int, const double2 *,
+                                                   const AdjPlanes<double> &, double *, double *, cudaStream_t);
 template cudaError_t launch_dot<float>(const float2 *, const float2 *, const float2 *, size_t, double *, double2 *,
                                        cudaStream_t);
 template cudaError_t launch_dot<double>(const double2 *, const double2 *, const double2 *, size_t, double *,

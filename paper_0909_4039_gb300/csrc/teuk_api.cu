@@ -1432,7 +1432,13 @@ int teuk_adjoint_step(teuk_ctx *c, const void *d_lam_in, void *d_lam_out, int64_
         p.uout = (double2 *)d_lam_out;
         p.first = first ? 1 : 0;
         p.nfix = n;
-        e = launch_adjoint_step<double>(p, tr, (const double2 *)d_gseed, part, acc, st);
+        // full steps with a prepared workspace read the coefficient planes
+        // (the FP64 pipe bounds this step)
+        if (!first && d_ws == c->adj_ws)
+            e = launch_adjoint_planes<double>(p, adjoint_spin_tile_rows(c), (const double2 *)d_gseed,
+                                              adjoint_planes<double>(c, d_ws), part, acc, st);
+        else
+            e = launch_adjoint_step<double>(p, tr, (const double2 *)d_gseed, part, acc, st);
     }
     if (e != cudaSuccess) return cuda_err(c, e, "adjoint step");
     return TEUK_OK;

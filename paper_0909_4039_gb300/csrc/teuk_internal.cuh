@@ -332,6 +332,12 @@ template <typename T>
 cudaError_t launch_adjoint_spin(const StepParams<T> &p, int tile_rows, const typename V2<T>::t *sin,
                                 const typename V2<T>::t *tape, const double2 *gseed, const AdjPlanes<T> &A,
                                 double *part, double *acc, cudaStream_t st);
+// The adjoint step without the spin term through the FP64 coefficient
+// planes (the same lam_n and source sums as launch_adjoint_step up to
+// rounding; full steps of FP64 contexts only).
+template <typename T>
+cudaError_t launch_adjoint_planes(const StepParams<T> &p, int tile_rows, const double2 *gseed, const AdjPlanes<T> &A,
+                                  double *part, double *acc, cudaStream_t st);
 template <typename T>
 int adjoint_grid(int Nr, int tile_rows);
 template <typename T>
