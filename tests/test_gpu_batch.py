@@ -232,3 +232,35 @@ def test_batch_wide_theta_class():
     b.close()
     for st in sts:
         st.close()
+
+
+def test_long_run_batch_full_size_window():
+    """The long-run workload at full size (65536 x 256, a = 0.999) in the
+    batched launch configuration its eight-instance run uses (Ntheta = 256
+    class, two steps per launch): two instances (r0 = 4 and 20) step
+    together for seven steps.  The first starts from random data over every
+    tile and is compared with the FP64 oracle within the FP32 tolerance; the
+    second (zero data, its own source) equals its solo run bit for bit."""
+    from oracle import oracle as O
+    ws = inputs.long_run_batch(2)
+    nsteps = 7
+    u0 = inputs.random_state(ws[0].Nr, ws[0].Ntheta, seed=77)
+    sts = [gpu_stepper(w, "fp32", wave_capacity=nsteps + 1) for w in ws]
+    sts[0].set_state(u0, 0)
+    b = _batch(sts)
+    til = b.tiling()
+    assert til["steps_per_launch"] == 2, til
+    b.step(nsteps)
+    b.synchronize()
+    got = [(st.get_state(), st.waveform(0, nsteps + 1)) for st in sts]
+    b.close()
+    for st in sts:
+        st.close()
+    solo = gpu_stepper(ws[1], "fp32", wave_capacity=nsteps + 1)
+    solo.step(nsteps)
+    assert np.array_equal(solo.get_state(), got[1][0])
+    assert np.array_equal(solo.waveform(0, nsteps + 1), got[1][1])
+    solo.close()
+    uo, ho = O.run(oracle_problem(ws[0]), u0, nsteps)
+    assert rel_l2(got[0][0], uo) <= FP32_TOL, rel_l2(got[0][0], uo)
+    assert rel_l2(got[0][1], ho) <= FP32_TOL, rel_l2(got[0][1], ho)
