@@ -120,24 +120,26 @@ def kernel_source_sha1() -> str:
     return h.hexdigest()
 
 
-def _profiled_traffic(kernel: str):
-    """DRAM bytes per time step of the step kernel from the committed ncu
-    summary (bytes per launch / steps per launch), only while the kernel
-    source is the one that was profiled."""
-    import hashlib
+def _profiled_traffic(kernel: str, workload: str = "16384x128", steps_per_launch: int = 2):
+    """DRAM bytes per time step of a step kernel from its committed ncu
+    summary (profiles/<kernel>_<workload>_fp32.md: bytes per launch / steps
+    per launch), only while the kernel source is the one that was profiled
+    and the run launches the profiled number of steps per launch.  Returns
+    (bytes per step, the tile heights of the profiled launch) or (None, None)."""
     import re
-    md = os.path.join(ROOT, "profiles", f"{kernel}_16384x128_fp32.md")
+    md = os.path.join(ROOT, "profiles", f"{kernel}_{workload}_fp32.md")
     try:
         text = open(md).read()
-        sha = kernel_source_sha1()
-        m1 = re.search(r"traffic_bytes_per_launch:\s*(\d+)", text)
-        m2 = re.search(r"source_sha1:\s*([0-9a-f]{40})", text)
-        m3 = re.search(r"steps_per_launch:\s*(\d+)", text)
-        if m1 and m2 and m2.group(1) == sha:
-            return int(m1.group(1)) // (int(m3.group(1)) if m3 else 1)
     except OSError:
-        pass
-    return None
+        return None, None
+    m1 = re.search(r"traffic_bytes_per_launch:\s*(\d+)", text)
+    m2 = re.search(r"source_sha1:\s*([0-9a-f]{40})", text)
+    m3 = re.search(r"steps_per_launch:\s*(\d+)", text)
+    m4 = re.search(r"tile_rows:\s*([0-9, ]+)", text)
+    if not (m1 and m2 and m3) or m2.group(1) != kernel_source_sha1() or int(m3.group(1)) != steps_per_launch:
+        return None, None
+    rows = [int(x) for x in m4.group(1).replace(" ", "").split(",") if x] if m4 else None
+    return int(m1.group(1)) // steps_per_launch, rows
 
 
 # Algorithmic flops per point and step of the split scheme as the kernels
@@ -413,12 +415,15 @@ def batch_leg(kind: str, dev, launches: int, warmup: int):
         value = pts * nsteps / (total_ms * 1e-3) / 1e9
         peak, peak_src = _peaks()
         achieved = 32 * value
+        traffic, traffic_rows = _profiled_traffic("k_split_batch", kind, ks)
         return {"value": value, "unit": UNIT, "instances": len(allw), "points": pts, "steps": nsteps,
                 "ms_per_step": total_ms / nsteps, "steps_per_launch": ks,
                 "tile_rows": sorted(set(int(t) for t in tiling.get("tile_rows", []))),
                 "tiling_source": "teuk_batch_autotune(4 trial steps), before the timed launches",
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                             "frac": achieved / peak, "bytes_per_point": 32, "traffic": None,
+                             "frac": achieved / peak, "bytes_per_point": 32, "traffic": traffic,
+                             "traffic_profiled_tile_rows": traffic_rows,
+                             "per": "time step (achieved and traffic: per launch / steps_per_launch)",
                              "peak_source": f"{peak_src} hbm_gbs (copy, burst)"}}
     finally:
         for st in sts:
@@ -550,6 +555,8 @@ def run_native(args):
     finite = bool(np.isfinite(out_np).all() and np.isfinite(h).all())
 
     clocks = clk.summary()
+    traffic, traffic_rows = (_profiled_traffic(kernel, "16384x128", int(tiling.get("steps_per_launch", 1)))
+                             if prec == "fp32" and w.Nr == 16384 and w.Ntheta == 128 else (None, None))
     if prec == "fp64":
         # the FP64 step is bound by the FP64 pipe: its roofline is the ALU one
         sink = torch.zeros(1, dtype=torch.float64, device=dev)
@@ -572,7 +579,7 @@ def run_native(args):
         if prec == "fp64" else
         {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak,
-                     "traffic": _profiled_traffic(kernel) if prec == "fp32" else None,
+                     "traffic": traffic, "traffic_profiled_tile_rows": traffic_rows,
                      "per": "time step (achieved and traffic: per launch / steps_per_launch)",
                      "kernel": kernel, "bytes_per_point": bytes_per_pt,
                      "peak_source": f"{peak_src} hbm_gbs (copy, burst)",
@@ -689,6 +696,9 @@ def run_native_batch(args):
     bytes_per_pt = 32 if prec == "fp32" else 64
     peak, peak_src = _peaks()
     achieved = bytes_per_pt * pts / avg_s / 1e9
+    # the committed ncu summaries cover the whole FP32 batch on one GPU
+    traffic, traffic_rows = (_profiled_traffic("k_split_batch", args.workload, ks)
+                             if prec == "fp32" and ws == 1 else (None, None))
 
     # end to end: every instance's state from pinned host, the batched steps,
     # every state and waveform back to the host
@@ -730,8 +740,9 @@ def run_native_batch(args):
                    "tiling_source": tiling_source,
                    "iteration": "one timed iteration = one launch = steps_per_launch time steps"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": None, "kernel": "k_split_batch", "bytes_per_point": bytes_per_pt,
-                     "per": "time step (achieved: per launch / steps_per_launch)",
+                     "traffic": traffic, "traffic_profiled_tile_rows": traffic_rows,
+                     "kernel": "k_split_batch", "bytes_per_point": bytes_per_pt,
+                     "per": "time step (achieved and traffic: per launch / steps_per_launch)",
                      "peak_source": f"{peak_src} hbm_gbs (copy, burst)"},
         "e2e": e2e,
         "clocks": clk.summary(),
