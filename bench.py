@@ -5,9 +5,11 @@ Workload (synthetic, no dataset): s = -2, m = 2, a = 0.99, 16384 x 128 over
 r* in [-200, 1000], dt = dr*/2, circular-orbit Gaussian source at r0 = 6,
 FP32 state (FP64 coefficients, time, phase and extraction sums).  One bench
 step is one full time step of the hot path (implicit half steps, the
-Lax-Wendroff stages, boundary rows, source, FP64 extraction): a single
-kernel launch.  L2 is flushed (a 256 MB write) between timed steps, and each
-step is timed with CUDA events on the stepper's stream.
+Lax-Wendroff stages, boundary rows, source, FP64 extraction); a timed
+iteration is one kernel launch of one to three such steps (the measured
+autotuner's choice), and the rates are per time step.  L2 is flushed (a
+256 MB write) between timed launches, and each launch is timed with CUDA
+events on the stepper's stream.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
                   [--workload single|batch64|long8|adjoint4096]
@@ -467,7 +469,8 @@ def run_native(args):
     tiling = st.tiling()
     kernel = ("k_split_persist" if tiling.get("persistent")
               else ("k_split_pipe" if tiling.get("pipelined")
-                    else ("k_split_step2" if tiling.get("steps_per_launch", 1) == 2 else "k_split_step")))
+                    else {2: "k_split_step2", 3: "k_split_step3"}.get(tiling.get("steps_per_launch", 1),
+                                                                     "k_split_step")))
     stream = st.stream
     pts = w.Nr * w.Ntheta
 
@@ -478,8 +481,8 @@ def run_native(args):
         torch.cuda.synchronize(dev)
 
     # One timed iteration is one launch of the configured kernel: one time
-    # step, or two with the two-steps-per-launch kernel (the iterations add up
-    # to exactly --steps steps; an odd remainder is a one-step iteration).
+    # step, or two or three with the multi-step kernels (the iterations add up
+    # to exactly --steps steps; a remainder runs as one-step iterations).
     ks = int(tiling.get("steps_per_launch", 1))
     iters = [ks] * (args.steps // ks) + [1] * (args.steps % ks)
     # warm-up (flushed, untimed)
@@ -516,12 +519,14 @@ def run_native(args):
     achieved = bytes_per_pt * pts / avg_kernel_s / 1e9
     peak, peak_src = _peaks()
 
-    # steady state: the same steps back to back (state resident in L2), graph replays
-    nst = max(128, (args.steps // 128) * 128)
+    # steady state: the same steps back to back (state resident in L2), graph
+    # replays (a graph holds 64 steps, or 96 with three steps per launch; the
+    # warm-up captures it, and 384 steps are whole graphs either way)
+    nst = max(384, (args.steps // 384) * 384)
     barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with torch.cuda.stream(stream):
-        st.step(128)
+        st.step(192)
         e0.record(stream)
         st.step(nst)
         e1.record(stream)
@@ -915,7 +920,7 @@ def main():
     ap.add_argument("--consumers", type=int, default=480, help="consumer threads for --kernel persistent")
     ap.add_argument("--pipe-threads", type=int, choices=[256, 512], default=256,
                     help="threads per CTA for --kernel pipelined")
-    ap.add_argument("--steps-per-launch", type=int, choices=[1, 2], default=1,
+    ap.add_argument("--steps-per-launch", type=int, choices=[1, 2, 3], default=1,
                     help="time steps per launch for --kernel tiled")
     ap.add_argument("--no-autotune", action="store_true",
                     help="batch64 / long8: keep the batch's default configuration")

@@ -188,17 +188,19 @@ int teuk_tiling(const teuk_ctx *ctx, int *tile_rows, int *threads, size_t *smem_
  * tiles, each double-buffering them, so the copies of a CTA's next tile
  * land while the current one computes); 0: the tiled kernel (one CTA per
  * tile).  *grid is the number of CTAs per launch.
- * *steps_per_launch is 2 when the tiled kernel advances two time steps per
- * launch (temporal blocking: two halo rows on either side, one state read
- * and write per two steps), else 1.  Any pointer may be NULL.  For the
- * literal scheme *persistent = 0 and *steps_per_launch = 1. */
+ * *steps_per_launch is 2 or 3 when the tiled kernel advances that many
+ * time steps per launch (temporal blocking: as many halo rows on either
+ * side, one state read and write per launch), else 1.  Any pointer may be
+ * NULL.  For the literal scheme *persistent = 0 and *steps_per_launch = 1. */
 int teuk_kernel_config(const teuk_ctx *ctx, int *persistent, int *consumer_threads, int *grid,
                        int *steps_per_launch);
 
 /* Measured tile autotuner.  Ranks the launch configurations that fit on the
  * device (tile heights of the tiled kernel with one or two steps per launch,
- * and tile height x consumer count of the persistent kernel) by a
- * wave-quantisation cost model, times the best four of each kind for
+ * the pipelined kernel, and tile height x consumer count of the persistent
+ * kernel) by a wave-quantisation cost model, times the best four of each
+ * kind, and the tiled kernel with three steps per launch at the heights of
+ * the four two-step candidates, for
  * trial_steps launches each on this grid (CUDA events on `stream`), in two
  * interleaved rounds, and keeps the fastest per time step (a candidate's
  * better round).  The trials overwrite the
@@ -223,10 +225,11 @@ int teuk_autotune_cold(teuk_ctx *ctx, int trial_steps, void *d_flush, size_t flu
 int teuk_set_tiling(teuk_ctx *ctx, int tile_rows);
 
 /* Select the tiled split-scheme kernel with the given tile height and
- * steps_per_launch = 1 (as teuk_set_tiling) or 2 (two time steps per launch;
- * the first step of a run and an odd last step still take one).  The
- * result does not depend on the choice.  TEUK_E_INVAL if the tile does not
- * fit or steps_per_launch is not 1 or 2. */
+ * steps_per_launch = 1 (as teuk_set_tiling), 2 or 3 (that many time steps
+ * per launch; the first step of a run and the steps left over at the end of
+ * a call still take one each).  The result does not depend on the choice.
+ * TEUK_E_INVAL if the tile does not fit, tile_rows is above 254 - 2
+ * steps_per_launch, or steps_per_launch is not 1, 2 or 3. */
 int teuk_set_tiling_steps(teuk_ctx *ctx, int tile_rows, int steps_per_launch);
 
 /* Select the pipelined split-scheme kernel (two time steps per launch,

@@ -58,9 +58,9 @@ struct teuk_ctx {
     int persist, nc, grid;
     int pipe;                // the pipelined two-step kernel (grid persistent CTAs)
     size_t persist_smem;
-    int ks;                  // time steps per launch of the tiled kernel (1 or 2)
+    int ks;                  // time steps per launch of the tiled kernel (1, 2 or 3)
     int wait0;               // teuk_set_wait_limit (< 0: default bound)
-    size_t smem2;            // shared memory of the two-step kernel
+    size_t smem2;            // shared memory of the two- or three-step kernel
     const void *adj_ws;      // adjoint workspace whose coefficient planes teuk_adjoint_prepare filled
     // graphs, one per starting level
     cudaGraphExec_t graph[2];
@@ -236,7 +236,7 @@ struct TileCand {
     double cost;             // model cost per time step
     int R;                   // tile_rows + 2
     int persist, nc, grid;
-    int ks;                  // time steps per launch (tiled kernel)
+    int ks;                  // time steps per launch (tiled kernel: 1, 2 or 3)
     int pipe;                // 1: the pipelined two-step kernel (grid persistent CTAs)
     size_t smem;
 };
@@ -300,6 +300,38 @@ static bool tiled2_cand(const teuk_ctx *c, int TR, int nsm, TileCand *out)
     out->nc = 0;
     out->grid = (int)tiles;
     out->ks = 2;
+    out->pipe = 0;
+    out->smem = sm;
+    return true;
+}
+
+// A three-steps-per-launch candidate of height TR: per step, a third of a
+// tile whose steps cover TR + 6, TR + 4 and TR + 2 rows (implicit) and
+// TR + 4, TR + 2 and TR (LW).  The model leaves it out of the default
+// choice (tile_candidates); the autotuners time it at the heights of the
+// model-best two-step candidates.
+static bool tiled3_cand(const teuk_ctx *c, int TR, int nsm, TileCand *out)
+{
+    const int N = (int)c->d.Ntheta;
+    const bool f32 = c->d.precision == TEUK_FP32;
+    const int threads = 256;
+    if (TR > kMaxTileRows - 6) return false;
+    size_t sm = f32 ? split3_smem_bytes<float>(TR, N) : split3_smem_bytes<double>(TR, N);
+    if (sm > 227 * 1024) return false;
+    int k = f32 ? split3_blocks_per_sm<float>(N, threads, sm) : split3_blocks_per_sm<double>(N, threads, sm);
+    if (k < 1) return false;
+    const long long Nr = c->d.Nr;
+    long long tiles = (Nr + TR - 1) / TR;
+    long long waves = (tiles + (long long)k * nsm - 1) / ((long long)k * nsm);
+    int rpp = threads / implicit_group(N);
+    auto rpad = [&](int r) { return ((r + rpp - 1) / rpp) * rpp; };
+    double rows = 0.6 * (rpad(TR + 6) + rpad(TR + 4) + rpad(TR + 2)) + 0.4 * (3.0 * TR + 9.0) + 4.0;
+    out->cost = (double)waves * k * rows * (k == 1 ? 1.2 : 1.0) / 3.0;
+    out->R = TR + 2;
+    out->persist = 0;
+    out->nc = 0;
+    out->grid = (int)tiles;
+    out->ks = 3;
     out->pipe = 0;
     out->smem = sm;
     return true;
@@ -410,7 +442,7 @@ static bool apply_cand(teuk_ctx *c, const TileCand &k)
     c->grid = (k.persist || k.pipe) ? k.grid : 0;
     c->persist_smem = k.persist ? k.smem : 0;
     c->ks = k.persist ? 1 : k.ks;
-    c->smem2 = (!k.persist && k.ks == 2) ? k.smem : 0;
+    c->smem2 = (!k.persist && k.ks >= 2) ? k.smem : 0;
     return true;
 }
 
@@ -539,11 +571,17 @@ cudaError_t launch_one(teuk_ctx *c, int in_level, cudaStream_t st)
     return c->d.scheme == TEUK_SCHEME_SPLIT ? launch_split<double>(c, p, st) : launch_literal_step<double>(p, st);
 }
 
-// One launch of the configured kernel from level in_level: two steps when
-// the tiled kernel takes two per launch and the state is shifted (a full
-// step follows), else one; *steps receives the count.
+// One launch of the configured kernel from level in_level: two or three
+// steps when the tiled kernel takes that many per launch and the state is
+// shifted (full steps follow), else one; *steps receives the count.
 cudaError_t launch_unit(teuk_ctx *c, int in_level, cudaStream_t st, int *steps)
 {
+    if (c->d.scheme == TEUK_SCHEME_SPLIT && c->ks == 3 && c->shifted) {
+        *steps = 3;
+        if (c->d.precision == TEUK_FP32)
+            return launch_split_step3<float>(make_params<float>(c, in_level), c->threads, c->smem2, st);
+        return launch_split_step3<double>(make_params<double>(c, in_level), c->threads, c->smem2, st);
+    }
     if (c->d.scheme == TEUK_SCHEME_SPLIT && c->ks == 2 && c->shifted) {
         *steps = 2;
         if (c->d.precision == TEUK_FP32) {
@@ -903,8 +941,10 @@ int teuk_step(teuk_ctx *c, int64_t nsteps, void *stream)
         left -= 1;
     }
     // steps per launch from here on (the state is shifted)
-    const int ks = (c->d.scheme == TEUK_SCHEME_SPLIT && c->ks == 2) ? 2 : 1;
-    bool use_graph = st != nullptr && c->d.scheme == TEUK_SCHEME_SPLIT && left >= 2 * kGraphChunk;
+    const int ks = (c->d.scheme == TEUK_SCHEME_SPLIT && c->ks >= 2) ? c->ks : 1;
+    // steps per captured graph: a multiple of ks over an even number of launches
+    const int chunk = ks == 3 ? 3 * kGraphChunk / 2 : kGraphChunk;
+    bool use_graph = st != nullptr && c->d.scheme == TEUK_SCHEME_SPLIT && left >= 2 * chunk;
     if (use_graph) {
         int g = c->cur;
         if (c->graph[g] && c->graph_stream[g] != st) {
@@ -916,7 +956,7 @@ int teuk_step(teuk_ctx *c, int64_t nsteps, void *stream)
             CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal), "begin capture");
             int lev = g, done = 0;
             cudaError_t le = cudaSuccess;
-            while (done < kGraphChunk && le == cudaSuccess) {
+            while (done < chunk && le == cudaSuccess) {
                 int k = 0;
                 le = launch_unit(c, lev, st, &k);
                 done += k;
@@ -933,9 +973,9 @@ int teuk_step(teuk_ctx *c, int64_t nsteps, void *stream)
             }
             c->graph_stream[g] = st;
         }
-        while (left >= kGraphChunk) {
+        while (left >= chunk) {
             CK(cudaGraphLaunch(c->graph[g], st), "graph launch");
-            left -= kGraphChunk;
+            left -= chunk;
         }
     }
     while (left >= ks) {
@@ -1039,6 +1079,14 @@ static int autotune_impl(teuk_ctx *c, int trial_steps, void *flush, size_t flush
             }
         }
     }
+    // three steps per launch at the heights of the two-step candidates
+    {
+        const size_t n2 = cand.size();
+        for (size_t k = 0; k < n2; ++k) {
+            TileCand t3;
+            if (cand[k].ks == 2 && !cand[k].pipe && tiled3_cand(c, cand[k].R - 2, sm_count(), &t3)) cand.push_back(t3);
+        }
+    }
     if (cand.empty()) return set_err(c, TEUK_E_CUDA, "no tile of the split kernel fits on this device");
     drop_graphs(c);
     cudaEvent_t e0, e1;
@@ -1130,11 +1178,14 @@ int teuk_set_tiling_steps(teuk_ctx *c, int tile_rows, int steps_per_launch)
 {
     if (!c) return TEUK_E_STATE;
     if (steps_per_launch == 1) return teuk_set_tiling(c, tile_rows);
-    if (steps_per_launch != 2) return set_err(c, TEUK_E_INVAL, "steps_per_launch must be 1 or 2");
-    if (c->d.scheme != TEUK_SCHEME_SPLIT) return set_err(c, TEUK_E_INVAL, "two steps per launch need the split scheme");
-    if (tile_rows < 1 || tile_rows > 250) return set_err(c, TEUK_E_INVAL, "tile_rows out of range [1, 250]");
+    if (steps_per_launch != 2 && steps_per_launch != 3)
+        return set_err(c, TEUK_E_INVAL, "steps_per_launch must be 1, 2 or 3");
+    if (c->d.scheme != TEUK_SCHEME_SPLIT)
+        return set_err(c, TEUK_E_INVAL, "several steps per launch need the split scheme");
+    const int trmax = kMaxTileRows - 2 * steps_per_launch;
+    if (tile_rows < 1 || tile_rows > trmax) return set_err(c, TEUK_E_INVAL, "tile_rows out of range [1, %d]", trmax);
     TileCand t;
-    if (!tiled2_cand(c, tile_rows, sm_count(), &t))
+    if (!(steps_per_launch == 3 ? tiled3_cand(c, tile_rows, sm_count(), &t) : tiled2_cand(c, tile_rows, sm_count(), &t)))
         return set_err(c, TEUK_E_INVAL, "tile does not fit in shared memory");
     TileCand tt;
     if (!tiled_cand(c, tile_rows, sm_count(), &tt)) return set_err(c, TEUK_E_INVAL, "tile does not fit in shared memory");

@@ -58,7 +58,7 @@ template <typename C> __device__ __forceinline__ C zero_c2()
 // Every sum of two products below is written with one explicit fma.  Left
 // to the compiler, a*b + c*d may fuse either product, and which one it fuses
 // depends on the code around the inlined call; kernels that share these
-// helpers (one or two steps per launch, batched, persistent) then round the
+// helpers (one to three steps per launch, batched, persistent) then round the
 // same expression differently.  With the fusion fixed they agree bit for bit.
 template <typename C> __device__ __forceinline__ C cmul(C a, C b)
 {
@@ -1398,23 +1398,23 @@ __device__ void extract_warp(const StepParams<T> &p, const typename V2<T>::t *ro
 // tile rows (used to output the physical state).
 // The work of one CTA: tile number `tile` of the grid described by p, whose
 // step takes `ntiles` CTAs (the last of them to start advances the step
-// index), for KS = 1 or 2 time steps per launch.  The tile holds its TR output
-// rows plus KS halo rows on either side (R = TR + 2 KS; tile row lr is global
-// row g0 + lr, g0 = i0 - KS).  With KS = 2 the first step updates rows
-// 1 .. R-2 and the second the TR output rows; the state read and written per
-// step halves at the cost of recomputing the extra halo rows.  The result is
-// bitwise that of KS single steps.
+// index), for KS = 1, 2 or 3 time steps per launch.  The tile holds its TR
+// output rows plus KS halo rows on either side (R = TR + 2 KS; tile row lr is
+// global row g0 + lr, g0 = i0 - KS).  Step k (from 0) updates rows
+// k + 1 .. R - 2 - k, so the last one updates the TR output rows; the state
+// read and written per step falls to 1/KS at the cost of recomputing the
+// extra halo rows.  The result is bitwise that of KS single steps.
 template <typename T, int S, int KS>
 __device__ __forceinline__ void split_tile(const StepParams<T> &p, int tile, int ntiles)
 {
     typedef typename V2<T>::t c2;
     constexpr int kMaxChunks = 8;
-    static_assert(KS == 1 || KS == 2, "one or two steps per launch");
+    static_assert(KS >= 1 && KS <= 3, "one to three steps per launch");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double2 sph[2 * KS];
     __shared__ long long s_n;
     __shared__ __align__(8) unsigned long long s_mbar[kMaxChunks];
-    __shared__ int s_plan[kMaxTileRows + 4];   // stored scan levels of the tile rows
+    __shared__ int s_plan[kMaxTileRows + 6];   // stored scan levels of the tile rows
     const int Nr = p.Nr, N = p.Nth, TR = p.tile_rows, R = TR + 2 * KS, P = p.pitch;
     const int tid = threadIdx.x, NT = blockDim.x;
     const int i0 = tile * TR, g0 = i0 - KS;
@@ -1425,10 +1425,10 @@ __device__ __forceinline__ void split_tile(const StepParams<T> &p, int tile, int
     c2 *sPi = (c2 *)(smem_raw + plan.pi);
     T *sSt = (T *)(smem_raw + plan.rt);   // step-table entries (SField) of the tile's positions
     T *sTh = (T *)(smem_raw + plan.th);
-    c2 *xPhi = (c2 *)(smem_raw + plan.total);   // KS = 2: copy of the extraction row
+    c2 *xPhi = (c2 *)(smem_raw + plan.total);   // KS > 1: copy of the extraction row
     c2 *xPi = xPhi + N;
     // implicit step of this launch: dt/2 for the first step and for the state
-    // output (one step per launch only; with two steps per launch it is the
+    // output (one step per launch only; with more steps per launch it is the
     // full step, chosen at compile time so that its constants are read at
     // fixed parameter offsets)
     const ImpConst<T> &K = (KS == 1 && (p.first || p.imp_only)) ? p.half : p.full;
@@ -1541,7 +1541,7 @@ __device__ __forceinline__ void split_tile(const StepParams<T> &p, int tile, int
         }
     }
     for (int idx = tid; idx < NTF * N; idx += NT) sTh[idx] = p.thtab[idx];
-    // Every implicit step of the launch uses K: with two steps per launch K
+    // Every implicit step of the launch uses K: with more steps per launch K
     // is the full step (the launcher refuses first steps and state outputs).
     for (int lr = tid; lr < R; lr += NT) {
         const int gi = g0 + lr;
@@ -1614,7 +1614,7 @@ __device__ __forceinline__ void split_tile(const StepParams<T> &p, int tile, int
     // ---- B and C, once per time step of the launch.  Step k (from 0) runs
     // the implicit stage on tile rows k .. R-1-k and the Lax-Wendroff stages
     // on rows k+1 .. R-2-k, so the output rows KS .. KS+TR-1 are exact after
-    // the last step.  One loop body serves every step: the two-step kernel's
+    // the last step.  One loop body serves every step: a multi-step kernel's
     // code is no larger than the one-step kernel's.
     int ok = 1;   // every bounded wait of this thread succeeded
     const auto sync_all = [] { __syncthreads(); };

@@ -380,6 +380,13 @@ template <typename T>
 int split2_blocks_per_sm(int Nth, int threads, size_t smem);
 template <typename T>
 cudaError_t launch_split_step2(const StepParams<T> &p, int threads, size_t smem, cudaStream_t st);
+// The same with three time steps per launch (tiles of tile_rows + 6 rows).
+template <typename T>
+size_t split3_smem_bytes(int tile_rows, int Nth);
+template <typename T>
+int split3_blocks_per_sm(int Nth, int threads, size_t smem);
+template <typename T>
+cudaError_t launch_split_step3(const StepParams<T> &p, int threads, size_t smem, cudaStream_t st);
 // Scan levels of every row's implicit solves for the steps dt (p.full) and
 // dt/2 (p.half), written to plan_full / plan_half ([Nr] ints each).
 template <typename T>

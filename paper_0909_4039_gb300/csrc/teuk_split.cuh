@@ -44,6 +44,14 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && S <= 4) ? 2 : 1) k_spl
     split_tile<T, S, 2>(p, (int)blockIdx.x, (int)gridDim.x);
 }
 
+// Three time steps per launch: the tile carries three halo rows on either
+// side, and the state moves once per three steps.
+template <typename T, int S>
+__global__ void __launch_bounds__(256, (sizeof(T) == 4 && S <= 4) ? 2 : 1) k_split_step3(const StepParams<T> p)
+{
+    split_tile<T, S, 3>(p, (int)blockIdx.x, (int)gridDim.x);
+}
+
 // Batched split step: every CTA takes entry blockIdx.x of the tile list,
 // (instance, tile), stages that instance's parameters in shared memory and
 // computes the tile.  One launch advances every instance of the batch by one
@@ -645,6 +653,48 @@ cudaError_t launch_split_step2(const StepParams<T> &p, int threads, size_t smem,
 {
     if (p.first || p.imp_only) return cudaErrorInvalidValue;   // two full steps only
     auto fn = split2_fn<T>(p.Nth);
+    cudaError_t e = smem_limit_max((const void *)fn);
+    if (e != cudaSuccess) return e;
+    int grid = (p.Nr + p.tile_rows - 1) / p.tile_rows;
+    fn<<<grid, threads, smem, st>>>(p);
+    return cudaGetLastError();
+}
+
+template <typename T>
+static void (*split3_fn(int Nth))(const StepParams<T>)
+{
+    const int seg = implicit_seg(Nth);
+    return seg == kSegNarrow ? k_split_step3<T, kSegNarrow>
+                             : (seg == kSeg ? k_split_step3<T, kSeg> : k_split_step3<T, kSegWide>);
+}
+
+template <typename T>
+size_t split3_smem_bytes(int tile_rows, int Nth)
+{
+    return split_smem_plan(tile_rows + 6, Nth, (int)sizeof(T)).total + 2 * (size_t)Nth * sizeof(typename V2<T>::t);
+}
+
+template <typename T>
+int split3_blocks_per_sm(int Nth, int threads, size_t smem)
+{
+    auto fn = split3_fn<T>(Nth);
+    if (smem_limit_max((const void *)fn) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, threads, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return nb;
+}
+
+template <typename T>
+cudaError_t launch_split_step3(const StepParams<T> &p, int threads, size_t smem, cudaStream_t st)
+{
+    if (p.first || p.imp_only) return cudaErrorInvalidValue;   // three full steps only
+    auto fn = split3_fn<T>(p.Nth);
     cudaError_t e = smem_limit_max((const void *)fn);
     if (e != cudaSuccess) return e;
     int grid = (p.Nr + p.tile_rows - 1) / p.tile_rows;

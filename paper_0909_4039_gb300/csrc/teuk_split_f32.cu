@@ -12,6 +12,9 @@ template cudaError_t launch_split_batch<float>(const StepParams<float> *, const 
 template size_t split2_smem_bytes<float>(int, int);
 template int split2_blocks_per_sm<float>(int, int, size_t);
 template cudaError_t launch_split_step2<float>(const StepParams<float> &, int, size_t, cudaStream_t);
+template size_t split3_smem_bytes<float>(int, int);
+template int split3_blocks_per_sm<float>(int, int, size_t);
+template cudaError_t launch_split_step3<float>(const StepParams<float> &, int, size_t, cudaStream_t);
 template int split_blocks_per_sm<float>(int, int, size_t);
 template size_t split_smem_bytes<float>(int, int);
 template cudaError_t launch_split_step<float>(const StepParams<float> &, int, size_t, cudaStream_t);

@@ -12,6 +12,9 @@ template cudaError_t launch_split_batch<double>(const StepParams<double> *, cons
 template size_t split2_smem_bytes<double>(int, int);
 template int split2_blocks_per_sm<double>(int, int, size_t);
 template cudaError_t launch_split_step2<double>(const StepParams<double> &, int, size_t, cudaStream_t);
+template size_t split3_smem_bytes<double>(int, int);
+template int split3_blocks_per_sm<double>(int, int, size_t);
+template cudaError_t launch_split_step3<double>(const StepParams<double> &, int, size_t, cudaStream_t);
 template int split_blocks_per_sm<double>(int, int, size_t);
 template size_t split_smem_bytes<double>(int, int);
 template cudaError_t launch_split_step<double>(const StepParams<double> &, int, size_t, cudaStream_t);

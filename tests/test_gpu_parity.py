@@ -323,10 +323,12 @@ def test_persistent_kernel_rejected_where_unavailable():
     st.close()
 
 
-TWO_STEP = [
-    # Nr, Ntheta, tile_rows, steps (odd counts end with a single step; >= 128 replays graphs)
+MULTI_STEP = [
+    # Nr, Ntheta, tile_rows, steps (left-over steps run singly; >= 128 steps replay graphs
+    # with two steps per launch, >= 192 with three)
     (700, 128, 24, 41),
     (333, 64, 21, 140),
+    (400, 64, 17, 200),
     (1000, 32, 60, 27),
     (150, 16, 10, 33),
     (257, 33, 9, 12),
@@ -334,19 +336,20 @@ TWO_STEP = [
 ]
 
 
-@pytest.mark.parametrize("Nr,Nth,tr,steps", TWO_STEP)
+@pytest.mark.parametrize("Nr,Nth,tr,steps", MULTI_STEP)
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
-def test_two_steps_per_launch_matches_single_steps(Nr, Nth, tr, steps, precision):
-    """The tiled kernel with two time steps per launch (two halo rows, the
-    first step on the widened tile, a sample of the middle step from a copy
-    of the extraction row) gives bitwise the states and waveform of single
-    steps; the oracle agrees within the tolerance."""
+def test_multi_step_launches_match_single_steps(Nr, Nth, tr, steps, precision):
+    """The tiled kernel with two or three time steps per launch (as many
+    halo rows, each step on a tile one row narrower on either side, samples
+    of the inner steps from a copy of the extraction row) gives bitwise the
+    states and waveform of single steps; the oracle agrees within the
+    tolerance."""
     from oracle import oracle as O
     w = inputs.Workload("two", s=-2, m=2, a=0.9, Nr=Nr, Ntheta=Nth, rs_min=-60.0, rs_max=240.0, steps=steps,
                         r0=8.0, amp=0.8 + 0.3j, sig_r=0.9, sig_th=0.25, rs_ext=150.0)
     u0 = inputs.random_state(w.Nr, w.Ntheta, seed=Nr + 3 * Nth)
     outs = []
-    for ks in (1, 2):
+    for ks in (1, 2, 3):
         st = gpu_stepper(w, precision, wave_capacity=steps + 2)
         st.set_tiling(tr, ks)
         assert st.tiling()["steps_per_launch"] == ks and st.tiling()["tile_rows"] == tr
@@ -354,26 +357,28 @@ def test_two_steps_per_launch_matches_single_steps(Nr, Nth, tr, steps, precision
         st.step(steps)
         outs.append((st.get_state(), st.waveform(0, steps + 1), st.current_step))
         st.close()
-    assert outs[0][2] == outs[1][2] == steps
-    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+    assert outs[0][2] == outs[1][2] == outs[2][2] == steps
+    for k in (1, 2):
+        assert np.array_equal(outs[0][0], outs[k][0]) and np.array_equal(outs[0][1], outs[k][1]), k + 1
     if steps <= 41:
         uo, ho = O.run(oracle_problem(w), u0, steps)
         tol = FP64_TOL if precision == "fp64" else FP32_TOL
-        assert rel_l2(outs[1][0], uo) <= tol and rel_l2(outs[1][1], ho) <= tol
+        for k in (1, 2):
+            assert rel_l2(outs[k][0], uo) <= tol and rel_l2(outs[k][1], ho) <= tol
 
 
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
 def test_kernel_variants_agree_bitwise_over_long_runs(precision):
-    """Every launch configuration of the split step (tile heights, one or two
-    steps per launch, the persistent kernel) evaluates each point with the
+    """Every launch configuration of the split step (tile heights, one to
+    three steps per launch, the pipelined and persistent kernels) evaluates each point with the
     same fused multiply-adds, so 1001 steps give the same state bit for bit.
     Rounding differences that only show once in millions of point updates
     surface here, not in short runs."""
     w = inputs.Workload("long", s=-2, m=2, a=0.7, Nr=457, Ntheta=128, rs_min=-60.0, rs_max=240.0, steps=1001,
                         r0=12.0, amp=0.8 - 0.8j, sig_r=0.9, sig_th=0.25, rs_ext=150.0)
     u0 = inputs.random_state(w.Nr, w.Ntheta, seed=104)
-    configs = [("tiled", 30, 1), ("tiled", 7, 2), ("tiled", 26, 2), ("tiled", 12, 1), ("pipelined", 12, 256),
-               ("pipelined", 2, 256)]
+    configs = [("tiled", 30, 1), ("tiled", 7, 2), ("tiled", 26, 2), ("tiled", 12, 1), ("tiled", 28, 3),
+               ("tiled", 5, 3), ("pipelined", 12, 256), ("pipelined", 2, 256)]
     if precision == "fp32":
         configs.append(("persistent", 8, 480))
     outs = []
